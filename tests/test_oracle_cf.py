@@ -1,0 +1,84 @@
+"""Pins of the oracle's Caratheodory-Fejer coefficients (Sec. II.C).
+
+A near-best approximation is pinned by what characterises best approximation:
+the error curve equioscillates at K+2 points with magnitude ~|lambda| (the
+equioscillation theorem quoted in Sec. II.C), and its maximum is below the
+error of the Chebyshev truncation of the same degree.
+"""
+import numpy as np
+import pytest
+
+
+def _real_series(oracle, a, part):
+    M = int(a + 25 * np.cbrt(a + 1) + 60)
+    j = oracle.bessel_j(a, M)
+    m = np.arange(M + 1)
+    w = np.where(m == 0, 1.0, 2.0)
+    sgn = np.where((m // 2) % 2 == 1, -1.0, 1.0)
+    coef = w * sgn * j
+    if part == "cos":
+        coef[m % 2 == 1] = 0.0
+        f = lambda x: np.cos(a * x)
+    else:
+        coef[m % 2 == 0] = 0.0
+        f = lambda x: np.sin(a * x)
+    return coef, f
+
+
+def _alternations(err, level):
+    """Number of sign alternations among the extrema of err with |err| >= level."""
+    idx = np.where(np.abs(err) >= level)[0]
+    signs = np.sign(err[idx])
+    count = 1
+    for k in range(1, len(signs)):
+        if signs[k] != signs[k - 1]:
+            count += 1
+    return count
+
+
+@pytest.mark.parametrize("a,K,part", [(10.0, 12, "cos"), (10.0, 13, "sin"), (30.0, 36, "cos"),
+                                      (30.0, 35, "sin"), (60.0, 70, "cos")])
+def test_cf_equioscillates(oracle, a, K, part):
+    coef, f = _real_series(oracle, a, part)
+    p, lam = oracle.cf_real(coef, K)
+    x = np.cos(np.linspace(0, np.pi, 200001))
+    err = f(x) - np.polynomial.chebyshev.chebval(x, p)
+    emax = np.max(np.abs(err))
+    # |lambda| estimates the error to a few digits
+    assert abs(emax - abs(lam)) <= 2e-3 * abs(lam)
+    # K+2 alternation points at (nearly) the maximal level; the cos/sin parts have
+    # parity, so their effective degree is the largest even/odd number <= K
+    deg = K if (K % 2 == 0) == (part == "cos") else K - 1
+    assert _alternations(err, 0.98 * emax) >= deg + 2
+    # better than the Chebyshev truncation of the same degree
+    cheb_err = np.max(np.abs(f(x) - np.polynomial.chebyshev.chebval(x, coef[: K + 1])))
+    assert emax < cheb_err
+
+
+@pytest.mark.parametrize("a,tol", [(10.0, 1e-8), (30.0, 2.0 ** -23), (100.0, 1e-12), (430.0, 2.0 ** -23)])
+def test_cf_complex_coefficients(oracle, a, tol):
+    """The combined CF polynomial for exp(-i a x) meets tol, never needs more terms
+    than Chebyshev, and its error is below the Chebyshev error at equal degree."""
+    phase = np.exp(0.6j)
+    cf, Kf, est = oracle.cf_coeffs(a, tol, phase)
+    ch, Kc, _ = oracle.cheb_coeffs(a, tol, phase)
+    assert Kf <= Kc
+    x = np.cos(np.linspace(0, np.pi, 40001))
+    f = phase * np.exp(-1j * a * x)
+    e_cf = np.max(np.abs(f - np.polynomial.chebyshev.chebval(x, cf)))
+    e_ch = np.max(np.abs(f - np.polynomial.chebyshev.chebval(x, ch[: Kf + 1])))
+    assert e_cf <= tol * 1.01
+    assert e_cf <= e_ch
+    assert e_cf <= est * 1.01 + 64 * Kf * 2.0 ** -53  # plus chebval rounding
+
+
+def test_cf_expmv_matches_dense(oracle):
+    """The CF path through the full pipeline agrees with the dense reference."""
+    from paper_2608_12058_b300 import inputs as I
+
+    n = 8
+    h, J = I.sk_instance(n, 7)
+    psi = I.random_state(n, 8)
+    y, info = oracle.expmv(h, J, 0.9, 4.0, psi, 1e-10, method="cf")
+    ref = oracle.dense_expmv(h, J, 0.9, 4.0, psi)
+    assert np.linalg.norm(y - ref) <= 1e-10 + info["eval_bound"]

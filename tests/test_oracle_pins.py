@@ -1,0 +1,352 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with a retyping of itself: every check is a
+library routine used as a single step (numpy eigh/norm, scipy/mpmath Bessel,
+scipy Hadamard), a closed form, an invariant, or a value printed in the paper.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2608_12058_b300 import inputs as I
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Ising diagonal (Sec. I)
+
+@pytest.mark.parametrize("n,seed", [(3, 1), (7, 2), (11, 3)])
+def test_energy_invariants(oracle, n, seed):
+    """Walsh-function orthogonality fixes the first two moments of E over all z:
+    sum_z E(z) = 0 and sum_z E(z)^2 = N (sum_{i<j} J_ij^2 + sum_i h_i^2).
+    Flipping every spin leaves the J part unchanged and negates the h part."""
+    h, J = I.sk_instance(n, seed)
+    E = oracle.energies(h, J)
+    N = 1 << n
+    assert abs(E.sum()) < 1e-9 * N
+    np.testing.assert_allclose((E ** 2).sum(), N * (np.sum(np.triu(J, 1) ** 2) + np.sum(h ** 2)),
+                               rtol=1e-12)
+    Eh = oracle.energies(h, np.zeros_like(J))
+    EJ = oracle.energies(np.zeros_like(h), J)
+    z = np.arange(N)
+    zc = z ^ (N - 1)
+    np.testing.assert_allclose(EJ[zc], EJ[z], atol=1e-12)
+    np.testing.assert_allclose(Eh[zc], -Eh[z], atol=1e-12)
+    np.testing.assert_allclose(Eh + EJ, E, atol=1e-12)
+    # single-spin fields: E for h = e_i is s_i(z) = 1 - 2 bit_i(z)
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        np.testing.assert_array_equal(oracle.energies(e, np.zeros_like(J)), 1.0 - 2.0 * ((z >> i) & 1))
+    # a single coupling J_ij reads only i<j and gives s_i s_j
+    Jt = np.zeros((n, n))
+    Jt[0, n - 1] = 1.0
+    np.testing.assert_array_equal(oracle.energies(np.zeros(n), Jt),
+                                  (1.0 - 2.0 * (z & 1)) * (1.0 - 2.0 * ((z >> (n - 1)) & 1)))
+    np.testing.assert_array_equal(oracle.energies(np.zeros(n), Jt.T), np.zeros(N))
+
+
+@pytest.mark.parametrize("n,gamma", [(4, 0.7), (8, 1.3), (9, 0.0)])
+def test_bounds_are_induced_l1_norm(oracle, n, gamma):
+    """Sec. II.A: r equals the induced 1-norm of H - c (numpy's matrix 1-norm) and
+    bounds the spectral radius of H - c (numpy eigvalsh)."""
+    h, J = I.sk_instance(n, 5)
+    emin, emax, c, r = oracle.bounds(h, J, gamma)
+    H = oracle.dense_hamiltonian(h, J, gamma)
+    Hs = H - c * np.eye(1 << n)
+    np.testing.assert_allclose(r, np.linalg.norm(Hs, 1), rtol=1e-13)
+    w = np.linalg.eigvalsh(Hs)
+    assert np.max(np.abs(w)) <= r * (1 + 1e-13)
+    np.testing.assert_allclose([emin, emax], [np.min(np.diag(H)), np.max(np.diag(H))], rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Bessel values by Miller's algorithm (Sec. II.B.1)
+
+@pytest.mark.parametrize("a", [1e-10, 0.3, 1.0, 7.5, 30.0, 99.0, 430.0, 1300.0])
+def test_bessel_against_scipy(oracle, a):
+    from scipy.special import jv
+
+    mmax = int(a + 40 + 10 * np.cbrt(a))
+    j = oracle.bessel_j(a, mmax)
+    m = np.arange(mmax + 1)
+    ref = jv(m, a)
+    big = np.abs(ref) > 1e-250
+    # scipy's jv is good to ~1e-14 absolute in the oscillatory region (the tight
+    # check against 40-digit mpmath is below); relative accuracy in the decaying tail
+    err = np.abs(j - ref)
+    assert np.all(err[big] <= 3e-14)
+    tail = big & (m > a + 5)
+    if np.any(tail):
+        np.testing.assert_allclose(j[tail], ref[tail], rtol=1e-11)
+
+
+@pytest.mark.parametrize("a", [0.5, 12.25, 99.0, 250.0, 1300.0])
+def test_bessel_against_mpmath(oracle, a):
+    import mpmath
+
+    mpmath.mp.dps = 40
+    j = oracle.bessel_j(a, int(a) + 30)
+    for m in sorted({0, 1, 2, 15, 16, int(a) // 2, max(int(a) - 1, 0), int(a), int(a) + 10, int(a) + 25}):
+        ref = float(mpmath.besselj(m, a))
+        assert abs(j[m] - ref) <= 1e-16 + 1e-14 * abs(ref), (m, j[m], ref)
+
+
+@pytest.mark.parametrize("a", [0.1, 3.0, 77.7, 800.0])
+def test_bessel_identities(oracle, a):
+    """J_0^2 + 2 sum J_m^2 = 1 (Parseval of Eq. cheb), three-term recurrence, J_m(-a)."""
+    mmax = int(a + 60 + 20 * np.cbrt(a))
+    j = oracle.bessel_j(a, mmax)
+    assert abs(j[0] ** 2 + 2 * np.sum(j[1:] ** 2) - 1.0) < 1e-14
+    m = np.arange(1, mmax - 1)
+    resid = j[m - 1] + j[m + 1] - (2 * m / a) * j[m]
+    assert np.max(np.abs(resid)) < 1e-13 * max(1.0, 2 * mmax / a)
+    jn = oracle.bessel_j(-a, mmax)
+    np.testing.assert_allclose(jn, j * (-1.0) ** np.arange(mmax + 1), rtol=0, atol=0)
+
+
+# --------------------------------------------------------------------------
+# Chebyshev coefficients (Eq. cheb) and the truncation rule (Eq. TruncError)
+
+@pytest.mark.parametrize("a,tol", [(0.0, 1e-12), (0.01, 1e-14), (5.0, 1e-10), (99.0, 2.0 ** -24),
+                                   (430.0, 1e-12), (1300.0, 2.0 ** -23)])
+def test_series_reproduces_exponential(oracle, a, tol):
+    """The truncated series evaluated by numpy's chebval at x = cos(theta) is
+    exp(-i a x) within the stated tail bound (Eq. cheb is exact)."""
+    phase = np.exp(-0.37j)
+    c, K, tb = oracle.cheb_coeffs(a, tol, phase)
+    assert tb <= tol
+    x = np.cos(np.linspace(0, np.pi, 4001))
+    p = np.polynomial.chebyshev.chebval(x, c)
+    err = np.max(np.abs(p - phase * np.exp(-1j * a * x)))
+    assert err <= tb + 64 * K * 2.0 ** -53 + 1e-15
+    # dropping the last kept coefficient must violate the tolerance (K is minimal)
+    if K > 0:
+        assert tb + abs(c[K]) > tol
+
+
+def test_paper_term_count(oracle):
+    """Sec. II.B.2: 151 Chebyshev terms for exp(ix) on [-99, 99] at double precision."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "paper_term_counts.txt"))
+            if l.strip() and not l.startswith("#")]
+    for a, tol, terms, _ in rows:
+        _, K, _ = oracle.cheb_coeffs(float(a), float(tol))
+        assert K + 1 == int(terms)
+
+
+def test_term_count_growth(oracle):
+    """Fig. 1 / Sec. II.B.2: Chebyshev needs r + o(r) terms, far fewer than the
+    Taylor count ~ e r; the excess over r shrinks relative to r."""
+    prev = None
+    for a in [50.0, 200.0, 800.0, 3200.0]:
+        _, K, _ = oracle.cheb_coeffs(a, 2.0 ** -23)
+        assert a < K < a + 12 * a ** (1 / 3) + 30
+        assert K < np.e * a
+        excess = (K - a) / a
+        if prev is not None:
+            assert excess < prev
+        prev = excess
+
+
+# --------------------------------------------------------------------------
+# Matrix-free operator (Sec. II.D) and Clenshaw (Algorithm 2)
+
+def test_hypercube_operator_is_walsh_hadamard_diagonal(oracle):
+    """H_G = W diag(n - 2|w|) W / N with W the Sylvester-Hadamard matrix (scipy):
+    one Clenshaw run with coefficients (0, 1) applies Ht once."""
+    from scipy.linalg import hadamard
+
+    n = 6
+    N = 1 << n
+    psi = I.random_state(n, 3)
+    y = oracle.clenshaw(np.zeros(N), 1.0, np.array([0.0, 1.0], dtype=complex), psi)
+    W = hadamard(N)
+    pop = np.array([bin(w).count("1") for w in range(N)])
+    ref = W @ (np.diag(n - 2.0 * pop) @ (W @ psi)) / N
+    np.testing.assert_allclose(y, ref, atol=1e-13)
+    # and a pure diagonal
+    D = np.linspace(-1, 1, N)
+    y = oracle.clenshaw(D, 0.0, np.array([0.0, 1.0], dtype=complex), psi)
+    np.testing.assert_allclose(y, D * psi, atol=1e-15)
+
+
+def test_clenshaw_polynomial_degrees(oracle):
+    """Clenshaw with arbitrary coefficients equals sum_m c_m T_m(Ht) psi built from
+    numpy's Chebyshev-to-power conversion and explicit dense matrix powers;
+    covers the degree-0 and degree-1 special cases."""
+    n = 5
+    N = 1 << n
+    rng = np.random.default_rng(11)
+    D = rng.uniform(-0.5, 0.5, N)
+    g = 0.09
+    Ht = np.diag(D) + g * (oracle.dense_hamiltonian(np.zeros(n), np.zeros((n, n)), 1.0))
+    psi = I.random_state(n, 4)
+    for K in [0, 1, 2, 7]:
+        c = rng.standard_normal(K + 1) + 1j * rng.standard_normal(K + 1)
+        y = oracle.clenshaw(D, g, c, psi)
+        mono = np.polynomial.chebyshev.cheb2poly(c)
+        ref = np.zeros(N, dtype=complex)
+        P = np.eye(N)
+        for k in range(K + 1):
+            ref += mono[k] * (P @ psi)
+            P = P @ Ht
+        np.testing.assert_allclose(y, ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,seed,gamma,t,tol,psi_kind", [
+    (10, 0, 1.0, 1.0, 1e-12, "uniform"),
+    (8, 3, 0.4, 3.0, 1e-12, "random"),
+    (9, 4, 2.0, 7.5, 1e-10, "random"),
+    (6, 5, 1.1, 0.0, 1e-12, "random"),
+    (7, 6, 0.8, -2.0, 1e-12, "random"),
+])
+def test_expmv_matches_dense_eigh(oracle, n, seed, gamma, t, tol, psi_kind):
+    """Pin (i): exp(-itH) psi through numpy eigh of the explicit matrix."""
+    h, J = I.sk_instance(n, seed)
+    psi = I.uniform_state(n) if psi_kind == "uniform" else I.random_state(n, seed + 100)
+    y, info = oracle.expmv(h, J, gamma, t, psi, tol)
+    ref = oracle.dense_expmv(h, J, gamma, t, psi)
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert err <= tol + info["eval_bound"] + 1e-13
+    assert abs(info["norm"] - 1.0) < tol + 1e-12
+
+
+def test_config_n10_radius(oracle):
+    """The n=10 SK workload has r = (Emax-Emin)/2 + gamma n ~ 19.83 and K ~ 46."""
+    c = I.config_n10()
+    _, info = oracle.expmv(c.h, c.J, c.gamma, c.t, I.uniform_state(10), 1e-12)
+    assert abs(info["radius"] - 19.8312) < 1e-3
+    assert 40 <= info["K"] <= 50
+
+
+@pytest.mark.parametrize("n,gamma,t", [(5, 0.9, 1.7), (12, 0.35, 4.0), (16, 1.0, 2.5)])
+def test_expmv_transverse_field_closed_form(oracle, n, gamma, t):
+    """Pin (ii): with H_P = 0, exp(-it gamma sum X_j) is the product over qubits of
+    cos(gamma t) I - i sin(gamma t) X, so from |0...0>:
+    y(z) = cos(gamma t)^(n-|z|) (-i sin(gamma t))^|z|."""
+    h = np.zeros(n)
+    J = np.zeros((n, n))
+    psi = I.basis_state(n, 0)
+    y, info = oracle.expmv(h, J, gamma, t, psi, 1e-13)
+    z = np.arange(1 << n)
+    w = np.array([bin(v).count("1") for v in z])
+    ref = np.cos(gamma * t) ** (n - w) * (-1j * np.sin(gamma * t)) ** w
+    assert np.linalg.norm(y - ref) <= 1e-13 + info["eval_bound"] + 1e-12
+
+
+@pytest.mark.parametrize("n,t", [(6, 3.3), (13, 10.0)])
+def test_expmv_zero_field_pure_phase(oracle, n, t):
+    """Pin (iii): gamma = 0 gives y(z) = exp(-i t E(z)) psi(z); E from the independent
+    single-field/single-coupling decomposition checked above."""
+    h, J = I.sk_instance(n, 8)
+    psi = I.random_state(n, 9)
+    y, info = oracle.expmv(h, J, 0.0, t, psi, 1e-13)
+    E = oracle.energies(h, J)
+    ref = np.exp(-1j * t * E) * psi
+    assert np.linalg.norm(y - ref) <= 2e-13 + info["eval_bound"]
+
+
+def test_expmv_group_property_and_splitting(oracle):
+    """Pin (vi): exp(-i t1 H) exp(-i t2 H) = exp(-i (t1+t2) H), and time slicing gives
+    the same map; pin (vii): <phi, U psi> = <U(-t) phi, psi>."""
+    n = 9
+    h, J = I.sk_instance(n, 12)
+    psi = I.random_state(n, 13)
+    phi = I.random_state(n, 14)
+    y1, _ = oracle.expmv(h, J, 0.7, 1.25, psi, 1e-13)
+    y12, _ = oracle.expmv(h, J, 0.7, 2.0, y1, 1e-13)
+    y3, _ = oracle.expmv(h, J, 0.7, 3.25, psi, 1e-13)
+    y3s, info = oracle.expmv(h, J, 0.7, 3.25, psi, 1e-13, splits=4)
+    assert np.linalg.norm(y12 - y3) < 1e-11
+    assert np.linalg.norm(y3s - y3) < 1e-11
+    assert info["splits"] == 4
+    u_psi, _ = oracle.expmv(h, J, 0.7, 2.0, psi, 1e-13)
+    u_phi, _ = oracle.expmv(h, J, 0.7, -2.0, phi, 1e-13)
+    assert abs(np.vdot(phi, u_psi) - np.vdot(u_phi, psi)) < 1e-12
+
+
+def test_expmv_energy_conservation(oracle):
+    """Pin (v): <y|H|y> = <psi|H|psi> (H from the dense matrix)."""
+    n = 8
+    h, J = I.sk_instance(n, 21)
+    psi = I.random_state(n, 22)
+    y, _ = oracle.expmv(h, J, 1.4, 6.0, psi, 1e-13)
+    H = oracle.dense_hamiltonian(h, J, 1.4)
+    assert abs(np.vdot(y, H @ y) - np.vdot(psi, H @ psi)) < 1e-11
+
+
+def test_truncation_bound_holds(oracle):
+    """Pin (viii): the degree-K result differs from a much longer series by no more
+    than the tail bound of Eq. TruncError (||T_m(Ht)|| <= 1)."""
+    n = 9
+    h, J = I.sk_instance(n, 31)
+    psi = I.random_state(n, 32)
+    _, _, c, r = oracle.bounds(h, J, 1.0)
+    E = oracle.energies(h, J)
+    D = (E - c) / r
+    t = 4.0
+    a = t * r
+    phase = np.exp(-1j * t * c)
+    for tol in [1e-3, 1e-6, 1e-9]:
+        ck, K, tb = oracle.cheb_coeffs(a, tol, phase)
+        cl, _, _ = oracle.cheb_coeffs(a, 1e-15, phase)
+        y = oracle.clenshaw(D, 1.0 / r, ck, psi)
+        yl = oracle.clenshaw(D, 1.0 / r, cl, psi)
+        d = np.linalg.norm(y - yl)
+        assert d <= tb + 1e-13
+        assert d > 1e-3 * tb  # the bound is not vacuous
+
+
+def test_eval_bound_dominates_fp64_error(oracle):
+    """Sec. II.B.3: the a-posteriori evaluation bound exceeds the observed error of
+    the FP64 recurrence against the dense reference (minus truncation)."""
+    n = 10
+    h, J = I.sk_instance(n, 41)
+    psi = I.random_state(n, 42)
+    y, info = oracle.expmv(h, J, 1.0, 5.0, psi, 1e-14)
+    ref = oracle.dense_expmv(h, J, 1.0, 5.0, psi)
+    err = np.linalg.norm(y - ref)
+    assert err <= info["eval_bound"] + info["trunc_bound"] + 1e-13
+    assert info["eval_bound"] < 1e-11
+
+
+# --------------------------------------------------------------------------
+# Gradient oracle (dense, Frechet derivative)
+
+def test_dense_gradients_vs_finite_differences(oracle):
+    """The expm_frechet gradients agree with central differences of the dense map,
+    and dL/dt with the closed form 2 Re <y|H_P (-i H) y>."""
+    n = 4
+    h, J = I.sk_instance(n, 51)
+    psi = I.random_state(n, 52)
+    gam, t = 0.8, 1.3
+    g = oracle.dense_energy_gradients(h, J, gam, t, psi)
+
+    def loss(h_, J_, gam_, t_, psi_):
+        y = oracle.dense_expmv(h_, J_, gam_, t_, psi_)
+        E = oracle.energies(h_, J_)
+        return float(np.sum(E * np.abs(y) ** 2))
+
+    eps = 1e-6
+    fd = (loss(h, J, gam + eps, t, psi) - loss(h, J, gam - eps, t, psi)) / (2 * eps)
+    assert abs(fd - g["gamma"]) < 1e-7
+    fd = (loss(h, J, gam, t + eps, psi) - loss(h, J, gam, t - eps, psi)) / (2 * eps)
+    assert abs(fd - g["t"]) < 1e-7
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = eps
+        fd = (loss(h + e, J, gam, t, psi) - loss(h - e, J, gam, t, psi)) / (2 * eps)
+        assert abs(fd - g["h"][i]) < 1e-7
+    for (i, j) in [(0, 1), (1, 3), (2, 3)]:
+        E_ = np.zeros((n, n))
+        E_[i, j] = eps
+        fd = (loss(h, J + E_, gam, t, psi) - loss(h, J - E_, gam, t, psi)) / (2 * eps)
+        assert abs(fd - g["J"][i, j]) < 1e-7
+    # psi0 gradient (PyTorch convention: 2 dL/d conj(psi)) along a random direction
+    d = I.random_state(n, 53)
+    fd = (loss(h, J, gam, t, psi + eps * d) - loss(h, J, gam, t, psi - eps * d)) / (2 * eps)
+    assert abs(fd - np.real(np.vdot(g["psi0"], d))) < 1e-7
