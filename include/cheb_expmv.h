@@ -1,0 +1,159 @@
+/*
+ * cheb_expmv.h - C ABI of the B300 (sm_103a) library for psi(t) = exp(-i t H) psi,
+ * H = H_P + gamma * sum_j X_j on n qubits, evaluated as a truncated Chebyshev or
+ * Caratheodory-Fejer series with the matrix Clenshaw recurrence and a matrix-free
+ * hypercube matvec (Hopkins & Kendon, "Numerical methods for the simulation of
+ * quantum walks and quantum annealing").
+ *
+ * Conventions shared by every entry point
+ *   - n qubits, N = 2^n basis states; basis index z, qubit i is bit i of z (least
+ *     significant first), spin s_i(z) = 1 - 2*bit_i(z).
+ *   - Ising diagonal (Sec. I): E(z) = sum_{i<j} J[i*n+j] s_i s_j + sum_i h[i] s_i.
+ *     h has n doubles, J is an n x n row-major matrix of doubles of which only the
+ *     strict upper triangle (i < j) is read. Both are HOST pointers, read during
+ *     the call and not retained.
+ *   - States are DEVICE pointers to N interleaved complex numbers: complex64
+ *     (float re, float im) for CHEB_FP32, complex128 (double re, double im) for
+ *     CHEB_FP64, 16-byte aligned. The caller owns them.
+ *   - workspace is a DEVICE buffer of at least cheb_workspace_bytes(...) bytes,
+ *     256-byte aligned, owned by the caller; the library allocates no device
+ *     memory. Calls that share a workspace must not overlap on the GPU.
+ *   - stream is a cudaStream_t (NULL = legacy default stream). Work is enqueued on
+ *     it. Entry points that need a device result on the host (the spectral bounds,
+ *     or anything written to an info struct) synchronise that stream.
+ *   - Errors are returned as cheb_status_t, never by exit or exception. Argument
+ *     errors are detected before any work is enqueued. Device-side conditions
+ *     (non-finite results, a wait that ran out) are reported when the call
+ *     synchronises (i.e. when an info struct is requested).
+ */
+#ifndef CHEB_EXPMV_H
+#define CHEB_EXPMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CHEB_OK = 0,
+    CHEB_ERR_INVALID_ARG = 1,   /* bad size, null pointer, non-finite scalar, bad enum */
+    CHEB_ERR_WORKSPACE = 2,     /* workspace too small or misaligned */
+    CHEB_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    CHEB_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out */
+    CHEB_ERR_NONFINITE = 5,     /* the result contains NaN or Inf */
+    CHEB_ERR_UNSUPPORTED = 6    /* valid but outside what this build handles */
+} cheb_status_t;
+
+typedef enum { CHEB_METHOD_CHEBYSHEV = 0, CHEB_METHOD_CF = 1 } cheb_method_t;
+typedef enum { CHEB_FP32 = 0, CHEB_FP64 = 1 } cheb_precision_t;
+
+/* Kernel path for the Clenshaw steps. AUTO picks the fastest available path for
+ * (n, precision); PLAIN forces the one-pass kernel that reads every bit-flip
+ * partner from global memory (the reference GPU path); FUSED forces the
+ * shared-memory tiled kernels (FP32, n >= 13 only). */
+typedef enum { CHEB_PATH_AUTO = 0, CHEB_PATH_PLAIN = 1, CHEB_PATH_FUSED = 2 } cheb_path_t;
+
+typedef struct {
+    int K;               /* polynomial degree per time slice (matvecs per slice) */
+    int time_splits;     /* number of equal time slices */
+    int64_t matvecs;     /* total operator applications = K * time_splits */
+    double emin, emax;   /* range of the Ising diagonal E(z) */
+    double center;       /* c = (emax + emin) / 2, the spectral shift (Sec. II.A) */
+    double radius;       /* r = (emax - emin) / 2 + |gamma| n = ||H - c||_1 (Sec. II.A) */
+    double a;            /* (t / time_splits) * r, the argument of the series */
+    double trunc_bound;  /* truncation bound (Eq. TruncError) or CF estimate, summed over slices */
+    double norm;         /* ||y||_2, FP64 reduction on the device */
+    double energy;       /* <y|H_P|y>, FP64 reduction on the device */
+} cheb_info_t;
+
+/* Human-readable name of a status code (static string). */
+const char* cheb_status_string(cheb_status_t status);
+
+/* Library version string (static). */
+const char* cheb_version(void);
+
+/*
+ * Host coefficient generator (Sec. II.B.1, Eq. cheb, Eq. TruncError; Sec. II.C for CF).
+ * Coefficients of f(x) = exp(-i a x) * phase on [-1, 1] in the Chebyshev basis,
+ * c_0 = J_0(a) * phase, c_m = 2 (-i)^m J_m(a) * phase (CHEB_METHOD_CHEBYSHEV), or the
+ * Caratheodory-Fejer near-minimax correction of that series (CHEB_METHOD_CF).
+ * K is the smallest degree whose truncation bound sum_{m>K} |c_m| (Chebyshev) or
+ * CF error estimate is <= tol.
+ *   coeffs:  HOST buffer of 2*(max_K+1) doubles, receives (re, im) of c_0..c_K.
+ *   K:       receives the degree. err_bound (nullable) receives the bound/estimate.
+ * Errors: INVALID_ARG (non-finite a, tol <= 0, bad method, null pointers),
+ *         UNSUPPORTED (K would exceed max_K).
+ */
+cheb_status_t cheb_coefficients(double a, double phase_re, double phase_im, double tol,
+                                cheb_method_t method, int max_K, double* coeffs, int* K,
+                                double* err_bound);
+
+/* Workspace bytes needed by cheb_expmv / cheb_ising_bounds / cheb_energy at
+ * (n, precision). Returns 0 for an unsupported n (outside 1..33). */
+size_t cheb_workspace_bytes(int n, cheb_precision_t precision);
+
+/*
+ * Spectral bounds (Sec. II.A): exact minimum and maximum of E(z) over all 2^n basis
+ * states, computed on the device from the couplings (energies are summed exactly
+ * in 64-bit fixed point). Synchronises the stream.
+ *   emin, emax: HOST outputs.
+ */
+cheb_status_t cheb_ising_bounds(int n, const double* h, const double* J, void* workspace,
+                                size_t workspace_bytes, void* stream, double* emin, double* emax);
+
+/*
+ * psi <- exp(-i t H) psi, H = diag(E) + gamma * sum_j X_j (Sec. I).
+ * Pipeline: spectral bounds c, r (Sec. II.A); for each of the time slices,
+ * coefficients of exp(-i a x) with a = (t/s) r and the global phase exp(-i (t/s) c)
+ * (Eq. cheb, Eq. TruncError / Sec. II.C); the matrix Clenshaw recurrence
+ * (Algorithm 2, Eq. recursion) with Ht = (H - c)/r applied matrix-free (Sec. II.D),
+ * b_k written in place over b_{k+2}, the result written into psi.
+ *   psi:          DEVICE in/out, N complex numbers of the given precision.
+ *   tol:          bound on the truncation error per unit norm, split evenly over slices.
+ *   time_splits:  number of slices s >= 1, or 0 for automatic (1 unless the degree
+ *                 would exceed the coefficient table, 65536).
+ *   info:         nullable; when given, the call synchronises and fills it (including
+ *                 the FP64 norm and energy of the result).
+ * Errors: INVALID_ARG, WORKSPACE, CUDA, NONFINITE (info given and y not finite),
+ *         UNSUPPORTED.
+ */
+cheb_status_t cheb_expmv(int n, const double* h, const double* J, double gamma, double t,
+                         void* psi, cheb_precision_t precision, double tol, cheb_method_t method,
+                         int time_splits, void* workspace, size_t workspace_bytes, void* stream,
+                         cheb_info_t* info);
+
+/* Same as cheb_expmv with an explicit kernel path (cheb_path_t); used to time the
+ * plain one-pass GPU path against the fused path. */
+cheb_status_t cheb_expmv_path(int n, const double* h, const double* J, double gamma, double t,
+                              void* psi, cheb_precision_t precision, double tol,
+                              cheb_method_t method, int time_splits, int path, void* workspace,
+                              size_t workspace_bytes, void* stream, cheb_info_t* info);
+
+/*
+ * General polynomial p(Ht) psi (Algorithm 2 with caller-supplied coefficients):
+ * psi <- sum_{m=0}^{K} c_m T_m(Ht) psi with Ht = (H - center) / radius and
+ * H = diag(E) + gamma * sum_j X_j. The caller chooses center and radius (radius > 0);
+ * the series is only meaningful when ||Ht|| <= 1 (radius >= the value cheb_expmv uses).
+ *   coeffs: HOST array of 2*(K+1) doubles (re, im), 0 <= K <= 65536.
+ * Errors: INVALID_ARG, WORKSPACE, CUDA, UNSUPPORTED.
+ */
+cheb_status_t cheb_poly_apply(int n, const double* h, const double* J, double gamma,
+                              double center, double radius, int K, const double* coeffs,
+                              void* psi, cheb_precision_t precision, int path, void* workspace,
+                              size_t workspace_bytes, void* stream);
+
+/*
+ * <psi|H_P|psi> and ||psi||^2 in FP64 on the device (Ising diagonal recomputed from
+ * the couplings). Synchronises the stream. energy, norm2: HOST outputs.
+ */
+cheb_status_t cheb_energy(int n, const double* h, const double* J, const void* psi,
+                          cheb_precision_t precision, void* workspace, size_t workspace_bytes,
+                          void* stream, double* energy, double* norm2);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEB_EXPMV_H */

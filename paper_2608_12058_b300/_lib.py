@@ -1,0 +1,89 @@
+"""ctypes binding of the C ABI in include/cheb_expmv.h (argument marshalling only).
+
+The library is loaded from this package directory. If it is missing it is built
+with nvcc; if that fails, loading raises - there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+c_int, c_double, c_size_t, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_int),
+        ("time_splits", ctypes.c_int),
+        ("matvecs", ctypes.c_int64),
+        ("emin", c_double),
+        ("emax", c_double),
+        ("center", c_double),
+        ("radius", c_double),
+        ("a", c_double),
+        ("trunc_bound", c_double),
+        ("norm", c_double),
+        ("energy", c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# name -> (restype, argtypes); mirrors include/cheb_expmv.h
+SIGNATURES = {
+    "cheb_status_string": (ctypes.c_char_p, [c_int]),
+    "cheb_version": (ctypes.c_char_p, []),
+    "cheb_coefficients": (c_int, [c_double, c_double, c_double, c_double, c_int, c_int, _dp, _ip, _dp]),
+    "cheb_workspace_bytes": (c_size_t, [c_int, c_int]),
+    "cheb_ising_bounds": (c_int, [c_int, _dp, _dp, c_void_p, c_size_t, c_void_p, _dp, _dp]),
+    "cheb_expmv": (c_int, [c_int, _dp, _dp, c_double, c_double, c_void_p, c_int, c_double, c_int, c_int,
+                           c_void_p, c_size_t, c_void_p, ctypes.POINTER(Info)]),
+    "cheb_expmv_path": (c_int, [c_int, _dp, _dp, c_double, c_double, c_void_p, c_int, c_double, c_int, c_int,
+                                c_int, c_void_p, c_size_t, c_void_p, ctypes.POINTER(Info)]),
+    "cheb_poly_apply": (c_int, [c_int, _dp, _dp, c_double, c_double, c_double, c_int, _dp, c_void_p, c_int,
+                                c_int, c_void_p, c_size_t, c_void_p]),
+    "cheb_energy": (c_int, [c_int, _dp, _dp, c_void_p, c_int, c_void_p, c_size_t, c_void_p, _dp, _dp]),
+}
+
+STATUS = {0: "CHEB_OK", 1: "CHEB_ERR_INVALID_ARG", 2: "CHEB_ERR_WORKSPACE", 3: "CHEB_ERR_CUDA",
+          4: "CHEB_ERR_TIMEOUT", 5: "CHEB_ERR_NONFINITE", 6: "CHEB_ERR_UNSUPPORTED"}
+
+
+class ChebError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib():
+    """Load (building first if needed) the CUDA library; raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if _build.needs_build():
+                _build.build()
+            L = ctypes.CDLL(_build.LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(code: int, where: str):
+    if code != 0:
+        raise ChebError(code, where)

@@ -1,0 +1,159 @@
+"""Python front end: the C-ABI calls with PyTorch providing device memory and streams.
+
+Every numerical step runs in the CUDA library; this module only converts
+arguments (numpy couplings -> host double pointers, torch tensors -> device
+pointers, the current torch stream -> cudaStream_t) and caches workspaces.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _lib
+
+PREC = {"fp32": 0, "fp64": 1}
+METHOD = {"chebyshev": 0, "cf": 1}
+PATH = {"auto": 0, "plain": 1, "fused": 2}
+
+_ws_cache = {}
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def precision_of(psi) -> str:
+    import torch
+
+    if psi.dtype == torch.complex64:
+        return "fp32"
+    if psi.dtype == torch.complex128:
+        return "fp64"
+    raise TypeError(f"psi must be complex64 or complex128, got {psi.dtype}")
+
+
+def _check_state(psi, n: int):
+    import torch
+
+    if not isinstance(psi, torch.Tensor) or not psi.is_cuda:
+        raise TypeError("psi must be a CUDA tensor")
+    if not psi.is_contiguous() or psi.numel() != (1 << n):
+        raise ValueError(f"psi must be contiguous with 2^{n} elements")
+
+
+def workspace_bytes(n: int, precision: str) -> int:
+    return int(_lib.lib().cheb_workspace_bytes(n, PREC[precision]))
+
+
+def workspace(n: int, precision: str, device=None):
+    """A cached device workspace (torch uint8 tensor) large enough for (n, precision)."""
+    import torch
+
+    dev = torch.device(device if device is not None else "cuda")
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    need = workspace_bytes(n, precision)
+    if need == 0:
+        raise ValueError(f"unsupported n={n}")
+    key = dev.index
+    ws = _ws_cache.get(key)
+    if ws is None or ws.numel() < need:
+        _ws_cache.pop(key, None)
+        ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        _ws_cache[key] = ws
+    return ws
+
+
+def _ws_ptr(ws):
+    p = ws.data_ptr()
+    return (p + 255) // 256 * 256, ws.numel() - ((p + 255) // 256 * 256 - p)
+
+
+def _stream_ptr(device=None):
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def release_workspaces():
+    _ws_cache.clear()
+
+
+def coefficients(a: float, tol: float, method: str = "chebyshev", phase: complex = 1.0, max_K: int = 1 << 16):
+    """Host coefficient generator; returns (complex array c_0..c_K, err_bound)."""
+    buf = np.empty(2 * (max_K + 1))
+    K = ctypes.c_int(0)
+    err = ctypes.c_double(0.0)
+    code = _lib.lib().cheb_coefficients(float(a), float(np.real(phase)), float(np.imag(phase)), float(tol),
+                                        METHOD[method], int(max_K), _dp(buf), ctypes.byref(K), ctypes.byref(err))
+    _lib.check(code, "cheb_coefficients")
+    return buf[: 2 * (K.value + 1)].view(np.complex128).copy(), err.value
+
+
+def ising_bounds(h, J, device=None):
+    h, J = _f64(h), _f64(J)
+    n = h.shape[0]
+    ws = workspace(n, "fp32", device)
+    p, nb = _ws_ptr(ws)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    code = _lib.lib().cheb_ising_bounds(n, _dp(h), _dp(J), ctypes.c_void_p(p), nb, _stream_ptr(ws.device),
+                                        ctypes.byref(lo), ctypes.byref(hi))
+    _lib.check(code, "cheb_ising_bounds")
+    return lo.value, hi.value
+
+
+def expmv(h, J, gamma: float, t: float, psi, tol: Optional[float] = None, method: str = "chebyshev",
+          time_splits: int = 0, path: str = "auto", info: bool = True):
+    """psi <- exp(-i t H) psi in place on the GPU; returns the info dict (or None)."""
+    h, J = _f64(h), _f64(J)
+    n = h.shape[0]
+    _check_state(psi, n)
+    prec = precision_of(psi)
+    if tol is None:
+        tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+    ws = workspace(n, prec, psi.device)
+    p, nb = _ws_ptr(ws)
+    inf = _lib.Info()
+    code = _lib.lib().cheb_expmv_path(n, _dp(h), _dp(J), float(gamma), float(t), ctypes.c_void_p(psi.data_ptr()),
+                                      PREC[prec], float(tol), METHOD[method], int(time_splits), PATH[path],
+                                      ctypes.c_void_p(p), nb, _stream_ptr(psi.device),
+                                      ctypes.byref(inf) if info else None)
+    _lib.check(code, "cheb_expmv")
+    return inf.as_dict() if info else None
+
+
+def poly_apply(h, J, gamma: float, center: float, radius: float, coeffs, psi, path: str = "auto"):
+    """psi <- sum_m c_m T_m((H - center)/radius) psi in place on the GPU."""
+    h, J = _f64(h), _f64(J)
+    n = h.shape[0]
+    _check_state(psi, n)
+    prec = precision_of(psi)
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.complex128)).view(np.float64)
+    K = c.shape[0] // 2 - 1
+    ws = workspace(n, prec, psi.device)
+    p, nb = _ws_ptr(ws)
+    code = _lib.lib().cheb_poly_apply(n, _dp(h), _dp(J), float(gamma), float(center), float(radius), K, _dp(c),
+                                      ctypes.c_void_p(psi.data_ptr()), PREC[prec], PATH[path], ctypes.c_void_p(p),
+                                      nb, _stream_ptr(psi.device))
+    _lib.check(code, "cheb_poly_apply")
+
+
+def energy(h, J, psi):
+    """(<psi|H_P|psi>, ||psi||^2) in FP64 on the GPU."""
+    h, J = _f64(h), _f64(J)
+    n = h.shape[0]
+    _check_state(psi, n)
+    prec = precision_of(psi)
+    ws = workspace(n, prec, psi.device)
+    p, nb = _ws_ptr(ws)
+    e, nn = ctypes.c_double(), ctypes.c_double()
+    code = _lib.lib().cheb_energy(n, _dp(h), _dp(J), ctypes.c_void_p(psi.data_ptr()), PREC[prec],
+                                  ctypes.c_void_p(p), nb, _stream_ptr(psi.device), ctypes.byref(e), ctypes.byref(nn))
+    _lib.check(code, "cheb_energy")
+    return e.value, nn.value

@@ -1,0 +1,380 @@
+// C ABI entry points (include/cheb_expmv.h): argument checks, workspace layout,
+// fixed-point operator tables, coefficient generation and the Clenshaw step loop.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/cheb_expmv.h"
+#include "cheb_internal.h"
+#include "fused.cuh"
+#include "kernels.cuh"
+
+namespace cheb {
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+Layout make_layout(int n, int precision) {
+    Layout L;
+    L.n = n;
+    L.M = n < kTileBits ? n : kTileBits;
+    L.cbytes = precision == 0 ? 8 : 16;
+    size_t off = 0;
+    L.status = off;
+    off += 256;
+    L.part = off;
+    off = align_up(off + 4 * kRedBlocks * sizeof(double), 256);
+    L.jq = off;
+    off = align_up(off + ((size_t)n * n + n + 1) * sizeof(int64_t), 256);
+    L.tiles = off;
+    off = align_up(off + ((size_t)1 << (n - L.M)) * (L.M + 1) * sizeof(int64_t), 256);
+    L.elow = off;
+    off = align_up(off + ((size_t)1 << L.M) * sizeof(int64_t), 256);
+    L.coef = off;
+    off = align_up(off + (size_t)(kMaxK + 1) * 2 * sizeof(double), 256);
+    off += fused_scratch_bytes(n, precision);
+    off = align_up(off, 256);
+    L.b0 = off;
+    off = align_up(off + ((size_t)1 << n) * L.cbytes, 256);
+    L.b1 = off;
+    off = align_up(off + ((size_t)1 << n) * L.cbytes, 256);
+    L.total = off;
+    return L;
+}
+
+// Couplings in fixed point: value = integer * 2^-Q.
+struct FixedOp {
+    int Q = 0;
+    std::vector<int64_t> jq;  // J symmetric n*n, then h[n], then c
+};
+
+static bool finite_all(const double* p, size_t k) {
+    for (size_t i = 0; i < k; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// Largest Q <= 62 with bound * 2^Q <= 2^61 (so every partial sum fits in int64).
+static int choose_scale(long double bound) {
+    if (!(bound > 0)) return 62;
+    int e = (int)std::ceil(std::log2((double)bound));
+    int Q = 61 - e;
+    return Q > 62 ? 62 : Q;
+}
+
+// J/scale, h/scale, c/scale quantised at the largest safe Q.
+static FixedOp make_fixed(int n, const double* h, const double* J, double center, double scale) {
+    FixedOp F;
+    long double bound = std::fabs((long double)center);
+    for (int i = 0; i < n; ++i) {
+        bound += std::fabs((long double)h[i]);
+        for (int j = i + 1; j < n; ++j) bound += std::fabs((long double)J[(size_t)i * n + j]);
+    }
+    bound /= (long double)scale;
+    F.Q = choose_scale(bound);
+    const long double mul = std::ldexp(1.0L, F.Q) / (long double)scale;
+    F.jq.assign((size_t)n * n + n + 1, 0);
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            int64_t q = (int64_t)std::llroundl((long double)J[(size_t)i * n + j] * mul);
+            F.jq[(size_t)i * n + j] = q;
+            F.jq[(size_t)j * n + i] = q;
+        }
+    for (int i = 0; i < n; ++i) F.jq[(size_t)n * n + i] = (int64_t)std::llroundl((long double)h[i] * mul);
+    F.jq[(size_t)n * n + n] = (int64_t)std::llroundl((long double)center * mul);
+    return F;
+}
+
+struct Ctx {
+    int n;
+    int prec;
+    Layout L;
+    unsigned char* ws;
+    cudaStream_t s;
+    int64_t* tiles() const { return (int64_t*)(ws + L.tiles); }
+    int64_t* elow() const { return (int64_t*)(ws + L.elow); }
+    int* flags() const { return (int*)(ws + L.status); }
+    int64_t* i64out() const { return (int64_t*)(ws + L.status + 64); }
+    double* f64out() const { return (double*)(ws + L.status + 128); }
+    double* part() const { return (double*)(ws + L.part); }
+};
+
+#define CUDA_TRY(x)                                   \
+    do {                                              \
+        if ((x) != cudaSuccess) return CHEB_ERR_CUDA; \
+    } while (0)
+
+static cheb_status_t upload_tables(const Ctx& C, const FixedOp& F) {
+    CUDA_TRY(cudaMemcpyAsync(C.ws + C.L.jq, F.jq.data(), F.jq.size() * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, C.s));
+    launch_tables(C.n, C.L.M, (const int64_t*)(C.ws + C.L.jq), C.tiles(), C.elow(), C.s);
+    CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+static cheb_status_t check_common(int n, const double* h, const double* J, int prec, void* ws,
+                                  size_t ws_bytes) {
+    if (n < 1 || n > kMaxQubits) return CHEB_ERR_INVALID_ARG;
+    if (!h || !J) return CHEB_ERR_INVALID_ARG;
+    if (prec != CHEB_FP32 && prec != CHEB_FP64) return CHEB_ERR_INVALID_ARG;
+    if (!finite_all(h, n) || !finite_all(J, (size_t)n * n)) return CHEB_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & 255) != 0) return CHEB_ERR_WORKSPACE;
+    if (ws_bytes < make_layout(n, prec).total) return CHEB_ERR_WORKSPACE;
+    return CHEB_OK;
+}
+
+static cheb_status_t bounds_impl(Ctx& C, const double* h, const double* J, double* emin, double* emax) {
+    FixedOp F = make_fixed(C.n, h, J, 0.0, 1.0);
+    cheb_status_t st = upload_tables(C, F);
+    if (st != CHEB_OK) return st;
+    launch_minmax(C.n, C.L.M, C.tiles(), C.elow(), (int64_t*)C.part(), C.i64out(), C.s);
+    CUDA_TRY(cudaGetLastError());
+    int64_t mm[2];
+    CUDA_TRY(cudaMemcpyAsync(mm, C.i64out(), sizeof(mm), cudaMemcpyDeviceToHost, C.s));
+    CUDA_TRY(cudaStreamSynchronize(C.s));
+    *emin = std::ldexp((double)mm[0], -F.Q);
+    *emax = std::ldexp((double)mm[1], -F.Q);
+    return CHEB_OK;
+}
+
+// One Clenshaw run (Algorithm 2) of the coefficients c over psi, in place.
+static cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::complex<double>>& c,
+                                  int Q, double g) {
+    const int K = (int)c.size() - 1;
+    const int64_t N = (int64_t)1 << C.n;
+    if (K == 0) {
+        launch_scale(C.prec, N, psi, psi, c[0].real(), c[0].imag(), C.s);
+        CUDA_TRY(cudaGetLastError());
+        return CHEB_OK;
+    }
+    const int small_max = C.prec == 0 ? kSmallMaxF32 : kSmallMaxF64;
+    if (path == CHEB_PATH_AUTO && C.n <= small_max) {
+        static_assert(sizeof(std::complex<double>) == 2 * sizeof(double), "layout");
+        CUDA_TRY(cudaMemcpyAsync(C.ws + C.L.coef, c.data(), c.size() * sizeof(std::complex<double>),
+                                 cudaMemcpyHostToDevice, C.s));
+        CUDA_TRY(launch_small(C.prec, C.n, K, (const double*)(C.ws + C.L.coef), Q, C.tiles(), C.elow(), g,
+                              psi, C.s));
+        return CHEB_OK;
+    }
+    bool fused = false;
+    if (path == CHEB_PATH_FUSED || path == CHEB_PATH_AUTO) fused = fused_supported(C.n, C.prec);
+    if (path == CHEB_PATH_FUSED && !fused) return CHEB_ERR_UNSUPPORTED;
+    unsigned char* B[2] = {C.ws + C.L.b0, C.ws + C.L.b1};
+    launch_scale(C.prec, N, psi, B[1], c[K].real(), c[K].imag(), C.s);
+    FusedPlan plan;
+    if (fused) plan = fused_plan(C.n, C.prec);
+    int cur = 1;
+    for (int k = K - 1; k >= 0; --k) {
+        StepArgs a;
+        a.n = C.n;
+        a.M = C.L.M;
+        a.Q = Q;
+        a.tiles = C.tiles();
+        a.elow = C.elow();
+        a.b1 = B[cur];
+        a.b2 = B[cur ^ 1];
+        a.psi = psi;
+        a.out = (k == 0) ? psi : (void*)B[cur ^ 1];
+        a.ck_re = c[k].real();
+        a.ck_im = c[k].imag();
+        a.scale = (k == 0) ? 1.0 : 2.0;
+        a.sgn = (k == K - 1) ? 0.0 : -1.0;
+        a.g = g;
+        if (fused) {
+            cudaError_t e = launch_step_fused(plan, a, C.ws + C.L.coef + (size_t)(kMaxK + 1) * 2 * sizeof(double),
+                                              C.flags(), C.s);
+            if (e != cudaSuccess) return CHEB_ERR_CUDA;
+        } else {
+            launch_step_plain(C.prec, a, C.s);
+        }
+        cur ^= 1;
+    }
+    CUDA_TRY(cudaGetLastError());
+    return CHEB_OK;
+}
+
+static cheb_status_t read_flags(const Ctx& C) {
+    int f = 0;
+    CUDA_TRY(cudaMemcpyAsync(&f, C.flags(), sizeof(int), cudaMemcpyDeviceToHost, C.s));
+    CUDA_TRY(cudaStreamSynchronize(C.s));
+    if (f & kFlagTimeout) return CHEB_ERR_TIMEOUT;
+    if (f & kFlagBadLaunch) return CHEB_ERR_CUDA;
+    return CHEB_OK;
+}
+
+static cheb_status_t expmv_impl(int n, const double* h, const double* J, double gamma, double t, void* psi,
+                                int prec, double tol, int method, int splits, int path, void* ws,
+                                size_t ws_bytes, void* stream, cheb_info_t* info) {
+    cheb_status_t st = check_common(n, h, J, prec, ws, ws_bytes);
+    if (st != CHEB_OK) return st;
+    if (!psi || ((uintptr_t)psi & 15) != 0) return CHEB_ERR_INVALID_ARG;
+    if (!std::isfinite(gamma) || !std::isfinite(t) || !(tol > 0) || !std::isfinite(tol)) return CHEB_ERR_INVALID_ARG;
+    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF) return CHEB_ERR_INVALID_ARG;
+    if (splits < 0 || path < 0 || path > 2) return CHEB_ERR_INVALID_ARG;
+    Ctx C{n, prec, make_layout(n, prec), (unsigned char*)ws, (cudaStream_t)stream};
+    CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), C.s));
+    double emin = 0, emax = 0;
+    st = bounds_impl(C, h, J, &emin, &emax);
+    if (st != CHEB_OK) return st;
+    const double c = 0.5 * (emax + emin);
+    double r = 0.5 * (emax - emin) + std::fabs(gamma) * n;
+    if (!(r > 0)) r = 1.0;  // H is the constant c: any radius is exact
+    FixedOp F = make_fixed(n, h, J, c, r);
+    if (F.Q < 24) return CHEB_ERR_UNSUPPORTED;
+    st = upload_tables(C, F);
+    if (st != CHEB_OK) return st;
+    // coefficients, with automatic slicing when the degree exceeds the table
+    int s = splits > 0 ? splits : 1;
+    std::vector<std::complex<double>> coef;
+    double err = 0.0;
+    int K = -1;
+    for (int attempt = 0; attempt < 24; ++attempt) {
+        const double ts = t / s;
+        const std::complex<double> phase = std::polar(1.0, -ts * c);
+        K = make_coefficients(ts * r, phase, tol / s, method, kMaxK, coef, &err);
+        if (K >= 0 || splits > 0) break;
+        s *= 2;
+    }
+    if (K < 0) return CHEB_ERR_UNSUPPORTED;
+    const double g = gamma / r;
+    for (int q = 0; q < s; ++q) {
+        st = clenshaw_run(C, path, psi, coef, F.Q, g);
+        if (st != CHEB_OK) return st;
+    }
+    if (info) {
+        launch_norm_energy(prec, n, C.L.M, F.Q, C.tiles(), C.elow(), c, r, psi, C.part(), C.f64out(), C.s);
+        CUDA_TRY(cudaGetLastError());
+        double ne[2];
+        CUDA_TRY(cudaMemcpyAsync(ne, C.f64out(), sizeof(ne), cudaMemcpyDeviceToHost, C.s));
+        st = read_flags(C);
+        if (st != CHEB_OK) return st;
+        info->K = K;
+        info->time_splits = s;
+        info->matvecs = (int64_t)K * s;
+        info->emin = emin;
+        info->emax = emax;
+        info->center = c;
+        info->radius = r;
+        info->a = (t / s) * r;
+        info->trunc_bound = err * s;
+        info->norm = std::sqrt(ne[0]);
+        info->energy = ne[1];
+        if (!std::isfinite(ne[0]) || !std::isfinite(ne[1])) return CHEB_ERR_NONFINITE;
+    }
+    return CHEB_OK;
+}
+
+}  // namespace cheb
+
+using namespace cheb;
+
+extern "C" {
+
+const char* cheb_status_string(cheb_status_t s) {
+    switch (s) {
+        case CHEB_OK: return "ok";
+        case CHEB_ERR_INVALID_ARG: return "invalid argument";
+        case CHEB_ERR_WORKSPACE: return "workspace too small or misaligned";
+        case CHEB_ERR_CUDA: return "CUDA runtime error";
+        case CHEB_ERR_TIMEOUT: return "device wait timed out";
+        case CHEB_ERR_NONFINITE: return "non-finite result";
+        case CHEB_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+const char* cheb_version(void) { return "cheb_expmv 0.1 (sm_103a)"; }
+
+cheb_status_t cheb_coefficients(double a, double phase_re, double phase_im, double tol, cheb_method_t method,
+                                int max_K, double* coeffs, int* K, double* err_bound) {
+    if (!std::isfinite(a) || !(tol > 0) || !std::isfinite(tol) || !coeffs || !K || max_K < 0)
+        return CHEB_ERR_INVALID_ARG;
+    if (!std::isfinite(phase_re) || !std::isfinite(phase_im)) return CHEB_ERR_INVALID_ARG;
+    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF) return CHEB_ERR_INVALID_ARG;
+    std::vector<std::complex<double>> c;
+    double err = 0;
+    int k = make_coefficients(a, std::complex<double>(phase_re, phase_im), tol, method, max_K, c, &err);
+    if (k < 0) return CHEB_ERR_UNSUPPORTED;
+    for (int m = 0; m <= k; ++m) {
+        coeffs[2 * m] = c[m].real();
+        coeffs[2 * m + 1] = c[m].imag();
+    }
+    *K = k;
+    if (err_bound) *err_bound = err;
+    return CHEB_OK;
+}
+
+size_t cheb_workspace_bytes(int n, cheb_precision_t precision) {
+    if (n < 1 || n > kMaxQubits) return 0;
+    if (precision != CHEB_FP32 && precision != CHEB_FP64) return 0;
+    return make_layout(n, precision).total;
+}
+
+cheb_status_t cheb_ising_bounds(int n, const double* h, const double* J, void* workspace, size_t workspace_bytes,
+                                void* stream, double* emin, double* emax) {
+    cheb_status_t st = check_common(n, h, J, CHEB_FP32, workspace, workspace_bytes);
+    if (st != CHEB_OK) return st;
+    if (!emin || !emax) return CHEB_ERR_INVALID_ARG;
+    Ctx C{n, 0, make_layout(n, 0), (unsigned char*)workspace, (cudaStream_t)stream};
+    return bounds_impl(C, h, J, emin, emax);
+}
+
+cheb_status_t cheb_expmv(int n, const double* h, const double* J, double gamma, double t, void* psi,
+                         cheb_precision_t precision, double tol, cheb_method_t method, int time_splits,
+                         void* workspace, size_t workspace_bytes, void* stream, cheb_info_t* info) {
+    return expmv_impl(n, h, J, gamma, t, psi, precision, tol, method, time_splits, CHEB_PATH_AUTO, workspace,
+                      workspace_bytes, stream, info);
+}
+
+cheb_status_t cheb_expmv_path(int n, const double* h, const double* J, double gamma, double t, void* psi,
+                              cheb_precision_t precision, double tol, cheb_method_t method, int time_splits,
+                              int path, void* workspace, size_t workspace_bytes, void* stream,
+                              cheb_info_t* info) {
+    return expmv_impl(n, h, J, gamma, t, psi, precision, tol, method, time_splits, path, workspace,
+                      workspace_bytes, stream, info);
+}
+
+cheb_status_t cheb_poly_apply(int n, const double* h, const double* J, double gamma, double center,
+                              double radius, int K, const double* coeffs, void* psi, cheb_precision_t precision,
+                              int path, void* workspace, size_t workspace_bytes, void* stream) {
+    cheb_status_t st = check_common(n, h, J, precision, workspace, workspace_bytes);
+    if (st != CHEB_OK) return st;
+    if (!psi || ((uintptr_t)psi & 15) != 0 || !coeffs) return CHEB_ERR_INVALID_ARG;
+    if (!std::isfinite(gamma) || !std::isfinite(center) || !(radius > 0) || !std::isfinite(radius))
+        return CHEB_ERR_INVALID_ARG;
+    if (K < 0 || K > kMaxK || path < 0 || path > 2) return CHEB_ERR_INVALID_ARG;
+    if (!finite_all(coeffs, 2 * (size_t)(K + 1))) return CHEB_ERR_INVALID_ARG;
+    Ctx C{n, precision, make_layout(n, precision), (unsigned char*)workspace, (cudaStream_t)stream};
+    CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), C.s));
+    FixedOp F = make_fixed(n, h, J, center, radius);
+    if (F.Q < 24) return CHEB_ERR_UNSUPPORTED;
+    st = upload_tables(C, F);
+    if (st != CHEB_OK) return st;
+    std::vector<std::complex<double>> c(K + 1);
+    for (int m = 0; m <= K; ++m) c[m] = std::complex<double>(coeffs[2 * m], coeffs[2 * m + 1]);
+    return clenshaw_run(C, path, psi, c, F.Q, gamma / radius);
+}
+
+cheb_status_t cheb_energy(int n, const double* h, const double* J, const void* psi, cheb_precision_t precision,
+                          void* workspace, size_t workspace_bytes, void* stream, double* energy, double* norm2) {
+    cheb_status_t st = check_common(n, h, J, precision, workspace, workspace_bytes);
+    if (st != CHEB_OK) return st;
+    if (!psi || ((uintptr_t)psi & 15) != 0 || !energy || !norm2) return CHEB_ERR_INVALID_ARG;
+    Ctx C{n, precision, make_layout(n, precision), (unsigned char*)workspace, (cudaStream_t)stream};
+    FixedOp F = make_fixed(n, h, J, 0.0, 1.0);
+    st = upload_tables(C, F);
+    if (st != CHEB_OK) return st;
+    launch_norm_energy(precision, n, C.L.M, F.Q, C.tiles(), C.elow(), 0.0, 1.0, psi, C.part(), C.f64out(), C.s);
+    CUDA_TRY(cudaGetLastError());
+    double ne[2];
+    CUDA_TRY(cudaMemcpyAsync(ne, C.f64out(), sizeof(ne), cudaMemcpyDeviceToHost, C.s));
+    CUDA_TRY(cudaStreamSynchronize(C.s));
+    *norm2 = ne[0];
+    *energy = ne[1];
+    return CHEB_OK;
+}
+
+}  // extern "C"

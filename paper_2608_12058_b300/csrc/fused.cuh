@@ -1,0 +1,30 @@
+// Fused shared-memory Clenshaw step for the FP32 path (fused.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+
+#include "kernels.cuh"
+
+namespace cheb {
+
+// How the n bit flips of one step are split between the passes:
+//   low pass:  bits [0, M) from the shared-memory tile, bits [M, M + l) from
+//              partner tiles read through L2;
+//   high pass: bits [n - h, n) from a strided shared-memory tile (h may be 0).
+struct FusedPlan {
+    int n = 0;
+    int prec = 0;
+    int M = 0;
+    int l = 0;
+    int h = 0;
+    int grid_low = 0;
+    int grid_high = 0;
+};
+
+size_t fused_scratch_bytes(int n, int prec);
+bool fused_supported(int n, int prec);
+FusedPlan fused_plan(int n, int prec);
+cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& a, void* scratch, int* flags,
+                              cudaStream_t s);
+
+}  // namespace cheb

@@ -1,0 +1,434 @@
+// Device kernels of the single-pass path: energy tables, spectral bounds, the
+// plain one-pass Clenshaw step (FP32 and FP64), the whole-run shared-memory
+// kernel for small n, and the FP64 norm / energy reductions.
+//
+// Energies are exact sums of fixed-point integers. With the basis index split
+// as z = (T, x), T = z >> M (tile) and x = z & (2^M - 1):
+//   E(z) - c = A(T) + sum_{i<M} s_i(x) f_i(T) + elow(x),
+//   f_i(T) = sum_{j>=M} J_ij s_j(T),
+//   A(T)   = sum_{M<=i<j} J_ij s_i s_j + sum_{i>=M} h_i s_i - c,
+//   elow(x)= sum_{i<j<M} J_ij s_i s_j + sum_{i<M} h_i s_i,
+// which is the Ising diagonal of Sec. I regrouped by bit position and generated
+// on the device from the couplings (Sec. III.A) instead of being stored.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "cheb_internal.h"
+#include "kernels.cuh"
+
+namespace cheb {
+
+__device__ __forceinline__ int64_t sgn_sel(uint64_t bit, int64_t v) { return bit ? -v : v; }
+
+// ---------------------------------------------------------------------------
+__global__ void k_tables(int n, int M, const int64_t* __restrict__ jq, int64_t* __restrict__ tiles,
+                         int64_t* __restrict__ elow) {
+    const int64_t ntiles = (int64_t)1 << (n - M);
+    const int64_t nlow = (int64_t)1 << M;
+    const int64_t* J = jq;
+    const int64_t* h = jq + (size_t)n * n;
+    const int64_t c = jq[(size_t)n * n + n];
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < ntiles + nlow;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        if (idx < ntiles) {
+            const uint64_t zh = (uint64_t)idx << M;
+            int64_t* row = tiles + idx * (M + 1);
+            for (int i = 0; i < M; ++i) {
+                int64_t f = 0;
+                for (int j = M; j < n; ++j) f += sgn_sel((zh >> j) & 1, J[(size_t)i * n + j]);
+                row[i] = f;
+            }
+            int64_t A = -c;
+            for (int i = M; i < n; ++i) {
+                int64_t hi = h[i];
+                for (int j = i + 1; j < n; ++j) hi += sgn_sel((zh >> j) & 1, J[(size_t)i * n + j]);
+                A += sgn_sel((zh >> i) & 1, hi);
+            }
+            row[M] = A;
+        } else {
+            const uint64_t x = (uint64_t)(idx - ntiles);
+            int64_t e = 0;
+            for (int i = 0; i < M; ++i) {
+                int64_t hi = h[i];
+                for (int j = i + 1; j < M; ++j) hi += sgn_sel((x >> j) & 1, J[(size_t)i * n + j]);
+                e += sgn_sel((x >> i) & 1, hi);
+            }
+            elow[x] = e;
+        }
+    }
+}
+
+void launch_tables(int n, int M, const int64_t* jq, int64_t* tiles, int64_t* elow, cudaStream_t s) {
+    int64_t total = ((int64_t)1 << (n - M)) + ((int64_t)1 << M);
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 4 * 148 * 8) blocks = 4 * 148 * 8;
+    k_tables<<<(unsigned)blocks, 256, 0, s>>>(n, M, jq, tiles, elow);
+}
+
+// ---------------------------------------------------------------------------
+// Spectral bounds (Sec. II.A): exact min / max of the fixed-point energies.
+__global__ void __launch_bounds__(256) k_minmax(int n, int M, const int64_t* __restrict__ tiles,
+                                                const int64_t* __restrict__ elow,
+                                                int64_t* __restrict__ part) {
+    __shared__ int64_t f[kTileBits + 1];
+    __shared__ int64_t rmin[256], rmax[256];
+    const int64_t ntiles = (int64_t)1 << (n - M);
+    const int nlow = 1 << M;
+    int64_t mn = INT64_MAX, mx = INT64_MIN;
+    for (int64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x <= M) f[threadIdx.x] = tiles[T * (M + 1) + threadIdx.x];
+        __syncthreads();
+        const int64_t A = f[M];
+        for (int x = threadIdx.x; x < nlow; x += blockDim.x) {
+            int64_t e = A + elow[x];
+            for (int i = 0; i < M; ++i) e += sgn_sel((x >> i) & 1, f[i]);
+            mn = e < mn ? e : mn;
+            mx = e > mx ? e : mx;
+        }
+    }
+    rmin[threadIdx.x] = mn;
+    rmax[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            rmin[threadIdx.x] = min(rmin[threadIdx.x], rmin[threadIdx.x + w]);
+            rmax[threadIdx.x] = max(rmax[threadIdx.x], rmax[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = rmin[0];
+        part[kRedBlocks + blockIdx.x] = rmax[0];
+    }
+}
+
+__global__ void k_minmax_final(const int64_t* __restrict__ part, int nb, int64_t* __restrict__ out) {
+    __shared__ int64_t rmin[256], rmax[256];
+    int64_t mn = INT64_MAX, mx = INT64_MIN;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        mn = min(mn, part[b]);
+        mx = max(mx, part[kRedBlocks + b]);
+    }
+    rmin[threadIdx.x] = mn;
+    rmax[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            rmin[threadIdx.x] = min(rmin[threadIdx.x], rmin[threadIdx.x + w]);
+            rmax[threadIdx.x] = max(rmax[threadIdx.x], rmax[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = rmin[0];
+        out[1] = rmax[0];
+    }
+}
+
+void launch_minmax(int n, int M, const int64_t* tiles, const int64_t* elow, int64_t* part,
+                   int64_t* out2, cudaStream_t s) {
+    int64_t ntiles = (int64_t)1 << (n - M);
+    int nb = (int)(ntiles < kRedBlocks ? ntiles : kRedBlocks);
+    k_minmax<<<nb, 256, 0, s>>>(n, M, tiles, elow, part);
+    k_minmax_final<<<1, 256, 0, s>>>(part, nb, out2);
+}
+
+// ---------------------------------------------------------------------------
+// Complex element types.
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+template <typename R>
+__global__ void k_scale(int64_t N, const typename Cx<R>::T* __restrict__ src,
+                        typename Cx<R>::T* dst, R cr, R ci) {
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N;
+         z += (int64_t)gridDim.x * blockDim.x) {
+        auto v = src[z];
+        typename Cx<R>::T o;
+        o.x = cr * v.x - ci * v.y;
+        o.y = cr * v.y + ci * v.x;
+        dst[z] = o;
+    }
+}
+
+static unsigned grid_for(int64_t N, int threads, int64_t cap = (int64_t)148 * 64) {
+    int64_t b = (N + threads - 1) / threads;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+void launch_scale(int prec, int64_t N, const void* src, void* dst, double cr, double ci, cudaStream_t s) {
+    if (prec == 0)
+        k_scale<float><<<grid_for(N, 256), 256, 0, s>>>(N, (const float2*)src, (float2*)dst, (float)cr, (float)ci);
+    else
+        k_scale<double><<<grid_for(N, 256), 256, 0, s>>>(N, (const double2*)src, (double2*)dst, cr, ci);
+}
+
+// ---------------------------------------------------------------------------
+// Dt(z) from the fixed-point tables.
+__device__ __forceinline__ int64_t energy_fixed(int M, const int64_t* __restrict__ tiles,
+                                                const int64_t* __restrict__ elow, uint64_t z) {
+    const uint64_t T = z >> M;
+    const uint64_t x = z & ((1ull << M) - 1);
+    const int64_t* row = tiles + T * (M + 1);
+    int64_t e = __ldg(row + M) + __ldg(elow + x);
+    for (int i = 0; i < M; ++i) e += sgn_sel((x >> i) & 1, __ldg(row + i));
+    return e;
+}
+
+// int64 at scale 2^-Q -> float-float (hi exact, lo carries the next 24 bits).
+__device__ __forceinline__ void fixed_to_ff(int64_t e, int Q, float& hi, float& lo) {
+    const int sh = Q - 24;
+    const int64_t ih = e >> sh;
+    const int64_t il = e - (ih << sh);
+    hi = __ll2float_rn(ih) * 5.9604644775390625e-08f;  // 2^-24
+    lo = __ll2float_rn(il) * __int_as_float((127 - Q) << 23);
+}
+
+// Plain one-pass step: every flip partner read straight from global memory.
+template <typename R>
+__global__ void __launch_bounds__(256) k_step_plain(StepArgs a, R ghi, R glo) {
+    using C = typename Cx<R>::T;
+    const int64_t N = (int64_t)1 << a.n;
+    const C* __restrict__ b1 = (const C*)a.b1;
+    const C* b2 = (const C*)a.b2;
+    const C* psi = (const C*)a.psi;
+    C* out = (C*)a.out;
+    const R ckr = (R)a.ck_re, cki = (R)a.ck_im, sc = (R)a.scale, sg = (R)a.sgn;
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N;
+         z += (int64_t)gridDim.x * blockDim.x) {
+        R sx = 0, sy = 0;
+        for (int j = 0; j < a.n; ++j) {
+            C p = b1[z ^ ((int64_t)1 << j)];
+            sx += p.x;
+            sy += p.y;
+        }
+        const C v = b1[z];
+        const int64_t e = energy_fixed(a.M, a.tiles, a.elow, (uint64_t)z);
+        R hx, hy;
+        if constexpr (sizeof(R) == 4) {
+            float dhi, dlo;
+            fixed_to_ff(e, a.Q, dhi, dlo);
+            hx = fmaf(dhi, v.x, dlo * v.x) + fmaf(ghi, sx, glo * sx);
+            hy = fmaf(dhi, v.y, dlo * v.y) + fmaf(ghi, sy, glo * sy);
+        } else {
+            const double d = __ll2double_rn(e) * ldexp(1.0, -a.Q);
+            hx = d * v.x + ghi * sx;
+            hy = d * v.y + ghi * sy;
+        }
+        R ox = sc * hx, oy = sc * hy;
+        if (a.sgn != 0.0) {
+            const C w = b2[z];
+            ox += sg * w.x;
+            oy += sg * w.y;
+        }
+        const C p = psi[z];
+        ox += ckr * p.x - cki * p.y;
+        oy += ckr * p.y + cki * p.x;
+        C o;
+        o.x = ox;
+        o.y = oy;
+        out[z] = o;
+    }
+}
+
+void launch_step_plain(int prec, const StepArgs& a, cudaStream_t s) {
+    const int64_t N = (int64_t)1 << a.n;
+    const unsigned grid = grid_for(N, 256, (int64_t)1 << 30);
+    if (prec == 0) {
+        float ghi = (float)a.g;
+        float glo = (float)(a.g - (double)ghi);
+        k_step_plain<float><<<grid, 256, 0, s>>>(a, ghi, glo);
+    } else {
+        k_step_plain<double><<<grid, 256, 0, s>>>(a, a.g, 0.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Small n: one CTA runs the whole recurrence with psi, b1, b2 in shared memory.
+// Each thread owns the same elements for all steps and keeps their Dt in registers.
+template <typename R, int PER>
+__global__ void __launch_bounds__(1024) k_small(int n, int K, const double2* __restrict__ coef, int Q,
+                                                const int64_t* __restrict__ tiles,
+                                                const int64_t* __restrict__ elow, double g,
+                                                typename Cx<R>::T* psi_g) {
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = 1 << n;
+    C* sp = (C*)smem_raw;
+    C* s1 = sp + N;
+    C* s2 = s1 + N;
+    const int M = n;  // one tile when n <= kTileBits
+    R dhi[PER], dlo[PER];
+    const double2 cK = coef[K];
+    for (int q = 0; q < PER; ++q) {
+        const int z = threadIdx.x + q * blockDim.x;
+        if (z < N) {
+            const int64_t e = energy_fixed(M, tiles, elow, (uint64_t)z);
+            if constexpr (sizeof(R) == 4) {
+                float h_, l_;
+                fixed_to_ff(e, Q, h_, l_);
+                dhi[q] = h_;
+                dlo[q] = l_;
+            } else {
+                dhi[q] = __ll2double_rn(e) * ldexp(1.0, -Q);
+                dlo[q] = 0;
+            }
+            const C p = psi_g[z];
+            sp[z] = p;
+            C b;
+            b.x = (R)cK.x * p.x - (R)cK.y * p.y;
+            b.y = (R)cK.x * p.y + (R)cK.y * p.x;
+            s1[z] = b;
+            C zero;
+            zero.x = 0;
+            zero.y = 0;
+            s2[z] = zero;
+        }
+    }
+    R ghi, glo;
+    if constexpr (sizeof(R) == 4) {
+        ghi = (float)g;
+        glo = (float)(g - (double)ghi);
+    } else {
+        ghi = g;
+        glo = 0;
+    }
+    __syncthreads();
+    C* b1 = s1;
+    C* b2 = s2;
+    for (int k = K - 1; k >= 0; --k) {
+        const double2 ck = coef[k];
+        const R sc = (k == 0) ? R(1) : R(2);
+        for (int q = 0; q < PER; ++q) {
+            const int z = threadIdx.x + q * blockDim.x;
+            if (z < N) {
+                R sx = 0, sy = 0;
+                for (int j = 0; j < n; ++j) {
+                    const C p = b1[z ^ (1 << j)];
+                    sx += p.x;
+                    sy += p.y;
+                }
+                const C v = b1[z];
+                R hx, hy;
+                if constexpr (sizeof(R) == 4) {
+                    hx = fmaf(dhi[q], v.x, dlo[q] * v.x) + fmaf(ghi, sx, glo * sx);
+                    hy = fmaf(dhi[q], v.y, dlo[q] * v.y) + fmaf(ghi, sy, glo * sy);
+                } else {
+                    hx = dhi[q] * v.x + ghi * sx;
+                    hy = dhi[q] * v.y + ghi * sy;
+                }
+                const C w = b2[z];
+                const C p = sp[z];
+                C o;
+                o.x = sc * hx - w.x + (R)ck.x * p.x - (R)ck.y * p.y;
+                o.y = sc * hy - w.y + (R)ck.x * p.y + (R)ck.y * p.x;
+                if (k == 0) psi_g[z] = o;
+                else b2[z] = o;
+            }
+        }
+        __syncthreads();
+        C* t = b1;
+        b1 = b2;
+        b2 = t;
+    }
+}
+
+cudaError_t launch_small(int prec, int n, int K, const double* coef_dev, int Q, const int64_t* tiles,
+                         const int64_t* elow, double g, void* psi, cudaStream_t s) {
+    const int N = 1 << n;
+    const int threads = N < 1024 ? (N < 32 ? 32 : N) : 1024;
+    const size_t cb = prec == 0 ? 8 : 16;
+    const size_t smem = 3 * (size_t)N * cb;
+    if (prec == 0) {
+        auto kern = k_small<float, 8>;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<1, threads, smem, s>>>(n, K, (const double2*)coef_dev, Q, tiles, elow, g, (float2*)psi);
+    } else {
+        auto kern = k_small<double, 4>;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<1, threads, smem, s>>>(n, K, (const double2*)coef_dev, Q, tiles, elow, g, (double2*)psi);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// ||y||^2 and <y|H_P|y> = sum_z (c + r Dt(z)) |y(z)|^2 in FP64, two-stage and
+// deterministic (fixed block partition, fixed tree order).
+template <typename R>
+__global__ void __launch_bounds__(256) k_norm_energy(int n, int M, int Q, const int64_t* __restrict__ tiles,
+                                                     const int64_t* __restrict__ elow, double c, double r,
+                                                     const typename Cx<R>::T* __restrict__ y,
+                                                     double* __restrict__ part) {
+    __shared__ double sn[256], se[256];
+    const int64_t N = (int64_t)1 << n;
+    const double sc = ldexp(1.0, -Q);
+    double an = 0.0, ae = 0.0;
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N;
+         z += (int64_t)gridDim.x * blockDim.x) {
+        const auto v = y[z];
+        const double p2 = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        const double E = c + r * (__ll2double_rn(energy_fixed(M, tiles, elow, (uint64_t)z)) * sc);
+        an += p2;
+        ae += E * p2;
+    }
+    sn[threadIdx.x] = an;
+    se[threadIdx.x] = ae;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sn[threadIdx.x] += sn[threadIdx.x + w];
+            se[threadIdx.x] += se[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = sn[0];
+        part[kRedBlocks + blockIdx.x] = se[0];
+    }
+}
+
+__global__ void k_sum2_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    __shared__ double sn[256], se[256];
+    double an = 0.0, ae = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        an += part[b];
+        ae += part[kRedBlocks + b];
+    }
+    sn[threadIdx.x] = an;
+    se[threadIdx.x] = ae;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sn[threadIdx.x] += sn[threadIdx.x + w];
+            se[threadIdx.x] += se[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sn[0];
+        out[1] = se[0];
+    }
+}
+
+void launch_norm_energy(int prec, int n, int M, int Q, const int64_t* tiles, const int64_t* elow,
+                        double c, double r, const void* psi, double* part, double* out2, cudaStream_t s) {
+    const int64_t N = (int64_t)1 << n;
+    const int nb = (int)grid_for(N, 256, kRedBlocks);
+    if (prec == 0)
+        k_norm_energy<float><<<nb, 256, 0, s>>>(n, M, Q, tiles, elow, c, r, (const float2*)psi, part);
+    else
+        k_norm_energy<double><<<nb, 256, 0, s>>>(n, M, Q, tiles, elow, c, r, (const double2*)psi, part);
+    k_sum2_final<<<1, 256, 0, s>>>(part, nb, out2);
+}
+
+}  // namespace cheb

@@ -1,0 +1,45 @@
+// Launchers for the device kernels (kernels.cu, fused.cu). All launches are
+// asynchronous on the given stream; none of them allocates memory.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace cheb {
+
+// Arguments of one Clenshaw step (Eq. recursion, Algorithm 2):
+//   out = scale * (Dt .* b1 + g * sum_j X_j b1) + sgn * b2 + ck * psi,
+// with Dt(z) = (E(z) - c) / r reconstructed from the fixed-point tables and
+// g = gamma / r. scale = 2 for the inner steps and 1 for the final step;
+// sgn = -1 normally and 0 when b_{k+2} is the zero vector. `out` may alias b2
+// (in-place update) or psi (final step), never b1.
+struct StepArgs {
+    int n;
+    int M;              // tile bits of the energy tables
+    int Q;              // fixed-point scale: value = int * 2^-Q
+    const int64_t* tiles;
+    const int64_t* elow;
+    const void* b1;
+    const void* b2;
+    const void* psi;
+    void* out;
+    double ck_re, ck_im;
+    double scale;
+    double sgn;
+    double g;           // gamma / r (the FP32 kernels split it into hi + lo)
+};
+
+void launch_tables(int n, int M, const int64_t* jq, int64_t* tiles, int64_t* elow, cudaStream_t s);
+void launch_minmax(int n, int M, const int64_t* tiles, const int64_t* elow, int64_t* part,
+                   int64_t* out2, cudaStream_t s);
+void launch_scale(int prec, int64_t N, const void* src, void* dst, double cr, double ci,
+                  cudaStream_t s);
+void launch_step_plain(int prec, const StepArgs& a, cudaStream_t s);
+// Whole Clenshaw run for n <= kSmallMax*: one CTA keeps psi, b1, b2 in shared memory.
+cudaError_t launch_small(int prec, int n, int K, const double* coef_dev, int Q,
+                         const int64_t* tiles, const int64_t* elow, double g, void* psi,
+                         cudaStream_t s);
+void launch_norm_energy(int prec, int n, int M, int Q, const int64_t* tiles, const int64_t* elow,
+                        double c, double r, const void* psi, double* part, double* out2,
+                        cudaStream_t s);
+
+}  // namespace cheb

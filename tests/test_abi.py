@@ -1,0 +1,120 @@
+"""The C-ABI library builds, loads and exports every declared symbol; its host-only
+entry points (coefficient generator, workspace query, argument checks) work
+without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2608_12058_b300 import _lib, api
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(cheb_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib.lib()
+    declared = _declared_functions()
+    assert len(declared) >= 8
+    for name in declared:
+        assert hasattr(L, name), name
+    # the binding describes each of them
+    for name in declared:
+        assert name in _lib.SIGNATURES, name
+
+
+def test_status_strings_and_version():
+    L = _lib.lib()
+    for code in range(7):
+        assert L.cheb_status_string(code)
+    assert b"sm_103a" in L.cheb_version()
+
+
+def test_workspace_bytes():
+    L = _lib.lib()
+    assert L.cheb_workspace_bytes(0, 0) == 0
+    assert L.cheb_workspace_bytes(34, 0) == 0
+    assert L.cheb_workspace_bytes(10, 2) == 0
+    w24 = L.cheb_workspace_bytes(24, 0)
+    assert w24 >= 2 * (1 << 24) * 8
+    assert L.cheb_workspace_bytes(24, 1) >= 2 * (1 << 24) * 16
+    # two Clenshaw vectors plus small tables: the state is the caller's (Sec. II.D's
+    # in-place b2 += H b1 leaves psi, b1, b2 as the only vectors)
+    assert w24 < 2 * (1 << 24) * 8 * 1.05
+
+
+@pytest.mark.parametrize("a,tol,method", [(0.0, 1e-12, "chebyshev"), (19.83, 1e-12, "chebyshev"),
+                                          (430.0, 2.0 ** -23, "chebyshev"), (1300.0, 2.0 ** -23, "chebyshev"),
+                                          (30.0, 1e-9, "cf"), (430.0, 2.0 ** -23, "cf")])
+def test_coefficients_match_oracle(oracle, a, tol, method):
+    """The product's generator (sum-of-squares Miller normalisation, its own
+    eigensolver for CF) and the oracle's agree coefficient by coefficient."""
+    phase = np.exp(-0.25j)
+    c, err = api.coefficients(a, tol, method, phase)
+    if method == "chebyshev":
+        ref, K, tb = oracle.cheb_coeffs(a, tol, phase)
+    else:
+        ref, K, tb = oracle.cf_coeffs(a, tol, phase)
+    assert len(c) == K + 1
+    assert np.max(np.abs(c - ref)) < 1e-14
+    assert abs(err - tb) <= 1e-3 * tb + 1e-30
+
+
+def test_coefficients_paper_term_count():
+    """Sec. II.B.2: 151 terms for exp(ix) on [-99, 99] at u = 2^-53."""
+    c, _ = api.coefficients(99.0, 2.0 ** -53)
+    assert len(c) == 151
+
+
+def test_coefficients_reject_bad_arguments():
+    L = _lib.lib()
+    buf = np.zeros(16)
+    K = ctypes.c_int()
+    dp = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert L.cheb_coefficients(float("nan"), 1, 0, 1e-6, 0, 7, dp, ctypes.byref(K), None) == 1
+    assert L.cheb_coefficients(1.0, 1, 0, 0.0, 0, 7, dp, ctypes.byref(K), None) == 1
+    assert L.cheb_coefficients(1.0, 1, 0, 1e-6, 5, 7, dp, ctypes.byref(K), None) == 1
+    # degree would exceed the buffer
+    assert L.cheb_coefficients(100.0, 1, 0, 1e-6, 0, 7, dp, ctypes.byref(K), None) == 6
+
+
+def test_expmv_rejects_bad_arguments_before_touching_the_device():
+    L = _lib.lib()
+    n = 4
+    h = np.zeros(n)
+    J = np.zeros((n, n))
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: the checks come first
+    ws = L.cheb_workspace_bytes(n, 0)
+    # n out of range
+    assert L.cheb_expmv(0, dp(h), dp(J), 1.0, 1.0, fake, 0, 1e-6, 0, 0, fake, ws, None, None) == 1
+    # null couplings
+    assert L.cheb_expmv(n, None, dp(J), 1.0, 1.0, fake, 0, 1e-6, 0, 0, fake, ws, None, None) == 1
+    # non-finite coupling
+    hb = h.copy()
+    hb[1] = np.inf
+    assert L.cheb_expmv(n, dp(hb), dp(J), 1.0, 1.0, fake, 0, 1e-6, 0, 0, fake, ws, None, None) == 1
+    # workspace too small / misaligned / missing
+    assert L.cheb_expmv(n, dp(h), dp(J), 1.0, 1.0, fake, 0, 1e-6, 0, 0, fake, ws - 1, None, None) == 2
+    assert L.cheb_expmv(n, dp(h), dp(J), 1.0, 1.0, fake, 0, 1e-6, 0, 0, ctypes.c_void_p((1 << 20) + 8), ws,
+                        None, None) == 2
+    assert L.cheb_expmv(n, dp(h), dp(J), 1.0, 1.0, fake, 0, 1e-6, 0, 0, None, ws, None, None) == 2
+    # bad precision enum, bad method, bad tolerance, misaligned psi, non-finite t
+    assert L.cheb_expmv(n, dp(h), dp(J), 1.0, 1.0, fake, 7, 1e-6, 0, 0, fake, ws, None, None) == 1
+    assert L.cheb_expmv(n, dp(h), dp(J), 1.0, 1.0, fake, 0, 1e-6, 9, 0, fake, ws, None, None) == 1
+    assert L.cheb_expmv(n, dp(h), dp(J), 1.0, 1.0, fake, 0, -1.0, 0, 0, fake, ws, None, None) == 1
+    assert L.cheb_expmv(n, dp(h), dp(J), 1.0, 1.0, ctypes.c_void_p((1 << 20) + 4), 0, 1e-6, 0, 0, fake, ws,
+                        None, None) == 1
+    assert L.cheb_expmv(n, dp(h), dp(J), 1.0, float("inf"), fake, 0, 1e-6, 0, 0, fake, ws, None, None) == 1
+    assert L.cheb_expmv(n, dp(h), dp(J), 1.0, 1.0, fake, 0, 1e-6, 0, -1, fake, ws, None, None) == 1

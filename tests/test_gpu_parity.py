@@ -1,0 +1,171 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 against the oracle's result on the same seeded input):
+FP64 recurrence 1e-12, FP32 recurrence 1e-5, the bars stated for the method.
+Sizes span the whole-vector shared-memory kernel (n <= 13 FP32 / 12 FP64), the
+boundary, and several tiles of the multi-tile paths.
+"""
+import numpy as np
+import pytest
+
+from paper_2608_12058_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _run(h, J, gamma, t, psi_np, prec, tol, method="chebyshev", path="auto", splits=0):
+    torch = _torch()
+    from paper_2608_12058_b300 import api
+
+    dt = torch.complex64 if prec == "fp32" else torch.complex128
+    psi = torch.from_numpy(psi_np.astype(np.complex128)).to(dt).cuda()
+    info = api.expmv(h, J, gamma, t, psi, tol=tol, method=method, path=path, time_splits=splits)
+    torch.cuda.synchronize()
+    return psi.cpu().numpy().astype(np.complex128), info
+
+
+def _rel(y, ref):
+    return np.linalg.norm(y - ref) / np.linalg.norm(ref)
+
+
+CASES = [
+    # n, seed, gamma, t, psi kind
+    (1, 1, 0.7, 2.0, "random"),
+    (3, 2, 1.3, 5.0, "random"),
+    (10, 0, 1.0, 1.0, "uniform"),     # the n=10 SK workload
+    (12, 3, 0.8, 6.0, "random"),
+    (13, 4, 1.1, 4.0, "random"),
+    (14, 5, 0.6, 8.0, "random"),
+    (16, 6, 1.0, 5.0, "uniform"),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,seed,gamma,t,kind", CASES)
+def test_expmv_matches_oracle(cuda_lib, oracle, prec, n, seed, gamma, t, kind):
+    h, J = I.sk_instance(n, seed)
+    psi = I.uniform_state(n) if kind == "uniform" else I.random_state(n, seed + 7)
+    tol = 1e-12 if prec == "fp64" else 2.0 ** -23
+    ref, oinfo = oracle.expmv(h, J, gamma, t, psi, tol)
+    y, info = _run(h, J, gamma, t, psi, prec, tol)
+    assert info["K"] == oinfo["K"]
+    assert abs(info["radius"] - oinfo["radius"]) <= 1e-13 * oinfo["radius"]
+    err = _rel(y, ref)
+    assert err <= TOL[prec], err
+    assert abs(info["norm"] - np.linalg.norm(y)) < (1e-6 if prec == "fp32" else 1e-12)
+    assert abs(info["energy"] - oinfo["energy"]) < (1e-4 if prec == "fp32" else 1e-10) * max(1, abs(oinfo["energy"]))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [4, 11, 15])
+def test_plain_path_matches_oracle(cuda_lib, oracle, prec, n):
+    """The one-pass kernel (every partner read from global memory) at sizes where
+    the automatic choice would take another kernel."""
+    h, J = I.sk_instance(n, 40 + n)
+    psi = I.random_state(n, 41 + n)
+    tol = 1e-12 if prec == "fp64" else 2.0 ** -23
+    ref, _ = oracle.expmv(h, J, 0.9, 3.0, psi, tol)
+    y, _ = _run(h, J, 0.9, 3.0, psi, prec, tol, path="plain")
+    assert _rel(y, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cf_method_matches_oracle(cuda_lib, oracle, prec):
+    n = 12
+    h, J = I.sk_instance(n, 77)
+    psi = I.random_state(n, 78)
+    tol = 1e-10 if prec == "fp64" else 2.0 ** -23
+    ref, oinfo = oracle.expmv(h, J, 1.2, 6.0, psi, tol, method="cf")
+    y, info = _run(h, J, 1.2, 6.0, psi, prec, tol, method="cf")
+    assert info["K"] == oinfo["K"]
+    assert _rel(y, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [9, 14])
+def test_time_splits_match_oracle(cuda_lib, oracle, prec, n):
+    h, J = I.sk_instance(n, 90 + n)
+    psi = I.random_state(n, 91)
+    tol = 1e-12 if prec == "fp64" else 2.0 ** -23
+    ref, oinfo = oracle.expmv(h, J, 0.7, 9.0, psi, tol, splits=3)
+    y, info = _run(h, J, 0.7, 9.0, psi, prec, tol, splits=3)
+    assert info["time_splits"] == 3 and info["K"] == oinfo["K"]
+    assert _rel(y, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_degenerate_degrees(cuda_lib, oracle, prec):
+    """t = 0 (degree 0: y = psi) and a tiny t with a loose tolerance (degree 1)."""
+    n = 11
+    h, J = I.sk_instance(n, 5)
+    psi = I.random_state(n, 6)
+    y, info = _run(h, J, 1.0, 0.0, psi, prec, 1e-6)
+    assert info["K"] == 0
+    assert _rel(y, psi) <= TOL[prec]
+    ref, oinfo = oracle.expmv(h, J, 1.0, 1e-4, psi, 1e-2)
+    y, info = _run(h, J, 1.0, 1e-4, psi, prec, 1e-2)
+    assert info["K"] == oinfo["K"] == 1
+    assert _rel(y, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [8, 17])
+def test_closed_forms(cuda_lib, prec, n):
+    """H_P = 0: product of cos(gt) I - i sin(gt) X over qubits; gamma = 0: pure phases."""
+    gamma, t = 0.9, 1.7
+    y, _ = _run(np.zeros(n), np.zeros((n, n)), gamma, t, I.basis_state(n, 0), prec, 1e-13 if prec == "fp64" else 2.0 ** -23)
+    w = np.array([bin(v).count("1") for v in range(1 << n)])
+    ref = np.cos(gamma * t) ** (n - w) * (-1j * np.sin(gamma * t)) ** w
+    assert _rel(y, ref) <= TOL[prec]
+    h, J = I.sk_instance(n, 3)
+    psi = I.random_state(n, 4)
+    y, _ = _run(h, J, 0.0, 3.0, psi, prec, 1e-13 if prec == "fp64" else 2.0 ** -23)
+    from oracle import oracle as O
+
+    E = O.energies(h, J)
+    assert _rel(y, np.exp(-3j * E) * psi) <= TOL[prec]
+
+
+def test_bounds_and_energy_entry_points(cuda_lib, oracle):
+    torch = _torch()
+    from paper_2608_12058_b300 import api
+
+    for n in [5, 13, 18]:
+        h, J = I.sk_instance(n, 60 + n, "uniform")
+        lo, hi = api.ising_bounds(h, J)
+        emin, emax, _, _ = oracle.bounds(h, J, 1.0)
+        assert abs(lo - emin) < 1e-12 and abs(hi - emax) < 1e-12
+        psi = I.random_state(n, 3)
+        e, nn = api.energy(h, J, torch.from_numpy(psi).cuda())
+        re, rn = oracle.energy_norm(h, J, psi)
+        assert abs(e - re) < 1e-12 * max(1, abs(re)) and abs(nn - rn) < 1e-13
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_poly_apply_matches_oracle_clenshaw(cuda_lib, oracle, prec):
+    """Caller-supplied Chebyshev coefficients (degree-50 random series, the kind of
+    polynomial timed in Fig. 4 / Fig. 6), same Ht as the oracle's Clenshaw."""
+    torch = _torch()
+    from paper_2608_12058_b300 import api
+
+    n = 14
+    h, J = I.sk_instance(n, 101)
+    rng = np.random.default_rng(5)
+    c = (rng.standard_normal(51) + 1j * rng.standard_normal(51)) / 8
+    emin, emax, center, r = oracle.bounds(h, J, 0.6)
+    D = (oracle.energies(h, J) - center) / r
+    psi = I.random_state(n, 102)
+    ref = oracle.clenshaw(D, 0.6 / r, c, psi)
+    dt = torch.complex64 if prec == "fp32" else torch.complex128
+    x = torch.from_numpy(psi).to(dt).cuda()
+    api.poly_apply(h, J, 0.6, center, r, c, x)
+    y = x.cpu().numpy().astype(np.complex128)
+    assert _rel(y, ref) <= TOL[prec]
