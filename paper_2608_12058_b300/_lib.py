@@ -52,6 +52,8 @@ SIGNATURES = {
     "cheb_poly_apply": (c_int, [c_int, _dp, _dp, c_double, c_double, c_double, c_int, _dp, c_void_p, c_int,
                                 c_int, c_void_p, c_size_t, c_void_p]),
     "cheb_energy": (c_int, [c_int, _dp, _dp, c_void_p, c_int, c_void_p, c_size_t, c_void_p, _dp, _dp]),
+    "cheb_set_fused_split": (c_int, [c_int, c_int, c_int]),
+    "cheb_get_fused_split": (c_int, [c_int, _ip, _ip]),
 }
 
 STATUS = {0: "CHEB_OK", 1: "CHEB_ERR_INVALID_ARG", 2: "CHEB_ERR_WORKSPACE", 3: "CHEB_ERR_CUDA",

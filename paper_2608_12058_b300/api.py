@@ -144,6 +144,17 @@ def poly_apply(h, J, gamma: float, center: float, radius: float, coeffs, psi, pa
     _lib.check(code, "cheb_poly_apply")
 
 
+def set_fused_split(n: int, l: int, h: int = 0):
+    """Choose how the fused FP32 step splits the n bits (13 + l + h = n); l = -1 resets."""
+    _lib.check(_lib.lib().cheb_set_fused_split(int(n), int(l), int(h)), "cheb_set_fused_split")
+
+
+def get_fused_split(n: int):
+    l, h = ctypes.c_int(), ctypes.c_int()
+    _lib.check(_lib.lib().cheb_get_fused_split(int(n), ctypes.byref(l), ctypes.byref(h)), "cheb_get_fused_split")
+    return l.value, h.value
+
+
 def energy(h, J, psi):
     """(<psi|H_P|psi>, ||psi||^2) in FP64 on the GPU."""
     h, J = _f64(h), _f64(J)

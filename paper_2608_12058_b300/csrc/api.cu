@@ -174,6 +174,7 @@ static cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector
         a.Q = Q;
         a.tiles = C.tiles();
         a.elow = C.elow();
+        a.jq = (const int64_t*)(C.ws + C.L.jq);
         a.b1 = B[cur];
         a.b2 = B[cur ^ 1];
         a.psi = psi;
@@ -356,6 +357,18 @@ cheb_status_t cheb_poly_apply(int n, const double* h, const double* J, double ga
     std::vector<std::complex<double>> c(K + 1);
     for (int m = 0; m <= K; ++m) c[m] = std::complex<double>(coeffs[2 * m], coeffs[2 * m + 1]);
     return clenshaw_run(C, path, psi, c, F.Q, gamma / radius);
+}
+
+cheb_status_t cheb_set_fused_split(int n, int l, int h) {
+    return fused_set_split(n, l, h) ? CHEB_OK : CHEB_ERR_INVALID_ARG;
+}
+
+cheb_status_t cheb_get_fused_split(int n, int* l, int* h) {
+    if (!l || !h || !fused_supported(n, 0)) return CHEB_ERR_INVALID_ARG;
+    FusedPlan p = fused_plan(n, 0);
+    *l = p.l;
+    *h = p.h;
+    return CHEB_OK;
 }
 
 cheb_status_t cheb_energy(int n, const double* h, const double* J, const void* psi, cheb_precision_t precision,

@@ -1,18 +1,524 @@
-// Fused FP32 Clenshaw step (placeholder until the tiled kernels land).
+// Fused FP32 Clenshaw step for n >= 13: the matrix-free hypercube matvec of
+// Sec. II.D fused with the recurrence b_k = 2 Ht b_{k+1} - b_{k+2} + c_k psi
+// (Eq. recursion), split over at most two passes over memory.
+//
+//  * High pass (only when n > 13 + l): bits [n-h, n). A tile is 2^h rows of 16
+//    consecutive amplitudes (128 B) whose top h bits run over all values; each
+//    thread loads its own rows (coalesced 128-bit loads, prefetched one tile
+//    ahead in registers), exchanges them through shared memory and forms the
+//    flip sum over the h bits. It writes q = scale*g*S_high + sgn*b_{k+2} into
+//    the slot of b_{k+2}.
+//  * Low pass: bits [0, 13) from a 64 KB contiguous tile of b_{k+1} staged in
+//    shared memory by a 1-D TMA bulk copy (double-buffered, mbarrier-tracked),
+//    plus bits [13, 13 + l) read from the partner tiles through L2 (persistent
+//    CTAs walk the tiles in order, so partners 2^j tiles away are in flight or
+//    just used). It recomputes the Ising diagonal from the fixed-point tables
+//    (float-float: hi + lo, exact to ~2^-48) and writes
+//    out = scale*(Dt.*b1 + g*S_low) + slot_coeff*slot + c_k*psi.
+//
+// Thread layout of the low pass (512 threads, 16 amplitudes each): a thread's
+// float4 holds the pair {2t', 2t'+1}; bit 0 is inside the float4, bits 1..9 are
+// the thread index (partners read from shared memory; 8 consecutive threads read
+// 8 consecutive 16-byte words, so there are no bank conflicts), bits 10..12 index
+// the thread's 8 float4 registers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <map>
+#include <mutex>
+
+#include "cheb_internal.h"
 #include "fused.cuh"
 
 namespace cheb {
 
+namespace {
+
+constexpr int kLowBits = 13;                      // = kTileBits
+constexpr int kLowThreads = 512;
+constexpr int kTile = 1 << kLowBits;              // amplitudes per low tile
+constexpr int kTileF4 = kTile / 2;                // float4 per tile
+constexpr uint32_t kTileBytes = kTile * 8;        // 64 KB
+constexpr int kMaxL2Bits = 9;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after kWaitCycles and reports it through the flags word.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* flags) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            atomicOr(flags, kFlagTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ int64_t sel(uint32_t bit, int64_t v) { return bit ? -v : v; }
+
+__device__ __forceinline__ void to_ff(int64_t e, int Q, float& hi, float& lo) {
+    const int sh = Q - 24;
+    const int64_t ih = e >> sh;
+    const int64_t il = e - (ih << sh);
+    hi = __ll2float_rn(ih) * 5.9604644775390625e-08f;  // 2^-24
+    lo = __ll2float_rn(il) * __int_as_float((127 - Q) << 23);
+}
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+struct LowArgs {
+    const float4* b1;
+    const float4* slot;
+    const float4* psi;
+    float4* out;
+    const int64_t* tiles;  // (kLowBits + 1) int64 per tile
+    const int64_t* jq;     // J symmetric n*n, h[n], c
+    int* flags;
+    int n;
+    int l;
+    int Q;
+    int64_t ntiles;
+    float ck_re, ck_im, scale, slot_coeff, ghi, glo;
+};
+
+__global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4* buf0 = (float4*)smem;
+    float4* buf1 = buf0 + kTileF4;
+    uint64_t* bar = (uint64_t*)(smem + 2 * kTileBytes);
+    int64_t* erho = (int64_t*)(smem + 2 * kTileBytes + 64);  // 16 entries
+    const int t = threadIdx.x;
+    const int n = a.n;
+    const int64_t* J = a.jq;
+    const int64_t* hq = a.jq + (size_t)n * n;
+
+    // Per-thread constants of the energy decomposition (bits 1..9 = thread bits,
+    // bits 0, 10, 11, 12 = register bits).
+    int64_t e_tau = 0;
+    for (int i = 1; i <= 9; ++i) {
+        int64_t hi = hq[i];
+        for (int j = i + 1; j <= 9; ++j) hi += sel((t >> (j - 1)) & 1, J[i * n + j]);
+        e_tau += sel((t >> (i - 1)) & 1, hi);
+    }
+    const int rbit[4] = {0, 10, 11, 12};
+    int64_t phi[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = rbit[q];
+        int64_t v = hq[i];
+        for (int j = 1; j <= 9; ++j) v += sel((t >> (j - 1)) & 1, J[i * n + j]);
+        phi[q] = v;
+    }
+    if (t < 16) {
+        // t = (p << 1) | w over register bits {0: w, 10..12: p}
+        int64_t e = 0;
+        for (int q1 = 0; q1 < 4; ++q1)
+            for (int q2 = q1 + 1; q2 < 4; ++q2)
+                e += sel(((t >> q1) ^ (t >> q2)) & 1, J[rbit[q1] * n + rbit[q2]]);
+        erho[t] = e;
+    }
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const float2 ck = make_float2(a.ck_re, a.ck_im);
+    int64_t T = blockIdx.x;
+    if (t == 0 && T < a.ntiles) {
+        mbar_expect_tx(&bar[0], kTileBytes);
+        tma_load_1d(buf0, a.b1 + T * kTileF4, kTileBytes, &bar[0]);
+    }
+    for (int it = 0; T < a.ntiles; ++it, T += gridDim.x) {
+        const int b = it & 1;
+        float4* cur = b ? buf1 : buf0;
+        const int64_t Tn = T + gridDim.x;
+        if (t == 0 && Tn < a.ntiles) {
+            fence_proxy_async();
+            mbar_expect_tx(&bar[b ^ 1], kTileBytes);
+            tma_load_1d(b ? buf0 : buf1, a.b1 + Tn * kTileF4, kTileBytes, &bar[b ^ 1]);
+        }
+        const int64_t base_f4 = T * kTileF4 + t;
+        // flips of bits 13 .. 13+l-1: partner tiles through L2
+        float4 S[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) S[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < a.l; ++j) {
+            const int64_t pb = (T ^ ((int64_t)1 << j)) * kTileF4 + t;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) S[p] = add4(S[p], __ldg(a.b1 + pb + p * kLowThreads));
+        }
+        // energy of this tile's 16 amplitudes per thread
+        const int64_t* row = a.tiles + T * (kLowBits + 1);
+        int64_t base = __ldg(row + kLowBits) + e_tau;
+#pragma unroll
+        for (int i = 1; i <= 9; ++i) base += sel((t >> (i - 1)) & 1, __ldg(row + i));
+        const int64_t g0 = __ldg(row + 0) + phi[0];
+        const int64_t g10 = __ldg(row + 10) + phi[1];
+        const int64_t g11 = __ldg(row + 11) + phi[2];
+        const int64_t g12 = __ldg(row + 12) + phi[3];
+
+        const bool ok = mbar_wait(&bar[b], (it >> 1) & 1, a.flags);
+        if (__syncthreads_or(!ok)) {
+            // give up on this launch; let the copy already issued for the next tile land first
+            if (Tn < a.ntiles) mbar_wait(&bar[b ^ 1], ((it + 1) >> 1) & 1, a.flags);
+            break;
+        }
+        {
+            float4 v[8];
+#pragma unroll
+            for (int p = 0; p < 8; ++p) v[p] = cur[t + p * kLowThreads];
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                // bit 0 (inside the pair) and bits 10..12 (registers)
+                S[p].x += v[p].z;
+                S[p].y += v[p].w;
+                S[p].z += v[p].x;
+                S[p].w += v[p].y;
+                S[p] = add4(S[p], v[p ^ 1]);
+                S[p] = add4(S[p], v[p ^ 2]);
+                S[p] = add4(S[p], v[p ^ 4]);
+            }
+            // bits 1..9 (thread index) from shared memory
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int pt = t ^ (1 << j);
+#pragma unroll
+                for (int p = 0; p < 8; ++p) S[p] = add4(S[p], cur[pt + p * kLowThreads]);
+            }
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const int64_t Gp = base + sel(p & 1, g10) + sel((p >> 1) & 1, g11) + sel((p >> 2) & 1, g12);
+                const int64_t e0 = Gp + g0 + erho[(p << 1) | 0];
+                const int64_t e1 = Gp - g0 + erho[(p << 1) | 1];
+                float d0h, d0l, d1h, d1l;
+                to_ff(e0, a.Q, d0h, d0l);
+                to_ff(e1, a.Q, d1h, d1l);
+                const int64_t idx = base_f4 + p * kLowThreads;
+                const float4 ps = a.psi[idx];
+                float4 o;
+                o.x = fmaf(d0h, v[p].x, d0l * v[p].x) + fmaf(a.ghi, S[p].x, a.glo * S[p].x);
+                o.y = fmaf(d0h, v[p].y, d0l * v[p].y) + fmaf(a.ghi, S[p].y, a.glo * S[p].y);
+                o.z = fmaf(d1h, v[p].z, d1l * v[p].z) + fmaf(a.ghi, S[p].z, a.glo * S[p].z);
+                o.w = fmaf(d1h, v[p].w, d1l * v[p].w) + fmaf(a.ghi, S[p].w, a.glo * S[p].w);
+                o.x = a.scale * o.x + (ck.x * ps.x - ck.y * ps.y);
+                o.y = a.scale * o.y + (ck.x * ps.y + ck.y * ps.x);
+                o.z = a.scale * o.z + (ck.x * ps.z - ck.y * ps.w);
+                o.w = a.scale * o.w + (ck.x * ps.w + ck.y * ps.z);
+                if (a.slot_coeff != 0.f) {
+                    const float4 q = a.slot[idx];
+                    o.x += a.slot_coeff * q.x;
+                    o.y += a.slot_coeff * q.y;
+                    o.z += a.slot_coeff * q.z;
+                    o.w += a.slot_coeff * q.w;
+                }
+                a.out[idx] = o;
+            }
+        }
+        __syncthreads();  // everyone is done with `cur` before it is refilled
+    }
+}
+
+// ---------------------------------------------------------------------------
+// High pass over the top H bits. Rows of 16 amplitudes (8 float4); row index
+// rho in [0, 2^H) selects the top bits. Thread t: u = t & 7 (float4 within the
+// row), rho low bits = t >> 3 (up to 6 bits), rho high bits = register index p.
+template <int H>
+struct HighCfg {
+    static constexpr int kRowBitsT = H < 6 ? H : 6;          // row bits in the thread index
+    static constexpr int kThreads = 8 << kRowBitsT;          // 64 .. 512
+    static constexpr int kP = 1 << (H - kRowBitsT);          // float4 registers per thread
+    static constexpr int kRows = 1 << H;
+};
+
+struct HighArgs {
+    const float4* b1;
+    float4* slot;       // in: b_{k+2} (if sgn != 0); out: q
+    int n;
+    int64_t ntiles;     // 2^(n - H - 4)
+    float scale_g;      // scale * (gamma / r), float-float hi part
+    float scale_glo;    // lo part
+    float sgn;
+};
+
+template <int H>
+__global__ void __launch_bounds__(HighCfg<H>::kThreads, 1) k_high(const HighArgs a) {
+    using Cfg = HighCfg<H>;
+    extern __shared__ __align__(16) float4 tile[];  // kRows * 8 float4
+    const int t = threadIdx.x;
+    const int u = t & 7;
+    const int rlo = t >> 3;
+    const int64_t row_stride_f4 = (int64_t)1 << (a.n - H - 1);  // 2^(n-H) amplitudes
+    float4 nxt[Cfg::kP];
+    int64_t T = blockIdx.x;
+    if (T < a.ntiles) {
+#pragma unroll
+        for (int p = 0; p < Cfg::kP; ++p) {
+            const int rho = rlo | (p << Cfg::kRowBitsT);
+            nxt[p] = __ldg(a.b1 + T * 8 + rho * row_stride_f4 + u);
+        }
+    }
+    for (; T < a.ntiles; T += gridDim.x) {
+        float4 v[Cfg::kP];
+#pragma unroll
+        for (int p = 0; p < Cfg::kP; ++p) {
+            v[p] = nxt[p];
+            const int rho = rlo | (p << Cfg::kRowBitsT);
+            tile[rho * 8 + u] = v[p];
+        }
+        const int64_t Tn = T + gridDim.x;
+        if (Tn < a.ntiles) {
+#pragma unroll
+            for (int p = 0; p < Cfg::kP; ++p) {
+                const int rho = rlo | (p << Cfg::kRowBitsT);
+                nxt[p] = __ldg(a.b1 + Tn * 8 + rho * row_stride_f4 + u);
+            }
+        }
+        __syncthreads();
+        float4 S[Cfg::kP];
+#pragma unroll
+        for (int p = 0; p < Cfg::kP; ++p) {
+            S[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int b = 1; b < Cfg::kP; b <<= 1) S[p] = add4(S[p], v[p ^ b]);
+        }
+#pragma unroll
+        for (int j = 0; j < Cfg::kRowBitsT; ++j) {
+#pragma unroll
+            for (int p = 0; p < Cfg::kP; ++p) {
+                const int rho = (rlo ^ (1 << j)) | (p << Cfg::kRowBitsT);
+                S[p] = add4(S[p], tile[rho * 8 + u]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < Cfg::kP; ++p) {
+            const int rho = rlo | (p << Cfg::kRowBitsT);
+            const int64_t idx = T * 8 + rho * row_stride_f4 + u;
+            float4 q;
+            q.x = fmaf(a.scale_g, S[p].x, a.scale_glo * S[p].x);
+            q.y = fmaf(a.scale_g, S[p].y, a.scale_glo * S[p].y);
+            q.z = fmaf(a.scale_g, S[p].z, a.scale_glo * S[p].z);
+            q.w = fmaf(a.scale_g, S[p].w, a.scale_glo * S[p].w);
+            if (a.sgn != 0.f) {
+                const float4 w = a.slot[idx];
+                q.x += a.sgn * w.x;
+                q.y += a.sgn * w.y;
+                q.z += a.sgn * w.z;
+                q.w += a.sgn * w.w;
+            }
+            a.slot[idx] = q;
+        }
+        __syncthreads();  // tile reused by the next iteration
+    }
+}
+
+int g_num_sms = 0;
+std::mutex g_mu;
+
+int num_sms() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    return g_num_sms;
+}
+
+template <int H>
+cudaError_t launch_high_t(const HighArgs& a, cudaStream_t s) {
+    using Cfg = HighCfg<H>;
+    const size_t smem = (size_t)Cfg::kRows * 8 * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(k_high<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_high<H>, Cfg::kThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)num_sms() * per_sm);
+    if (grid < 1) grid = 1;
+    k_high<H><<<(unsigned)grid, Cfg::kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_high(int H, const HighArgs& a, cudaStream_t s) {
+    switch (H) {
+        case 3: return launch_high_t<3>(a, s);
+        case 4: return launch_high_t<4>(a, s);
+        case 5: return launch_high_t<5>(a, s);
+        case 6: return launch_high_t<6>(a, s);
+        case 7: return launch_high_t<7>(a, s);
+        case 8: return launch_high_t<8>(a, s);
+        case 9: return launch_high_t<9>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
 size_t fused_scratch_bytes(int, int) { return 0; }
-bool fused_supported(int, int) { return false; }
+
+// Two passes cover at most 13 + 9 + 9 = 31 bits; larger n runs the plain kernel.
+constexpr int kFusedMaxQubits = kLowBits + kMaxL2Bits + 9;
+
+bool fused_supported(int n, int prec) { return prec == 0 && n >= kLowBits && n <= kFusedMaxQubits; }
+
+// Caller-chosen splits (cheb_set_fused_split), per n; l < 0 means "default".
+static int g_split_l[kMaxQubits + 1];
+static int g_split_h[kMaxQubits + 1];
+static bool g_split_init = false;
+
+static void split_table_init() {
+    if (!g_split_init) {
+        for (int i = 0; i <= kMaxQubits; ++i) g_split_l[i] = g_split_h[i] = -1;
+        g_split_init = true;
+    }
+}
+
+bool fused_split_valid(int n, int l, int h) {
+    return n >= kLowBits && n <= kMaxQubits && l >= 0 && l <= kMaxL2Bits && (h == 0 || (h >= 3 && h <= 9)) &&
+           kLowBits + l + h == n;
+}
+
+bool fused_set_split(int n, int l, int h) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    split_table_init();
+    if (n < kLowBits || n > kMaxQubits) return false;
+    if (l < 0) {
+        g_split_l[n] = g_split_h[n] = -1;
+        return true;
+    }
+    if (!fused_split_valid(n, l, h)) return false;
+    g_split_l[n] = l;
+    g_split_h[n] = h;
+    return true;
+}
+
+// Split of the n bits: low pass takes 13 + l, the high pass the top h.
 FusedPlan fused_plan(int n, int prec) {
     FusedPlan p;
     p.n = n;
     p.prec = prec;
+    p.M = kLowBits;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        split_table_init();
+        if (n >= kLowBits && n <= kMaxQubits && g_split_l[n] >= 0) {
+            p.l = g_split_l[n];
+            p.h = g_split_h[n];
+            return p;
+        }
+    }
+    const int rest = n - kLowBits;
+    if (rest <= 8) {
+        p.l = rest;
+        p.h = 0;
+    } else if (rest <= 8 + 9) {
+        // as many bits as possible in the high pass (it costs one extra stream of
+        // b_{k+1} and of the slot), the remainder through L2
+        p.h = std::min(9, rest);
+        p.l = rest - p.h;
+        if (p.h < 3) {
+            p.h = 3;
+            p.l = rest - 3;
+        }
+    } else {
+        p.h = 9;
+        p.l = rest - 9;
+    }
     return p;
 }
-cudaError_t launch_step_fused(const FusedPlan&, const StepArgs&, void*, int*, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, int* flags, cudaStream_t st) {
+    if (plan.prec != 0 || plan.n != s.n || plan.l < 0 || plan.l > kMaxL2Bits || plan.h < 0 || plan.h > 9 ||
+        (plan.h > 0 && plan.h < 3) || plan.M + plan.l + plan.h != s.n || s.M != kLowBits)
+        return cudaErrorInvalidValue;
+    const float ghi = (float)s.g;
+    const float glo = (float)(s.g - (double)ghi);
+    float slot_coeff = (float)s.sgn;
+    if (plan.h > 0) {
+        HighArgs ha;
+        ha.b1 = (const float4*)s.b1;
+        ha.slot = (float4*)s.b2;
+        ha.n = s.n;
+        ha.ntiles = (int64_t)1 << (s.n - plan.h - 4);
+        ha.scale_g = (float)s.scale * ghi;
+        ha.scale_glo = (float)s.scale * glo;
+        ha.sgn = (float)s.sgn;
+        cudaError_t e = launch_high(plan.h, ha, st);
+        if (e != cudaSuccess) return e;
+        slot_coeff = 1.0f;  // the slot now holds q
+    }
+    LowArgs la;
+    la.b1 = (const float4*)s.b1;
+    la.slot = (const float4*)s.b2;
+    la.psi = (const float4*)s.psi;
+    la.out = (float4*)s.out;
+    la.tiles = s.tiles;
+    la.jq = s.jq;
+    la.flags = flags;
+    la.n = s.n;
+    la.l = plan.l;
+    la.Q = s.Q;
+    la.ntiles = (int64_t)1 << (s.n - kLowBits);
+    la.ck_re = (float)s.ck_re;
+    la.ck_im = (float)s.ck_im;
+    la.scale = (float)s.scale;
+    la.slot_coeff = slot_coeff;
+    la.ghi = ghi;
+    la.glo = glo;
+    const size_t smem = 2 * (size_t)kTileBytes + 64 + 16 * sizeof(int64_t);
+    cudaError_t e = cudaFuncSetAttribute(k_low, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int64_t grid = std::min<int64_t>(la.ntiles, num_sms());
+    k_low<<<(unsigned)grid, kLowThreads, smem, st>>>(la);
+    return cudaGetLastError();
 }
 
 }  // namespace cheb

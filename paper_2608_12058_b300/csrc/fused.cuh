@@ -22,6 +22,9 @@ struct FusedPlan {
 };
 
 size_t fused_scratch_bytes(int n, int prec);
+bool fused_split_valid(int n, int l, int h);
+// Override the split for n (l < 0 restores the default); false if invalid.
+bool fused_set_split(int n, int l, int h);
 bool fused_supported(int n, int prec);
 FusedPlan fused_plan(int n, int prec);
 cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& a, void* scratch, int* flags,

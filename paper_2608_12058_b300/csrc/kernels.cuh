@@ -18,6 +18,7 @@ struct StepArgs {
     int Q;              // fixed-point scale: value = int * 2^-Q
     const int64_t* tiles;
     const int64_t* elow;
+    const int64_t* jq;  // fixed-point couplings: J symmetric n*n, h[n], c
     const void* b1;
     const void* b2;
     const void* psi;
