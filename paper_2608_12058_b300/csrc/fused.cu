@@ -1,31 +1,30 @@
-// Fused FP32 Clenshaw step for n >= 13: the matrix-free hypercube matvec of
+// Fused FP32 Clenshaw step for n >= 12: the matrix-free hypercube matvec of
 // Sec. II.D fused with the recurrence b_k = 2 Ht b_{k+1} - b_{k+2} + c_k psi
 // (Eq. recursion), split over at most two passes over memory.
 //
-//  * High pass (only when n > 13 + l): bits [n-h, n). A tile is 2^h rows of 16
+//  * High pass (only when h > 0): bits [n-h, n). A tile is 2^h rows of 16
 //    consecutive amplitudes (128 B) whose top h bits run over all values; each
 //    thread loads its own rows (coalesced 128-bit loads, prefetched one tile
-//    ahead in registers), exchanges them through shared memory and forms the
-//    flip sum over the h bits. It writes q = scale*g*S_high + sgn*b_{k+2} into
-//    the slot of b_{k+2}.
-//  * Low pass: bits [0, 13) from a 64 KB contiguous tile of b_{k+1} staged in
-//    shared memory by a 1-D TMA bulk copy (double-buffered, mbarrier-tracked),
-//    plus bits [13, 13 + l) read from the partner tiles through L2 (persistent
-//    CTAs walk the tiles in order, so partners 2^j tiles away are in flight or
-//    just used). It recomputes the Ising diagonal from the fixed-point tables
-//    (float-float: hi + lo, exact to ~2^-48) and writes
-//    out = scale*(Dt.*b1 + g*S_low) + slot_coeff*slot + c_k*psi.
+//    ahead), exchanges them through shared memory and forms the flip sum over
+//    the h bits. It writes q = scale*g*S_high + sgn*b_{k+2} into the slot of
+//    b_{k+2}.
+//  * Low pass: bits [0, 12) from a 32 KB contiguous tile of b_{k+1}, with psi and
+//    the slot tile beside it, all three staged in shared memory by 1-D TMA bulk
+//    copies in a two-stage mbarrier pipeline; bits [12, 12 + l) from the partner
+//    tiles through L2 (persistent CTAs walk the tiles in order, so partners 2^j
+//    tiles away are in flight or were just used). It recomputes the Ising
+//    diagonal from the fixed-point tables (float-float hi + lo, exact to ~2^-48)
+//    and writes out = scale*(Dt.*b1 + g*S_low) + slot_coeff*slot + c_k*psi.
 //
-// Thread layout of the low pass (512 threads, 16 amplitudes each): a thread's
-// float4 holds the pair {2t', 2t'+1}; bit 0 is inside the float4, bits 1..9 are
-// the thread index (partners read from shared memory; 8 consecutive threads read
-// 8 consecutive 16-byte words, so there are no bank conflicts), bits 10..12 index
-// the thread's 8 float4 registers.
+// Thread layout of the low pass (512 threads, 8 amplitudes each): a thread's
+// float4 p holds amplitudes {2t + 1024p, 2t + 1024p + 1}: bit 0 lies inside the
+// float4, bits 1..9 are the thread index (partners read from shared memory;
+// 8 consecutive threads read 8 consecutive 16-byte words, free of bank
+// conflicts), bits 10..11 index the thread's 4 float4 registers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
-#include <map>
 #include <mutex>
 
 #include "cheb_internal.h"
@@ -35,13 +34,15 @@ namespace cheb {
 
 namespace {
 
-constexpr int kLowBits = 13;                      // = kTileBits
+constexpr int kLowBits = kTileBits;                // 12
 constexpr int kLowThreads = 512;
-constexpr int kTile = 1 << kLowBits;              // amplitudes per low tile
-constexpr int kTileF4 = kTile / 2;                // float4 per tile
-constexpr uint32_t kTileBytes = kTile * 8;        // 64 KB
-constexpr int kMaxL2Bits = 9;
-constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr int kTile = 1 << kLowBits;               // amplitudes per low tile
+constexpr int kTileF4 = kTile / 2;                 // float4 per tile
+constexpr int kPerThread = kTileF4 / kLowThreads;  // float4 per thread (4)
+constexpr uint32_t kTileBytes = kTile * 8;         // 32 KB
+constexpr int kMaxL2Bits = 10;
+constexpr long long kWaitCycles = 4000000000LL;    // ~2 s at 2 GHz
+static_assert(kPerThread == 4, "layout assumes 4 float4 per thread");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -107,8 +108,31 @@ __device__ __forceinline__ void to_ff(int64_t e, int Q, float& hi, float& lo) {
     lo = __ll2float_rn(il) * __int_as_float((127 - Q) << 23);
 }
 
-__device__ __forceinline__ float4 add4(float4 a, float4 b) {
-    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
+
+// Two complex numbers (a float4) accumulated with packed FP32x2 adds.
+struct Acc {
+    float2 a, b;
+    __device__ __forceinline__ void zero() { a = b = make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void add(float4 v) {
+        a = __fadd2_rn(a, lo2(v));
+        b = __fadd2_rn(b, hi2(v));
+    }
+};
+
+// o = scale*(d*v + g*s) + cs*q + ck*ps for one complex amplitude, float-float
+// d = dh + dl and g = gh + gl.
+__device__ __forceinline__ float2 combine(float dh, float dl, float2 v, float2 gh, float2 gl, float2 s,
+                                          float2 scale, float2 cs, float2 q, float2 ckr, float2 cki_s,
+                                          float2 ps) {
+    float2 h = __ffma2_rn(dup(dh), v, __fmul2_rn(dup(dl), v));
+    h = __fadd2_rn(h, __ffma2_rn(gh, s, __fmul2_rn(gl, s)));
+    float2 o = __ffma2_rn(scale, h, __fmul2_rn(cs, q));
+    o = __ffma2_rn(ckr, ps, o);
+    o = __ffma2_rn(cki_s, make_float2(ps.y, ps.x), o);  // cki_s = (-cki, cki)
+    return o;
 }
 
 struct LowArgs {
@@ -126,39 +150,42 @@ struct LowArgs {
     float ck_re, ck_im, scale, slot_coeff, ghi, glo;
 };
 
+// Shared memory: 2 stages x {b1, psi, slot} tiles, then 2 mbarriers and erho[8].
+constexpr size_t kLowSmem = 2 * 3 * (size_t)kTileBytes + 64 + 8 * sizeof(int64_t);
+
 __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    float4* buf0 = (float4*)smem;
-    float4* buf1 = buf0 + kTileF4;
-    uint64_t* bar = (uint64_t*)(smem + 2 * kTileBytes);
-    int64_t* erho = (int64_t*)(smem + 2 * kTileBytes + 64);  // 16 entries
+    uint64_t* bar = (uint64_t*)(smem + 6 * kTileBytes);
+    int64_t* erho = (int64_t*)(smem + 6 * kTileBytes + 64);
     const int t = threadIdx.x;
     const int n = a.n;
     const int64_t* J = a.jq;
     const int64_t* hq = a.jq + (size_t)n * n;
+    const bool need_slot = a.slot_coeff != 0.f;
+    const uint32_t stage_bytes = (need_slot ? 3u : 2u) * kTileBytes;
 
-    // Per-thread constants of the energy decomposition (bits 1..9 = thread bits,
-    // bits 0, 10, 11, 12 = register bits).
+    // Energy decomposition constants: bits 1..9 are the thread index, bits 0, 10,
+    // 11 vary inside the thread.
     int64_t e_tau = 0;
     for (int i = 1; i <= 9; ++i) {
         int64_t hi = hq[i];
         for (int j = i + 1; j <= 9; ++j) hi += sel((t >> (j - 1)) & 1, J[i * n + j]);
         e_tau += sel((t >> (i - 1)) & 1, hi);
     }
-    const int rbit[4] = {0, 10, 11, 12};
-    int64_t phi[4];
+    const int rbit[3] = {0, 10, 11};
+    int64_t phi[3];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 3; ++q) {
         const int i = rbit[q];
         int64_t v = hq[i];
         for (int j = 1; j <= 9; ++j) v += sel((t >> (j - 1)) & 1, J[i * n + j]);
         phi[q] = v;
     }
-    if (t < 16) {
-        // t = (p << 1) | w over register bits {0: w, 10..12: p}
+    if (t < 8) {
+        // t = (p << 1) | w over register bits {0: w, 10..11: p}
         int64_t e = 0;
-        for (int q1 = 0; q1 < 4; ++q1)
-            for (int q2 = q1 + 1; q2 < 4; ++q2)
+        for (int q1 = 0; q1 < 3; ++q1)
+            for (int q2 = q1 + 1; q2 < 3; ++q2)
                 e += sel(((t >> q1) ^ (t >> q2)) & 1, J[rbit[q1] * n + rbit[q2]]);
         erho[t] = e;
     }
@@ -169,32 +196,54 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
     }
     __syncthreads();
 
-    const float2 ck = make_float2(a.ck_re, a.ck_im);
+    auto issue = [&](int stage, int64_t T) {
+        float4* dst = (float4*)(smem + (size_t)stage * 3 * kTileBytes);
+        mbar_expect_tx(&bar[stage], stage_bytes);
+        tma_load_1d(dst, a.b1 + T * kTileF4, kTileBytes, &bar[stage]);
+        tma_load_1d(dst + kTileF4, a.psi + T * kTileF4, kTileBytes, &bar[stage]);
+        if (need_slot) tma_load_1d(dst + 2 * kTileF4, a.slot + T * kTileF4, kTileBytes, &bar[stage]);
+    };
+
+    const float2 ckr = dup(a.ck_re), cki_s = make_float2(-a.ck_im, a.ck_im);
+    const float2 gh = dup(a.ghi), gl = dup(a.glo), sc = dup(a.scale), cs = dup(a.slot_coeff);
     int64_t T = blockIdx.x;
-    if (t == 0 && T < a.ntiles) {
-        mbar_expect_tx(&bar[0], kTileBytes);
-        tma_load_1d(buf0, a.b1 + T * kTileF4, kTileBytes, &bar[0]);
-    }
+    if (t == 0 && T < a.ntiles) issue(0, T);
     for (int it = 0; T < a.ntiles; ++it, T += gridDim.x) {
         const int b = it & 1;
-        float4* cur = b ? buf1 : buf0;
+        const float4* sb1 = (const float4*)(smem + (size_t)b * 3 * kTileBytes);
+        const float4* spsi = sb1 + kTileF4;
+        const float4* sslot = sb1 + 2 * kTileF4;
         const int64_t Tn = T + gridDim.x;
         if (t == 0 && Tn < a.ntiles) {
             fence_proxy_async();
-            mbar_expect_tx(&bar[b ^ 1], kTileBytes);
-            tma_load_1d(b ? buf0 : buf1, a.b1 + Tn * kTileF4, kTileBytes, &bar[b ^ 1]);
+            issue(b ^ 1, Tn);
         }
-        const int64_t base_f4 = T * kTileF4 + t;
-        // flips of bits 13 .. 13+l-1: partner tiles through L2
-        float4 S[8];
+        // flips of bits 12 .. 12+l-1 from partner tiles (through L2), two bits per batch
+        Acc S[kPerThread];
 #pragma unroll
-        for (int p = 0; p < 8; ++p) S[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int j = 0; j < a.l; ++j) {
-            const int64_t pb = (T ^ ((int64_t)1 << j)) * kTileF4 + t;
+        for (int p = 0; p < kPerThread; ++p) S[p].zero();
+        int j = 0;
+        for (; j + 1 < a.l; j += 2) {
+            const float4* q0 = a.b1 + (T ^ ((int64_t)1 << j)) * kTileF4 + t;
+            const float4* q1 = a.b1 + (T ^ ((int64_t)1 << (j + 1))) * kTileF4 + t;
+            float4 x0[kPerThread], x1[kPerThread];
 #pragma unroll
-            for (int p = 0; p < 8; ++p) S[p] = add4(S[p], __ldg(a.b1 + pb + p * kLowThreads));
+            for (int p = 0; p < kPerThread; ++p) {
+                x0[p] = __ldg(q0 + p * kLowThreads);
+                x1[p] = __ldg(q1 + p * kLowThreads);
+            }
+#pragma unroll
+            for (int p = 0; p < kPerThread; ++p) {
+                S[p].add(x0[p]);
+                S[p].add(x1[p]);
+            }
         }
-        // energy of this tile's 16 amplitudes per thread
+        if (j < a.l) {
+            const float4* q0 = a.b1 + (T ^ ((int64_t)1 << j)) * kTileF4 + t;
+#pragma unroll
+            for (int p = 0; p < kPerThread; ++p) S[p].add(__ldg(q0 + p * kLowThreads));
+        }
+        // energies of this thread's 8 amplitudes
         const int64_t* row = a.tiles + T * (kLowBits + 1);
         int64_t base = __ldg(row + kLowBits) + e_tau;
 #pragma unroll
@@ -202,66 +251,47 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
         const int64_t g0 = __ldg(row + 0) + phi[0];
         const int64_t g10 = __ldg(row + 10) + phi[1];
         const int64_t g11 = __ldg(row + 11) + phi[2];
-        const int64_t g12 = __ldg(row + 12) + phi[3];
 
         const bool ok = mbar_wait(&bar[b], (it >> 1) & 1, a.flags);
         if (__syncthreads_or(!ok)) {
-            // give up on this launch; let the copy already issued for the next tile land first
+            // give up on this launch; let the copies already issued for the next tile land first
             if (Tn < a.ntiles) mbar_wait(&bar[b ^ 1], ((it + 1) >> 1) & 1, a.flags);
             break;
         }
-        {
-            float4 v[8];
+        float4 v[kPerThread];
 #pragma unroll
-            for (int p = 0; p < 8; ++p) v[p] = cur[t + p * kLowThreads];
+        for (int p = 0; p < kPerThread; ++p) v[p] = sb1[t + p * kLowThreads];
 #pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                // bit 0 (inside the pair) and bits 10..12 (registers)
-                S[p].x += v[p].z;
-                S[p].y += v[p].w;
-                S[p].z += v[p].x;
-                S[p].w += v[p].y;
-                S[p] = add4(S[p], v[p ^ 1]);
-                S[p] = add4(S[p], v[p ^ 2]);
-                S[p] = add4(S[p], v[p ^ 4]);
-            }
-            // bits 1..9 (thread index) from shared memory
-#pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                const int pt = t ^ (1 << j);
-#pragma unroll
-                for (int p = 0; p < 8; ++p) S[p] = add4(S[p], cur[pt + p * kLowThreads]);
-            }
-#pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                const int64_t Gp = base + sel(p & 1, g10) + sel((p >> 1) & 1, g11) + sel((p >> 2) & 1, g12);
-                const int64_t e0 = Gp + g0 + erho[(p << 1) | 0];
-                const int64_t e1 = Gp - g0 + erho[(p << 1) | 1];
-                float d0h, d0l, d1h, d1l;
-                to_ff(e0, a.Q, d0h, d0l);
-                to_ff(e1, a.Q, d1h, d1l);
-                const int64_t idx = base_f4 + p * kLowThreads;
-                const float4 ps = a.psi[idx];
-                float4 o;
-                o.x = fmaf(d0h, v[p].x, d0l * v[p].x) + fmaf(a.ghi, S[p].x, a.glo * S[p].x);
-                o.y = fmaf(d0h, v[p].y, d0l * v[p].y) + fmaf(a.ghi, S[p].y, a.glo * S[p].y);
-                o.z = fmaf(d1h, v[p].z, d1l * v[p].z) + fmaf(a.ghi, S[p].z, a.glo * S[p].z);
-                o.w = fmaf(d1h, v[p].w, d1l * v[p].w) + fmaf(a.ghi, S[p].w, a.glo * S[p].w);
-                o.x = a.scale * o.x + (ck.x * ps.x - ck.y * ps.y);
-                o.y = a.scale * o.y + (ck.x * ps.y + ck.y * ps.x);
-                o.z = a.scale * o.z + (ck.x * ps.z - ck.y * ps.w);
-                o.w = a.scale * o.w + (ck.x * ps.w + ck.y * ps.z);
-                if (a.slot_coeff != 0.f) {
-                    const float4 q = a.slot[idx];
-                    o.x += a.slot_coeff * q.x;
-                    o.y += a.slot_coeff * q.y;
-                    o.z += a.slot_coeff * q.z;
-                    o.w += a.slot_coeff * q.w;
-                }
-                a.out[idx] = o;
-            }
+        for (int p = 0; p < kPerThread; ++p) {
+            // bit 0 (the other half of the float4), bits 10..11 (other registers)
+            S[p].a = __fadd2_rn(S[p].a, hi2(v[p]));
+            S[p].b = __fadd2_rn(S[p].b, lo2(v[p]));
+            S[p].add(v[p ^ 1]);
+            S[p].add(v[p ^ 2]);
         }
-        __syncthreads();  // everyone is done with `cur` before it is refilled
+        // bits 1..9: the partner thread's float4 in shared memory
+#pragma unroll
+        for (int jj = 0; jj < 9; ++jj) {
+            const int pt = t ^ (1 << jj);
+#pragma unroll
+            for (int p = 0; p < kPerThread; ++p) S[p].add(sb1[pt + p * kLowThreads]);
+        }
+#pragma unroll
+        for (int p = 0; p < kPerThread; ++p) {
+            const int64_t Gp = base + sel(p & 1, g10) + sel((p >> 1) & 1, g11);
+            const int64_t e0 = Gp + g0 + erho[(p << 1) | 0];
+            const int64_t e1 = Gp - g0 + erho[(p << 1) | 1];
+            float d0h, d0l, d1h, d1l;
+            to_ff(e0, a.Q, d0h, d0l);
+            to_ff(e1, a.Q, d1h, d1l);
+            const int li = t + p * kLowThreads;
+            const float4 ps = spsi[li];
+            const float4 q = need_slot ? sslot[li] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float2 o0 = combine(d0h, d0l, lo2(v[p]), gh, gl, S[p].a, sc, cs, lo2(q), ckr, cki_s, lo2(ps));
+            const float2 o1 = combine(d1h, d1l, hi2(v[p]), gh, gl, S[p].b, sc, cs, hi2(q), ckr, cki_s, hi2(ps));
+            a.out[T * kTileF4 + li] = make_float4(o0.x, o0.y, o1.x, o1.y);
+        }
+        __syncthreads();  // everyone is done with this stage before it is refilled
     }
 }
 
@@ -295,6 +325,8 @@ __global__ void __launch_bounds__(HighCfg<H>::kThreads, 1) k_high(const HighArgs
     const int u = t & 7;
     const int rlo = t >> 3;
     const int64_t row_stride_f4 = (int64_t)1 << (a.n - H - 1);  // 2^(n-H) amplitudes
+    const bool need_slot = a.sgn != 0.f;
+    const float2 g_hi = dup(a.scale_g), g_lo = dup(a.scale_glo), sg = dup(a.sgn);
     float4 nxt[Cfg::kP];
     int64_t T = blockIdx.x;
     if (T < a.ntiles) {
@@ -305,12 +337,12 @@ __global__ void __launch_bounds__(HighCfg<H>::kThreads, 1) k_high(const HighArgs
         }
     }
     for (; T < a.ntiles; T += gridDim.x) {
-        float4 v[Cfg::kP];
+        float4 w[Cfg::kP];
 #pragma unroll
         for (int p = 0; p < Cfg::kP; ++p) {
-            v[p] = nxt[p];
             const int rho = rlo | (p << Cfg::kRowBitsT);
-            tile[rho * 8 + u] = v[p];
+            tile[rho * 8 + u] = nxt[p];
+            if (need_slot) w[p] = a.slot[T * 8 + rho * row_stride_f4 + u];
         }
         const int64_t Tn = T + gridDim.x;
         if (Tn < a.ntiles) {
@@ -321,38 +353,29 @@ __global__ void __launch_bounds__(HighCfg<H>::kThreads, 1) k_high(const HighArgs
             }
         }
         __syncthreads();
-        float4 S[Cfg::kP];
 #pragma unroll
         for (int p = 0; p < Cfg::kP; ++p) {
-            S[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+            Acc S;
+            S.zero();
 #pragma unroll
-            for (int b = 1; b < Cfg::kP; b <<= 1) S[p] = add4(S[p], v[p ^ b]);
-        }
-#pragma unroll
-        for (int j = 0; j < Cfg::kRowBitsT; ++j) {
-#pragma unroll
-            for (int p = 0; p < Cfg::kP; ++p) {
-                const int rho = (rlo ^ (1 << j)) | (p << Cfg::kRowBitsT);
-                S[p] = add4(S[p], tile[rho * 8 + u]);
+            for (int b = 1; b < Cfg::kP; b <<= 1) {
+                const int rho = rlo | ((p ^ b) << Cfg::kRowBitsT);
+                S.add(tile[rho * 8 + u]);
             }
-        }
 #pragma unroll
-        for (int p = 0; p < Cfg::kP; ++p) {
+            for (int j = 0; j < Cfg::kRowBitsT; ++j) {
+                const int rho = (rlo ^ (1 << j)) | (p << Cfg::kRowBitsT);
+                S.add(tile[rho * 8 + u]);
+            }
             const int rho = rlo | (p << Cfg::kRowBitsT);
             const int64_t idx = T * 8 + rho * row_stride_f4 + u;
-            float4 q;
-            q.x = fmaf(a.scale_g, S[p].x, a.scale_glo * S[p].x);
-            q.y = fmaf(a.scale_g, S[p].y, a.scale_glo * S[p].y);
-            q.z = fmaf(a.scale_g, S[p].z, a.scale_glo * S[p].z);
-            q.w = fmaf(a.scale_g, S[p].w, a.scale_glo * S[p].w);
-            if (a.sgn != 0.f) {
-                const float4 w = a.slot[idx];
-                q.x += a.sgn * w.x;
-                q.y += a.sgn * w.y;
-                q.z += a.sgn * w.z;
-                q.w += a.sgn * w.w;
+            float2 q0 = __ffma2_rn(g_hi, S.a, __fmul2_rn(g_lo, S.a));
+            float2 q1 = __ffma2_rn(g_hi, S.b, __fmul2_rn(g_lo, S.b));
+            if (need_slot) {
+                q0 = __ffma2_rn(sg, lo2(w[p]), q0);
+                q1 = __ffma2_rn(sg, hi2(w[p]), q1);
             }
-            a.slot[idx] = q;
+            a.slot[idx] = make_float4(q0.x, q0.y, q1.x, q1.y);
         }
         __syncthreads();  // tile reused by the next iteration
     }
@@ -400,12 +423,12 @@ cudaError_t launch_high(int H, const HighArgs& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+// Two passes cover at most 12 + 10 + 9 = 31 bits; larger n runs the plain kernel.
+constexpr int kFusedMaxQubits = kLowBits + kMaxL2Bits + 9;
+
 }  // namespace
 
 size_t fused_scratch_bytes(int, int) { return 0; }
-
-// Two passes cover at most 13 + 9 + 9 = 31 bits; larger n runs the plain kernel.
-constexpr int kFusedMaxQubits = kLowBits + kMaxL2Bits + 9;
 
 bool fused_supported(int n, int prec) { return prec == 0 && n >= kLowBits && n <= kFusedMaxQubits; }
 
@@ -422,14 +445,14 @@ static void split_table_init() {
 }
 
 bool fused_split_valid(int n, int l, int h) {
-    return n >= kLowBits && n <= kMaxQubits && l >= 0 && l <= kMaxL2Bits && (h == 0 || (h >= 3 && h <= 9)) &&
-           kLowBits + l + h == n;
+    return n >= kLowBits && n <= kFusedMaxQubits && l >= 0 && l <= kMaxL2Bits &&
+           (h == 0 || (h >= 3 && h <= 9)) && kLowBits + l + h == n;
 }
 
 bool fused_set_split(int n, int l, int h) {
     std::lock_guard<std::mutex> lk(g_mu);
     split_table_init();
-    if (n < kLowBits || n > kMaxQubits) return false;
+    if (n < kLowBits || n > kFusedMaxQubits) return false;
     if (l < 0) {
         g_split_l[n] = g_split_h[n] = -1;
         return true;
@@ -440,7 +463,9 @@ bool fused_set_split(int n, int l, int h) {
     return true;
 }
 
-// Split of the n bits: low pass takes 13 + l, the high pass the top h.
+// Split of the n bits: the low pass takes 12 + l, the high pass the top h.
+// Default: one pass while the L2 partner bits stay few (n <= 21); beyond that
+// the smallest high pass that keeps l <= 8, and h = 9 once l must grow past 8.
 FusedPlan fused_plan(int n, int prec) {
     FusedPlan p;
     p.n = n;
@@ -456,28 +481,18 @@ FusedPlan fused_plan(int n, int prec) {
         }
     }
     const int rest = n - kLowBits;
-    if (rest <= 8) {
+    if (rest <= 9) {
         p.l = rest;
         p.h = 0;
-    } else if (rest <= 8 + 9) {
-        // as many bits as possible in the high pass (it costs one extra stream of
-        // b_{k+1} and of the slot), the remainder through L2
-        p.h = std::min(9, rest);
-        p.l = rest - p.h;
-        if (p.h < 3) {
-            p.h = 3;
-            p.l = rest - 3;
-        }
     } else {
-        p.h = 9;
-        p.l = rest - 9;
+        p.h = std::min(9, std::max(3, rest - 8));
+        p.l = rest - p.h;
     }
     return p;
 }
 
 cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, int* flags, cudaStream_t st) {
-    if (plan.prec != 0 || plan.n != s.n || plan.l < 0 || plan.l > kMaxL2Bits || plan.h < 0 || plan.h > 9 ||
-        (plan.h > 0 && plan.h < 3) || plan.M + plan.l + plan.h != s.n || s.M != kLowBits)
+    if (plan.prec != 0 || plan.n != s.n || !fused_split_valid(s.n, plan.l, plan.h) || s.M != kLowBits)
         return cudaErrorInvalidValue;
     const float ghi = (float)s.g;
     const float glo = (float)(s.g - (double)ghi);
@@ -513,11 +528,10 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, i
     la.slot_coeff = slot_coeff;
     la.ghi = ghi;
     la.glo = glo;
-    const size_t smem = 2 * (size_t)kTileBytes + 64 + 16 * sizeof(int64_t);
-    cudaError_t e = cudaFuncSetAttribute(k_low, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_low, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLowSmem);
     if (e != cudaSuccess) return e;
-    int64_t grid = std::min<int64_t>(la.ntiles, num_sms());
-    k_low<<<(unsigned)grid, kLowThreads, smem, st>>>(la);
+    const int64_t grid = std::min<int64_t>(la.ntiles, num_sms());
+    k_low<<<(unsigned)grid, kLowThreads, kLowSmem, st>>>(la);
     return cudaGetLastError();
 }
 

@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(1024) k_small(int n, int K, const double2* __r
     C* sp = (C*)smem_raw;
     C* s1 = sp + N;
     C* s2 = s1 + N;
-    const int M = n;  // one tile when n <= kTileBits
+    const int M = n < kTileBits ? n : kTileBits;  // same split as the workspace tables
     R dhi[PER], dlo[PER];
     const double2 cK = coef[K];
     for (int q = 0; q < PER; ++q) {

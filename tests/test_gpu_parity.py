@@ -172,17 +172,19 @@ def test_poly_apply_matches_oracle_clenshaw(cuda_lib, oracle, prec):
 
 
 SPLITS = [
-    # n, l, h: low-pass L2 bits and high-pass bits (13 + l + h = n)
-    (13, 0, 0),
-    (16, 3, 0),
-    (16, 0, 3),
-    (18, 0, 5),
-    (18, 2, 3),
-    (19, 0, 6),
-    (20, 1, 6),
-    (21, 0, 8),
-    (22, 0, 9),
-    (22, 6, 3),
+    # n, l, h: low-pass L2 bits and high-pass bits (12 + l + h = n)
+    (12, 0, 0),
+    (13, 1, 0),
+    (16, 4, 0),
+    (16, 1, 3),
+    (17, 0, 5),
+    (18, 3, 3),
+    (19, 1, 6),
+    (20, 2, 6),
+    (21, 1, 8),
+    (21, 0, 9),
+    (22, 10, 0),
+    (22, 7, 3),
 ]
 
 
