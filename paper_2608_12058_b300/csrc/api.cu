@@ -5,6 +5,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -66,7 +67,8 @@ static int choose_scale(long double bound) {
 }
 
 // J/scale, h/scale, c/scale quantised at the largest safe Q.
-static FixedOp make_fixed(int n, const double* h, const double* J, double center, double scale) {
+static FixedOp make_fixed(int n, const double* h, const double* J, double center, double scale,
+                          int max_q = 62) {
     FixedOp F;
     long double bound = std::fabs((long double)center);
     for (int i = 0; i < n; ++i) {
@@ -74,7 +76,7 @@ static FixedOp make_fixed(int n, const double* h, const double* J, double center
         for (int j = i + 1; j < n; ++j) bound += std::fabs((long double)J[(size_t)i * n + j]);
     }
     bound /= (long double)scale;
-    F.Q = choose_scale(bound);
+    F.Q = std::min(choose_scale(bound), max_q);
     const long double mul = std::ldexp(1.0L, F.Q) / (long double)scale;
     F.jq.assign((size_t)n * n + n + 1, 0);
     for (int i = 0; i < n; ++i)
@@ -223,7 +225,7 @@ static cheb_status_t expmv_impl(int n, const double* h, const double* J, double 
     const double c = 0.5 * (emax + emin);
     double r = 0.5 * (emax - emin) + std::fabs(gamma) * n;
     if (!(r > 0)) r = 1.0;  // H is the constant c: any radius is exact
-    FixedOp F = make_fixed(n, h, J, c, r);
+    FixedOp F = make_fixed(n, h, J, c, r, prec == CHEB_FP32 ? kMaxQF32 : 62);
     if (F.Q < 24) return CHEB_ERR_UNSUPPORTED;
     st = upload_tables(C, F);
     if (st != CHEB_OK) return st;
@@ -350,7 +352,7 @@ cheb_status_t cheb_poly_apply(int n, const double* h, const double* J, double ga
     if (!finite_all(coeffs, 2 * (size_t)(K + 1))) return CHEB_ERR_INVALID_ARG;
     Ctx C{n, precision, make_layout(n, precision), (unsigned char*)workspace, (cudaStream_t)stream};
     CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), C.s));
-    FixedOp F = make_fixed(n, h, J, center, radius);
+    FixedOp F = make_fixed(n, h, J, center, radius, precision == CHEB_FP32 ? kMaxQF32 : 62);
     if (F.Q < 24) return CHEB_ERR_UNSUPPORTED;
     st = upload_tables(C, F);
     if (st != CHEB_OK) return st;

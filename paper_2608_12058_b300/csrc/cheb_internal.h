@@ -22,6 +22,9 @@ constexpr int kMaxK = 1 << 16;        // coefficient table length per time slice
 constexpr int kSmallMaxF32 = 13;      // whole-vector-in-SMEM kernel limits
 constexpr int kSmallMaxF64 = 12;
 constexpr int kRedBlocks = 1184;      // partial-sum slots for two-stage reductions (8 x 148)
+// Largest fixed-point scale for the FP32 kernels: with |Dt| <= 1 the high 32-bit
+// word of a 2^-56 fixed-point value fits a float mantissa exactly.
+constexpr int kMaxQF32 = 56;
 
 // Status word written by kernels (bit flags), read by the host after a sync.
 enum DeviceFlag : int {

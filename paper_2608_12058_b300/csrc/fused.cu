@@ -16,11 +16,11 @@
 //    diagonal from the fixed-point tables (float-float hi + lo, exact to ~2^-48)
 //    and writes out = scale*(Dt.*b1 + g*S_low) + slot_coeff*slot + c_k*psi.
 //
-// Thread layout of the low pass (512 threads, 8 amplitudes each): a thread's
-// float4 p holds amplitudes {2t + 1024p, 2t + 1024p + 1}: bit 0 lies inside the
-// float4, bits 1..9 are the thread index (partners read from shared memory;
+// Thread layout of the low pass (1024 threads, 4 amplitudes each): a thread's
+// float4 p holds amplitudes {2t + 2048p, 2t + 2048p + 1}: bit 0 lies inside the
+// float4, bits 1..10 are the thread index (partners read from shared memory;
 // 8 consecutive threads read 8 consecutive 16-byte words, free of bank
-// conflicts), bits 10..11 index the thread's 4 float4 registers.
+// conflicts), bit 11 selects one of the thread's 2 float4 registers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,14 +35,14 @@ namespace cheb {
 namespace {
 
 constexpr int kLowBits = kTileBits;                // 12
-constexpr int kLowThreads = 512;
+constexpr int kLowThreads = 1024;
 constexpr int kTile = 1 << kLowBits;               // amplitudes per low tile
 constexpr int kTileF4 = kTile / 2;                 // float4 per tile
 constexpr int kPerThread = kTileF4 / kLowThreads;  // float4 per thread (4)
 constexpr uint32_t kTileBytes = kTile * 8;         // 32 KB
 constexpr int kMaxL2Bits = 10;
 constexpr long long kWaitCycles = 4000000000LL;    // ~2 s at 2 GHz
-static_assert(kPerThread == 4, "layout assumes 4 float4 per thread");
+static_assert(kPerThread == 2, "layout assumes 2 float4 per thread");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -100,14 +100,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* f
 
 __device__ __forceinline__ int64_t sel(uint32_t bit, int64_t v) { return bit ? -v : v; }
 
-__device__ __forceinline__ void to_ff(int64_t e, int Q, float& hi, float& lo) {
-    const int sh = Q - 24;
-    const int64_t ih = e >> sh;
-    const int64_t il = e - (ih << sh);
-    hi = __ll2float_rn(ih) * 5.9604644775390625e-08f;  // 2^-24
-    lo = __ll2float_rn(il) * __int_as_float((127 - Q) << 23);
-}
-
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
@@ -150,147 +142,167 @@ struct LowArgs {
     float ck_re, ck_im, scale, slot_coeff, ghi, glo;
 };
 
-// Shared memory: 2 stages x {b1, psi, slot} tiles, then 2 mbarriers and erho[8].
-constexpr size_t kLowSmem = 2 * 3 * (size_t)kTileBytes + 64 + 8 * sizeof(int64_t);
+// Per-tile energy scalars shared by the CTA: W[x] = A(T) + sum_{i=1..5} s_i f_i(T)
+// for the 5 lane bits x, W[32 + y] = sum_{i=6..10} s_i f_i(T) for the 5 warp bits y,
+// then f_11 + f_0 and f_11 - f_0.
+constexpr int kWEntries = 66;
+
+// Shared memory: 2 stages x {b1, psi, slot} tiles, 2 x kWEntries energy scalars,
+// then 2 mbarriers.
+constexpr size_t kWOff = 6 * (size_t)kTileBytes;
+constexpr size_t kBarOff = kWOff + 2 * kWEntries * sizeof(int64_t);
+constexpr size_t kLowSmem = kBarOff + 64;
+
+__device__ __forceinline__ void tile_scalars(const int64_t* __restrict__ row, int t, int64_t* w) {
+    if (t < 32) {
+        int64_t e = __ldg(row + kLowBits);
+#pragma unroll
+        for (int i = 1; i <= 5; ++i) e += sel((t >> (i - 1)) & 1, __ldg(row + i));
+        w[t] = e;
+    } else if (t < 64) {
+        int64_t e = 0;
+#pragma unroll
+        for (int i = 6; i <= 10; ++i) e += sel(((t - 32) >> (i - 6)) & 1, __ldg(row + i));
+        w[t] = e;
+    } else if (t == 64) {
+        w[64] = __ldg(row + 11) + __ldg(row + 0);
+    } else if (t == 65) {
+        w[65] = __ldg(row + 11) - __ldg(row + 0);
+    }
+}
 
 __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bar = (uint64_t*)(smem + 6 * kTileBytes);
-    int64_t* erho = (int64_t*)(smem + 6 * kTileBytes + 64);
+    int64_t* wsc = (int64_t*)(smem + kWOff);
+    uint64_t* bar = (uint64_t*)(smem + kBarOff);
     const int t = threadIdx.x;
     const int n = a.n;
-    const int64_t* J = a.jq;
-    const int64_t* hq = a.jq + (size_t)n * n;
     const bool need_slot = a.slot_coeff != 0.f;
     const uint32_t stage_bytes = (need_slot ? 3u : 2u) * kTileBytes;
 
-    // Energy decomposition constants: bits 1..9 are the thread index, bits 0, 10,
-    // 11 vary inside the thread.
-    int64_t e_tau = 0;
-    for (int i = 1; i <= 9; ++i) {
-        int64_t hi = hq[i];
-        for (int j = i + 1; j <= 9; ++j) hi += sel((t >> (j - 1)) & 1, J[i * n + j]);
-        e_tau += sel((t >> (i - 1)) & 1, hi);
-    }
-    const int rbit[3] = {0, 10, 11};
-    int64_t phi[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int i = rbit[q];
-        int64_t v = hq[i];
-        for (int j = 1; j <= 9; ++j) v += sel((t >> (j - 1)) & 1, J[i * n + j]);
-        phi[q] = v;
-    }
-    if (t < 8) {
-        // t = (p << 1) | w over register bits {0: w, 10..11: p}
-        int64_t e = 0;
-        for (int q1 = 0; q1 < 3; ++q1)
-            for (int q2 = q1 + 1; q2 < 3; ++q2)
-                e += sel(((t >> q1) ^ (t >> q2)) & 1, J[rbit[q1] * n + rbit[q2]]);
-        erho[t] = e;
+    // Thread constants of the energy split: K[p][w] collects every term of E that
+    // involves only bits 0..11 of z (bits 1..10 = thread index, bit 0 = w, bit 11 = p).
+    int64_t K00, K01, K10, K11;
+    {
+        const int64_t* J = a.jq;
+        const int64_t* hq = a.jq + (size_t)n * n;
+        int64_t e_tau = 0, phi0 = hq[0], phi11 = hq[11];
+        for (int i = 1; i <= 10; ++i) {
+            const uint32_t bi = (t >> (i - 1)) & 1;
+            int64_t hi = hq[i];
+            for (int j = i + 1; j <= 10; ++j) hi += sel((t >> (j - 1)) & 1, J[i * n + j]);
+            e_tau += sel(bi, hi);
+            phi0 += sel(bi, J[0 * n + i]);
+            phi11 += sel(bi, J[11 * n + i]);
+        }
+        const int64_t j0b = J[0 * n + 11];
+        K00 = e_tau + phi0 + phi11 + j0b;
+        K01 = e_tau - phi0 + phi11 - j0b;
+        K10 = e_tau + phi0 - phi11 - j0b;
+        K11 = e_tau - phi0 - phi11 + j0b;
     }
     if (t == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
+    int64_t T = blockIdx.x;
+    if (T < a.ntiles) tile_scalars(a.tiles + T * (kLowBits + 1), t, wsc);
     __syncthreads();
 
-    auto issue = [&](int stage, int64_t T) {
+    auto issue = [&](int stage, int64_t Tt) {
         float4* dst = (float4*)(smem + (size_t)stage * 3 * kTileBytes);
         mbar_expect_tx(&bar[stage], stage_bytes);
-        tma_load_1d(dst, a.b1 + T * kTileF4, kTileBytes, &bar[stage]);
-        tma_load_1d(dst + kTileF4, a.psi + T * kTileF4, kTileBytes, &bar[stage]);
-        if (need_slot) tma_load_1d(dst + 2 * kTileF4, a.slot + T * kTileF4, kTileBytes, &bar[stage]);
+        tma_load_1d(dst, a.b1 + Tt * kTileF4, kTileBytes, &bar[stage]);
+        tma_load_1d(dst + kTileF4, a.psi + Tt * kTileF4, kTileBytes, &bar[stage]);
+        if (need_slot) tma_load_1d(dst + 2 * kTileF4, a.slot + Tt * kTileF4, kTileBytes, &bar[stage]);
     };
 
     const float2 ckr = dup(a.ck_re), cki_s = make_float2(-a.ck_im, a.ck_im);
     const float2 gh = dup(a.ghi), gl = dup(a.glo), sc = dup(a.scale), cs = dup(a.slot_coeff);
-    int64_t T = blockIdx.x;
+    const int scale_hi = (127 + 32 - a.Q) << 23, scale_lo = (127 - a.Q) << 23;
     if (t == 0 && T < a.ntiles) issue(0, T);
     for (int it = 0; T < a.ntiles; ++it, T += gridDim.x) {
         const int b = it & 1;
         const float4* sb1 = (const float4*)(smem + (size_t)b * 3 * kTileBytes);
         const float4* spsi = sb1 + kTileF4;
         const float4* sslot = sb1 + 2 * kTileF4;
+        const int64_t* w = wsc + b * kWEntries;
         const int64_t Tn = T + gridDim.x;
-        if (t == 0 && Tn < a.ntiles) {
-            fence_proxy_async();
-            issue(b ^ 1, Tn);
+        if (Tn < a.ntiles) {
+            if (t == 0) {
+                fence_proxy_async();
+                issue(b ^ 1, Tn);
+            }
+            tile_scalars(a.tiles + Tn * (kLowBits + 1), t, wsc + (b ^ 1) * kWEntries);
         }
-        // flips of bits 12 .. 12+l-1 from partner tiles (through L2), two bits per batch
-        Acc S[kPerThread];
-#pragma unroll
-        for (int p = 0; p < kPerThread; ++p) S[p].zero();
+        // flips of bits 12 .. 12+l-1 from the partner tiles through L2
+        float2 S0a = make_float2(0.f, 0.f), S0b = S0a, S1a = S0a, S1b = S0a;
         int j = 0;
         for (; j + 1 < a.l; j += 2) {
             const float4* q0 = a.b1 + (T ^ ((int64_t)1 << j)) * kTileF4 + t;
             const float4* q1 = a.b1 + (T ^ ((int64_t)1 << (j + 1))) * kTileF4 + t;
-            float4 x0[kPerThread], x1[kPerThread];
-#pragma unroll
-            for (int p = 0; p < kPerThread; ++p) {
-                x0[p] = __ldg(q0 + p * kLowThreads);
-                x1[p] = __ldg(q1 + p * kLowThreads);
-            }
-#pragma unroll
-            for (int p = 0; p < kPerThread; ++p) {
-                S[p].add(x0[p]);
-                S[p].add(x1[p]);
-            }
+            const float4 x00 = __ldg(q0), x01 = __ldg(q0 + kLowThreads);
+            const float4 x10 = __ldg(q1), x11 = __ldg(q1 + kLowThreads);
+            S0a = __fadd2_rn(S0a, __fadd2_rn(lo2(x00), lo2(x10)));
+            S0b = __fadd2_rn(S0b, __fadd2_rn(hi2(x00), hi2(x10)));
+            S1a = __fadd2_rn(S1a, __fadd2_rn(lo2(x01), lo2(x11)));
+            S1b = __fadd2_rn(S1b, __fadd2_rn(hi2(x01), hi2(x11)));
         }
         if (j < a.l) {
             const float4* q0 = a.b1 + (T ^ ((int64_t)1 << j)) * kTileF4 + t;
-#pragma unroll
-            for (int p = 0; p < kPerThread; ++p) S[p].add(__ldg(q0 + p * kLowThreads));
+            const float4 x00 = __ldg(q0), x01 = __ldg(q0 + kLowThreads);
+            S0a = __fadd2_rn(S0a, lo2(x00));
+            S0b = __fadd2_rn(S0b, hi2(x00));
+            S1a = __fadd2_rn(S1a, lo2(x01));
+            S1b = __fadd2_rn(S1b, hi2(x01));
         }
-        // energies of this thread's 8 amplitudes
-        const int64_t* row = a.tiles + T * (kLowBits + 1);
-        int64_t base = __ldg(row + kLowBits) + e_tau;
-#pragma unroll
-        for (int i = 1; i <= 9; ++i) base += sel((t >> (i - 1)) & 1, __ldg(row + i));
-        const int64_t g0 = __ldg(row + 0) + phi[0];
-        const int64_t g10 = __ldg(row + 10) + phi[1];
-        const int64_t g11 = __ldg(row + 11) + phi[2];
-
         const bool ok = mbar_wait(&bar[b], (it >> 1) & 1, a.flags);
         if (__syncthreads_or(!ok)) {
             // give up on this launch; let the copies already issued for the next tile land first
             if (Tn < a.ntiles) mbar_wait(&bar[b ^ 1], ((it + 1) >> 1) & 1, a.flags);
             break;
         }
-        float4 v[kPerThread];
+        const float4 v0 = sb1[t], v1 = sb1[t + kLowThreads];
+        // bit 0 (other half of the float4) and bit 11 (the other register)
+        S0a = __fadd2_rn(S0a, __fadd2_rn(hi2(v0), lo2(v1)));
+        S0b = __fadd2_rn(S0b, __fadd2_rn(lo2(v0), hi2(v1)));
+        S1a = __fadd2_rn(S1a, __fadd2_rn(hi2(v1), lo2(v0)));
+        S1b = __fadd2_rn(S1b, __fadd2_rn(lo2(v1), hi2(v0)));
+        // bits 1..10: the partner thread's float4s in shared memory, summed in pairs
 #pragma unroll
-        for (int p = 0; p < kPerThread; ++p) v[p] = sb1[t + p * kLowThreads];
-#pragma unroll
-        for (int p = 0; p < kPerThread; ++p) {
-            // bit 0 (the other half of the float4), bits 10..11 (other registers)
-            S[p].a = __fadd2_rn(S[p].a, hi2(v[p]));
-            S[p].b = __fadd2_rn(S[p].b, lo2(v[p]));
-            S[p].add(v[p ^ 1]);
-            S[p].add(v[p ^ 2]);
+        for (int jj = 0; jj < 10; jj += 2) {
+            const int pa = t ^ (1 << jj), pb = t ^ (2 << jj);
+            const float4 y0 = sb1[pa], y1 = sb1[pa + kLowThreads];
+            const float4 z0 = sb1[pb], z1 = sb1[pb + kLowThreads];
+            S0a = __fadd2_rn(S0a, __fadd2_rn(lo2(y0), lo2(z0)));
+            S0b = __fadd2_rn(S0b, __fadd2_rn(hi2(y0), hi2(z0)));
+            S1a = __fadd2_rn(S1a, __fadd2_rn(lo2(y1), lo2(z1)));
+            S1b = __fadd2_rn(S1b, __fadd2_rn(hi2(y1), hi2(z1)));
         }
-        // bits 1..9: the partner thread's float4 in shared memory
-#pragma unroll
-        for (int jj = 0; jj < 9; ++jj) {
-            const int pt = t ^ (1 << jj);
-#pragma unroll
-            for (int p = 0; p < kPerThread; ++p) S[p].add(sb1[pt + p * kLowThreads]);
-        }
-#pragma unroll
-        for (int p = 0; p < kPerThread; ++p) {
-            const int64_t Gp = base + sel(p & 1, g10) + sel((p >> 1) & 1, g11);
-            const int64_t e0 = Gp + g0 + erho[(p << 1) | 0];
-            const int64_t e1 = Gp - g0 + erho[(p << 1) | 1];
-            float d0h, d0l, d1h, d1l;
-            to_ff(e0, a.Q, d0h, d0l);
-            to_ff(e1, a.Q, d1h, d1l);
-            const int li = t + p * kLowThreads;
-            const float4 ps = spsi[li];
-            const float4 q = need_slot ? sslot[li] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float2 o0 = combine(d0h, d0l, lo2(v[p]), gh, gl, S[p].a, sc, cs, lo2(q), ckr, cki_s, lo2(ps));
-            const float2 o1 = combine(d1h, d1l, hi2(v[p]), gh, gl, S[p].b, sc, cs, hi2(q), ckr, cki_s, hi2(ps));
-            a.out[T * kTileF4 + li] = make_float4(o0.x, o0.y, o1.x, o1.y);
-        }
+        // energies: e(p, w) = W[t & 31] + W[32 + (t >> 5)] +- (f11 +- f0) + K[p][w]
+        const int64_t base = w[t & 31] + w[32 + (t >> 5)];
+        const int64_t up = w[64], um = w[65];
+        const int64_t e00 = base + up + K00, e01 = base + um + K01;
+        const int64_t e10 = base - um + K10, e11 = base - up + K11;
+        const float4 ps0 = spsi[t], ps1 = spsi[t + kLowThreads];
+        const float4 q0 = need_slot ? sslot[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 q1 = need_slot ? sslot[t + kLowThreads] : make_float4(0.f, 0.f, 0.f, 0.f);
+        auto dd = [&](int64_t e, float& hi, float& lo) {
+            hi = __int2float_rn((int)(e >> 32)) * __int_as_float(scale_hi);
+            lo = __uint2float_rn((unsigned)(e & 0xffffffffll)) * __int_as_float(scale_lo);
+        };
+        float dh, dl;
+        dd(e00, dh, dl);
+        const float2 o00 = combine(dh, dl, lo2(v0), gh, gl, S0a, sc, cs, lo2(q0), ckr, cki_s, lo2(ps0));
+        dd(e01, dh, dl);
+        const float2 o01 = combine(dh, dl, hi2(v0), gh, gl, S0b, sc, cs, hi2(q0), ckr, cki_s, hi2(ps0));
+        dd(e10, dh, dl);
+        const float2 o10 = combine(dh, dl, lo2(v1), gh, gl, S1a, sc, cs, lo2(q1), ckr, cki_s, lo2(ps1));
+        dd(e11, dh, dl);
+        const float2 o11 = combine(dh, dl, hi2(v1), gh, gl, S1b, sc, cs, hi2(q1), ckr, cki_s, hi2(ps1));
+        a.out[T * kTileF4 + t] = make_float4(o00.x, o00.y, o01.x, o01.y);
+        a.out[T * kTileF4 + t + kLowThreads] = make_float4(o10.x, o10.y, o11.x, o11.y);
         __syncthreads();  // everyone is done with this stage before it is refilled
     }
 }
@@ -298,11 +310,11 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
 // ---------------------------------------------------------------------------
 // High pass over the top H bits. Rows of 16 amplitudes (8 float4); row index
 // rho in [0, 2^H) selects the top bits. Thread t: u = t & 7 (float4 within the
-// row), rho low bits = t >> 3 (up to 6 bits), rho high bits = register index p.
+// row), rho low bits = t >> 3 (up to 7 bits), rho high bits = register index p.
 template <int H>
 struct HighCfg {
-    static constexpr int kRowBitsT = H < 6 ? H : 6;          // row bits in the thread index
-    static constexpr int kThreads = 8 << kRowBitsT;          // 64 .. 512
+    static constexpr int kRowBitsT = H < 7 ? H : 7;          // row bits in the thread index
+    static constexpr int kThreads = 8 << kRowBitsT;          // 64 .. 1024
     static constexpr int kP = 1 << (H - kRowBitsT);          // float4 registers per thread
     static constexpr int kRows = 1 << H;
 };

@@ -179,13 +179,13 @@ __device__ __forceinline__ int64_t energy_fixed(int M, const int64_t* __restrict
     return e;
 }
 
-// int64 at scale 2^-Q -> float-float (hi exact, lo carries the next 24 bits).
+// int64 at scale 2^-Q (Q <= 56, |value| <= 1) -> float-float: the high 32-bit word
+// is exact in a float, the low word carries the next 24 bits.
 __device__ __forceinline__ void fixed_to_ff(int64_t e, int Q, float& hi, float& lo) {
-    const int sh = Q - 24;
-    const int64_t ih = e >> sh;
-    const int64_t il = e - (ih << sh);
-    hi = __ll2float_rn(ih) * 5.9604644775390625e-08f;  // 2^-24
-    lo = __ll2float_rn(il) * __int_as_float((127 - Q) << 23);
+    const int eh = (int)(e >> 32);
+    const unsigned el = (unsigned)(e & 0xffffffffll);
+    hi = __int2float_rn(eh) * __int_as_float((127 + 32 - Q) << 23);
+    lo = __uint2float_rn(el) * __int_as_float((127 - Q) << 23);
 }
 
 // Plain one-pass step: every flip partner read straight from global memory.
