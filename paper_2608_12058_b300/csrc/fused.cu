@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <mutex>
 
 #include "cheb_internal.h"
@@ -41,6 +42,7 @@ constexpr int kTileF4 = kTile / 2;                 // float4 per tile
 constexpr int kPerThread = kTileF4 / kLowThreads;  // float4 per thread (4)
 constexpr uint32_t kTileBytes = kTile * 8;         // 32 KB
 constexpr int kMaxL2Bits = 10;
+constexpr int kPrefetchDefault = 3;                // tiles per CTA prefetched into L2 ahead
 constexpr long long kWaitCycles = 4000000000LL;    // ~2 s at 2 GHz
 static_assert(kPerThread == 2, "layout assumes 2 float4 per thread");
 
@@ -71,6 +73,15 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Fire-and-forget bulk prefetch of global memory into L2 (no shared memory used).
+__device__ __forceinline__ void l2_prefetch_bulk(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void l2_prefetch_line(const void* src) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(src));
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -138,6 +149,7 @@ struct LowArgs {
     int n;
     int l;
     int Q;
+    int prefetch;          // tiles per CTA prefetched into L2 ahead of use
     int64_t ntiles;
     float ck_re, ck_im, scale, slot_coeff, ghi, glo;
 };
@@ -229,6 +241,15 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
         const float4* sslot = sb1 + 2 * kTileF4;
         const int64_t* w = wsc + b * kWEntries;
         const int64_t Tn = T + gridDim.x;
+        // Tiles several iterations ahead go to L2 now, so that the stage loads issued
+        // one iteration ahead find them there: DRAM stays busy with far more bytes in
+        // flight than the two shared-memory stages could hold.
+        const int64_t Tp = T + (int64_t)a.prefetch * gridDim.x;
+        if (t == 32 && Tp < a.ntiles) {
+            l2_prefetch_bulk(a.b1 + Tp * kTileF4, kTileBytes);
+            l2_prefetch_bulk(a.psi + Tp * kTileF4, kTileBytes);
+            if (need_slot) l2_prefetch_bulk(a.slot + Tp * kTileF4, kTileBytes);
+        }
         if (Tn < a.ntiles) {
             if (t == 0) {
                 fence_proxy_async();
@@ -323,6 +344,7 @@ struct HighArgs {
     const float4* b1;
     float4* slot;       // in: b_{k+2} (if sgn != 0); out: q
     int n;
+    int prefetch;       // tiles per CTA prefetched into L2 ahead of use
     int64_t ntiles;     // 2^(n - H - 4)
     float scale_g;      // scale * (gamma / r), float-float hi part
     float scale_glo;    // lo part
@@ -362,6 +384,16 @@ __global__ void __launch_bounds__(HighCfg<H>::kThreads, 1) k_high(const HighArgs
             for (int p = 0; p < Cfg::kP; ++p) {
                 const int rho = rlo | (p << Cfg::kRowBitsT);
                 nxt[p] = __ldg(a.b1 + Tn * 8 + rho * row_stride_f4 + u);
+            }
+        }
+        // rows of tiles further ahead go to L2 (one 128-byte line per row)
+        const int64_t Tp = T + (int64_t)a.prefetch * gridDim.x;
+        if (u == 0 && Tp < a.ntiles) {
+#pragma unroll
+            for (int p = 0; p < Cfg::kP; ++p) {
+                const int rho = rlo | (p << Cfg::kRowBitsT);
+                l2_prefetch_line(a.b1 + Tp * 8 + rho * row_stride_f4);
+                if (need_slot) l2_prefetch_line(a.slot + Tp * 8 + rho * row_stride_f4);
             }
         }
         __syncthreads();
@@ -503,6 +535,20 @@ FusedPlan fused_plan(int n, int prec) {
     return p;
 }
 
+// L2 prefetch distance in tiles per CTA: CHEB_L2_PREFETCH_TILES (0..16), default 3.
+static int prefetch_tiles() {
+    static int v = -1;
+    if (v < 0) {
+        int d = kPrefetchDefault;
+        if (const char* e = std::getenv("CHEB_L2_PREFETCH_TILES")) {
+            const int x = std::atoi(e);
+            if (x >= 0 && x <= 16) d = x;
+        }
+        v = d;
+    }
+    return v;
+}
+
 cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, int* flags, cudaStream_t st) {
     if (plan.prec != 0 || plan.n != s.n || !fused_split_valid(s.n, plan.l, plan.h) || s.M != kLowBits)
         return cudaErrorInvalidValue;
@@ -518,6 +564,7 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, i
         ha.scale_g = (float)s.scale * ghi;
         ha.scale_glo = (float)s.scale * glo;
         ha.sgn = (float)s.sgn;
+        ha.prefetch = prefetch_tiles();
         cudaError_t e = launch_high(plan.h, ha, st);
         if (e != cudaSuccess) return e;
         slot_coeff = 1.0f;  // the slot now holds q
@@ -540,6 +587,7 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, i
     la.slot_coeff = slot_coeff;
     la.ghi = ghi;
     la.glo = glo;
+    la.prefetch = prefetch_tiles();
     cudaError_t e = cudaFuncSetAttribute(k_low, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLowSmem);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(la.ntiles, num_sms());
