@@ -1,0 +1,353 @@
+"""Benchmark: exp(-itH) psi on the n=30 SK workload, amplitude-updates per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step is one full exp(-itH) psi through the library: spectral bounds on the
+device, host coefficients, K Clenshaw steps (fused FP32 kernels), FP64 norm and
+energy. Steps are applied back to back to the evolving state (the state, 8 GB,
+and the 16 GB of Clenshaw vectors are far larger than L2, so no flush is needed).
+Prints one JSON line on rank 0. For N > 1 (torchrun) every rank runs its own
+replica of the workload (the path does not shard: see the design doc) and the value is
+the sum of the ranks' work divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "amplitude-updates/s at n=30, HBM GB/s vs peak; FP32 vs FP64 at stated L2 error"
+UNIT = "amplitude-updates/s"
+TOL32 = 2.0 ** -23
+# Bounded CPU sample: the same SK family (h ~ U(-1,1), gamma = 1) at n = 20, t = 12.
+SAMPLE = dict(n=20, gamma=1.0, t=12.0, seed=0)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, max clock, throttle reasons) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_sample_run():
+    """The oracle, as it stands, on the bounded sample; returns (amp-updates/s, seconds, info)."""
+    from oracle import oracle as O
+    from paper_2608_12058_b300 import inputs as I
+
+    c = I.config_family(SAMPLE["n"], SAMPLE["gamma"], SAMPLE["t"], SAMPLE["seed"], "uniform")
+    psi = I.uniform_state(SAMPLE["n"])
+    t0 = time.perf_counter()
+    _, info = O.expmv(c.h, c.J, c.gamma, c.t, psi, TOL32)
+    dt = time.perf_counter() - t0
+    work = (1 << SAMPLE["n"]) * info["K"]
+    return work / dt, dt, info
+
+
+def cpu_baseline_dict(value, dt, info):
+    return {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"full oracle exp(-itH)psi on the n={SAMPLE['n']} member of the n=30 SK family "
+                       f"(h~U(-1,1), gamma={SAMPLE['gamma']}, t={SAMPLE['t']}, tol 2^-23, K={info['K']}), "
+                       f"FP64 C++ with OpenMP over elements, {dt:.1f} s")}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    v, dt, info = cpu_sample_run()
+    steps = max(1, args.steps)
+    vals = [v]
+    for _ in range(steps - 1):
+        vals.append(cpu_sample_run()[0])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": 0, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sk_n{SAMPLE['n']}_sample_of_n30_family", "n": SAMPLE["n"], "tol": TOL32,
+                       "method": "chebyshev"},
+            "cpu_baseline": cpu_baseline_dict(value, dt, info),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def traffic_from_profile():
+    """DRAM bytes per amplitude of the low pass from the committed ncu summary, if it
+    was taken on the kernel source that is built now; else None."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "k_low_traffic.json")
+    src = os.path.join(ROOT, "paper_2608_12058_b300", "csrc", "fused.cu")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if d.get("fused_cu_sha256_16") != h:
+            return None
+        return float(d["dram_bytes_per_amplitude"])
+    except Exception:
+        return None
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2608_12058_b300 import api
+    from paper_2608_12058_b300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    cfg = I.config_n30()
+    n = cfg.n
+    N = 1 << n
+    # accuracy at the n=24 configuration: FP32 fused vs FP64 recurrence (same tol rule)
+    acc = {}
+    if rank == 0 and not args.skip_accuracy:
+        c24 = I.config_n24()
+        x32 = torch.full((1 << 24,), 2 ** -12, dtype=torch.complex64, device=dev)
+        x64 = torch.full((1 << 24,), 2 ** -12, dtype=torch.complex128, device=dev)
+        i32 = api.expmv(c24.h, c24.J, c24.gamma, c24.t, x32, tol=TOL32)
+        i64 = api.expmv(c24.h, c24.J, c24.gamma, c24.t, x64, tol=1e-12)
+        d = torch.linalg.vector_norm(x32.to(torch.complex128) - x64).item() / torch.linalg.vector_norm(x64).item()
+        acc = {"workload": c24.name, "fp32_vs_fp64_rel_l2": d, "K_fp32": i32["K"], "K_fp64": i64["K"],
+               "bar": 1e-5}
+        del x32, x64
+        api.release_workspaces()
+        torch.cuda.empty_cache()
+
+    psi = torch.full((N,), 2 ** (-n / 2), dtype=torch.complex64, device=dev)
+    info = None
+    for _ in range(args.warmup):
+        info = api.expmv(cfg.h, cfg.J, cfg.gamma, cfg.t, psi, tol=TOL32)
+    if info is None:
+        info = api.expmv(cfg.h, cfg.J, cfg.gamma, cfg.t, psi, tol=TOL32)
+    K = info["K"] * info["time_splits"]
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    api.profile_reset()
+    api.profile_enable(True)
+    launches0 = api.launch_count()
+    barrier()
+    if sampler:
+        sampler.start()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        api.expmv(cfg.h, cfg.J, cfg.gamma, cfg.t, psi, tol=TOL32, info=False)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    launches = api.launch_count() - launches0
+    api.profile_enable(False)
+    ms = e0.elapsed_time(e1)
+    nlow, low_ms = api.profile_read("low")
+    nhigh, high_ms = api.profile_read("high")
+    api.profile_reset()
+    fin = api.energy(cfg.h, cfg.J, psi)
+
+    t_local = ms / 1e3
+    work_local = float(N) * K * args.steps
+    if pg is not None:
+        t = torch.tensor([t_local], device=dev)
+        w = torch.tensor([work_local], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        pg.all_reduce(w)
+        t_all, work_all = t.item(), w.item()
+    else:
+        t_all, work_all = t_local, work_local
+    value = work_all / t_all
+
+    # end to end: host (pinned) state in, host state out, every step
+    e2e = None
+    if not args.skip_e2e:
+        host = torch.empty((N,), dtype=torch.complex64, pin_memory=True)
+        host.copy_(psi.cpu())
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            psi.copy_(host, non_blocking=True)
+            api.expmv(cfg.h, cfg.J, cfg.gamma, cfg.t, psi, tol=TOL32, info=False)
+            host.copy_(psi, non_blocking=True)
+        f1.record(stream)
+        barrier()
+        te = f0.elapsed_time(f1) / 1e3
+        if pg is not None:
+            t = torch.tensor([te], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            te = t.item()
+        e2e = {"value": work_all / te, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
+        del host
+
+    # the plain one-pass FP32 and FP64 kernels on a short run of the same operator
+    # (FP64 is FP64-ALU bound on this part: a full expmv would take minutes)
+    extra = {}
+    if rank == 0 and not args.skip_fp64:
+        rng = np.random.default_rng(0)
+        ksteps = 4
+        coef = (rng.standard_normal(ksteps + 1) + 1j * rng.standard_normal(ksteps + 1)) / (4 * ksteps)
+        r = info["radius"]
+        for name, dt, path in [("fp32_plain", torch.complex64, "plain"), ("fp64_plain", torch.complex128, "plain")]:
+            x = torch.full((N,), 2 ** (-n / 2), dtype=dt, device=dev) if dt == torch.complex128 else psi
+            api.poly_apply(cfg.h, cfg.J, cfg.gamma, info["center"], r, coef[:2], x, path=path)
+            torch.cuda.synchronize()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            api.poly_apply(cfg.h, cfg.J, cfg.gamma, info["center"], r, coef, x, path=path)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            extra[name] = {"amp_updates_per_s": N * ksteps / (g0.elapsed_time(g1) / 1e3),
+                           "sample": f"{ksteps} Clenshaw steps at n=30"}
+            if dt == torch.complex128:
+                del x
+        api.release_workspaces()
+        torch.cuda.empty_cache()
+        extra["fused_over_fp64_plain"] = value / world / extra["fp64_plain"]["amp_updates_per_s"]
+
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+
+    peak, peak_kind = _peaks()
+    low_avg = low_ms / max(nlow, 1) / 1e3
+    alg_low = 32.0 * N  # bytes: read b1, psi, slot, write out (complex64)
+    achieved = alg_low / low_avg / 1e9 if nlow else None
+    tpa = traffic_from_profile()
+    roof = {"bound": "hbm", "kernel": "k_low (fused low pass)", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": (tpa * N) if tpa is not None else None, "peak_kind": f"{peak_kind} hbm_gbs",
+            "algorithmic_bytes_per_launch": alg_low, "launches_timed": nlow,
+            "avg_launch_ms": low_avg * 1e3,
+            "step_alg_GBps": 32.0 * N * K * args.steps / t_local / 1e9,
+            "high_pass_avg_launch_ms": (high_ms / nhigh) if nhigh else None,
+            "share_low": low_ms / ms, "share_high": high_ms / ms}
+    cpu_v, cpu_dt, cpu_info = cpu_sample_run()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg.name, "n": n, "gamma": cfg.gamma, "t": cfg.t, "K": info["K"],
+                   "time_splits": info["time_splits"], "radius": info["radius"], "tol": TOL32,
+                   "method": "chebyshev", "precision": "fp32 (complex64 vectors, float-float operator)",
+                   "fused_split": list(api.get_fused_split(n)), "l2": "inputs larger than L2 (24 GB working set)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "cpu_baseline": cpu_baseline_dict(cpu_v, cpu_dt, cpu_info),
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "accuracy": acc,
+        "plain_paths": extra,
+        "final_norm2": fin[1], "final_energy": fin[0],
+    }
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-accuracy", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -168,6 +168,28 @@ cheb_status_t cheb_energy(int n, const double* h, const double* J, const void* p
                           cheb_precision_t precision, void* workspace, size_t workspace_bytes,
                           void* stream, double* energy, double* norm2);
 
+/*
+ * Instrumentation (no counterpart in the paper; used to attribute time).
+ * cheb_launch_count: number of kernels this library has launched in this process
+ *   (all devices, monotone).
+ * cheb_profile_enable(1): from now on, bracket every Clenshaw step kernel with a
+ *   pair of CUDA events on its stream (a few microseconds of overhead per step).
+ * cheb_profile_read(kind, count, total_ms): synchronises the recorded events and
+ *   returns how many launches of that kind were timed and their summed device
+ *   time. cheb_profile_reset drops the records.
+ * Kinds: 3 plain one-pass step, 6 fused low pass, 7 fused high pass.
+ */
+typedef enum {
+    CHEB_KERNEL_STEP_PLAIN = 3,
+    CHEB_KERNEL_FUSED_LOW = 6,
+    CHEB_KERNEL_FUSED_HIGH = 7
+} cheb_kernel_kind_t;
+
+long long cheb_launch_count(void);
+cheb_status_t cheb_profile_enable(int on);
+cheb_status_t cheb_profile_reset(void);
+cheb_status_t cheb_profile_read(int kind, long long* count, double* total_ms);
+
 #ifdef __cplusplus
 }
 #endif

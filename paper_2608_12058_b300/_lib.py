@@ -54,6 +54,10 @@ SIGNATURES = {
     "cheb_energy": (c_int, [c_int, _dp, _dp, c_void_p, c_int, c_void_p, c_size_t, c_void_p, _dp, _dp]),
     "cheb_set_fused_split": (c_int, [c_int, c_int, c_int]),
     "cheb_get_fused_split": (c_int, [c_int, _ip, _ip]),
+    "cheb_launch_count": (ctypes.c_longlong, []),
+    "cheb_profile_enable": (c_int, [c_int]),
+    "cheb_profile_reset": (c_int, []),
+    "cheb_profile_read": (c_int, [c_int, ctypes.POINTER(ctypes.c_longlong), _dp]),
 }
 
 STATUS = {0: "CHEB_OK", 1: "CHEB_ERR_INVALID_ARG", 2: "CHEB_ERR_WORKSPACE", 3: "CHEB_ERR_CUDA",

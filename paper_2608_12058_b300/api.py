@@ -155,6 +155,30 @@ def get_fused_split(n: int):
     return l.value, h.value
 
 
+KERNEL_KIND = {"plain": 3, "low": 6, "high": 7}
+
+
+def launch_count() -> int:
+    """Kernels launched by the CUDA library so far in this process."""
+    return int(_lib.lib().cheb_launch_count())
+
+
+def profile_enable(on: bool = True):
+    _lib.check(_lib.lib().cheb_profile_enable(1 if on else 0), "cheb_profile_enable")
+
+
+def profile_reset():
+    _lib.check(_lib.lib().cheb_profile_reset(), "cheb_profile_reset")
+
+
+def profile_read(kind: str):
+    """(launches timed, total device ms) for 'plain', 'low' or 'high' step kernels."""
+    c, ms = ctypes.c_longlong(), ctypes.c_double()
+    _lib.check(_lib.lib().cheb_profile_read(KERNEL_KIND[kind], ctypes.byref(c), ctypes.byref(ms)),
+               "cheb_profile_read")
+    return int(c.value), float(ms.value)
+
+
 def energy(h, J, psi):
     """(<psi|H_P|psi>, ||psi||^2) in FP64 on the GPU."""
     h, J = _f64(h), _f64(J)

@@ -450,7 +450,10 @@ cudaError_t launch_high_t(const HighArgs& a, cudaStream_t s) {
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)num_sms() * per_sm);
     if (grid < 1) grid = 1;
+    note_launch(kKindHigh);
+    const int pi = prof_begin(kKindHigh, s);
     k_high<H><<<(unsigned)grid, Cfg::kThreads, smem, s>>>(a);
+    prof_end(pi, s);
     return cudaGetLastError();
 }
 
@@ -591,7 +594,10 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, i
     cudaError_t e = cudaFuncSetAttribute(k_low, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLowSmem);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(la.ntiles, num_sms());
+    note_launch(kKindLow);
+    const int pi = prof_begin(kKindLow, st);
     k_low<<<(unsigned)grid, kLowThreads, kLowSmem, st>>>(la);
+    prof_end(pi, st);
     return cudaGetLastError();
 }
 

@@ -62,6 +62,7 @@ void launch_tables(int n, int M, const int64_t* jq, int64_t* tiles, int64_t* elo
     int64_t total = ((int64_t)1 << (n - M)) + ((int64_t)1 << M);
     int64_t blocks = (total + 255) / 256;
     if (blocks > 4 * 148 * 8) blocks = 4 * 148 * 8;
+    note_launch(kKindTables);
     k_tables<<<(unsigned)blocks, 256, 0, s>>>(n, M, jq, tiles, elow);
 }
 
@@ -130,7 +131,9 @@ void launch_minmax(int n, int M, const int64_t* tiles, const int64_t* elow, int6
                    int64_t* out2, cudaStream_t s) {
     int64_t ntiles = (int64_t)1 << (n - M);
     int nb = (int)(ntiles < kRedBlocks ? ntiles : kRedBlocks);
+    note_launch(kKindMinmax);
     k_minmax<<<nb, 256, 0, s>>>(n, M, tiles, elow, part);
+    note_launch(kKindMinmax);
     k_minmax_final<<<1, 256, 0, s>>>(part, nb, out2);
 }
 
@@ -161,6 +164,7 @@ static unsigned grid_for(int64_t N, int threads, int64_t cap = (int64_t)148 * 64
 }
 
 void launch_scale(int prec, int64_t N, const void* src, void* dst, double cr, double ci, cudaStream_t s) {
+    note_launch(kKindScale);
     if (prec == 0)
         k_scale<float><<<grid_for(N, 256), 256, 0, s>>>(N, (const float2*)src, (float2*)dst, (float)cr, (float)ci);
     else
@@ -241,9 +245,15 @@ void launch_step_plain(int prec, const StepArgs& a, cudaStream_t s) {
     if (prec == 0) {
         float ghi = (float)a.g;
         float glo = (float)(a.g - (double)ghi);
+        note_launch(kKindStepPlain);
+        const int pi = prof_begin(kKindStepPlain, s);
         k_step_plain<float><<<grid, 256, 0, s>>>(a, ghi, glo);
+        prof_end(pi, s);
     } else {
+        note_launch(kKindStepPlain);
+        const int pi = prof_begin(kKindStepPlain, s);
         k_step_plain<double><<<grid, 256, 0, s>>>(a, a.g, 0.0);
+        prof_end(pi, s);
     }
 }
 
@@ -349,6 +359,7 @@ cudaError_t launch_small(int prec, int n, int K, const double* coef_dev, int Q, 
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
+        note_launch(kKindSmall);
         kern<<<1, threads, smem, s>>>(n, K, (const double2*)coef_dev, Q, tiles, elow, g, (float2*)psi);
     } else {
         auto kern = k_small<double, 4>;
@@ -356,6 +367,7 @@ cudaError_t launch_small(int prec, int n, int K, const double* coef_dev, int Q, 
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
+        note_launch(kKindSmall);
         kern<<<1, threads, smem, s>>>(n, K, (const double2*)coef_dev, Q, tiles, elow, g, (double2*)psi);
     }
     return cudaGetLastError();
@@ -424,10 +436,12 @@ void launch_norm_energy(int prec, int n, int M, int Q, const int64_t* tiles, con
                         double c, double r, const void* psi, double* part, double* out2, cudaStream_t s) {
     const int64_t N = (int64_t)1 << n;
     const int nb = (int)grid_for(N, 256, kRedBlocks);
+    note_launch(kKindReduce);
     if (prec == 0)
         k_norm_energy<float><<<nb, 256, 0, s>>>(n, M, Q, tiles, elow, c, r, (const float2*)psi, part);
     else
         k_norm_energy<double><<<nb, 256, 0, s>>>(n, M, Q, tiles, elow, c, r, (const double2*)psi, part);
+    note_launch(kKindReduce);
     k_sum2_final<<<1, 256, 0, s>>>(part, nb, out2);
 }
 

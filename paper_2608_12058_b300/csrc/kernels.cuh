@@ -6,6 +6,22 @@
 
 namespace cheb {
 
+// Kernel kinds for launch counting and event timing (cheb_kernel_kind_t).
+enum KernelKind : int {
+    kKindTables = 0,
+    kKindMinmax = 1,
+    kKindScale = 2,
+    kKindStepPlain = 3,
+    kKindSmall = 4,
+    kKindReduce = 5,
+    kKindLow = 6,
+    kKindHigh = 7,
+};
+void note_launch(int kind);
+// Event-bracketed timing of one launch when profiling is on (prof_begin returns -1 otherwise).
+int prof_begin(int kind, cudaStream_t s);
+void prof_end(int idx, cudaStream_t s);
+
 // Arguments of one Clenshaw step (Eq. recursion, Algorithm 2):
 //   out = scale * (Dt .* b1 + g * sum_j X_j b1) + sgn * b2 + ck * psi,
 // with Dt(z) = (E(z) - c) / r reconstructed from the fixed-point tables and
