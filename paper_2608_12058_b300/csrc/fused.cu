@@ -42,7 +42,7 @@ constexpr int kTileF4 = kTile / 2;                 // float4 per tile
 constexpr int kPerThread = kTileF4 / kLowThreads;  // float4 per thread (4)
 constexpr uint32_t kTileBytes = kTile * 8;         // 32 KB
 constexpr int kMaxL2Bits = 10;
-constexpr int kPrefetchDefault = 3;                // tiles per CTA prefetched into L2 ahead
+constexpr int kPrefetchDefault = 0;                // tiles per CTA prefetched into L2 ahead (0 = off)
 constexpr long long kWaitCycles = 4000000000LL;    // ~2 s at 2 GHz
 static_assert(kPerThread == 2, "layout assumes 2 float4 per thread");
 
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
         // one iteration ahead find them there: DRAM stays busy with far more bytes in
         // flight than the two shared-memory stages could hold.
         const int64_t Tp = T + (int64_t)a.prefetch * gridDim.x;
-        if (t == 32 && Tp < a.ntiles) {
+        if (a.prefetch > 0 && t == 32 && Tp < a.ntiles) {
             l2_prefetch_bulk(a.b1 + Tp * kTileF4, kTileBytes);
             l2_prefetch_bulk(a.psi + Tp * kTileF4, kTileBytes);
             if (need_slot) l2_prefetch_bulk(a.slot + Tp * kTileF4, kTileBytes);
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(HighCfg<H>::kThreads, 1) k_high(const HighArgs
         }
         // rows of tiles further ahead go to L2 (one 128-byte line per row)
         const int64_t Tp = T + (int64_t)a.prefetch * gridDim.x;
-        if (u == 0 && Tp < a.ntiles) {
+        if (a.prefetch > 0 && u == 0 && Tp < a.ntiles) {
 #pragma unroll
             for (int p = 0; p < Cfg::kP; ++p) {
                 const int rho = rlo | (p << Cfg::kRowBitsT);
@@ -538,7 +538,8 @@ FusedPlan fused_plan(int n, int prec) {
     return p;
 }
 
-// L2 prefetch distance in tiles per CTA: CHEB_L2_PREFETCH_TILES (0..16), default 3.
+// L2 prefetch distance in tiles per CTA: CHEB_L2_PREFETCH_TILES (0..16), default 0
+// (off: on the B300 it did not raise either pass's bandwidth).
 static int prefetch_tiles() {
     static int v = -1;
     if (v < 0) {
