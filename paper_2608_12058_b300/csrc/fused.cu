@@ -511,8 +511,9 @@ bool fused_set_split(int n, int l, int h) {
 }
 
 // Split of the n bits: the low pass takes 12 + l, the high pass the top h.
-// Default: one pass while the L2 partner bits stay few (n <= 21); beyond that
-// the smallest high pass that keeps l <= 8, and h = 9 once l must grow past 8.
+// Default: one pass while 12 + l covers n with l <= 9 (n <= 21); beyond that a
+// high pass over as many top bits as possible (h <= 9) and at least 3 L2 bits,
+// the split that timed fastest at n = 24 and n = 30 on the B300.
 FusedPlan fused_plan(int n, int prec) {
     FusedPlan p;
     p.n = n;
@@ -532,7 +533,7 @@ FusedPlan fused_plan(int n, int prec) {
         p.l = rest;
         p.h = 0;
     } else {
-        p.h = std::min(9, std::max(3, rest - 8));
+        p.h = std::min(9, rest - 3);
         p.l = rest - p.h;
     }
     return p;
