@@ -124,6 +124,30 @@ cheb_status_t cheb_expmv(int n, const double* h, const double* J, double gamma, 
                          int time_splits, void* workspace, size_t workspace_bytes, void* stream,
                          cheb_info_t* info);
 
+/*
+ * cheb_expmv_noalloc: cheb_expmv without a caller-supplied workspace. The paper has
+ * no counterpart; it exists for callers that cannot allocate device memory (code
+ * running inside a pool or allocator that forbids foreign cudaMalloc calls, plugins
+ * that only receive their input and output buffers, programs that must not grow
+ * their device footprint after start-up).
+ *   - Scratch: a fixed 10 MiB array inside the library image (a __device__ array),
+ *     held by every GPU that loads the library's device code until the process
+ *     exits. It is enough for n <= 19 in FP32 and n <= 18 in FP64; larger n returns
+ *     CHEB_ERR_UNSUPPORTED before any work is enqueued.
+ *   - The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ *     routine. psi (device, in/out), h, J and info are as for cheb_expmv.
+ *   - The first call on each device looks up the array's device address (with that
+ *     device current) and caches it; make that first call before any stream capture.
+ *   - All calls share the one array. Calls that overlap on the GPU (other streams,
+ *     other host threads on the same device) race on it and must be serialised by
+ *     the caller.
+ * Errors: as cheb_expmv, plus UNSUPPORTED for sizes beyond the scratch array.
+ */
+cheb_status_t cheb_expmv_noalloc(int n, const double* h, const double* J, double gamma, double t,
+                                 void* psi, cheb_precision_t precision, double tol,
+                                 cheb_method_t method, int time_splits, void* stream,
+                                 cheb_info_t* info);
+
 /* Same as cheb_expmv with an explicit kernel path (cheb_path_t); used to time the
  * plain one-pass GPU path against the fused path. */
 cheb_status_t cheb_expmv_path(int n, const double* h, const double* J, double gamma, double t,

@@ -54,6 +54,8 @@ SIGNATURES = {
     "cheb_energy": (c_int, [c_int, _dp, _dp, c_void_p, c_int, c_void_p, c_size_t, c_void_p, _dp, _dp]),
     "cheb_set_fused_split": (c_int, [c_int, c_int, c_int]),
     "cheb_get_fused_split": (c_int, [c_int, _ip, _ip]),
+    "cheb_expmv_noalloc": (c_int, [c_int, _dp, _dp, c_double, c_double, c_void_p, c_int, c_double, c_int, c_int,
+                                   c_void_p, ctypes.POINTER(Info)]),
     "cheb_launch_count": (ctypes.c_longlong, []),
     "cheb_profile_enable": (c_int, [c_int]),
     "cheb_profile_reset": (c_int, []),

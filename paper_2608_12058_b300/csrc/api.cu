@@ -208,7 +208,7 @@ static cheb_status_t read_flags(const Ctx& C) {
     return CHEB_OK;
 }
 
-static cheb_status_t expmv_impl(int n, const double* h, const double* J, double gamma, double t, void* psi,
+cheb_status_t expmv_impl(int n, const double* h, const double* J, double gamma, double t, void* psi,
                                 int prec, double tol, int method, int splits, int path, void* ws,
                                 size_t ws_bytes, void* stream, cheb_info_t* info) {
     cheb_status_t st = check_common(n, h, J, prec, ws, ws_bytes);
