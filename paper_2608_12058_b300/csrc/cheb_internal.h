@@ -17,7 +17,7 @@ int make_coefficients(double a, std::complex<double> phase, double tol, int meth
 
 // ---- constants ------------------------------------------------------------
 constexpr int kMaxQubits = 33;        // 3 complex64 vectors of 2^33 fit in 270 GB
-constexpr int kTileBits = 12;         // low bits of the per-tile energy decomposition
+constexpr int kTileBits = 11;         // low bits of the per-tile energy decomposition
 constexpr int kMaxK = 1 << 16;        // coefficient table length per time slice
 constexpr int kSmallMaxF32 = 13;      // whole-vector-in-SMEM kernel limits
 constexpr int kSmallMaxF64 = 12;

@@ -7,18 +7,21 @@
 
 namespace cheb {
 
-// How the n bit flips of one step are split between the passes:
-//   low pass:  bits [0, M) from the shared-memory tile, bits [M, M + l) from
-//              partner tiles read through L2;
-//   high pass: bits [n - h, n) from a strided shared-memory tile (h may be 0).
+// How the n bit flips of one step are split between passes over memory:
+//   low pass:      bits [0, M) from the shared-memory tile, bits [M, M + l) from
+//                  partner tiles that TMA fetches from L2;
+//   strided passes: the remaining h = n - M - l bits, in npass ranges of 3..9 bits
+//                  each, [lo[k], lo[k] + hb[k]), each from a strided shared-memory
+//                  tile of 2^hb rows of 16 amplitudes.
 struct FusedPlan {
     int n = 0;
     int prec = 0;
     int M = 0;
     int l = 0;
     int h = 0;
-    int grid_low = 0;
-    int grid_high = 0;
+    int npass = 0;
+    int lo[4] = {0, 0, 0, 0};
+    int hb[4] = {0, 0, 0, 0};
 };
 
 size_t fused_scratch_bytes(int n, int prec);

@@ -91,21 +91,21 @@ def test_coefficients_reject_bad_arguments():
 
 def test_fused_split_table():
     """Every default split covers exactly the n bits; invalid overrides are refused."""
-    for n in range(12, 32):
+    for n in range(11, 34):
         l, h = api.get_fused_split(n)
-        assert 12 + l + h == n and 0 <= l <= 10 and (h == 0 or 3 <= h <= 9), (n, l, h)
+        assert 11 + l + h == n and 0 <= l <= 4 and (h == 0 or h >= 3), (n, l, h)
     with pytest.raises(_lib.ChebError):
-        api.set_fused_split(20, 3, 3)  # 12 + 3 + 3 != 20
+        api.set_fused_split(20, 3, 3)  # 11 + 3 + 3 != 20
     with pytest.raises(_lib.ChebError):
-        api.set_fused_split(20, 6, 2)  # h = 2 is not a supported high pass
+        api.set_fused_split(20, 7, 2)  # h = 2 is not a strided pass
     with pytest.raises(_lib.ChebError):
-        api.set_fused_split(11, 0, 0)
+        api.set_fused_split(10, 0, 0)
     with pytest.raises(_lib.ChebError):
-        api.set_fused_split(32, 10, 10)
-    api.set_fused_split(20, 2, 6)
-    assert api.get_fused_split(20) == (2, 6)
+        api.set_fused_split(33, 7, 15)  # more L2 partner bits than allowed
+    api.set_fused_split(20, 3, 6)
+    assert api.get_fused_split(20) == (3, 6)
     api.set_fused_split(20, -1)
-    assert api.get_fused_split(20) == (8, 0)
+    assert api.get_fused_split(20) == (0, 9)
 
 
 def test_expmv_rejects_bad_arguments_before_touching_the_device():

@@ -172,19 +172,23 @@ def test_poly_apply_matches_oracle_clenshaw(cuda_lib, oracle, prec):
 
 
 SPLITS = [
-    # n, l, h: low-pass L2 bits and high-pass bits (12 + l + h = n)
-    (12, 0, 0),
-    (13, 1, 0),
-    (16, 4, 0),
-    (16, 1, 3),
-    (17, 0, 5),
-    (18, 3, 3),
-    (19, 1, 6),
-    (20, 2, 6),
-    (21, 1, 8),
-    (21, 0, 9),
-    (22, 10, 0),
-    (22, 7, 3),
+    # n, l, h: L2 partner bits of the low pass and strided bits (11 + l + h = n);
+    # h > 9 runs two strided passes
+    (11, 0, 0),
+    (12, 1, 0),
+    (15, 4, 0),
+    (16, 2, 3),
+    (16, 0, 5),
+    (17, 6, 0),
+    (17, 3, 3),
+    (18, 1, 6),
+    (19, 0, 8),
+    (20, 2, 7),
+    (21, 1, 9),
+    (21, 6, 4),
+    (22, 0, 11),
+    (22, 4, 7),
+    (23, 0, 12),
 ]
 
 
