@@ -204,31 +204,54 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
         for (int i = 0; i < kNP; ++i) last_p[i] = -1;
         int it = 0;
         long long pj = 0;
+        // Energy partial sums of a tile: W[x] = A + sum_{i=1..5} s_i f_i over the lane
+        // bits x, W[32 + y] = sum_{i=6..9} s_i f_i over the warp bits y, f10 +- f0.
+        // Each lane needs at most 6 table entries of a tile; they are loaded one tile
+        // ahead so that the load latency never delays the copies issued below.
+        int64_t r0[6], r1[4];  // this lane's entries of the current tile
+        auto load_row = [&](int64_t Tt, int64_t* x0, int64_t* x1) {
+            const int64_t* row = a.tiles + Tt * (kLowBits + 1);
+            x0[0] = __ldg(row + kLowBits);
+#pragma unroll
+            for (int i = 1; i <= 5; ++i) x0[i] = __ldg(row + i);
+            if (lane < 16) {
+#pragma unroll
+                for (int i = 6; i <= 9; ++i) x1[i - 6] = __ldg(row + i);
+            } else {
+                x1[0] = __ldg(row + 10);
+                x1[1] = __ldg(row + 0);
+            }
+        };
+        if ((int64_t)blockIdx.x < a.ntiles) load_row(blockIdx.x, r0, r1);
         for (int64_t T = blockIdx.x; T < a.ntiles; T += gridDim.x, ++it) {
             const int s = it % kNS, k = it / kNS;
+            int64_t n0[6], n1[4];
+            const int64_t Tn = T + gridDim.x;
+            if (Tn < a.ntiles) load_row(Tn, n0, n1);
             int ok = 1;
             if (lane == 0 && k > 0) ok = mbar_wait(&empty_s[s], (k - 1) & 1, a.flags, abort);
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-            // energy partial sums of tile T: W[x] = A + sum_{i=1..5} s_i f_i over the lane
-            // bits x, W[32 + y] = sum_{i=6..9} s_i f_i over the warp bits y, f10 +- f0.
-            const int64_t* row = a.tiles + T * (kLowBits + 1);
             int64_t* W = wall + s * kW;
             {
-                int64_t e = __ldg(row + kLowBits);
+                int64_t e = r0[0];
 #pragma unroll
-                for (int i = 1; i <= 5; ++i) e += sel((lane >> (i - 1)) & 1, __ldg(row + i));
+                for (int i = 1; i <= 5; ++i) e += sel((lane >> (i - 1)) & 1, r0[i]);
                 W[lane] = e;
                 if (lane < 16) {
                     int64_t f = 0;
 #pragma unroll
-                    for (int i = 6; i <= 9; ++i) f += sel((lane >> (i - 6)) & 1, __ldg(row + i));
+                    for (int i = 6; i <= 9; ++i) f += sel((lane >> (i - 6)) & 1, r1[i - 6]);
                     W[32 + lane] = f;
                 } else if (lane == 16) {
-                    W[48] = __ldg(row + 10) + __ldg(row + 0);
+                    W[48] = r1[0] + r1[1];
                 } else if (lane == 17) {
-                    W[49] = __ldg(row + 10) - __ldg(row + 0);
+                    W[49] = r1[0] - r1[1];
                 }
             }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) r0[i] = n0[i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) r1[i] = n1[i];
             __syncwarp();
             if (lane == 0) {
                 __threadfence_block();
@@ -396,7 +419,7 @@ __device__ __forceinline__ int64_t strided_base(const StridedArgs& a, int64_t T)
 template <int H>
 __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const StridedArgs a) {
     using Cfg = StridedCfg<H>;
-    extern __shared__ __align__(16) float4 tile[];  // kRows * 8 float4
+    extern __shared__ __align__(16) float4 tiles2[];  // 2 x kRows * 8 float4 (double-buffered)
     const int t = threadIdx.x;
     const int u = t & 7;
     const int rlo = t >> 3;
@@ -413,7 +436,10 @@ __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const St
             nxt[p] = __ldg(a.b1 + base + rho * row_stride_f4 + u);
         }
     }
-    for (; T < a.ntiles; T += gridDim.x) {
+    for (int it = 0; T < a.ntiles; T += gridDim.x, ++it) {
+        // With two buffers one barrier per tile suffices: the buffer written now was
+        // last read two iterations ago, before the previous iteration's barrier.
+        float4* tile = tiles2 + (it & 1) * (Cfg::kRows * 8);
         const int64_t base = strided_base<H>(a, T);
         float4 w[Cfg::kP];
 #pragma unroll
@@ -456,7 +482,6 @@ __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const St
             }
             a.slot[idx] = make_float4(q0.x, q0.y, q1.x, q1.y);
         }
-        __syncthreads();  // tile reused by the next iteration
     }
 }
 
@@ -477,7 +502,7 @@ int num_sms() {
 template <int H>
 cudaError_t launch_strided_t(const StridedArgs& a, cudaStream_t s) {
     using Cfg = StridedCfg<H>;
-    const size_t smem = (size_t)Cfg::kRows * 8 * sizeof(float4);
+    const size_t smem = 2 * (size_t)Cfg::kRows * 8 * sizeof(float4);
     cudaError_t e = cudaFuncSetAttribute(k_strided<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
