@@ -406,6 +406,7 @@ struct StridedArgs {
     float scale_g;      // scale * (gamma / r), float-float hi part
     float scale_glo;    // lo part
     float sgn;          // coefficient of the slot's old content
+    int* flags_ws;      // status word (bounded waits of the warp-specialised variant)
 };
 
 template <int H>
@@ -485,6 +486,116 @@ __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const St
     }
 }
 
+// Warp-specialised strided pass for 6..9 bits: a producer warp copies the tile's
+// 2^H rows of b_{k+1} (128 B each, 1-D TMA) into a ring of stages; 512 consumer
+// threads (u = t & 7, rho low bits = t >> 3, rho high bits = register p) read the
+// partner rows from shared memory. The slot rows of the next tile are loaded into
+// registers one tile ahead.
+template <int H>
+struct StridedWsCfg {
+    static constexpr int kRows = 1 << H;
+    static constexpr uint32_t kStageBytes = (uint32_t)kRows * 128;
+    static constexpr int kNS = (int)((192u * 1024u) / kStageBytes) < 6 ? (int)((192u * 1024u) / kStageBytes) : 6;
+    static constexpr int kP = 1 << (H - 6);
+    static constexpr size_t kBarOff = (size_t)kNS * kStageBytes;
+    static constexpr size_t kSmem = kBarOff + 2 * kNS * sizeof(uint64_t) + 16;
+};
+
+template <int H>
+__global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs a) {
+    using Cfg = StridedWsCfg<H>;
+    static_assert(H >= 6 && H <= 9 && Cfg::kNS >= 2, "strided ring");
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = (uint64_t*)(smem + Cfg::kBarOff);
+    uint64_t* empty = full + Cfg::kNS;
+    volatile int* abort = (volatile int*)(empty + Cfg::kNS);
+    const int t = threadIdx.x;
+    const int warp = t >> 5, lane = t & 31;
+    const int64_t row_stride_f4 = (int64_t)1 << (a.lo - 1);
+    if (t == 0) {
+        for (int i = 0; i < Cfg::kNS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kCons / 32);
+        }
+        *abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == kCons / 32) {
+        int last[Cfg::kNS];
+        for (int i = 0; i < Cfg::kNS; ++i) last[i] = -1;
+        int it = 0;
+        for (int64_t T = blockIdx.x; T < a.ntiles; T += gridDim.x, ++it) {
+            const int s = it % Cfg::kNS, k = it / Cfg::kNS;
+            int ok = 1;
+            if (lane == 0) {
+                if (k > 0) ok = mbar_wait(&empty[s], (k - 1) & 1, a.flags_ws, abort);
+                if (ok) mbar_expect_tx(&full[s], Cfg::kStageBytes);
+                last[s] = k;
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            __syncwarp();
+            const int64_t base = strided_base<H>(a, T);
+            unsigned char* dst = smem + (size_t)s * Cfg::kStageBytes;
+            for (int r = lane; r < Cfg::kRows; r += 32)
+                tma_load_1d(dst + (size_t)r * 128, a.b1 + base + r * row_stride_f4, 128, &full[s]);
+        }
+        if (lane == 0)
+            for (int i = 0; i < Cfg::kNS; ++i)
+                if (last[i] >= 0) mbar_drain(&full[i], last[i] & 1, a.flags_ws);
+        return;
+    }
+    const int u = t & 7;
+    const int rlo = t >> 3;  // 6 bits
+    const bool need_slot = a.sgn != 0.f;
+    const float2 g_hi = dup(a.scale_g), g_lo = dup(a.scale_glo), sg = dup(a.sgn);
+    float4 w[Cfg::kP];
+    if (need_slot && (int64_t)blockIdx.x < a.ntiles) {
+        const int64_t base = strided_base<H>(a, blockIdx.x);
+#pragma unroll
+        for (int p = 0; p < Cfg::kP; ++p) w[p] = a.slot[base + (rlo | (p << 6)) * row_stride_f4 + u];
+    }
+    int it = 0;
+    for (int64_t T = blockIdx.x; T < a.ntiles; T += gridDim.x, ++it) {
+        const int s = it % Cfg::kNS;
+        const int64_t base = strided_base<H>(a, T);
+        float4 wn[Cfg::kP];
+        const int64_t Tn = T + gridDim.x;
+        if (need_slot && Tn < a.ntiles) {
+            const int64_t bn = strided_base<H>(a, Tn);
+#pragma unroll
+            for (int p = 0; p < Cfg::kP; ++p) wn[p] = a.slot[bn + (rlo | (p << 6)) * row_stride_f4 + u];
+        }
+        if (!mbar_wait(&full[s], (it / Cfg::kNS) & 1, a.flags_ws, abort)) break;
+        const float4* tile = (const float4*)(smem + (size_t)s * Cfg::kStageBytes);
+        float4 q[Cfg::kP];
+#pragma unroll
+        for (int p = 0; p < Cfg::kP; ++p) {
+            Acc S;
+            S.zero();
+#pragma unroll
+            for (int b = 1; b < Cfg::kP; b <<= 1) S.add(tile[((rlo | ((p ^ b) << 6))) * 8 + u]);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) S.add(tile[((rlo ^ (1 << j)) | (p << 6)) * 8 + u]);
+            float2 q0 = __ffma2_rn(g_hi, S.a, __fmul2_rn(g_lo, S.a));
+            float2 q1 = __ffma2_rn(g_hi, S.b, __fmul2_rn(g_lo, S.b));
+            if (need_slot) {
+                q0 = __ffma2_rn(sg, lo2(w[p]), q0);
+                q1 = __ffma2_rn(sg, hi2(w[p]), q1);
+            }
+            q[p] = make_float4(q0.x, q0.y, q1.x, q1.y);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+#pragma unroll
+        for (int p = 0; p < Cfg::kP; ++p) a.slot[base + (rlo | (p << 6)) * row_stride_f4 + u] = q[p];
+        if (need_slot) {
+#pragma unroll
+            for (int p = 0; p < Cfg::kP; ++p) w[p] = wn[p];
+        }
+    }
+}
+
 int g_num_sms = 0;
 std::mutex g_mu;
 
@@ -517,15 +628,31 @@ cudaError_t launch_strided_t(const StridedArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int H>
+cudaError_t launch_strided_ws_t(const StridedArgs& a, cudaStream_t s) {
+    using Cfg = StridedWsCfg<H>;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_strided_ws<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>(a.ntiles, num_sms());
+    note_launch(kKindHigh);
+    const int pi = prof_begin(kKindHigh, s);
+    k_strided_ws<H><<<(unsigned)grid, kLowThreads, Cfg::kSmem, s>>>(a);
+    prof_end(pi, s);
+    return cudaGetLastError();
+}
+
+// Passes of 6..9 bits use the warp-specialised TMA kernel, narrower ones the
+// register-prefetch kernel.
 cudaError_t launch_strided(int H, const StridedArgs& a, cudaStream_t s) {
     switch (H) {
         case 3: return launch_strided_t<3>(a, s);
         case 4: return launch_strided_t<4>(a, s);
         case 5: return launch_strided_t<5>(a, s);
-        case 6: return launch_strided_t<6>(a, s);
-        case 7: return launch_strided_t<7>(a, s);
-        case 8: return launch_strided_t<8>(a, s);
-        case 9: return launch_strided_t<9>(a, s);
+        case 6: return launch_strided_ws_t<6>(a, s);
+        case 7: return launch_strided_ws_t<7>(a, s);
+        case 8: return launch_strided_ws_t<8>(a, s);
+        case 9: return launch_strided_ws_t<9>(a, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -636,6 +763,7 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, i
         sa.scale_g = (float)s.scale * ghi;
         sa.scale_glo = (float)s.scale * glo;
         sa.sgn = (k == 0) ? (float)s.sgn : 1.0f;
+        sa.flags_ws = flags;
         cudaError_t e = launch_strided(plan.hb[k], sa, st);
         if (e != cudaSuccess) return e;
         slot_coeff = 1.0f;  // the slot now holds q
