@@ -20,6 +20,8 @@
 // amplitudes {2t + 1024p, 2t + 1024p + 1}: bit 0 inside the float4, bits 1..9 = t
 // (partners read from shared memory; 8 consecutive threads read 8 consecutive
 // 16-byte words, free of bank conflicts), bit 10 = p.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -486,14 +488,17 @@ __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const St
     }
 }
 
-// Warp-specialised strided pass for 6..9 bits: a producer warp copies the tile's
-// 2^H rows of b_{k+1} (128 B each, 1-D TMA) into a ring of stages; 512 consumer
-// threads (u = t & 7, rho low bits = t >> 3, rho high bits = register p) read the
-// partner rows from shared memory. The slot rows of the next tile are loaded into
-// registers one tile ahead.
+// Warp-specialised strided pass for 6..9 bits. The vector is viewed as a 4-D
+// tensor of float32: (32 floats = one 128-byte row of 16 amplitudes) x (2^(lo-4)
+// rows below the range) x (2^H rows of the range) x (rows above it). A producer
+// lane copies each tile's 2^H rows with one or two tensor TMA copies (boxes of up
+// to 256 rows) into a ring of stages; 512 consumer threads (u = t & 7, rho low bits
+// = t >> 3, rho high bits = register p) read the partner rows from shared memory.
+// The slot rows of the next tile are loaded into registers one tile ahead.
 template <int H>
 struct StridedWsCfg {
     static constexpr int kRows = 1 << H;
+    static constexpr int kBox = kRows < 256 ? kRows : 256;
     static constexpr uint32_t kStageBytes = (uint32_t)kRows * 128;
     static constexpr int kNS = (int)((192u * 1024u) / kStageBytes) < 6 ? (int)((192u * 1024u) / kStageBytes) : 6;
     static constexpr int kP = 1 << (H - 6);
@@ -501,8 +506,17 @@ struct StridedWsCfg {
     static constexpr size_t kSmem = kBarOff + 2 * kNS * sizeof(uint64_t) + 16;
 };
 
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
 template <int H>
-__global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs a) {
+__global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs a, const __grid_constant__ CUtensorMap map) {
     using Cfg = StridedWsCfg<H>;
     static_assert(H >= 6 && H <= 9 && Cfg::kNS >= 2, "strided ring");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -512,6 +526,7 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
     const int64_t row_stride_f4 = (int64_t)1 << (a.lo - 1);
+    const int sh = a.lo - 4;
     if (t == 0) {
         for (int i = 0; i < Cfg::kNS; ++i) {
             mbar_init(&full[i], 1);
@@ -522,27 +537,24 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs
     }
     __syncthreads();
     if (warp == kCons / 32) {
+        if (lane != 0) return;
         int last[Cfg::kNS];
         for (int i = 0; i < Cfg::kNS; ++i) last[i] = -1;
         int it = 0;
         for (int64_t T = blockIdx.x; T < a.ntiles; T += gridDim.x, ++it) {
             const int s = it % Cfg::kNS, k = it / Cfg::kNS;
-            int ok = 1;
-            if (lane == 0) {
-                if (k > 0) ok = mbar_wait(&empty[s], (k - 1) & 1, a.flags_ws, abort);
-                if (ok) mbar_expect_tx(&full[s], Cfg::kStageBytes);
-                last[s] = k;
-            }
-            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-            __syncwarp();
-            const int64_t base = strided_base<H>(a, T);
+            if (k > 0 && !mbar_wait(&empty[s], (k - 1) & 1, a.flags_ws, abort)) break;
+            mbar_expect_tx(&full[s], Cfg::kStageBytes);
+            last[s] = k;
+            const int tlo = (int)(T & (((int64_t)1 << sh) - 1));
+            const int thi = (int)(T >> sh);
             unsigned char* dst = smem + (size_t)s * Cfg::kStageBytes;
-            for (int r = lane; r < Cfg::kRows; r += 32)
-                tma_load_1d(dst + (size_t)r * 128, a.b1 + base + r * row_stride_f4, 128, &full[s]);
+#pragma unroll
+            for (int c = 0; c < Cfg::kRows / Cfg::kBox; ++c)
+                tma_load_4d(dst + (size_t)c * Cfg::kBox * 128, &map, 0, tlo, c * Cfg::kBox, thi, &full[s]);
         }
-        if (lane == 0)
-            for (int i = 0; i < Cfg::kNS; ++i)
-                if (last[i] >= 0) mbar_drain(&full[i], last[i] & 1, a.flags_ws);
+        for (int i = 0; i < Cfg::kNS; ++i)
+            if (last[i] >= 0) mbar_drain(&full[i], last[i] & 1, a.flags_ws);
         return;
     }
     const int u = t & 7;
@@ -568,7 +580,6 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs
         }
         if (!mbar_wait(&full[s], (it / Cfg::kNS) & 1, a.flags_ws, abort)) break;
         const float4* tile = (const float4*)(smem + (size_t)s * Cfg::kStageBytes);
-        float4 q[Cfg::kP];
 #pragma unroll
         for (int p = 0; p < Cfg::kP; ++p) {
             Acc S;
@@ -582,17 +593,12 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs
             if (need_slot) {
                 q0 = __ffma2_rn(sg, lo2(w[p]), q0);
                 q1 = __ffma2_rn(sg, hi2(w[p]), q1);
+                w[p] = wn[p];
             }
-            q[p] = make_float4(q0.x, q0.y, q1.x, q1.y);
+            a.slot[base + (rlo | (p << 6)) * row_stride_f4 + u] = make_float4(q0.x, q0.y, q1.x, q1.y);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-#pragma unroll
-        for (int p = 0; p < Cfg::kP; ++p) a.slot[base + (rlo | (p << 6)) * row_stride_f4 + u] = q[p];
-        if (need_slot) {
-#pragma unroll
-            for (int p = 0; p < Cfg::kP; ++p) w[p] = wn[p];
-        }
+        if (lane == 0) mbar_arrive(&empty[s]);  // this warp's shared-memory reads are done
     }
 }
 
@@ -628,31 +634,60 @@ cudaError_t launch_strided_t(const StridedArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
 template <int H>
-cudaError_t launch_strided_ws_t(const StridedArgs& a, cudaStream_t s) {
+cudaError_t launch_strided_ws_t(const StridedArgs& a, int n, cudaStream_t s) {
     using Cfg = StridedWsCfg<H>;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    // (row of 32 floats) x (rows below the range) x (rows in the range) x (rows above)
+    cuuint64_t dims[4] = {32, (cuuint64_t)1 << (a.lo - 4), (cuuint64_t)1 << H, (cuuint64_t)1 << (n - a.lo - H)};
+    cuuint64_t strides[3] = {128, (cuuint64_t)1 << (a.lo + 3), (cuuint64_t)1 << (a.lo + H + 3)};
+    cuuint32_t box[4] = {32, 1, (cuuint32_t)Cfg::kBox, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUtensorMap map;
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)a.b1, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     cudaError_t e =
         cudaFuncSetAttribute(k_strided_ws<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(a.ntiles, num_sms());
     note_launch(kKindHigh);
     const int pi = prof_begin(kKindHigh, s);
-    k_strided_ws<H><<<(unsigned)grid, kLowThreads, Cfg::kSmem, s>>>(a);
+    k_strided_ws<H><<<(unsigned)grid, kLowThreads, Cfg::kSmem, s>>>(a, map);
     prof_end(pi, s);
     return cudaGetLastError();
 }
 
 // Passes of 6..9 bits use the warp-specialised TMA kernel, narrower ones the
 // register-prefetch kernel.
-cudaError_t launch_strided(int H, const StridedArgs& a, cudaStream_t s) {
+cudaError_t launch_strided(int H, const StridedArgs& a, int n, cudaStream_t s) {
     switch (H) {
         case 3: return launch_strided_t<3>(a, s);
         case 4: return launch_strided_t<4>(a, s);
         case 5: return launch_strided_t<5>(a, s);
-        case 6: return launch_strided_ws_t<6>(a, s);
-        case 7: return launch_strided_ws_t<7>(a, s);
-        case 8: return launch_strided_ws_t<8>(a, s);
-        case 9: return launch_strided_ws_t<9>(a, s);
+        case 6: return launch_strided_ws_t<6>(a, n, s);
+        case 7: return launch_strided_ws_t<7>(a, n, s);
+        case 8: return launch_strided_ws_t<8>(a, n, s);
+        case 9: return launch_strided_ws_t<9>(a, n, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -764,7 +799,7 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, i
         sa.scale_glo = (float)s.scale * glo;
         sa.sgn = (k == 0) ? (float)s.sgn : 1.0f;
         sa.flags_ws = flags;
-        cudaError_t e = launch_strided(plan.hb[k], sa, st);
+        cudaError_t e = launch_strided(plan.hb[k], sa, s.n, st);
         if (e != cudaSuccess) return e;
         slot_coeff = 1.0f;  // the slot now holds q
     }
