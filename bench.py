@@ -140,11 +140,11 @@ def run_reference(args, world, rank):
 
 
 def traffic_from_profile():
-    """DRAM bytes per amplitude of the low pass from the committed ncu summary, if it
-    was taken on the kernel source that is built now; else None."""
+    """DRAM bytes per amplitude per launch of each fused kernel, from the committed
+    ncu summary, if it was taken on the kernel source that is built now; else None."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", "k_low_traffic.json")
+    path = os.path.join(ROOT, "profiles", "fused_dram_traffic.json")
     src = os.path.join(ROOT, "paper_2608_12058_b300", "csrc", "fused.cu")
     try:
         with open(path) as f:
@@ -152,7 +152,7 @@ def traffic_from_profile():
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if d.get("fused_cu_sha256_16") != h:
             return None
-        return float(d["dram_bytes_per_amplitude"])
+        return {k: float(v) for k, v in d["dram_bytes_per_amplitude"].items()}
     except Exception:
         return None
 
@@ -296,18 +296,28 @@ def run_ours(args, world, rank, local):
         return
 
     peak, peak_kind = _peaks()
-    low_avg = low_ms / max(nlow, 1) / 1e3
-    alg_low = 32.0 * N  # bytes: read b1, psi, slot, write out (complex64)
-    achieved = alg_low / low_avg / 1e9 if nlow else None
-    tpa = traffic_from_profile()
-    roof = {"bound": "hbm", "kernel": "k_low (fused low pass)", "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-            "traffic": (tpa * N) if tpa is not None else None, "peak_kind": f"{peak_kind} hbm_gbs",
-            "algorithmic_bytes_per_launch": alg_low, "launches_timed": nlow,
-            "avg_launch_ms": low_avg * 1e3,
-            "step_alg_GBps": 32.0 * N * K * args.steps / t_local / 1e9,
-            "high_pass_avg_launch_ms": (high_ms / nhigh) if nhigh else None,
-            "share_low": low_ms / ms, "share_high": high_ms / ms}
+    traffic = traffic_from_profile()
+
+    def kernel_roof(name, count, total_ms, bytes_per_amp):
+        if not count:
+            return None
+        avg_s = total_ms / count / 1e3
+        alg = bytes_per_amp * N
+        achieved = alg / avg_s / 1e9
+        tpa = traffic.get(name) if traffic else None
+        return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": (tpa * N) if tpa is not None else None,
+                "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": alg,
+                "algorithmic_bytes_per_amplitude": bytes_per_amp, "launches_timed": count,
+                "avg_launch_ms": avg_s * 1e3, "share": total_ms / ms}
+
+    # low pass: read b1, psi, slot, write out; strided pass: read b1, slot, write slot
+    r_low = kernel_roof("k_low", nlow, low_ms, 32.0)
+    r_str = kernel_roof("k_strided", nhigh, high_ms, 24.0)
+    cands = [r for r in (r_low, r_str) if r is not None]
+    roof = dict(max(cands, key=lambda r: r["share"]))
+    roof["other_kernels"] = [r for r in cands if r["kernel"] != roof["kernel"]]
+    roof["step_alg_GBps"] = 32.0 * N * K * args.steps / t_local / 1e9
     cpu_v, cpu_dt, cpu_info = cpu_sample_run()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
