@@ -148,6 +148,51 @@ cheb_status_t cheb_expmv_noalloc(int n, const double* h, const double* J, double
                                  cheb_method_t method, int time_splits, void* stream,
                                  cheb_info_t* info);
 
+/*
+ * Piecewise-constant annealing schedule (the constant-H building block of the
+ * time-dependent evolution of Sec. III.B): for s = 0..S-1,
+ *   psi <- exp(-i t_s H_s) psi,   H_s = diag(E) + gamma_s sum_j X_j.
+ * The spectral scan runs once (E is shared); each segment uses its own radius
+ * r_s = (Emax - Emin)/2 + |gamma_s| n and series (Eq. cheb / Sec. II.C) with
+ * tolerance tol / S, so the whole schedule meets tol in the truncation bound.
+ *   gamma_s, t_s: HOST arrays of S doubles.
+ *   boundaries:   nullable DEVICE buffer of S states (S * 2^n complex of the given
+ *                 precision); receives the state at the start of each segment.
+ *   infos:        nullable HOST array of S cheb_info_t (per segment; norm and energy
+ *                 of the state after that segment). Requesting infos synchronises
+ *                 the stream once per segment.
+ * Workspace: cheb_workspace_bytes(n, precision). Errors: as cheb_expmv.
+ */
+cheb_status_t cheb_anneal(int n, const double* h, const double* J, int S, const double* gamma_s,
+                          const double* t_s, void* psi, cheb_precision_t precision, double tol,
+                          cheb_method_t method, void* boundaries, void* workspace,
+                          size_t workspace_bytes, void* stream, cheb_info_t* infos);
+
+/*
+ * Batched independent instances (Sec. III.A batches many small problems per launch):
+ * psi_i <- exp(-i t_i H_i) psi_i for i = 0..B-1, each with its own n_i, couplings,
+ * gamma_i and t_i, and its own spectral interval and polynomial (the paper pads the
+ * batch to the largest radius instead).
+ *   n:        HOST array of B sizes (1..33).
+ *   offsets:  HOST array of B element offsets of each state in psi_cat (complex
+ *             elements of the given precision; each state must start 16-byte aligned).
+ *   h_cat:    HOST, the h vectors concatenated (sum n_i doubles).
+ *   J_cat:    HOST, the n_i x n_i row-major J matrices concatenated (sum n_i^2 doubles).
+ *   gamma, t: HOST arrays of B doubles.   psi_cat: DEVICE, in/out.
+ *   workspace: cheb_batched_workspace_bytes(B, n, precision) bytes (256-aligned).
+ *   infos:    nullable HOST array of B cheb_info_t; requesting it synchronises.
+ * The spectral bounds of all instances need one synchronisation of the stream.
+ * Instances with n <= 13 (FP32) or n <= 12 (FP64) run together in one launch;
+ * larger ones run on an internal pool of streams joined back into `stream`.
+ * Errors: as cheb_expmv.
+ */
+size_t cheb_batched_workspace_bytes(int B, const int* n, cheb_precision_t precision);
+cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* offsets, const double* h_cat,
+                                 const double* J_cat, const double* gamma, const double* t,
+                                 void* psi_cat, cheb_precision_t precision, double tol,
+                                 cheb_method_t method, void* workspace, size_t workspace_bytes,
+                                 void* stream, cheb_info_t* infos);
+
 /* Same as cheb_expmv with an explicit kernel path (cheb_path_t); used to time the
  * plain one-pass GPU path against the fused path. */
 cheb_status_t cheb_expmv_path(int n, const double* h, const double* J, double gamma, double t,

@@ -200,6 +200,18 @@ def expmv(h, J, gamma: float, t: float, psi, tol: float = 1e-12, method: str = "
     return y.view(np.complex128), d
 
 
+def anneal(h, J, gammas, ts, psi, tol: float = 1e-12, method: str = "chebyshev"):
+    """Piecewise-constant schedule: psi <- exp(-i t_s H(gamma_s)) psi for each segment,
+    each segment with tolerance tol / S. Returns (final state, list of segment starts)."""
+    S = len(gammas)
+    cur = np.asarray(psi, dtype=np.complex128).copy()
+    starts = []
+    for g, t in zip(gammas, ts):
+        starts.append(cur.copy())
+        cur, _ = expmv(h, J, float(g), float(t), cur, tol / S, method)
+    return cur, starts
+
+
 def energy_norm(h, J, psi):
     h, J = _f64(h), _f64(J)
     x = _c128_view(psi)

@@ -128,6 +128,78 @@ def expmv(h, J, gamma: float, t: float, psi, tol: Optional[float] = None, method
     return inf.as_dict() if info else None
 
 
+def anneal(h, J, gammas, ts, psi, tol: Optional[float] = None, method: str = "chebyshev", boundaries=None,
+           info: bool = True):
+    """psi <- prod_s exp(-i t_s H(gamma_s)) psi in place (piecewise-constant schedule).
+
+    boundaries: optional CUDA tensor of shape (S, 2^n), same dtype as psi, that
+    receives the state at the start of every segment. Returns per-segment infos."""
+    h, J = _f64(h), _f64(J)
+    gammas, ts = _f64(gammas), _f64(ts)
+    n = h.shape[0]
+    S = gammas.shape[0]
+    assert ts.shape[0] == S
+    _check_state(psi, n)
+    prec = precision_of(psi)
+    if tol is None:
+        tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+    bptr = None
+    if boundaries is not None:
+        if boundaries.dtype != psi.dtype or tuple(boundaries.shape) != (S, 1 << n) or not boundaries.is_contiguous():
+            raise ValueError("boundaries must be a contiguous (S, 2^n) tensor of psi's dtype")
+        bptr = ctypes.c_void_p(boundaries.data_ptr())
+    ws = workspace(n, prec, psi.device)
+    p, nb = _ws_ptr(ws)
+    infos = (_lib.Info * S)() if info else None
+    code = _lib.lib().cheb_anneal(n, _dp(h), _dp(J), S, _dp(gammas), _dp(ts), ctypes.c_void_p(psi.data_ptr()),
+                                  PREC[prec], float(tol), METHOD[method], bptr, ctypes.c_void_p(p), nb,
+                                  _stream_ptr(psi.device), infos)
+    _lib.check(code, "cheb_anneal")
+    return [x.as_dict() for x in infos] if info else None
+
+
+def batch_offsets(ns):
+    """Contiguous layout of a batch: element offset of each state (padded to even)."""
+    off, cur = [], 0
+    for n in ns:
+        off.append(cur)
+        cur += max(1 << int(n), 2)
+    return np.array(off, dtype=np.int64), cur
+
+
+def expmv_batched(ns, hs, Js, gammas, ts, psi_cat, offsets=None, tol: Optional[float] = None,
+                  method: str = "chebyshev", info: bool = True):
+    """psi_i <- exp(-i t_i H_i) psi_i for independent instances packed in psi_cat."""
+    import torch
+
+    ns = np.ascontiguousarray(np.asarray(ns, dtype=np.int32))
+    B = ns.shape[0]
+    h_cat = np.ascontiguousarray(np.concatenate([_f64(h) for h in hs]))
+    J_cat = np.ascontiguousarray(np.concatenate([_f64(J).ravel() for J in Js]))
+    gammas, ts = _f64(gammas), _f64(ts)
+    if offsets is None:
+        offsets, _ = batch_offsets(ns)
+    offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    if not isinstance(psi_cat, torch.Tensor) or not psi_cat.is_cuda or not psi_cat.is_contiguous():
+        raise TypeError("psi_cat must be a contiguous CUDA tensor")
+    prec = precision_of(psi_cat)
+    if tol is None:
+        tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+    ip = ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    need = int(_lib.lib().cheb_batched_workspace_bytes(B, ip, PREC[prec]))
+    if need == 0:
+        raise ValueError("invalid batch sizes")
+    ws = torch.empty(need + 256, dtype=torch.uint8, device=psi_cat.device)
+    p, nb = _ws_ptr(ws)
+    infos = (_lib.Info * B)() if info else None
+    code = _lib.lib().cheb_expmv_batched(B, ip, offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(h_cat),
+                                         _dp(J_cat), _dp(gammas), _dp(ts), ctypes.c_void_p(psi_cat.data_ptr()),
+                                         PREC[prec], float(tol), METHOD[method], ctypes.c_void_p(p), nb,
+                                         _stream_ptr(psi_cat.device), infos)
+    _lib.check(code, "cheb_expmv_batched")
+    return [x.as_dict() for x in infos] if info else None
+
+
 def poly_apply(h, J, gamma: float, center: float, radius: float, coeffs, psi, path: str = "auto"):
     """psi <- sum_m c_m T_m((H - center)/radius) psi in place on the GPU."""
     h, J = _f64(h), _f64(J)

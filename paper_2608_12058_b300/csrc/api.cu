@@ -13,6 +13,7 @@
 #include "cheb_internal.h"
 #include "fused.cuh"
 #include "kernels.cuh"
+#include "pipeline.h"
 
 namespace cheb {
 
@@ -46,13 +47,7 @@ Layout make_layout(int n, int precision) {
     return L;
 }
 
-// Couplings in fixed point: value = integer * 2^-Q.
-struct FixedOp {
-    int Q = 0;
-    std::vector<int64_t> jq;  // J symmetric n*n, then h[n], then c
-};
-
-static bool finite_all(const double* p, size_t k) {
+bool finite_all(const double* p, size_t k) {
     for (size_t i = 0; i < k; ++i)
         if (!std::isfinite(p[i])) return false;
     return true;
@@ -67,8 +62,7 @@ static int choose_scale(long double bound) {
 }
 
 // J/scale, h/scale, c/scale quantised at the largest safe Q.
-static FixedOp make_fixed(int n, const double* h, const double* J, double center, double scale,
-                          int max_q = 62) {
+FixedOp make_fixed(int n, const double* h, const double* J, double center, double scale, int max_q) {
     FixedOp F;
     long double bound = std::fabs((long double)center);
     for (int i = 0; i < n; ++i) {
@@ -90,26 +84,7 @@ static FixedOp make_fixed(int n, const double* h, const double* J, double center
     return F;
 }
 
-struct Ctx {
-    int n;
-    int prec;
-    Layout L;
-    unsigned char* ws;
-    cudaStream_t s;
-    int64_t* tiles() const { return (int64_t*)(ws + L.tiles); }
-    int64_t* elow() const { return (int64_t*)(ws + L.elow); }
-    int* flags() const { return (int*)(ws + L.status); }
-    int64_t* i64out() const { return (int64_t*)(ws + L.status + 64); }
-    double* f64out() const { return (double*)(ws + L.status + 128); }
-    double* part() const { return (double*)(ws + L.part); }
-};
-
-#define CUDA_TRY(x)                                   \
-    do {                                              \
-        if ((x) != cudaSuccess) return CHEB_ERR_CUDA; \
-    } while (0)
-
-static cheb_status_t upload_tables(const Ctx& C, const FixedOp& F) {
+cheb_status_t upload_tables(const Ctx& C, const FixedOp& F) {
     CUDA_TRY(cudaMemcpyAsync(C.ws + C.L.jq, F.jq.data(), F.jq.size() * sizeof(int64_t),
                              cudaMemcpyHostToDevice, C.s));
     launch_tables(C.n, C.L.M, (const int64_t*)(C.ws + C.L.jq), C.tiles(), C.elow(), C.s);
@@ -117,8 +92,7 @@ static cheb_status_t upload_tables(const Ctx& C, const FixedOp& F) {
     return CHEB_OK;
 }
 
-static cheb_status_t check_common(int n, const double* h, const double* J, int prec, void* ws,
-                                  size_t ws_bytes) {
+cheb_status_t check_common(int n, const double* h, const double* J, int prec, void* ws, size_t ws_bytes) {
     if (n < 1 || n > kMaxQubits) return CHEB_ERR_INVALID_ARG;
     if (!h || !J) return CHEB_ERR_INVALID_ARG;
     if (prec != CHEB_FP32 && prec != CHEB_FP64) return CHEB_ERR_INVALID_ARG;
@@ -128,7 +102,7 @@ static cheb_status_t check_common(int n, const double* h, const double* J, int p
     return CHEB_OK;
 }
 
-static cheb_status_t bounds_impl(Ctx& C, const double* h, const double* J, double* emin, double* emax) {
+cheb_status_t bounds_impl(Ctx& C, const double* h, const double* J, double* emin, double* emax) {
     FixedOp F = make_fixed(C.n, h, J, 0.0, 1.0);
     cheb_status_t st = upload_tables(C, F);
     if (st != CHEB_OK) return st;
@@ -143,8 +117,8 @@ static cheb_status_t bounds_impl(Ctx& C, const double* h, const double* J, doubl
 }
 
 // One Clenshaw run (Algorithm 2) of the coefficients c over psi, in place.
-static cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::complex<double>>& c,
-                                  int Q, double g) {
+cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::complex<double>>& c, int Q,
+                           double g) {
     const int K = (int)c.size() - 1;
     const int64_t N = (int64_t)1 << C.n;
     if (K == 0) {
@@ -199,12 +173,30 @@ static cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector
     return CHEB_OK;
 }
 
-static cheb_status_t read_flags(const Ctx& C) {
+cheb_status_t read_flags(const Ctx& C) {
     int f = 0;
     CUDA_TRY(cudaMemcpyAsync(&f, C.flags(), sizeof(int), cudaMemcpyDeviceToHost, C.s));
     CUDA_TRY(cudaStreamSynchronize(C.s));
     if (f & kFlagTimeout) return CHEB_ERR_TIMEOUT;
     if (f & kFlagBadLaunch) return CHEB_ERR_CUDA;
+    return CHEB_OK;
+}
+
+cheb_status_t slice_coefficients(double t, double c, double r, double tol, int method, int splits,
+                                 std::vector<std::complex<double>>& coef, int* K_out, int* s_out, double* err) {
+    // coefficients, with automatic slicing when the degree exceeds the table
+    int s = splits > 0 ? splits : 1;
+    int K = -1;
+    for (int attempt = 0; attempt < 24; ++attempt) {
+        const double ts = t / s;
+        const std::complex<double> phase = std::polar(1.0, -ts * c);
+        K = make_coefficients(ts * r, phase, tol / s, method, kMaxK, coef, err);
+        if (K >= 0 || splits > 0) break;
+        s *= 2;
+    }
+    if (K < 0) return CHEB_ERR_UNSUPPORTED;
+    *K_out = K;
+    *s_out = s;
     return CHEB_OK;
 }
 
@@ -229,19 +221,11 @@ cheb_status_t expmv_impl(int n, const double* h, const double* J, double gamma, 
     if (F.Q < 24) return CHEB_ERR_UNSUPPORTED;
     st = upload_tables(C, F);
     if (st != CHEB_OK) return st;
-    // coefficients, with automatic slicing when the degree exceeds the table
-    int s = splits > 0 ? splits : 1;
+    int s = 1, K = -1;
     std::vector<std::complex<double>> coef;
     double err = 0.0;
-    int K = -1;
-    for (int attempt = 0; attempt < 24; ++attempt) {
-        const double ts = t / s;
-        const std::complex<double> phase = std::polar(1.0, -ts * c);
-        K = make_coefficients(ts * r, phase, tol / s, method, kMaxK, coef, &err);
-        if (K >= 0 || splits > 0) break;
-        s *= 2;
-    }
-    if (K < 0) return CHEB_ERR_UNSUPPORTED;
+    st = slice_coefficients(t, c, r, tol, method, splits, coef, &K, &s, &err);
+    if (st != CHEB_OK) return st;
     const double g = gamma / r;
     for (int q = 0; q < s; ++q) {
         st = clenshaw_run(C, path, psi, coef, F.Q, g);

@@ -261,12 +261,10 @@ void launch_step_plain(int prec, const StepArgs& a, cudaStream_t s) {
 // Small n: one CTA runs the whole recurrence with psi, b1, b2 in shared memory.
 // Each thread owns the same elements for all steps and keeps their Dt in registers.
 template <typename R, int PER>
-__global__ void __launch_bounds__(1024) k_small(int n, int K, const double2* __restrict__ coef, int Q,
-                                                const int64_t* __restrict__ tiles,
-                                                const int64_t* __restrict__ elow, double g,
-                                                typename Cx<R>::T* psi_g) {
+__device__ __forceinline__ void small_run(int n, int K, const double2* __restrict__ coef, int Q,
+                                          const int64_t* __restrict__ tiles, const int64_t* __restrict__ elow,
+                                          double g, typename Cx<R>::T* psi_g, unsigned char* smem_raw) {
     using C = typename Cx<R>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = 1 << n;
     C* sp = (C*)smem_raw;
     C* s1 = sp + N;
@@ -345,6 +343,47 @@ __global__ void __launch_bounds__(1024) k_small(int n, int K, const double2* __r
         b1 = b2;
         b2 = t;
     }
+}
+
+template <typename R, int PER>
+__global__ void __launch_bounds__(1024) k_small(int n, int K, const double2* __restrict__ coef, int Q,
+                                                const int64_t* __restrict__ tiles,
+                                                const int64_t* __restrict__ elow, double g,
+                                                typename Cx<R>::T* psi_g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    small_run<R, PER>(n, K, coef, Q, tiles, elow, g, psi_g, smem_raw);
+}
+
+// Many independent small instances, one CTA each (the batching of Sec. III.A with
+// every instance keeping its own polynomial).
+template <typename R, int PER>
+__global__ void __launch_bounds__(1024) k_small_batched(const SmallDesc* __restrict__ d) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmallDesc x = d[blockIdx.x];
+    if (x.K <= 0) return;
+    small_run<R, PER>(x.n, x.K, (const double2*)x.coef, x.Q, x.tiles, x.elow, x.g, (typename Cx<R>::T*)x.psi,
+                      smem_raw);
+}
+
+cudaError_t launch_small_batched(int prec, int count, int max_n, const SmallDesc* descs, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int N = 1 << max_n;
+    const int threads = N < 1024 ? (N < 32 ? 32 : N) : 1024;
+    const size_t smem = 3 * (size_t)N * (prec == 0 ? 8 : 16);
+    if (prec == 0) {
+        auto kern = k_small_batched<float, 8>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        note_launch(kKindSmall);
+        kern<<<count, threads, smem, s>>>(descs);
+    } else {
+        auto kern = k_small_batched<double, 4>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        note_launch(kKindSmall);
+        kern<<<count, threads, smem, s>>>(descs);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_small(int prec, int n, int K, const double* coef_dev, int Q, const int64_t* tiles,

@@ -55,6 +55,19 @@ void launch_step_plain(int prec, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_small(int prec, int n, int K, const double* coef_dev, int Q,
                          const int64_t* tiles, const int64_t* elow, double g, void* psi,
                          cudaStream_t s);
+// One small instance of a batch (whole run in one CTA's shared memory).
+struct SmallDesc {
+    int n;
+    int K;                 // degree; K <= 0 skips the instance
+    int Q;                 // fixed-point scale of its tables
+    int pad;
+    double g;              // gamma / r
+    const double* coef;    // (K+1) complex doubles, device
+    const int64_t* tiles;  // its energy tables
+    const int64_t* elow;
+    void* psi;             // its state, in/out
+};
+cudaError_t launch_small_batched(int prec, int count, int max_n, const SmallDesc* descs, cudaStream_t s);
 void launch_norm_energy(int prec, int n, int M, int Q, const int64_t* tiles, const int64_t* elow,
                         double c, double r, const void* psi, double* part, double* out2,
                         cudaStream_t s);

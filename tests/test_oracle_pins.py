@@ -350,3 +350,19 @@ def test_dense_gradients_vs_finite_differences(oracle):
     d = I.random_state(n, 53)
     fd = (loss(h, J, gam, t, psi + eps * d) - loss(h, J, gam, t, psi - eps * d)) / (2 * eps)
     assert abs(fd - np.real(np.vdot(g["psi0"], d))) < 1e-7
+
+
+def test_anneal_matches_dense_product(oracle):
+    """A piecewise-constant schedule is the ordered product of the segments' dense
+    exponentials (eigh of each explicit H_s)."""
+    n = 7
+    h, J = I.sk_instance(n, 61)
+    psi = I.random_state(n, 62)
+    gammas = np.array([1.5, 0.9, 0.4, 0.1])
+    ts = np.array([0.5, 0.7, 0.3, 1.1])
+    y, starts = oracle.anneal(h, J, gammas, ts, psi, 1e-13)
+    ref = psi.copy()
+    for g, t, st in zip(gammas, ts, starts):
+        np.testing.assert_allclose(st, ref, atol=1e-12)
+        ref = oracle.dense_expmv(h, J, g, t, ref)
+    assert np.linalg.norm(y - ref) < 1e-12
