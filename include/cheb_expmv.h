@@ -193,6 +193,46 @@ cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* offsets, co
                                  cheb_method_t method, void* workspace, size_t workspace_bytes,
                                  void* stream, cheb_info_t* infos);
 
+/*
+ * Reverse-mode gradients (no counterpart in the paper; derived from Algorithm 2).
+ * For a real loss L of the schedule's final state y and ybar = dL/dy in the
+ * convention dL = Re<ybar, dy> (torch's for complex tensors; for L = |y|^2,
+ * ybar = 2y), the adjoint of the Clenshaw recurrence gives
+ *   bbar_0 = ybar, bbar_1 = Ht bbar_0, bbar_k = 2 Ht bbar_{k-1} - bbar_{k-2},
+ *   psibar = sum_k conj(c_k) bbar_k,
+ *   dL = Re sum_{k<K} w_k <bbar_k, dHt b_{k+1}>  (w_0 = 1, w_k = 2),
+ * with the forward vectors b_k regenerated upward from (b_1, b_2) and reset from
+ * anchor checkpoints. The spectral interval (c, r) is held fixed (the exact
+ * exp(-itH) does not depend on it); dL/dt_s uses the exact dy/dt = -i H y.
+ *
+ * cheb_adjoint_workspace_bytes(n, precision, anchors): workspace for
+ *   cheb_anneal_adjoint with room for `anchors` checkpoint pairs (>= 1; more
+ *   anchors = shorter upward regeneration; about sqrt(K) is plenty).
+ * cheb_anneal_adjoint:
+ *   boundaries: DEVICE, the S segment-start states written by cheb_anneal.
+ *   psi_T:      DEVICE, the final state.
+ *   grad:       DEVICE in/out: in = ybar at the final state; out = psibar at the
+ *               initial state.
+ *   grad_gamma, grad_t (HOST, S doubles), grad_h (HOST, n), grad_J (HOST, n*n,
+ *   strict upper triangle filled, rest zero): nullable outputs.
+ *   S = 1 with boundaries = the input state is the gradient of one cheb_expmv.
+ * cheb_energy_grad: L = <psi|H_P|psi> (FP64 reduction), grad_psi (DEVICE out) =
+ *   2 H_P psi, grad_h, grad_J as above (HOST). Workspace as for the adjoint with
+ *   anchors = 0 allowed.
+ * Errors: INVALID_ARG, WORKSPACE, CUDA, TIMEOUT, UNSUPPORTED (time slicing needed).
+ */
+size_t cheb_adjoint_workspace_bytes(int n, cheb_precision_t precision, int anchors);
+cheb_status_t cheb_anneal_adjoint(int n, const double* h, const double* J, int S, const double* gamma_s,
+                                  const double* t_s, const void* boundaries, const void* psi_T,
+                                  void* grad, cheb_precision_t precision, double tol,
+                                  cheb_method_t method, double* grad_gamma, double* grad_t,
+                                  double* grad_h, double* grad_J, void* workspace,
+                                  size_t workspace_bytes, void* stream);
+cheb_status_t cheb_energy_grad(int n, const double* h, const double* J, const void* psi,
+                               void* grad_psi, cheb_precision_t precision, double* energy,
+                               double* grad_h, double* grad_J, void* workspace,
+                               size_t workspace_bytes, void* stream);
+
 /* Same as cheb_expmv with an explicit kernel path (cheb_path_t); used to time the
  * plain one-pass GPU path against the fused path. */
 cheb_status_t cheb_expmv_path(int n, const double* h, const double* J, double gamma, double t,

@@ -61,6 +61,11 @@ SIGNATURES = {
     "cheb_batched_workspace_bytes": (c_size_t, [c_int, _ip, c_int]),
     "cheb_expmv_batched": (c_int, [c_int, _ip, ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp, _dp, c_void_p, c_int,
                                    c_double, c_int, c_void_p, c_size_t, c_void_p, ctypes.POINTER(Info)]),
+    "cheb_adjoint_workspace_bytes": (c_size_t, [c_int, c_int, c_int]),
+    "cheb_anneal_adjoint": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, c_void_p, c_void_p, c_void_p, c_int, c_double,
+                                    c_int, _dp, _dp, _dp, _dp, c_void_p, c_size_t, c_void_p]),
+    "cheb_energy_grad": (c_int, [c_int, _dp, _dp, c_void_p, c_void_p, c_int, _dp, _dp, _dp, c_void_p, c_size_t,
+                                 c_void_p]),
     "cheb_launch_count": (ctypes.c_longlong, []),
     "cheb_profile_enable": (c_int, [c_int]),
     "cheb_profile_reset": (c_int, []),

@@ -200,6 +200,62 @@ def expmv_batched(ns, hs, Js, gammas, ts, psi_cat, offsets=None, tol: Optional[f
     return [x.as_dict() for x in infos] if info else None
 
 
+def _adjoint_workspace(n: int, prec: str, device, anchors: int):
+    import torch
+
+    need = int(_lib.lib().cheb_adjoint_workspace_bytes(n, PREC[prec], max(1, anchors)))
+    if need == 0:
+        raise ValueError(f"unsupported n={n}")
+    return torch.empty(need + 256, dtype=torch.uint8, device=device)
+
+
+def anneal_adjoint(h, J, gammas, ts, boundaries, psi_T, grad, tol: Optional[float] = None,
+                   method: str = "chebyshev", anchors: int = 16):
+    """Gradients of a loss on the final state of a schedule (see cheb_anneal_adjoint).
+
+    grad (CUDA tensor like psi_T) holds dL/dpsi_T on entry and dL/dpsi_0 on return.
+    Returns dict of numpy arrays: gamma (S), t (S), h (n), J (n x n, upper triangle)."""
+    h, J = _f64(h), _f64(J)
+    gammas, ts = _f64(gammas), _f64(ts)
+    n, S = h.shape[0], gammas.shape[0]
+    prec = precision_of(psi_T)
+    if tol is None:
+        tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+    for x in (boundaries, psi_T, grad):
+        if not x.is_cuda or not x.is_contiguous() or x.dtype != psi_T.dtype:
+            raise ValueError("boundaries, psi_T and grad must be contiguous CUDA tensors of one complex dtype")
+    ws = _adjoint_workspace(n, prec, psi_T.device, anchors)
+    p, nb = _ws_ptr(ws)
+    gg, gt, gh, gJ = np.zeros(S), np.zeros(S), np.zeros(n), np.zeros((n, n))
+    code = _lib.lib().cheb_anneal_adjoint(n, _dp(h), _dp(J), S, _dp(gammas), _dp(ts),
+                                          ctypes.c_void_p(boundaries.data_ptr()), ctypes.c_void_p(psi_T.data_ptr()),
+                                          ctypes.c_void_p(grad.data_ptr()), PREC[prec], float(tol), METHOD[method],
+                                          _dp(gg), _dp(gt), _dp(gh), _dp(gJ), ctypes.c_void_p(p), nb,
+                                          _stream_ptr(psi_T.device))
+    _lib.check(code, "cheb_anneal_adjoint")
+    return {"gamma": gg, "t": gt, "h": gh, "J": gJ}
+
+
+def energy_grad(h, J, psi):
+    """(energy, dL/dpsi = 2 H_P psi as a new tensor, dL/dh, dL/dJ) for L = <psi|H_P|psi>."""
+    import torch
+
+    h, J = _f64(h), _f64(J)
+    n = h.shape[0]
+    _check_state(psi, n)
+    prec = precision_of(psi)
+    ws = _adjoint_workspace(n, prec, psi.device, 1)
+    p, nb = _ws_ptr(ws)
+    g = torch.empty_like(psi)
+    e = ctypes.c_double()
+    gh, gJ = np.zeros(n), np.zeros((n, n))
+    code = _lib.lib().cheb_energy_grad(n, _dp(h), _dp(J), ctypes.c_void_p(psi.data_ptr()),
+                                       ctypes.c_void_p(g.data_ptr()), PREC[prec], ctypes.byref(e), _dp(gh), _dp(gJ),
+                                       ctypes.c_void_p(p), nb, _stream_ptr(psi.device))
+    _lib.check(code, "cheb_energy_grad")
+    return e.value, g, gh, gJ
+
+
 def poly_apply(h, J, gamma: float, center: float, radius: float, coeffs, psi, path: str = "auto"):
     """psi <- sum_m c_m T_m((H - center)/radius) psi in place on the GPU."""
     h, J = _f64(h), _f64(J)

@@ -1,0 +1,111 @@
+"""Reverse-Clenshaw gradients (cheb_anneal_adjoint, cheb_energy_grad) through the
+torch.autograd wrappers, against the FP64 oracle's exact Frechet-derivative
+gradients and against central finite differences of the GPU forward map."""
+import numpy as np
+import pytest
+
+from paper_2608_12058_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _params(h, J, gammas, ts):
+    import torch
+
+    t = lambda x: torch.tensor(np.asarray(x, dtype=np.float64), requires_grad=True)
+    return t(h), t(J), t(gammas), t(ts)
+
+
+def test_expmv_gradients_match_frechet_oracle(cuda_lib, oracle):
+    import torch
+
+    from paper_2608_12058_b300 import autograd as AG
+
+    n = 5
+    h, J = I.sk_instance(n, 21)
+    psi0 = I.random_state(n, 22)
+    gam, tt = 0.8, 1.3
+    ref = oracle.dense_energy_gradients(h, J, gam, tt, psi0)
+    th, tJ, tg, tT = _params(h, J, [gam], [tt])
+    x = torch.from_numpy(psi0).cuda().requires_grad_(True)
+    y = AG.anneal(x, th, tJ, tg, tT, tol=1e-13)
+    L = AG.energy(y, th, tJ)
+    L.backward()
+    assert abs(L.item() - ref["loss"]) < 1e-11
+    assert abs(tg.grad[0].item() - ref["gamma"]) < 1e-9 * max(1, abs(ref["gamma"]))
+    assert abs(tT.grad[0].item() - ref["t"]) < 1e-9 * max(1, abs(ref["t"]))
+    np.testing.assert_allclose(th.grad.numpy(), ref["h"], atol=1e-9)
+    np.testing.assert_allclose(np.triu(tJ.grad.numpy(), 1), np.triu(ref["J"], 1), atol=1e-9)
+    np.testing.assert_allclose(x.grad.cpu().numpy(), ref["psi0"], atol=1e-9)
+
+
+def _energy_after(h, J, gammas, ts, psi0, dtype):
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    x = torch.from_numpy(psi0).to(dtype).cuda()
+    api.anneal(h, J, gammas, ts, x, tol=1e-13 if dtype == torch.complex128 else 2.0 ** -23, info=False)
+    return api.energy(h, J, x)[0]
+
+
+@pytest.mark.parametrize("n,S", [(8, 4), (12, 3)])
+def test_anneal_gradients_vs_finite_differences(cuda_lib, n, S):
+    import torch
+
+    from paper_2608_12058_b300 import autograd as AG
+
+    a = I.config_anneal(n=n, S=S, seed=5)
+    psi0 = I.uniform_state(n)
+    th, tJ, tg, tT = _params(a.h, a.J, a.gammas, a.ts)
+    x = torch.from_numpy(psi0).cuda()
+    L = AG.energy(AG.anneal(x, th, tJ, tg, tT, tol=1e-13), th, tJ)
+    L.backward()
+    eps = 1e-5
+
+    def fd(mod):
+        hp, Jp, gp, tp = [np.array(v, dtype=np.float64) for v in (a.h, a.J, a.gammas, a.ts)]
+        hm, Jm, gm, tm = [np.array(v, dtype=np.float64) for v in (a.h, a.J, a.gammas, a.ts)]
+        mod(hp, Jp, gp, tp, +eps)
+        mod(hm, Jm, gm, tm, -eps)
+        return (_energy_after(hp, Jp, gp, tp, psi0, torch.complex128) -
+                _energy_after(hm, Jm, gm, tm, psi0, torch.complex128)) / (2 * eps)
+
+    for s in range(S):
+        def mg(h_, J_, g_, t_, e, s=s):
+            g_[s] += e
+        def mt(h_, J_, g_, t_, e, s=s):
+            t_[s] += e
+        assert abs(fd(mg) - tg.grad[s].item()) < 1e-6, ("gamma", s)
+        assert abs(fd(mt) - tT.grad[s].item()) < 1e-6, ("t", s)
+    for i in [0, n // 2, n - 1]:
+        def mh(h_, J_, g_, t_, e, i=i):
+            h_[i] += e
+        assert abs(fd(mh) - th.grad[i].item()) < 1e-6, ("h", i)
+    for (i, j) in [(0, 1), (1, n - 1), (n - 2, n - 1)]:
+        def mJ(h_, J_, g_, t_, e, i=i, j=j):
+            J_[i, j] += e
+        assert abs(fd(mJ) - tJ.grad[i, j].item()) < 1e-6, ("J", i, j)
+
+
+def test_fp32_adjoint_close_to_fp64(cuda_lib):
+    """The FP32 path (fused kernels forward, FP32 adjoint vectors, FP64 reductions)
+    agrees with the FP64 gradients to 1e-4 relative."""
+    import torch
+
+    from paper_2608_12058_b300 import autograd as AG
+
+    n, S = 15, 6
+    a = I.config_anneal(n=n, S=S, seed=9)
+    psi0 = I.uniform_state(n)
+    grads = {}
+    for dt in (torch.complex64, torch.complex128):
+        th, tJ, tg, tT = _params(a.h, a.J, a.gammas, a.ts)
+        x = torch.from_numpy(psi0).to(dt).cuda().requires_grad_(True)
+        L = AG.energy(AG.anneal(x, th, tJ, tg, tT), th, tJ)
+        L.backward()
+        grads[dt] = (tg.grad.numpy(), tT.grad.numpy(), th.grad.numpy(), tJ.grad.numpy(),
+                     x.grad.cpu().numpy().astype(np.complex128))
+    for k in range(5):
+        g32, g64 = grads[torch.complex64][k], grads[torch.complex128][k]
+        assert np.linalg.norm(g32 - g64) <= 1e-4 * np.linalg.norm(g64), k
