@@ -200,14 +200,21 @@ cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* offsets, co
  * ybar = 2y), the adjoint of the Clenshaw recurrence gives
  *   bbar_0 = ybar, bbar_1 = Ht bbar_0, bbar_k = 2 Ht bbar_{k-1} - bbar_{k-2},
  *   psibar = sum_k conj(c_k) bbar_k,
- *   dL = Re sum_{k<K} w_k <bbar_k, dHt b_{k+1}>  (w_0 = 1, w_k = 2),
- * with the forward vectors b_k regenerated upward from (b_1, b_2) and reset from
- * anchor checkpoints. The spectral interval (c, r) is held fixed (the exact
- * exp(-itH) does not depend on it); dL/dt_s uses the exact dy/dt = -i H y.
+ *   dL = Re sum_{k<K} w_k <bbar_k, dHt b_{k+1}>  (w_0 = 1, w_k = 2).
+ * The forward vectors b_k of each segment are recomputed from its start state and
+ * either all kept (workspace for K vectors) or regenerated upward from (b_1, b_2)
+ * and reset from anchor pairs. The spectral interval (c, r) is held fixed (the
+ * exact exp(-itH) does not depend on it); dL/dt_s uses the exact dy/dt = -i H y.
+ * The gamma derivative uses Ht b_{k+1} = (b_k + b_{k+2} - c_k psi)/2, so no extra
+ * operator applications are needed. The relative phase that round-off introduces
+ * between the adjoint and the stored forward states is removed per segment from the
+ * invariant <bbar_s, y_s> = <ybar_T, y_T>.
  *
- * cheb_adjoint_workspace_bytes(n, precision, anchors): workspace for
- *   cheb_anneal_adjoint with room for `anchors` checkpoint pairs (>= 1; more
- *   anchors = shorter upward regeneration; about sqrt(K) is plenty).
+ * cheb_adjoint_workspace_bytes(n, precision, store_vectors): workspace for
+ *   cheb_anneal_adjoint with a pool of `store_vectors` state vectors. A segment of
+ *   degree K keeps every b_k when store_vectors >= K; otherwise it needs
+ *   store_vectors >= 8 (a ring of 6 plus (store_vectors - 6)/2 anchor pairs).
+ *   store_vectors = 0 sizes the workspace of cheb_energy_grad.
  * cheb_anneal_adjoint:
  *   boundaries: DEVICE, the S segment-start states written by cheb_anneal.
  *   psi_T:      DEVICE, the final state.
@@ -217,11 +224,11 @@ cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* offsets, co
  *   strict upper triangle filled, rest zero): nullable outputs.
  *   S = 1 with boundaries = the input state is the gradient of one cheb_expmv.
  * cheb_energy_grad: L = <psi|H_P|psi> (FP64 reduction), grad_psi (DEVICE out) =
- *   2 H_P psi, grad_h, grad_J as above (HOST). Workspace as for the adjoint with
- *   anchors = 0 allowed.
- * Errors: INVALID_ARG, WORKSPACE, CUDA, TIMEOUT, UNSUPPORTED (time slicing needed).
+ *   2 H_P psi, grad_h, grad_J as above (HOST).
+ * Errors: INVALID_ARG, WORKSPACE (too small, or a segment with K > store_vectors
+ *   and store_vectors < 8), CUDA, TIMEOUT, UNSUPPORTED (time slicing needed).
  */
-size_t cheb_adjoint_workspace_bytes(int n, cheb_precision_t precision, int anchors);
+size_t cheb_adjoint_workspace_bytes(int n, cheb_precision_t precision, int store_vectors);
 cheb_status_t cheb_anneal_adjoint(int n, const double* h, const double* J, int S, const double* gamma_s,
                                   const double* t_s, const void* boundaries, const void* psi_T,
                                   void* grad, cheb_precision_t precision, double tol,
@@ -281,15 +288,18 @@ cheb_status_t cheb_energy(int n, const double* h, const double* J, const void* p
  * Instrumentation (no counterpart in the paper; used to attribute time).
  * cheb_launch_count: number of kernels this library has launched in this process
  *   (all devices, monotone).
- * cheb_profile_enable(1): from now on, bracket every Clenshaw step kernel with a
- *   pair of CUDA events on its stream (a few microseconds of overhead per step).
+ * cheb_profile_enable(1): from now on, bracket every Clenshaw step kernel and
+ *   every adjoint accumulation kernel with a pair of CUDA events on its stream (a
+ *   few microseconds of overhead per step).
  * cheb_profile_read(kind, count, total_ms): synchronises the recorded events and
  *   returns how many launches of that kind were timed and their summed device
  *   time. cheb_profile_reset drops the records.
- * Kinds: 3 plain one-pass step, 6 fused low pass, 7 fused high pass.
+ * Kinds: 3 plain one-pass step, 5 adjoint accumulation (cheb_anneal_adjoint),
+ * 6 fused low pass, 7 fused strided (high-bit) pass.
  */
 typedef enum {
     CHEB_KERNEL_STEP_PLAIN = 3,
+    CHEB_KERNEL_ADJOINT_ACC = 5,
     CHEB_KERNEL_FUSED_LOW = 6,
     CHEB_KERNEL_FUSED_HIGH = 7
 } cheb_kernel_kind_t;

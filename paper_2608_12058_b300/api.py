@@ -200,20 +200,47 @@ def expmv_batched(ns, hs, Js, gammas, ts, psi_cat, offsets=None, tol: Optional[f
     return [x.as_dict() for x in infos] if info else None
 
 
-def _adjoint_workspace(n: int, prec: str, device, anchors: int):
+def _adjoint_workspace(n: int, prec: str, device, store_vectors: int):
     import torch
 
-    need = int(_lib.lib().cheb_adjoint_workspace_bytes(n, PREC[prec], max(1, anchors)))
+    need = int(_lib.lib().cheb_adjoint_workspace_bytes(n, PREC[prec], max(0, store_vectors)))
     if need == 0:
         raise ValueError(f"unsupported n={n}")
     return torch.empty(need + 256, dtype=torch.uint8, device=device)
 
 
+def _degree_upper_bound(h, J, gammas, ts, tol: float, method: str) -> int:
+    """Largest Chebyshev degree over the segments, from the 1-norm bound of the spectral
+    radius (the library's r never exceeds it, and K grows with r)."""
+    n = h.shape[0]
+    half = float(np.sum(np.abs(h)) + np.sum(np.abs(np.triu(J, 1))))
+    tol_s = tol / gammas.shape[0]
+    kmax = 0
+    for g, t in zip(gammas, ts):
+        c, _ = coefficients(abs(float(t)) * (half + abs(float(g)) * n), tol_s, method)
+        kmax = max(kmax, c.shape[0] - 1)
+    return kmax
+
+
+def _auto_store_vectors(n: int, prec: str, device, kmax: int) -> int:
+    """Keep every b_k of a segment when that fits in half of the free device memory,
+    else a ring plus about sqrt(K) anchor pairs."""
+    import torch
+
+    vb = (1 << n) * (8 if prec == "fp32" else 16)
+    free, _ = torch.cuda.mem_get_info(device)
+    if (kmax + 1) * vb <= free // 2:
+        return kmax + 1
+    return 6 + 2 * max(1, int(np.ceil(np.sqrt(max(kmax, 1)))))
+
+
 def anneal_adjoint(h, J, gammas, ts, boundaries, psi_T, grad, tol: Optional[float] = None,
-                   method: str = "chebyshev", anchors: int = 16):
+                   method: str = "chebyshev", store_vectors: Optional[int] = None):
     """Gradients of a loss on the final state of a schedule (see cheb_anneal_adjoint).
 
     grad (CUDA tensor like psi_T) holds dL/dpsi_T on entry and dL/dpsi_0 on return.
+    store_vectors: state vectors of workspace for the Clenshaw vectors b_k (>= K keeps
+    all of them; fewer regenerates them from anchors; None chooses by free memory).
     Returns dict of numpy arrays: gamma (S), t (S), h (n), J (n x n, upper triangle)."""
     h, J = _f64(h), _f64(J)
     gammas, ts = _f64(gammas), _f64(ts)
@@ -224,7 +251,10 @@ def anneal_adjoint(h, J, gammas, ts, boundaries, psi_T, grad, tol: Optional[floa
     for x in (boundaries, psi_T, grad):
         if not x.is_cuda or not x.is_contiguous() or x.dtype != psi_T.dtype:
             raise ValueError("boundaries, psi_T and grad must be contiguous CUDA tensors of one complex dtype")
-    ws = _adjoint_workspace(n, prec, psi_T.device, anchors)
+    if store_vectors is None:
+        store_vectors = _auto_store_vectors(n, prec, psi_T.device,
+                                            _degree_upper_bound(h, J, gammas, ts, tol, method))
+    ws = _adjoint_workspace(n, prec, psi_T.device, store_vectors)
     p, nb = _ws_ptr(ws)
     gg, gt, gh, gJ = np.zeros(S), np.zeros(S), np.zeros(n), np.zeros((n, n))
     code = _lib.lib().cheb_anneal_adjoint(n, _dp(h), _dp(J), S, _dp(gammas), _dp(ts),
@@ -244,7 +274,7 @@ def energy_grad(h, J, psi):
     n = h.shape[0]
     _check_state(psi, n)
     prec = precision_of(psi)
-    ws = _adjoint_workspace(n, prec, psi.device, 1)
+    ws = _adjoint_workspace(n, prec, psi.device, 0)
     p, nb = _ws_ptr(ws)
     g = torch.empty_like(psi)
     e = ctypes.c_double()
@@ -283,7 +313,7 @@ def get_fused_split(n: int):
     return l.value, h.value
 
 
-KERNEL_KIND = {"plain": 3, "low": 6, "high": 7}
+KERNEL_KIND = {"plain": 3, "adjoint_acc": 5, "low": 6, "high": 7}
 
 
 def launch_count() -> int:
@@ -300,7 +330,8 @@ def profile_reset():
 
 
 def profile_read(kind: str):
-    """(launches timed, total device ms) for 'plain', 'low' or 'high' step kernels."""
+    """(launches timed, total device ms) for 'plain', 'low' or 'high' step kernels or
+    'adjoint_acc' (the adjoint's per-step accumulation)."""
     c, ms = ctypes.c_longlong(), ctypes.c_double()
     _lib.check(_lib.lib().cheb_profile_read(KERNEL_KIND[kind], ctypes.byref(c), ctypes.byref(ms)),
                "cheb_profile_read")

@@ -23,23 +23,23 @@ def _np(x):
 
 class AnnealFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, psi0, h, J, gammas, ts, tol, method, anchors):
+    def forward(ctx, psi0, h, J, gammas, ts, tol, method, store_vectors):
         hn, Jn, gn, tn = _np(h), _np(J), _np(gammas), _np(ts)
         S = gn.shape[0]
         y = psi0.detach().clone().contiguous()
         bnd = torch.empty((S, y.numel()), dtype=y.dtype, device=y.device)
         api.anneal(hn, Jn, gn, tn, y, tol=tol, method=method, boundaries=bnd, info=False)
         ctx.save_for_backward(bnd, y)
-        ctx.params = (hn, Jn, gn, tn, tol, method, anchors)
+        ctx.params = (hn, Jn, gn, tn, tol, method, store_vectors)
         ctx.dev = (h.device, J.device, gammas.device, ts.device)
         return y
 
     @staticmethod
     def backward(ctx, grad_out):
         bnd, y = ctx.saved_tensors
-        hn, Jn, gn, tn, tol, method, anchors = ctx.params
+        hn, Jn, gn, tn, tol, method, store_vectors = ctx.params
         g = grad_out.detach().to(y.dtype).contiguous().clone()
-        out = api.anneal_adjoint(hn, Jn, gn, tn, bnd, y, g, tol=tol, method=method, anchors=anchors)
+        out = api.anneal_adjoint(hn, Jn, gn, tn, bnd, y, g, tol=tol, method=method, store_vectors=store_vectors)
         dh = torch.from_numpy(out["h"]).to(ctx.dev[0])
         dJ = torch.from_numpy(out["J"]).to(ctx.dev[1])
         dg = torch.from_numpy(out["gamma"]).to(ctx.dev[2])
@@ -63,15 +63,15 @@ class EnergyFn(torch.autograd.Function):
         return g * s, gh * s, gJ * s
 
 
-def anneal(psi0, h, J, gammas, ts, tol=None, method="chebyshev", anchors=16):
-    return AnnealFn.apply(psi0, h, J, gammas, ts, tol, method, anchors)
+def anneal(psi0, h, J, gammas, ts, tol=None, method="chebyshev", store_vectors=None):
+    return AnnealFn.apply(psi0, h, J, gammas, ts, tol, method, store_vectors)
 
 
-def expmv(psi0, h, J, gamma, t, tol=None, method="chebyshev", anchors=16):
+def expmv(psi0, h, J, gamma, t, tol=None, method="chebyshev", store_vectors=None):
     """Differentiable exp(-i t H) psi0 (a one-segment schedule)."""
     g = gamma.reshape(1) if isinstance(gamma, torch.Tensor) else torch.tensor([float(gamma)], dtype=torch.float64)
     tt = t.reshape(1) if isinstance(t, torch.Tensor) else torch.tensor([float(t)], dtype=torch.float64)
-    return AnnealFn.apply(psi0, h, J, g, tt, tol, method, anchors)
+    return AnnealFn.apply(psi0, h, J, g, tt, tol, method, store_vectors)
 
 
 def energy(psi, h, J):

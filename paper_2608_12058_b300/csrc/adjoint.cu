@@ -10,12 +10,21 @@
 // With Ht = D + g sum_j X_j, D = (E - c)/r, g = gamma/r, and the spectral interval
 // (c, r) held fixed (the exact exp(-itH) does not depend on it):
 //   dL/dD(z)  = G(z) = Re sum_k w_k conj(bbar_k(z)) b_{k+1}(z),
-//   dL/dgamma = (1/r) Re sum_k w_k <bbar_k, (sum_j X_j) b_{k+1}>,
+//   dL/dgamma = (1/r) Re sum_k w_k <bbar_k, (sum_j X_j) b_{k+1}>
+//             = (1/gamma) Re sum_k w_k <bbar_k, (Ht - D) b_{k+1}>,
 //   dL/dh_i   = (1/r) sum_z G(z) s_i(z),  dL/dJ_ij = (1/r) sum_z G(z) s_i(z) s_j(z),
 //   dL/dt     = Im <ybar, H y>            (from dy/dt = -i H y).
+// Ht b_{k+1} needs no matvec: the recurrence itself gives
+//   Ht b_{k+1} = (b_{k+2} + b_k - c_k psi)/2 (k >= 1),  Ht b_1 = y + b_2 - c_0 psi.
 // The b_k are needed in increasing k while the forward produces them decreasing;
 // they are regenerated upward, b_{k+2} = 2 Ht b_{k+1} - b_k + c_k psi, from (b_1, b_2),
-// and reset every C steps from anchor pairs saved by a forward recomputation.
+// and reset every C steps from anchor pairs saved by a forward recomputation. Both
+// recurrences run on the same step kernels as the forward pass.
+//
+// Round-off gauge: <bbar_s, y_s> = <ybar_T, y_T> holds exactly for every segment s
+// (it is <P^H a, b> = <a, P b>). In FP32 the adjoint chain and the stored forward
+// states drift in relative phase; that drift is measured from the invariant and
+// removed by rotating ybar at the start of each segment (and the returned psibar).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,7 +57,7 @@ __device__ __forceinline__ int64_t energy_fx(int M, const int64_t* __restrict__ 
 
 constexpr int kAdjThreads = 256;
 
-// Block-level FP64 sum into slot[blockIdx.x] (accumulated, fixed order).
+// Block-level FP64 sum of v, added into slot[blockIdx.x] (fixed order).
 __device__ __forceinline__ void block_accumulate(double v, double* slot) {
     __shared__ double red[kAdjThreads];
     red[threadIdx.x] = v;
@@ -58,126 +67,207 @@ __device__ __forceinline__ void block_accumulate(double v, double* slot) {
         __syncthreads();
     }
     if (threadIdx.x == 0) slot[blockIdx.x] += red[0];
+    __syncthreads();
 }
 
-struct AdjArgs {
-    int n, M, Q;
-    const int64_t* tiles;
-    const int64_t* elow;
-    double g;            // gamma / r
-    double inv_r;        // 1 / r (G is accumulated already divided by r)
-    // adjoint chain
-    const void* bb1;     // bbar_{k-1}
-    void* bb2;           // in: bbar_{k-2}; out: bbar_k
-    double alpha, beta;  // bbar_k = alpha * Ht bbar_{k-1} - beta * bbar_{k-2}
-    void* psibar;        // += conj(c_k) bbar_k
-    double cc_re, cc_im; // conj(c_k)
-    // forward regeneration
-    const void* f1;      // b_{k+1}
-    void* f0;            // in: b_k; out: b_{k+2} (when regen)
+// Error-free transformations (Knuth's TwoSum, FMA-based TwoProduct) for the FP32
+// path: a state concentrated on a few basis states makes per-element rounding add
+// up coherently, so the products and sums below keep their rounding errors.
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// s + c += a * b, with the rounding error of the product and of the sum kept in c.
+__device__ __forceinline__ void dot2_step(float a, float b, float& s, float& c) {
+    const float p = a * b;
+    const float ep = fmaf(a, b, -p);
+    float t, es;
+    two_sum(s, p, t, es);
+    s = t;
+    c += ep + es;
+}
+__device__ __forceinline__ FF ff_add(FF x, float yh, float yl) {
+    float s, e;
+    two_sum(x.h, yh, s, e);
+    e += x.l + yl;
+    FF r;
+    r.h = s + e;
+    r.l = e - (r.h - s);
+    return r;
+}
+
+// Elementwise work of up to kAccBatch consecutive adjoint steps k = k0 .. k0+m-1
+// (every constant that would scale all elements alike - the gauge phase, 1/r - is
+// applied in FP64 per segment):
+//   psibar (+)= conj(c_k) bbar_k                      (mode 1 add, 2 set)
+//   Gs     += w_k Re(conj(bbar_k) b_{k+1})            (pair: w_k != 0, i.e. k < K)
+//   hsum   += Re(conj(bbar_k) (b_k + b_{k+2} - c_k psi))   (pair; w_k hs = 1 for every k)
+// with b_0 := y (the segment's output) and b_{K+1} := 0, so that
+// hsum - sum_z D(z) Gs(z) = sum_k w_k Re <bbar_k, (Ht - D) b_{k+1}>, since
+// Ht b_{k+1} = hs (b_k + b_{k+2} - c_k psi) (hs = 1/2, and 1 at k = 0). c_k is used
+// as the step kernels hold it. Batching the steps reads each b_j, psi, psibar and
+// Gs once per batch instead of once per step.
+// FP32: Gs is a float-float pair per element and the products are compensated.
+constexpr int kAccBatch = 4;
+struct AccArgs {
+    int n, m, mode;
+    const void* bbar[kAccBatch];    // bbar_{k0+i}
+    const void* fb[kAccBatch + 2];  // b_{k0+j}; nullptr = the zero vector
     const void* psi;
-    double ck_re, ck_im; // c_k
-    int regen;           // produce b_{k+2}
-    int pair;            // accumulate the k-th gradient terms (k <= K-1)
-    double w;            // w_k
-    double* G;           // FP64 per element
-    double* dg_slots;    // per-block FP64 accumulators of Re<bbar_k, A b_{k+1}>
+    void* psibar;
+    void* Gs;
+    double* slots;
+    double cc_re[kAccBatch], cc_im[kAccBatch];  // conj(c_{k0+i})
+    double w[kAccBatch];                         // w_k, 0 when k = K (no pair)
 };
 
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_step(AdjArgs a) {
-    using C = typename Cx<R>::T;
+__global__ void __launch_bounds__(kAdjThreads) k_adj_acc(AccArgs a);
+
+template <>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_acc<float>(AccArgs a) {
     const int64_t N = (int64_t)1 << a.n;
-    const C* bb1 = (const C*)a.bb1;
-    C* bb2 = (C*)a.bb2;
-    const C* f1 = (const C*)a.f1;
-    C* f0 = (C*)a.f0;
-    const C* psi = (const C*)a.psi;
-    C* pb = (C*)a.psibar;
-    const double sc = ldexp(1.0, -a.Q);
-    double dg = 0.0;
+    const float2* psi = (const float2*)a.psi;
+    float2* pb = (float2*)a.psibar;
+    float2* Gs = (float2*)a.Gs;
+    bool any_pair = false;
+#pragma unroll
+    for (int i = 0; i < kAccBatch; ++i) any_pair |= (i < a.m) && a.w[i] != 0.0;
+    FF hs{0.f, 0.f};
     for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
-        const double D = __ll2double_rn(energy_fx(a.M, a.tiles, a.elow, (uint64_t)z)) * sc;
-        // flip sums of bbar_{k-1} and b_{k+1}
-        double sax = 0, say = 0, sbx = 0, sby = 0;
-        for (int j = 0; j < a.n; ++j) {
-            const int64_t zp = z ^ ((int64_t)1 << j);
-            const C u = bb1[zp];
-            const C v = f1[zp];
-            sax += u.x;
-            say += u.y;
-            sbx += v.x;
-            sby += v.y;
+        float2 f[kAccBatch + 2];
+#pragma unroll
+        for (int j = 0; j < kAccBatch + 2; ++j)
+            f[j] = (j < a.m + 2 && a.fb[j]) ? ((const float2*)a.fb[j])[z] : make_float2(0.f, 0.f);
+        float2 p = a.mode == 1 ? pb[z] : make_float2(0.f, 0.f);
+        const float2 ps = psi[z];
+        float gs = 0.f, gc = 0.f;   // sum_i w_i Re(conj(u_i) b_{k+1}), compensated
+        float ts = 0.f, tc = 0.f;   // sum_i Re(conj(u_i) (b_k + b_{k+2} - c_k psi)), compensated
+#pragma unroll
+        for (int i = 0; i < kAccBatch; ++i) {
+            if (i >= a.m) break;
+            const float2 u = ((const float2*)a.bbar[i])[z];
+            const float cr = (float)a.cc_re[i], ci = (float)a.cc_im[i];
+            p.x += cr * u.x - ci * u.y;
+            p.y += cr * u.y + ci * u.x;
+            if (a.w[i] != 0.0) {
+                const float w = (float)a.w[i];
+                dot2_step(w * u.x, f[i + 1].x, gs, gc);
+                dot2_step(w * u.y, f[i + 1].y, gs, gc);
+                // c_k psi with c_k = conj(cc): (cr x + ci y, cr y - ci x), as hi + lo
+                float qx = 0.f, qxl = 0.f, qy = 0.f, qyl = 0.f;
+                dot2_step(cr, ps.x, qx, qxl);
+                dot2_step(ci, ps.y, qx, qxl);
+                dot2_step(cr, ps.y, qy, qyl);
+                dot2_step(-ci, ps.x, qy, qyl);
+                dot2_step(u.x, f[i].x, ts, tc);
+                dot2_step(u.y, f[i].y, ts, tc);
+                dot2_step(u.x, f[i + 2].x, ts, tc);
+                dot2_step(u.y, f[i + 2].y, ts, tc);
+                dot2_step(-u.x, qx, ts, tc);
+                dot2_step(-u.y, qy, ts, tc);
+                tc -= u.x * qxl + u.y * qyl;
+            }
         }
-        const C u = bb1[z];
-        const C v = f1[z];
-        double ox = 0.0, oy = 0.0;
-        if (a.beta != 0.0) {  // the first step has no bbar_{k-2}; its slot holds stale data
-            const C old = bb2[z];
-            ox = old.x;
-            oy = old.y;
-        }
-        // bbar_k
-        double nx = a.alpha * (D * u.x + a.g * sax) - a.beta * ox;
-        double ny = a.alpha * (D * u.y + a.g * say) - a.beta * oy;
-        C nb;
-        nb.x = (R)nx;
-        nb.y = (R)ny;
-        bb2[z] = nb;
-        nx = nb.x;
-        ny = nb.y;
-        // psibar += conj(c_k) bbar_k
-        C p = pb[z];
-        p.x = (R)(p.x + a.cc_re * nx - a.cc_im * ny);
-        p.y = (R)(p.y + a.cc_re * ny + a.cc_im * nx);
         pb[z] = p;
-        if (a.pair) {
-            // Re(conj(bbar_k) b_{k+1}) and Re(conj(bbar_k) (A b_{k+1}))
-            a.G[z] += a.w * a.inv_r * (nx * v.x + ny * v.y);
-            dg += a.w * (nx * sbx + ny * sby);
-        }
-        if (a.regen) {
-            const C w0 = f0[z];
-            const C ps = psi[z];
-            C nf;
-            nf.x = (R)(2.0 * (D * v.x + a.g * sbx) - w0.x + a.ck_re * ps.x - a.ck_im * ps.y);
-            nf.y = (R)(2.0 * (D * v.y + a.g * sby) - w0.y + a.ck_re * ps.y + a.ck_im * ps.x);
-            f0[z] = nf;
+        if (any_pair) {
+            const float2 go = Gs[z];
+            FF g{go.x, go.y};
+            g = ff_add(g, gs, gc);
+            Gs[z] = make_float2(g.h, g.l);
+            hs = ff_add(hs, ts, tc);
         }
     }
-    if (a.pair) block_accumulate(dg, a.dg_slots);
+    if (any_pair) block_accumulate((double)hs.h + (double)hs.l, a.slots);
 }
 
-// k = 0 terms: psibar = conj(c_0) ybar, G += (1/r) Re(conj(ybar) b_1),
-// dg += Re(conj(ybar) A b_1).
+template <>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_acc<double>(AccArgs a) {
+    const int64_t N = (int64_t)1 << a.n;
+    const double2* psi = (const double2*)a.psi;
+    double2* pb = (double2*)a.psibar;
+    double* Gs = (double*)a.Gs;
+    bool any_pair = false;
+#pragma unroll
+    for (int i = 0; i < kAccBatch; ++i) any_pair |= (i < a.m) && a.w[i] != 0.0;
+    double hsum = 0.0;
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
+        double2 f[kAccBatch + 2];
+#pragma unroll
+        for (int j = 0; j < kAccBatch + 2; ++j)
+            f[j] = (j < a.m + 2 && a.fb[j]) ? ((const double2*)a.fb[j])[z] : make_double2(0.0, 0.0);
+        double2 p = a.mode == 1 ? pb[z] : make_double2(0.0, 0.0);
+        const double2 ps = psi[z];
+        double g = 0.0;
+#pragma unroll
+        for (int i = 0; i < kAccBatch; ++i) {
+            if (i >= a.m) break;
+            const double2 u = ((const double2*)a.bbar[i])[z];
+            const double cr = a.cc_re[i], ci = a.cc_im[i];
+            p.x += cr * u.x - ci * u.y;
+            p.y += cr * u.y + ci * u.x;
+            if (a.w[i] != 0.0) {
+                g += a.w[i] * (u.x * f[i + 1].x + u.y * f[i + 1].y);
+                const double sx = f[i].x + f[i + 2].x - (cr * ps.x + ci * ps.y);
+                const double sy = f[i].y + f[i + 2].y - (cr * ps.y - ci * ps.x);
+                hsum += u.x * sx + u.y * sy;
+            }
+        }
+        pb[z] = p;
+        if (any_pair) Gs[z] += g;
+    }
+    if (any_pair) block_accumulate(hsum, a.slots);
+}
+
+// End of a segment: G(z) += Gs(z)/r (FP64) and slots += sum_z D(z) Gs(z), with
+// D = (E - c)/r from the segment's fixed-point tables. Gs is a float-float pair
+// (FP32 path) or a double.
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_init(AdjArgs a) {
-    using C = typename Cx<R>::T;
-    const int64_t N = (int64_t)1 << a.n;
-    const C* yb = (const C*)a.bb1;
-    const C* b1 = (const C*)a.f1;
-    C* pb = (C*)a.psibar;
-    double dg = 0.0;
+__global__ void __launch_bounds__(kAdjThreads) k_fold(int n, int M, int Q, const int64_t* tiles, const int64_t* elow,
+                                                      const R* __restrict__ Gs, double inv_r, double* G,
+                                                      double* slots) {
+    const int64_t N = (int64_t)1 << n;
+    const double sc = ldexp(1.0, -Q);
+    constexpr int kW = sizeof(R) == 4 ? 2 : 1;
+    double acc = 0.0;
     for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
-        double sbx = 0, sby = 0;
-        for (int j = 0; j < a.n; ++j) {
-            const C v = b1[z ^ ((int64_t)1 << j)];
-            sbx += v.x;
-            sby += v.y;
-        }
-        const C y = yb[z];
-        const C v = b1[z];
-        C p;
-        p.x = (R)(a.cc_re * y.x - a.cc_im * y.y);
-        p.y = (R)(a.cc_re * y.y + a.cc_im * y.x);
-        pb[z] = p;
-        a.G[z] += a.inv_r * ((double)y.x * v.x + (double)y.y * v.y);
-        dg += (double)y.x * sbx + (double)y.y * sby;
+        double g = (double)Gs[kW * z];
+        if (kW == 2) g += (double)Gs[kW * z + 1];
+        acc += __ll2double_rn(energy_fx(M, tiles, elow, (uint64_t)z)) * sc * g;
+        G[z] += g * inv_r;
     }
-    block_accumulate(dg, a.dg_slots);
+    block_accumulate(acc, slots);
 }
 
-// Im <ybar, H y> with H = diag(E) + gamma sum_j X_j, E = c + r D.
+// Fallback for gamma = 0, where (Ht - D)/gamma is not available: the flip sums of
+// b_{k+1} are formed explicitly; slots += w Re(conj(bbar_k) sum_j X_j b_{k+1}).
+template <typename R>
+__global__ void __launch_bounds__(kAdjThreads) k_dg_flip(int n, const void* bbar_v, const void* f1_v, double w,
+                                                        double* slots) {
+    using C = typename Cx<R>::T;
+    const int64_t N = (int64_t)1 << n;
+    const C* bb = (const C*)bbar_v;
+    const C* f1 = (const C*)f1_v;
+    double dg = 0.0;
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
+        double sx = 0, sy = 0;
+        for (int j = 0; j < n; ++j) {
+            const C v = f1[z ^ ((int64_t)1 << j)];
+            sx += v.x;
+            sy += v.y;
+        }
+        const C u = bb[z];
+        dg += w * ((double)u.x * sx + (double)u.y * sy);
+    }
+    block_accumulate(dg, slots);
+}
+
+// <ybar, H y> and <ybar, y> (complex), H = diag(E) + gamma sum_j X_j, E = c + r D:
+// slots[0..3] x kRedBlocks = Re, Im of each.
 template <typename R>
 __global__ void __launch_bounds__(kAdjThreads) k_dt(int n, int M, int Q, const int64_t* tiles, const int64_t* elow,
                                                     double c, double r, double gamma, const void* ybar_v,
@@ -187,7 +277,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_dt(int n, int M, int Q, const i
     const C* yb = (const C*)ybar_v;
     const C* y = (const C*)y_v;
     const double sc = ldexp(1.0, -Q);
-    double acc = 0.0;
+    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
     for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
         const double E = c + r * (__ll2double_rn(energy_fx(M, tiles, elow, (uint64_t)z)) * sc);
         double sx = 0, sy = 0;
@@ -199,9 +289,32 @@ __global__ void __launch_bounds__(kAdjThreads) k_dt(int n, int M, int Q, const i
         const C v = y[z];
         const double hx = E * v.x + gamma * sx, hy = E * v.y + gamma * sy;
         const C u = yb[z];
-        acc += (double)u.x * hy - (double)u.y * hx;  // Im(conj(u) * h)
+        ar += (double)u.x * hx + (double)u.y * hy;
+        ai += (double)u.x * hy - (double)u.y * hx;
+        br += (double)u.x * v.x + (double)u.y * v.y;
+        bi += (double)u.x * v.y - (double)u.y * v.x;
     }
-    block_accumulate(acc, slots);
+    block_accumulate(ar, slots);
+    block_accumulate(ai, slots + kRedBlocks);
+    block_accumulate(br, slots + 2 * kRedBlocks);
+    block_accumulate(bi, slots + 3 * kRedBlocks);
+}
+
+// <a, b> (complex) into slots[0..1] x kRedBlocks.
+template <typename R>
+__global__ void __launch_bounds__(kAdjThreads) k_dot(int n, const void* a_v, const void* b_v, double* slots) {
+    using C = typename Cx<R>::T;
+    const int64_t N = (int64_t)1 << n;
+    const C* a = (const C*)a_v;
+    const C* b = (const C*)b_v;
+    double re = 0.0, im = 0.0;
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
+        const C u = a[z], v = b[z];
+        re += (double)u.x * v.x + (double)u.y * v.y;
+        im += (double)u.x * v.y - (double)u.y * v.x;
+    }
+    block_accumulate(re, slots);
+    block_accumulate(im, slots + kRedBlocks);
 }
 
 // Loss L = <psi|H_P|psi>: grad = 2 E psi; G += |psi|^2 (weight 1); value in slots.
@@ -265,17 +378,20 @@ __global__ void __launch_bounds__(kAdjThreads) k_grad_reduce(int n, const double
     if (threadIdx.x == 0) out[blockIdx.x] = red[0];
 }
 
-__global__ void k_sum_slots(const double* slots, int nb, double* out) {
+__global__ void k_sum_slots(const double* slots, int nb, int count, double* out) {
     __shared__ double red[256];
-    double a = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) a += slots[b];
-    red[threadIdx.x] = a;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    for (int q = 0; q < count; ++q) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) a += slots[q * kRedBlocks + b];
+        red[threadIdx.x] = a;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[q] = red[0];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = red[0];
 }
 
 unsigned grid_n(int64_t N) {
@@ -283,12 +399,16 @@ unsigned grid_n(int64_t N) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, kRedBlocks));
 }
 
-// Workspace of the adjoint: the forward layout, then 4 state vectors (bbar pair,
-// psibar, scratch), G (FP64 per element), anchors, gradient outputs.
+// Workspace of the adjoint: the forward layout (whose two Clenshaw vectors start the
+// ring of adjoint vectors), four more ring vectors, G (FP64 per element), Gs (8 bytes
+// per element), reduction slots, gradient outputs, then a pool of state vectors that
+// holds either every b_k of a segment or a ring of 6 plus anchor pairs.
+constexpr int kRing = kAccBatch + 2;
 struct AdjLayout {
     Layout fwd;
-    size_t bb0, bb1, pbar, tmp, G, slots, outs, anchors;
-    size_t per_anchor;
+    size_t ring[kRing];
+    size_t G, Gs, slots, outs, pool;
+    size_t vstride;
     size_t total_fixed;
 };
 
@@ -298,44 +418,51 @@ AdjLayout adj_layout(int n, int prec) {
     AdjLayout A;
     A.fwd = make_layout(n, prec);
     const size_t vb = ((size_t)1 << n) * A.fwd.cbytes;
+    A.vstride = a256(vb);
     size_t off = a256(A.fwd.total);
-    A.bb0 = off;
-    off = a256(off + vb);
-    A.bb1 = off;
-    off = a256(off + vb);
-    A.pbar = off;
-    off = a256(off + vb);
-    A.tmp = off;
-    off = a256(off + vb);
+    A.ring[0] = A.fwd.b0;
+    A.ring[1] = A.fwd.b1;
+    for (int i = 2; i < kRing; ++i) {
+        A.ring[i] = off;
+        off += A.vstride;
+    }
     A.G = off;
     off = a256(off + ((size_t)1 << n) * sizeof(double));
+    A.Gs = off;
+    off = a256(off + ((size_t)1 << n) * 8);  // float-float (FP32) or double (FP64)
     A.slots = off;
     off = a256(off + 4 * (size_t)kRedBlocks * sizeof(double));
     A.outs = off;
-    off = a256(off + ((size_t)n * n + n + 8) * sizeof(double));
-    A.anchors = off;
-    A.per_anchor = 2 * a256(vb);
+    off = a256(off + ((size_t)n * n + n + 16) * sizeof(double));
+    A.pool = off;
     A.total_fixed = off;
     return A;
 }
 
-template <typename R>
-cudaError_t launch_adj_step(const AdjArgs& a, cudaStream_t s) {
-    note_launch(kKindReduce);
-    k_adj_step<R><<<grid_n((int64_t)1 << a.n), kAdjThreads, 0, s>>>(a);
-    return cudaGetLastError();
-}
+// One Clenshaw-form step out = scale (D b1 + g sum_j X_j b1) + sgn b2 + ck psi on the
+// fastest kernel available for (n, precision).
+struct StepRunner {
+    bool fused = false;
+    FusedPlan plan;
+    int prec = 0;
+    int* flags = nullptr;
+    cudaError_t run(const StepArgs& a, cudaStream_t s) const {
+        if (fused) return launch_step_fused(plan, a, nullptr, flags, s);
+        launch_step_plain(prec, a, s);
+        return cudaGetLastError();
+    }
+};
 
 }  // namespace
 }  // namespace cheb
 
 using namespace cheb;
 
-extern "C" size_t cheb_adjoint_workspace_bytes(int n, cheb_precision_t precision, int anchors) {
-    if (n < 1 || n > kMaxQubits || anchors < 1) return 0;
+extern "C" size_t cheb_adjoint_workspace_bytes(int n, cheb_precision_t precision, int store_vectors) {
+    if (n < 1 || n > kMaxQubits || store_vectors < 0) return 0;
     if (precision != CHEB_FP32 && precision != CHEB_FP64) return 0;
     AdjLayout A = adj_layout(n, precision);
-    return A.total_fixed + (size_t)anchors * A.per_anchor;
+    return A.total_fixed + (size_t)store_vectors * A.vstride;
 }
 
 // Gradient of a loss on the output of a schedule (S = 1: a single exp(-itH) psi).
@@ -354,13 +481,14 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
     if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF) return CHEB_ERR_INVALID_ARG;
     if (((uintptr_t)boundaries | (uintptr_t)psi_T | (uintptr_t)grad) & 15) return CHEB_ERR_INVALID_ARG;
     AdjLayout A = adj_layout(n, precision);
-    if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < A.total_fixed + A.per_anchor) return CHEB_ERR_WORKSPACE;
-    const int max_anchors = (int)std::min<size_t>((ws_bytes - A.total_fixed) / A.per_anchor, 1 << 20);
+    if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < A.total_fixed) return CHEB_ERR_WORKSPACE;
+    const int64_t nvec = (int64_t)std::min<size_t>((ws_bytes - A.total_fixed) / A.vstride, 1 << 20);
     unsigned char* ws = (unsigned char*)workspace;
     cudaStream_t s0 = (cudaStream_t)stream;
     Ctx C{n, precision, A.fwd, ws, s0};
     const int64_t N = (int64_t)1 << n;
     const size_t vb = (size_t)N * A.fwd.cbytes;
+    const unsigned gb = grid_n(N);
     CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), s0));
     CUDA_TRY(cudaMemsetAsync(ws + A.G, 0, (size_t)N * sizeof(double), s0));
     double emin = 0, emax = 0;
@@ -370,12 +498,17 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
     const double tol_s = tol / S;
     double* slots = (double*)(ws + A.slots);
     double* outs = (double*)(ws + A.outs);
-    unsigned char* B0 = ws + A.fwd.b0;
-    unsigned char* B1 = ws + A.fwd.b1;
-    unsigned char* BB[2] = {ws + A.bb0, ws + A.bb1};
-    unsigned char* pbar = ws + A.pbar;
+    unsigned char* pool = ws + A.pool;
+    unsigned char* Gs = ws + A.Gs;
+    auto ring = [&](int k) { return ws + A.ring[k % kRing]; };  // bbar_k
     std::vector<double> gg(S), gt(S);
     const int Mt = A.fwd.M;
+    StepRunner runner;
+    runner.prec = precision;
+    runner.flags = C.flags();
+    runner.fused = fused_supported(n, precision) && n > (precision == CHEB_FP32 ? kSmallMaxF32 : kSmallMaxF64);
+    if (runner.fused) runner.plan = fused_plan(n, precision);
+    std::complex<double> BT(0.0, 0.0);
     for (int s = S - 1; s >= 0; --s) {
         double r = 0.5 * (emax - emin) + std::fabs(gamma_s[s]) * n;
         if (!(r > 0)) r = 1.0;
@@ -392,17 +525,25 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
         if (slices != 1) return CHEB_ERR_UNSUPPORTED;
         const void* psi_s = (const unsigned char*)boundaries + (size_t)s * vb;
         const void* y_s = (s == S - 1) ? psi_T : (const unsigned char*)boundaries + (size_t)(s + 1) * vb;
-        // dt_s = Im <ybar, H_s y_s>
+        // <ybar, H y_s> and the gauge invariant <ybar, y_s>
+        double theta = 0.0;
         {
-            CUDA_TRY(cudaMemsetAsync(slots, 0, kRedBlocks * sizeof(double), s0));
-            const unsigned gb = grid_n(N);
+            CUDA_TRY(cudaMemsetAsync(slots, 0, 4 * kRedBlocks * sizeof(double), s0));
             note_launch(kKindReduce);
             if (precision == CHEB_FP32)
                 k_dt<float><<<gb, kAdjThreads, 0, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), c, r, gamma_s[s], grad, y_s, slots);
             else
                 k_dt<double><<<gb, kAdjThreads, 0, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), c, r, gamma_s[s], grad, y_s, slots);
-            k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, outs + 0);
-            CUDA_TRY(cudaMemcpyAsync(&gt[s], outs + 0, sizeof(double), cudaMemcpyDeviceToHost, s0));
+            k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 4, outs);
+            double v4[4];
+            CUDA_TRY(cudaMemcpyAsync(v4, outs, sizeof(v4), cudaMemcpyDeviceToHost, s0));
+            CUDA_TRY(cudaStreamSynchronize(s0));
+            const std::complex<double> Ah(v4[0], v4[1]), Bs(v4[2], v4[3]);
+            if (s == S - 1) BT = Bs;
+            if (std::abs(BT) > 1e-300 && std::abs(Bs) > 1e-300) theta = std::arg(BT) - std::arg(Bs);
+            gt[s] = (std::polar(1.0, theta) * Ah).imag();
+            // the gauge moves into ybar: Re(e^{i th} conj(u) x) = Re(conj(e^{-i th} u) x)
+            if (theta != 0.0) launch_scale(precision, N, grad, grad, std::cos(theta), -std::sin(theta), s0);
         }
         if (K == 0) {
             // y = c_0 psi: psibar = conj(c_0) ybar, no operator dependence
@@ -410,127 +551,163 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
             gg[s] = 0.0;
             continue;
         }
-        // forward recomputation from psi_s down to (b_1, b_2), saving anchor pairs
-        const int C_gap = std::max(1, (K - 1 + max_anchors - 1) / max_anchors);
-        std::vector<int> anchor_k;  // anchors store (b_k, b_{k+1}) for k = 1 + m*C_gap < K
-        for (int k = 1; k < K; k += C_gap) anchor_k.push_back(k);
-        if ((int)anchor_k.size() > max_anchors) return CHEB_ERR_WORKSPACE;
-        unsigned char* Bv[2] = {B0, B1};
-        launch_scale(precision, N, psi_s, Bv[1], coef[K].real(), coef[K].imag(), s0);  // b_K
-        int cur = 1;
-        FusedPlan plan;
-        const bool fused = fused_supported(n, precision) && n > (precision == CHEB_FP32 ? kSmallMaxF32 : kSmallMaxF64);
-        if (fused) plan = fused_plan(n, precision);
-        for (int k = K - 1; k >= 1; --k) {
-            StepArgs a;
-            a.n = n;
-            a.M = Mt;
-            a.Q = F.Q;
-            a.tiles = C.tiles();
-            a.elow = C.elow();
-            a.jq = (const int64_t*)(ws + A.fwd.jq);
-            a.b1 = Bv[cur];
-            a.b2 = Bv[cur ^ 1];
+        // Where the b_k live: all of them in the pool (store), or a ring of kRing
+        // regenerated upward from anchor pairs (b_a, b_{a+1}) every `gap` steps.
+        const bool store = nvec >= K;
+        if (!store && nvec < kRing + 2) return CHEB_ERR_WORKSPACE;
+        const int n_anch = store ? 0 : (int)std::min<int64_t>((nvec - kRing) / 2, 1 << 16);
+        const int gap = store ? 0 : std::max(1, (K - 1 + n_anch) / (n_anch + 1));
+        auto bvec = [&](int j) -> unsigned char* {  // b_j, 1 <= j <= K
+            return store ? pool + (size_t)(j - 1) * A.vstride : pool + (size_t)(j % kRing) * A.vstride;
+        };
+        auto anchor_slot = [&](int a) -> int {  // anchor pair index for b_a, or -1
+            if (store || a < 1 + gap || (a - 1) % gap != 0 || a > K - 2) return -1;
+            const int m = (a - 1) / gap - 1;
+            return m < n_anch ? m : -1;
+        };
+        auto anchor_ptr = [&](int m, int which) {
+            return pool + (size_t)(kRing + 2 * m + which) * A.vstride;
+        };
+        StepArgs base{};
+        base.n = n;
+        base.M = Mt;
+        base.Q = F.Q;
+        base.tiles = C.tiles();
+        base.elow = C.elow();
+        base.jq = (const int64_t*)(ws + A.fwd.jq);
+        base.g = g;
+        // forward recomputation from psi_s down to b_1
+        launch_scale(precision, N, psi_s, bvec(K), coef[K].real(), coef[K].imag(), s0);
+        for (int j = K - 1; j >= 1; --j) {
+            StepArgs a = base;
+            a.b1 = bvec(j + 1);
+            a.b2 = (j + 2 <= K) ? bvec(j + 2) : bvec(j);  // not read when sgn = 0
             a.psi = psi_s;
-            a.out = Bv[cur ^ 1];
-            a.ck_re = coef[k].real();
-            a.ck_im = coef[k].imag();
+            a.out = bvec(j);
+            a.ck_re = coef[j].real();
+            a.ck_im = coef[j].imag();
             a.scale = 2.0;
-            a.sgn = (k == K - 1) ? 0.0 : -1.0;
-            a.g = g;
-            if (fused) {
-                if (launch_step_fused(plan, a, nullptr, C.flags(), s0) != cudaSuccess) return CHEB_ERR_CUDA;
-            } else {
-                launch_step_plain(precision, a, s0);
+            a.sgn = (j + 2 <= K) ? -1.0 : 0.0;
+            if (runner.run(a, s0) != cudaSuccess) return CHEB_ERR_CUDA;
+            const int m = anchor_slot(j);
+            if (m >= 0) {
+                CUDA_TRY(cudaMemcpyAsync(anchor_ptr(m, 0), bvec(j), vb, cudaMemcpyDeviceToDevice, s0));
+                CUDA_TRY(cudaMemcpyAsync(anchor_ptr(m, 1), bvec(j + 1), vb, cudaMemcpyDeviceToDevice, s0));
             }
-            cur ^= 1;  // Bv[cur] = b_k, Bv[cur ^ 1] = b_{k+1}
-            for (size_t m = 0; m < anchor_k.size(); ++m)
-                if (anchor_k[m] == k) {
-                    unsigned char* dst = ws + A.anchors + m * A.per_anchor;
-                    CUDA_TRY(cudaMemcpyAsync(dst, Bv[cur], vb, cudaMemcpyDeviceToDevice, s0));
-                    if (k + 1 < K)
-                        CUDA_TRY(cudaMemcpyAsync(dst + A.per_anchor / 2, Bv[cur ^ 1], vb, cudaMemcpyDeviceToDevice, s0));
-                    else
-                        launch_scale(precision, N, psi_s, dst + A.per_anchor / 2, coef[K].real(), coef[K].imag(), s0);
-                }
         }
-        // now Bv[cur] = b_1 and Bv[cur ^ 1] = b_2 (or b_K = b_1 and b_2 = 0 when K == 1)
-        unsigned char* f_k = Bv[cur];       // b_k   (k = 1)
-        unsigned char* f_k1 = Bv[cur ^ 1];  // b_{k+1}
-        if (K == 1) CUDA_TRY(cudaMemsetAsync(f_k1, 0, vb, s0));
-        // k = 0 terms
-        CUDA_TRY(cudaMemsetAsync(slots, 0, kRedBlocks * sizeof(double), s0));
-        AdjArgs x{};
-        x.n = n;
-        x.M = Mt;
-        x.Q = F.Q;
-        x.tiles = C.tiles();
-        x.elow = C.elow();
-        x.g = g;
-        x.inv_r = 1.0 / r;
-        x.G = (double*)(ws + A.G);
-        x.dg_slots = slots;
-        x.psi = psi_s;
-        x.psibar = pbar;
-        {
-            AdjArgs y0 = x;
-            y0.bb1 = grad;
-            y0.f1 = f_k;
-            y0.cc_re = coef[0].real();
-            y0.cc_im = -coef[0].imag();
+        int have = store ? K : std::min(K, kRing);  // b_1 .. b_have are current
+        // b_0 := y; bbar_0 = ybar moves into the ring and grad accumulates psibar
+        CUDA_TRY(cudaMemcpyAsync(ring(0), grad, vb, cudaMemcpyDeviceToDevice, s0));
+        CUDA_TRY(cudaMemsetAsync(slots, 0, 4 * kRedBlocks * sizeof(double), s0));
+        CUDA_TRY(cudaMemsetAsync(Gs, 0, (size_t)N * 8, s0));
+        const bool use_flip = gamma_s[s] == 0.0;
+        auto bk = [&](int j) -> const void* {  // b_j for 0 <= j <= K + 1
+            if (j == 0) return y_s;
+            if (j > K) return nullptr;
+            return bvec(j);
+        };
+        for (int k0 = 0; k0 <= K; k0 += kAccBatch) {
+            const int k1 = std::min(k0 + kAccBatch - 1, K);
+            // bbar_k = alpha Ht bbar_{k-1} - beta bbar_{k-2}: Clenshaw-form steps with c = 0
+            for (int k = std::max(k0, 1); k <= k1; ++k) {
+                StepArgs a = base;
+                a.b1 = ring(k - 1);
+                a.b2 = (k >= 2) ? ring(k - 2) : ring(k);  // not read when sgn = 0
+                a.psi = ring(k - 1);                      // multiplied by c = 0
+                a.out = ring(k);
+                a.ck_re = 0.0;
+                a.ck_im = 0.0;
+                a.scale = (k == 1) ? 1.0 : 2.0;
+                a.sgn = (k == 1) ? 0.0 : -1.0;
+                if (runner.run(a, s0) != cudaSuccess) return CHEB_ERR_CUDA;
+            }
+            // b_j up to k1 + 2: b_j = 2 Ht b_{j-1} - b_{j-2} + c_{j-2} psi, resetting
+            // (b_{j-2}, b_{j-1}) from an anchor where there is one
+            const int need = std::min(k1 + 2, K);
+            for (int j = have + 1; j <= need; ++j) {
+                const int m = anchor_slot(j - 2);
+                if (m >= 0) {
+                    CUDA_TRY(cudaMemcpyAsync(bvec(j - 2), anchor_ptr(m, 0), vb, cudaMemcpyDeviceToDevice, s0));
+                    CUDA_TRY(cudaMemcpyAsync(bvec(j - 1), anchor_ptr(m, 1), vb, cudaMemcpyDeviceToDevice, s0));
+                }
+                StepArgs a = base;
+                a.b1 = bvec(j - 1);
+                a.b2 = bvec(j - 2);
+                a.psi = psi_s;
+                a.out = bvec(j);
+                a.ck_re = coef[j - 2].real();
+                a.ck_im = coef[j - 2].imag();
+                a.scale = 2.0;
+                a.sgn = -1.0;
+                if (runner.run(a, s0) != cudaSuccess) return CHEB_ERR_CUDA;
+            }
+            have = std::max(have, need);
+            AccArgs x{};
+            x.n = n;
+            x.m = k1 - k0 + 1;
+            x.mode = (k0 == 0) ? 2 : 1;
+            x.psi = psi_s;
+            x.psibar = grad;
+            x.Gs = Gs;
+            x.slots = slots;
+            for (int i = 0; i < x.m; ++i) {
+                const int k = k0 + i;
+                x.bbar[i] = ring(k);
+                x.cc_re[i] = coef[k].real();
+                x.cc_im[i] = -coef[k].imag();
+                x.w[i] = (k <= K - 1) ? (k == 0 ? 1.0 : 2.0) : 0.0;
+            }
+            for (int j = 0; j < x.m + 2; ++j) x.fb[j] = bk(k0 + j);
             note_launch(kKindReduce);
-            if (precision == CHEB_FP32)
-                k_adj_init<float><<<grid_n(N), kAdjThreads, 0, s0>>>(y0);
-            else
-                k_adj_init<double><<<grid_n(N), kAdjThreads, 0, s0>>>(y0);
-        }
-        // bbar_{-1} is unused (beta = 0 at k = 1): BB[1] receives bbar_1
-        const void* bbm1 = grad;                 // bbar_{k-1}
-        unsigned char* bbm2 = BB[1];             // bbar_{k-2} slot, overwritten by bbar_k
-        unsigned char* spare = BB[0];
-        for (int k = 1; k <= K; ++k) {
-            // reset the regenerated pair at anchors
-            for (size_t m = 0; m < anchor_k.size(); ++m)
-                if (anchor_k[m] == k && k > 1) {
-                    const unsigned char* src = ws + A.anchors + m * A.per_anchor;
-                    CUDA_TRY(cudaMemcpyAsync(f_k, src, vb, cudaMemcpyDeviceToDevice, s0));
-                    CUDA_TRY(cudaMemcpyAsync(f_k1, src + A.per_anchor / 2, vb, cudaMemcpyDeviceToDevice, s0));
+            const int pi = prof_begin(kKindReduce, s0);
+            if (precision == CHEB_FP32) k_adj_acc<float><<<gb, kAdjThreads, 0, s0>>>(x);
+            else k_adj_acc<double><<<gb, kAdjThreads, 0, s0>>>(x);
+            prof_end(pi, s0);
+            CUDA_TRY(cudaGetLastError());
+            if (use_flip) {
+                for (int i = 0; i < x.m; ++i) {
+                    if (x.w[i] == 0.0) continue;
+                    note_launch(kKindReduce);
+                    double* sl = slots + kRedBlocks;
+                    if (precision == CHEB_FP32)
+                        k_dg_flip<float><<<gb, kAdjThreads, 0, s0>>>(n, x.bbar[i], x.fb[i + 1], x.w[i], sl);
+                    else
+                        k_dg_flip<double><<<gb, kAdjThreads, 0, s0>>>(n, x.bbar[i], x.fb[i + 1], x.w[i], sl);
                 }
-            AdjArgs y = x;
-            y.bb1 = bbm1;
-            y.bb2 = bbm2;
-            y.alpha = (k == 1) ? 1.0 : 2.0;
-            y.beta = (k == 1) ? 0.0 : 1.0;
-            y.cc_re = coef[k].real();
-            y.cc_im = -coef[k].imag();
-            y.f1 = f_k1;
-            y.f0 = f_k;
-            y.ck_re = coef[k].real();
-            y.ck_im = coef[k].imag();
-            y.pair = (k <= K - 1) ? 1 : 0;
-            y.regen = (k + 2 <= K) ? 1 : 0;
-            y.w = 2.0;
-            cudaError_t e = precision == CHEB_FP32 ? launch_adj_step<float>(y, s0) : launch_adj_step<double>(y, s0);
-            if (e != cudaSuccess) return CHEB_ERR_CUDA;
-            // rotate: bbar_k now in bbm2; next step reads it as bbar_{k-1}
-            const void* new_b1 = bbm2;
-            unsigned char* new_b2 = (k == 1) ? spare : (unsigned char*)bbm1;  // bbar_{k-1} becomes bbar_{k-2}
-            if (k == 1) {
-                // bbar_0 = ybar lives in the caller's buffer; copy it into the spare slot
-                CUDA_TRY(cudaMemcpyAsync(spare, grad, vb, cudaMemcpyDeviceToDevice, s0));
             }
-            bbm1 = new_b1;
-            bbm2 = new_b2;
-            // forward pair advances: (b_{k+1}, b_{k+2}) now in (f_k1, f_k)
-            std::swap(f_k, f_k1);
         }
-        k_sum_slots<<<1, 256, 0, s0>>>(slots, grid_n(N), outs + 1);
-        double dgv = 0.0;
-        CUDA_TRY(cudaMemcpyAsync(&dgv, outs + 1, sizeof(double), cudaMemcpyDeviceToHost, s0));
-        // psibar becomes ybar of the previous segment
-        CUDA_TRY(cudaMemcpyAsync(grad, pbar, vb, cudaMemcpyDeviceToDevice, s0));
+        // slots: [0] hsum, [1] flip sums (gamma = 0), [2] sum_z D Gs
+        note_launch(kKindReduce);
+        if (precision == CHEB_FP32)
+            k_fold<float><<<gb, kAdjThreads, 0, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), (const float*)Gs, 1.0 / r,
+                                                      (double*)(ws + A.G), slots + 2 * kRedBlocks);
+        else
+            k_fold<double><<<gb, kAdjThreads, 0, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), (const double*)Gs, 1.0 / r,
+                                                       (double*)(ws + A.G), slots + 2 * kRedBlocks);
+        k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 3, outs + 4);
+        double v3[3];
+        CUDA_TRY(cudaMemcpyAsync(v3, outs + 4, sizeof(v3), cudaMemcpyDeviceToHost, s0));
         CUDA_TRY(cudaStreamSynchronize(s0));
-        gg[s] = dgv / r;
+        // hsum - sum_z D(z) Gs(z) = sum_k w_k Re <bbar_k, (Ht - D) b_{k+1}> = gamma dL/dgamma
+        gg[s] = use_flip ? v3[1] / r : (v3[0] - v3[2]) / gamma_s[s];
+    }
+    // the returned psibar carries the accumulated relative phase drift; remove it
+    {
+        CUDA_TRY(cudaMemsetAsync(slots, 0, 2 * kRedBlocks * sizeof(double), s0));
+        note_launch(kKindReduce);
+        if (precision == CHEB_FP32)
+            k_dot<float><<<gb, kAdjThreads, 0, s0>>>(n, grad, boundaries, slots);
+        else
+            k_dot<double><<<gb, kAdjThreads, 0, s0>>>(n, grad, boundaries, slots);
+        k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 2, outs + 4);
+        double v2[2];
+        CUDA_TRY(cudaMemcpyAsync(v2, outs + 4, sizeof(v2), cudaMemcpyDeviceToHost, s0));
+        CUDA_TRY(cudaStreamSynchronize(s0));
+        const std::complex<double> B0(v2[0], v2[1]);
+        if (std::abs(BT) > 1e-300 && std::abs(B0) > 1e-300) {
+            const double th0 = std::arg(BT) - std::arg(B0);
+            launch_scale(precision, N, grad, grad, std::cos(th0), -std::sin(th0), s0);
+        }
     }
     // dh, dJ from G (already divided by r per segment)
     const int nblk = n + n * (n - 1) / 2;
@@ -582,7 +759,7 @@ extern "C" cheb_status_t cheb_energy_grad(int n, const double* h, const double* 
         k_energy_grad<float><<<gb, kAdjThreads, 0, s0>>>(n, A.fwd.M, F.Q, C.tiles(), C.elow(), 0.0, 1.0, psi, grad_psi, G, slots);
     else
         k_energy_grad<double><<<gb, kAdjThreads, 0, s0>>>(n, A.fwd.M, F.Q, C.tiles(), C.elow(), 0.0, 1.0, psi, grad_psi, G, slots);
-    k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, outs + n * n + n);
+    k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 1, outs + n * n + n);
     const int nblk = n + n * (n - 1) / 2;
     k_grad_reduce<<<nblk, kAdjThreads, 0, s0>>>(n, G, outs);
     std::vector<double> red(nblk + 1);

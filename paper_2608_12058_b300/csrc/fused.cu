@@ -402,7 +402,8 @@ struct StridedCfg {
 
 struct StridedArgs {
     const float4* b1;
-    float4* slot;       // in: b_{k+2} or the partial q; out: q
+    const float4* slot_in;  // b_{k+2} or the partial q (may equal slot)
+    float4* slot;           // receives q
     int lo;             // first bit of the range (>= 4)
     int64_t ntiles;     // 2^(n - H - 4)
     float scale_g;      // scale * (gamma / r), float-float hi part
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const St
         for (int p = 0; p < Cfg::kP; ++p) {
             const int rho = rlo | (p << Cfg::kRowBitsT);
             tile[rho * 8 + u] = nxt[p];
-            if (need_slot) w[p] = a.slot[base + rho * row_stride_f4 + u];
+            if (need_slot) w[p] = a.slot_in[base + rho * row_stride_f4 + u];
         }
         const int64_t Tn = T + gridDim.x;
         if (Tn < a.ntiles) {
@@ -565,7 +566,7 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs
     if (need_slot && (int64_t)blockIdx.x < a.ntiles) {
         const int64_t base = strided_base<H>(a, blockIdx.x);
 #pragma unroll
-        for (int p = 0; p < Cfg::kP; ++p) w[p] = a.slot[base + (rlo | (p << 6)) * row_stride_f4 + u];
+        for (int p = 0; p < Cfg::kP; ++p) w[p] = a.slot_in[base + (rlo | (p << 6)) * row_stride_f4 + u];
     }
     int it = 0;
     for (int64_t T = blockIdx.x; T < a.ntiles; T += gridDim.x, ++it) {
@@ -576,7 +577,7 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs
         if (need_slot && Tn < a.ntiles) {
             const int64_t bn = strided_base<H>(a, Tn);
 #pragma unroll
-            for (int p = 0; p < Cfg::kP; ++p) wn[p] = a.slot[bn + (rlo | (p << 6)) * row_stride_f4 + u];
+            for (int p = 0; p < Cfg::kP; ++p) wn[p] = a.slot_in[bn + (rlo | (p << 6)) * row_stride_f4 + u];
         }
         if (!mbar_wait(&full[s], (it / Cfg::kNS) & 1, a.flags_ws, abort)) break;
         const float4* tile = (const float4*)(smem + (size_t)s * Cfg::kStageBytes);
@@ -789,10 +790,14 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, i
     const float ghi = (float)s.g;
     const float glo = (float)(s.g - (double)ghi);
     float slot_coeff = (float)s.sgn;
+    // The strided passes build the partial q in `out` when out is a separate
+    // buffer (b2 is then left intact), else in place in b2.
+    float4* q = (s.out != s.psi && s.out != s.b1) ? (float4*)s.out : (float4*)s.b2;
     for (int k = 0; k < plan.npass; ++k) {
         StridedArgs sa;
         sa.b1 = (const float4*)s.b1;
-        sa.slot = (float4*)s.b2;
+        sa.slot_in = (k == 0) ? (const float4*)s.b2 : q;
+        sa.slot = q;
         sa.lo = plan.lo[k];
         sa.ntiles = (int64_t)1 << (s.n - plan.hb[k] - 4);
         sa.scale_g = (float)s.scale * ghi;
@@ -805,7 +810,7 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, i
     }
     LowArgs la;
     la.b1 = (const float4*)s.b1;
-    la.slot = (const float4*)s.b2;
+    la.slot = plan.npass > 0 ? q : (const float4*)s.b2;
     la.psi = (const float4*)s.psi;
     la.out = (float4*)s.out;
     la.tiles = s.tiles;

@@ -27,7 +27,8 @@ void prof_end(int idx, cudaStream_t s);
 // with Dt(z) = (E(z) - c) / r reconstructed from the fixed-point tables and
 // g = gamma / r. scale = 2 for the inner steps and 1 for the final step;
 // sgn = -1 normally and 0 when b_{k+2} is the zero vector. `out` may alias b2
-// (in-place update) or psi (final step), never b1.
+// (in-place update) or psi (final step), never b1; when it is a buffer of its own,
+// b2 and psi are left unchanged.
 struct StepArgs {
     int n;
     int M;              // tile bits of the energy tables

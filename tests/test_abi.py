@@ -54,6 +54,21 @@ def test_workspace_bytes():
     assert w24 < 2 * (1 << 24) * 8 * 1.05
 
 
+def test_adjoint_workspace_bytes():
+    """The adjoint's pool grows by one (256-byte aligned) state vector per stored
+    vector on top of a fixed part: 6 adjoint ring vectors, G (8 B/amp), Gs (8 B/amp)."""
+    L = _lib.lib()
+    assert L.cheb_adjoint_workspace_bytes(0, 0, 8) == 0
+    assert L.cheb_adjoint_workspace_bytes(22, 0, -1) == 0
+    assert L.cheb_adjoint_workspace_bytes(22, 2, 8) == 0
+    vb = (1 << 22) * 8
+    w0 = L.cheb_adjoint_workspace_bytes(22, 0, 0)
+    assert w0 >= 6 * vb + 2 * (1 << 22) * 8
+    assert w0 < (6 * vb + 2 * (1 << 22) * 8) * 1.05
+    assert L.cheb_adjoint_workspace_bytes(22, 0, 60) - w0 == 60 * vb
+    assert L.cheb_adjoint_workspace_bytes(22, 1, 8) - L.cheb_adjoint_workspace_bytes(22, 1, 0) == 8 * 2 * vb
+
+
 @pytest.mark.parametrize("a,tol,method", [(0.0, 1e-12, "chebyshev"), (19.83, 1e-12, "chebyshev"),
                                           (430.0, 2.0 ** -23, "chebyshev"), (1300.0, 2.0 ** -23, "chebyshev"),
                                           (30.0, 1e-9, "cf"), (430.0, 2.0 ** -23, "cf")])

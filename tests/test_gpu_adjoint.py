@@ -109,3 +109,68 @@ def test_fp32_adjoint_close_to_fp64(cuda_lib):
     for k in range(5):
         g32, g64 = grads[torch.complex64][k], grads[torch.complex128][k]
         assert np.linalg.norm(g32 - g64) <= 1e-4 * np.linalg.norm(g64), k
+
+
+def test_anneal_workload_n22_gradients(cuda_lib):
+    """The differentiable-anneal workload (n=22, 64 segments, complex64 forward, FP64
+    reductions): gradients for sampled parameters within 1e-4 of central finite
+    differences of the FP64 forward map."""
+    import torch
+
+    from paper_2608_12058_b300 import autograd as AG
+
+    a = I.config_anneal()
+    n, S = a.n, len(a.gammas)
+    psi0 = I.uniform_state(n)
+    th, tJ, tg, tT = _params(a.h, a.J, a.gammas, a.ts)
+    x = torch.from_numpy(psi0).to(torch.complex64).cuda()
+    L = AG.energy(AG.anneal(x, th, tJ, tg, tT), th, tJ)
+    L.backward()
+    eps = 1e-4
+
+    def fd(which, idx):
+        vals = []
+        for sgn in (+1, -1):
+            h_, J_, g_, t_ = [np.array(v, dtype=np.float64) for v in (a.h, a.J, a.gammas, a.ts)]
+            {"gamma": g_, "t": t_, "h": h_, "J": J_}[which][idx] += sgn * eps
+            vals.append(_energy_after(h_, J_, g_, t_, psi0, torch.complex128))
+        return (vals[0] - vals[1]) / (2 * eps)
+
+    checks = [("gamma", 10, tg.grad[10].item()), ("gamma", 60, tg.grad[60].item()),
+              ("t", 31, tT.grad[31].item()), ("h", 3, th.grad[3].item()), ("J", (2, 17), tJ.grad[2, 17].item())]
+    scale = max(abs(c[2]) for c in checks)
+    for which, idx, got in checks:
+        ref = fd(which, idx)
+        assert abs(got - ref) <= 1e-4 * max(abs(ref), scale), (which, idx, got, ref)
+
+
+@pytest.mark.parametrize("n,dtype_name,tol", [(12, "complex128", 1e-11), (16, "complex64", 2e-5)])
+def test_regenerated_and_stored_forward_vectors_agree(cuda_lib, n, dtype_name, tol):
+    """The two ways of providing b_k to the adjoint - all kept, or regenerated upward
+    from anchor pairs in a ring of 6 - give the same gradients (regeneration from
+    (b_1, b_2) drifts only by round-off over the few steps between anchors)."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    dt = getattr(torch, dtype_name)
+    a = I.config_anneal(n=n, S=3, seed=4)
+    x = torch.from_numpy(I.uniform_state(n)).to(dt).cuda()
+    bnd = torch.empty((3, 1 << n), dtype=dt, device="cuda")
+    infos = api.anneal(a.h, a.J, a.gammas, a.ts, x, boundaries=bnd)
+    # the host-side degree bound that sizes the automatic pool covers the library's K
+    tol_ = 1e-12 if dtype_name == "complex128" else 2.0 ** -23
+    kb = api._degree_upper_bound(np.asarray(a.h), np.asarray(a.J), np.asarray(a.gammas), np.asarray(a.ts),
+                                 tol_, "chebyshev")
+    assert max(i["K"] for i in infos) <= kb
+    _, g, _, _ = api.energy_grad(a.h, a.J, x)
+    outs, psibars = [], []
+    for sv in (None, 8, 14):
+        gr = g.clone()
+        outs.append(api.anneal_adjoint(a.h, a.J, a.gammas, a.ts, bnd, x, gr, store_vectors=sv))
+        psibars.append(gr.cpu().numpy().astype(np.complex128))
+    for o, pb in zip(outs[1:], psibars[1:]):
+        for key in ("gamma", "t", "h", "J"):
+            ref = outs[0][key]
+            assert np.linalg.norm(o[key] - ref) <= tol * np.linalg.norm(ref), key
+        assert np.linalg.norm(pb - psibars[0]) <= tol * np.linalg.norm(psibars[0])
