@@ -317,7 +317,10 @@ def run_ours(args, world, rank, local):
     cands = [r for r in (r_low, r_str) if r is not None]
     roof = dict(max(cands, key=lambda r: r["share"]))
     roof["other_kernels"] = [r for r in cands if r["kernel"] != roof["kernel"]]
-    roof["step_alg_GBps"] = 32.0 * N * K * args.steps / t_local / 1e9
+    # whole Clenshaw step: 32 B/amp in k_low plus 24 B/amp per strided pass
+    step_bytes = 32.0 + 24.0 * (nhigh / max(nlow, 1))
+    roof["step_alg_bytes_per_amplitude"] = step_bytes
+    roof["step_alg_GBps"] = step_bytes * N * K * args.steps / t_local / 1e9
     cpu_v, cpu_dt, cpu_info = cpu_sample_run()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
