@@ -248,17 +248,15 @@ cheb_status_t cheb_expmv_path(int n, const double* h, const double* J, double ga
                               size_t workspace_bytes, void* stream, cheb_info_t* info);
 
 /*
- * Bit split of the fused FP32 step for n qubits (n >= 13). Each Clenshaw step
+ * Bit split of the fused FP32 step for n qubits (n >= 11). Each Clenshaw step
  * needs all n bit-flip partners of every amplitude (Sec. II.D); the fused step
- * takes bits [0, 13) from a shared-memory tile, bits [13, 13 + l) from partner
- * tiles through L2, and the top h bits in a second, strided pass, with
- * 13 + l + h = n, 0 <= l <= 9, h = 0 or 3 <= h <= 9.
+ * takes bits [0, 11) from a shared-memory tile and bits [11, 11 + l) from partner
+ * tiles through L2 in one pass, and the remaining h bits in strided passes of 3..9
+ * bits each (at most four), with 11 + l + h = n, 0 <= l <= 6, h = 0 or h >= 3.
  * cheb_set_fused_split overrides the built-in choice for this n (process-wide,
  * all devices); l = -1 restores the default. cheb_get_fused_split reports the
  * split that the next call at this n will use.
- * Two passes cover at most 31 bits: for n = 32, 33 the FP32 path uses the plain
- * one-pass kernel.
- * Errors: INVALID_ARG for an impossible split or n outside 13..31.
+ * Errors: INVALID_ARG for an impossible split or n outside 11..33.
  */
 cheb_status_t cheb_set_fused_split(int n, int l, int h);
 cheb_status_t cheb_get_fused_split(int n, int* l, int* h);

@@ -303,7 +303,7 @@ def poly_apply(h, J, gamma: float, center: float, radius: float, coeffs, psi, pa
 
 
 def set_fused_split(n: int, l: int, h: int = 0):
-    """Choose how the fused FP32 step splits the n bits (13 + l + h = n); l = -1 resets."""
+    """Choose how the fused FP32 step splits the n bits (11 + l + h = n); l = -1 resets."""
     _lib.check(_lib.lib().cheb_set_fused_split(int(n), int(l), int(h)), "cheb_set_fused_split")
 
 
