@@ -492,19 +492,25 @@ __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const St
 // Warp-specialised strided pass for 6..9 bits. The vector is viewed as a 4-D
 // tensor of float32: (32 floats = one 128-byte row of 16 amplitudes) x (2^(lo-4)
 // rows below the range) x (2^H rows of the range) x (rows above it). A producer
-// lane copies each tile's 2^H rows with one or two tensor TMA copies (boxes of up
-// to 256 rows) into a ring of stages; 512 consumer threads (u = t & 7, rho low bits
-// = t >> 3, rho high bits = register p) read the partner rows from shared memory.
-// The slot rows of the next tile are loaded into registers one tile ahead.
+// lane copies each tile's 2^H rows of b_{k+1} with one or two tensor TMA copies
+// (boxes of up to 256 rows) into a ring of stages, and the slot rows in chunks of
+// 64 rows (one chunk per row group p) into a second ring, so that the consumers
+// only read shared memory. 512 consumer threads (u = t & 7, rho low bits = t >> 3,
+// rho high bits = p) form the flip sums from the partner rows and write q.
 template <int H>
 struct StridedWsCfg {
     static constexpr int kRows = 1 << H;
     static constexpr int kBox = kRows < 256 ? kRows : 256;
     static constexpr uint32_t kStageBytes = (uint32_t)kRows * 128;
-    static constexpr int kNS = (int)((192u * 1024u) / kStageBytes) < 6 ? (int)((192u * 1024u) / kStageBytes) : 6;
-    static constexpr int kP = 1 << (H - 6);
-    static constexpr size_t kBarOff = (size_t)kNS * kStageBytes;
-    static constexpr size_t kSmem = kBarOff + 2 * kNS * sizeof(uint64_t) + 16;
+    static constexpr int kP = 1 << (H - 6);                   // row groups of 64 rows
+    static constexpr uint32_t kChunkBytes = 64 * 128;         // slot rows of one group
+    static constexpr int kSR = 8;                             // slot chunk ring depth
+    static constexpr uint32_t kRingBytes = kSR * kChunkBytes;
+    static constexpr int kNSraw = (int)((200u * 1024u - kRingBytes) / kStageBytes);
+    static constexpr int kNS = kNSraw < 6 ? kNSraw : 6;      // b_{k+1} stages
+    static constexpr size_t kRingOff = (size_t)kNS * kStageBytes;
+    static constexpr size_t kBarOff = kRingOff + kRingBytes;
+    static constexpr size_t kSmem = kBarOff + (2 * kNS + 2 * kSR) * sizeof(uint64_t) + 16;
 };
 
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
@@ -517,21 +523,31 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
 }
 
 template <int H>
-__global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs a, const __grid_constant__ CUtensorMap map) {
+__global__ void __launch_bounds__(kLowThreads, 1)
+    k_strided_ws(const StridedArgs a, const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap) {
     using Cfg = StridedWsCfg<H>;
     static_assert(H >= 6 && H <= 9 && Cfg::kNS >= 2, "strided ring");
+    static_assert(Cfg::kSmem <= 227 * 1024, "shared memory");
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = (uint64_t*)(smem + Cfg::kBarOff);
     uint64_t* empty = full + Cfg::kNS;
-    volatile int* abort = (volatile int*)(empty + Cfg::kNS);
+    uint64_t* sfull = empty + Cfg::kNS;
+    uint64_t* sempty = sfull + Cfg::kSR;
+    volatile int* abort = (volatile int*)(sempty + Cfg::kSR);
+    unsigned char* ring = smem + Cfg::kRingOff;
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
     const int64_t row_stride_f4 = (int64_t)1 << (a.lo - 1);
     const int sh = a.lo - 4;
+    const bool need_slot = a.sgn != 0.f;
     if (t == 0) {
         for (int i = 0; i < Cfg::kNS; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], kCons / 32);
+        }
+        for (int i = 0; i < Cfg::kSR; ++i) {
+            mbar_init(&sfull[i], 1);
+            mbar_init(&sempty[i], kCons / 32);
         }
         *abort = 0;
         fence_mbar_init();
@@ -539,10 +555,12 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs
     __syncthreads();
     if (warp == kCons / 32) {
         if (lane != 0) return;
-        int last[Cfg::kNS];
+        int last[Cfg::kNS], slast[Cfg::kSR];
         for (int i = 0; i < Cfg::kNS; ++i) last[i] = -1;
+        for (int i = 0; i < Cfg::kSR; ++i) slast[i] = -1;
+        bool ok = true;
         int it = 0;
-        for (int64_t T = blockIdx.x; T < a.ntiles; T += gridDim.x, ++it) {
+        for (int64_t T = blockIdx.x; ok && T < a.ntiles; T += gridDim.x, ++it) {
             const int s = it % Cfg::kNS, k = it / Cfg::kNS;
             if (k > 0 && !mbar_wait(&empty[s], (k - 1) & 1, a.flags_ws, abort)) break;
             mbar_expect_tx(&full[s], Cfg::kStageBytes);
@@ -553,32 +571,34 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs
 #pragma unroll
             for (int c = 0; c < Cfg::kRows / Cfg::kBox; ++c)
                 tma_load_4d(dst + (size_t)c * Cfg::kBox * 128, &map, 0, tlo, c * Cfg::kBox, thi, &full[s]);
+            if (need_slot) {
+                for (int p = 0; p < Cfg::kP; ++p) {
+                    const int c = it * Cfg::kP + p, r = c % Cfg::kSR, kk = c / Cfg::kSR;
+                    if (kk > 0 && !mbar_wait(&sempty[r], (kk - 1) & 1, a.flags_ws, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&sfull[r], Cfg::kChunkBytes);
+                    slast[r] = kk;
+                    tma_load_4d(ring + (size_t)r * Cfg::kChunkBytes, &smap, 0, tlo, p * 64, thi, &sfull[r]);
+                }
+            }
         }
+        // let every issued copy land before the CTA exits
         for (int i = 0; i < Cfg::kNS; ++i)
             if (last[i] >= 0) mbar_drain(&full[i], last[i] & 1, a.flags_ws);
+        for (int i = 0; i < Cfg::kSR; ++i)
+            if (slast[i] >= 0) mbar_drain(&sfull[i], slast[i] & 1, a.flags_ws);
         return;
     }
     const int u = t & 7;
     const int rlo = t >> 3;  // 6 bits
-    const bool need_slot = a.sgn != 0.f;
     const float2 g_hi = dup(a.scale_g), g_lo = dup(a.scale_glo), sg = dup(a.sgn);
-    float4 w[Cfg::kP];
-    if (need_slot && (int64_t)blockIdx.x < a.ntiles) {
-        const int64_t base = strided_base<H>(a, blockIdx.x);
-#pragma unroll
-        for (int p = 0; p < Cfg::kP; ++p) w[p] = a.slot_in[base + (rlo | (p << 6)) * row_stride_f4 + u];
-    }
+    bool ok = true;
     int it = 0;
-    for (int64_t T = blockIdx.x; T < a.ntiles; T += gridDim.x, ++it) {
+    for (int64_t T = blockIdx.x; ok && T < a.ntiles; T += gridDim.x, ++it) {
         const int s = it % Cfg::kNS;
         const int64_t base = strided_base<H>(a, T);
-        float4 wn[Cfg::kP];
-        const int64_t Tn = T + gridDim.x;
-        if (need_slot && Tn < a.ntiles) {
-            const int64_t bn = strided_base<H>(a, Tn);
-#pragma unroll
-            for (int p = 0; p < Cfg::kP; ++p) wn[p] = a.slot_in[bn + (rlo | (p << 6)) * row_stride_f4 + u];
-        }
         if (!mbar_wait(&full[s], (it / Cfg::kNS) & 1, a.flags_ws, abort)) break;
         const float4* tile = (const float4*)(smem + (size_t)s * Cfg::kStageBytes);
 #pragma unroll
@@ -592,12 +612,20 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_strided_ws(const StridedArgs
             float2 q0 = __ffma2_rn(g_hi, S.a, __fmul2_rn(g_lo, S.a));
             float2 q1 = __ffma2_rn(g_hi, S.b, __fmul2_rn(g_lo, S.b));
             if (need_slot) {
-                q0 = __ffma2_rn(sg, lo2(w[p]), q0);
-                q1 = __ffma2_rn(sg, hi2(w[p]), q1);
-                w[p] = wn[p];
+                const int c = it * Cfg::kP + p, r = c % Cfg::kSR;
+                if (!mbar_wait(&sfull[r], (c / Cfg::kSR) & 1, a.flags_ws, abort)) {
+                    ok = false;
+                    break;
+                }
+                const float4 w = ((const float4*)(ring + (size_t)r * Cfg::kChunkBytes))[rlo * 8 + u];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sempty[r]);  // this warp's reads of the chunk are done
+                q0 = __ffma2_rn(sg, lo2(w), q0);
+                q1 = __ffma2_rn(sg, hi2(w), q1);
             }
             a.slot[base + (rlo | (p << 6)) * row_stride_f4 + u] = make_float4(q0.x, q0.y, q1.x, q1.y);
         }
+        if (!ok) break;
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);  // this warp's shared-memory reads are done
     }
@@ -662,18 +690,27 @@ cudaError_t launch_strided_ws_t(const StridedArgs& a, int n, cudaStream_t s) {
     cuuint64_t strides[3] = {128, (cuuint64_t)1 << (a.lo + 3), (cuuint64_t)1 << (a.lo + H + 3)};
     cuuint32_t box[4] = {32, 1, (cuuint32_t)Cfg::kBox, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUtensorMap map;
+    CUtensorMap map, smap;
     if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)a.b1, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
+    // slot rows in chunks of 64 rows of the range (only read when sgn != 0)
+    smap = map;
+    if (a.sgn != 0.f) {
+        cuuint32_t sbox[4] = {32, 1, 64, 1};
+        if (enc(&smap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)a.slot_in, dims, strides, sbox, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
     cudaError_t e =
         cudaFuncSetAttribute(k_strided_ws<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(a.ntiles, num_sms());
     note_launch(kKindHigh);
     const int pi = prof_begin(kKindHigh, s);
-    k_strided_ws<H><<<(unsigned)grid, kLowThreads, Cfg::kSmem, s>>>(a, map);
+    k_strided_ws<H><<<(unsigned)grid, kLowThreads, Cfg::kSmem, s>>>(a, map, smap);
     prof_end(pi, s);
     return cudaGetLastError();
 }
