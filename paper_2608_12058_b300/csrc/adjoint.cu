@@ -70,51 +70,23 @@ __device__ __forceinline__ void block_accumulate(double v, double* slot) {
     __syncthreads();
 }
 
-// Error-free transformations (Knuth's TwoSum, FMA-based TwoProduct) for the FP32
-// path: a state concentrated on a few basis states makes per-element rounding add
-// up coherently, so the products and sums below keep their rounding errors.
-struct FF {
-    float h, l;
-};
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-// s + c += a * b, with the rounding error of the product and of the sum kept in c.
-__device__ __forceinline__ void dot2_step(float a, float b, float& s, float& c) {
-    const float p = a * b;
-    const float ep = fmaf(a, b, -p);
-    float t, es;
-    two_sum(s, p, t, es);
-    s = t;
-    c += ep + es;
-}
-__device__ __forceinline__ FF ff_add(FF x, float yh, float yl) {
-    float s, e;
-    two_sum(x.h, yh, s, e);
-    e += x.l + yl;
-    FF r;
-    r.h = s + e;
-    r.l = e - (r.h - s);
-    return r;
-}
-
 // Elementwise work of up to kAccBatch consecutive adjoint steps k = k0 .. k0+m-1
 // (every constant that would scale all elements alike - the gauge phase, 1/r - is
 // applied in FP64 per segment):
 //   psibar (+)= conj(c_k) bbar_k                      (mode 1 add, 2 set)
 //   Gs     += w_k Re(conj(bbar_k) b_{k+1})            (pair: w_k != 0, i.e. k < K)
-//   hsum   += Re(conj(bbar_k) (b_k + b_{k+2} - c_k psi))   (pair; w_k hs = 1 for every k)
-// with b_0 := y (the segment's output) and b_{K+1} := 0, so that
-// hsum - sum_z D(z) Gs(z) = sum_k w_k Re <bbar_k, (Ht - D) b_{k+1}>, since
-// Ht b_{k+1} = hs (b_k + b_{k+2} - c_k psi) (hs = 1/2, and 1 at k = 0). c_k is used
-// as the step kernels hold it. Batching the steps reads each b_j, psi, psibar and
-// Gs once per batch instead of once per step.
-// FP32: Gs is a float-float pair per element and the products are compensated.
+//   hsum   += Re(conj(bbar_k) x_k),  x_k = b_k + b_{k+2} - c_k psi - w_k D b_{k+1}
+// with b_0 := y (the segment's output) and b_{K+1} := 0. Since
+// Ht b_{k+1} = hs (b_k + b_{k+2} - c_k psi) with w_k hs = 1 (hs = 1/2, and 1 at
+// k = 0), x_k = w_k (Ht - D) b_{k+1} = w_k g sum_j X_j b_{k+1}: the cancellation
+// between Ht and D happens per element, where its rounding is of the size of the
+// rounding of b_{k+2} itself, and the sums over z have none. c_k is used as the step
+// kernels hold it. Batching reads each b_j, psi, psibar and Gs once per batch.
 constexpr int kAccBatch = 4;
 struct AccArgs {
-    int n, m, mode;
+    int n, m, mode, M, Q;
+    const int64_t* tiles;
+    const int64_t* elow;
     const void* bbar[kAccBatch];    // bbar_{k0+i}
     const void* fb[kAccBatch + 2];  // b_{k0+j}; nullptr = the zero vector
     const void* psi;
@@ -125,122 +97,187 @@ struct AccArgs {
     double w[kAccBatch];                         // w_k, 0 when k = K (no pair)
 };
 
+// One block per tile of 2^M amplitudes (z = T 2^M + x): the tile's energy partial
+// sums over the low 5 and the next 6 bits of x go to shared memory once, so that
+// e(z) = A(T) + Wlo[x & 31] + Whi[x >> 5] + elow(x) costs three adds.
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_acc(AccArgs a);
+__global__ void __launch_bounds__(kAdjThreads) k_adj_acc(AccArgs a) {
+    using C = typename Cx<R>::T;
+    __shared__ int64_t Wlo[32], Whi[64];
+    const int M = a.M;
+    const int64_t tsize = (int64_t)1 << M;
+    const int64_t ntiles = (int64_t)1 << (a.n - M);
+    const C* psi = (const C*)a.psi;
+    C* pb = (C*)a.psibar;
+    R* Gs = (R*)a.Gs;
+    bool any_pair = false;
+#pragma unroll
+    for (int i = 0; i < kAccBatch; ++i) any_pair |= (i < a.m) && a.w[i] != 0.0;
+    // D = e 2^-Q from the fixed-point energy e (from its two 32-bit halves)
+    const R s_hi = (R)ldexp(1.0, 32 - a.Q), s_lo = (R)ldexp(1.0, -a.Q);
+    const int t = threadIdx.x;
+    R hsum = 0;  // a few elements per thread: no cancellation in these sums
+    for (int64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
+        const int64_t* row = a.tiles + T * (M + 1);
+        if (any_pair) {
+            __syncthreads();  // the previous tile's tables are no longer read
+            if (t < 96) {
+                const int lo = t < 32 ? 0 : 5, hi = t < 32 ? 5 : 11;
+                const int x = t < 32 ? t : (t - 32) << 5;
+                int64_t v = 0;
+                for (int i = lo; i < hi && i < M; ++i) v += sgn_sel((x >> i) & 1, __ldg(row + i));
+                if (t < 32) Wlo[t] = v;
+                else Whi[t - 32] = v;
+            }
+            __syncthreads();
+        }
+        const int64_t Abase = any_pair ? __ldg(row + M) : 0;
+        for (int64_t x = t; x < tsize; x += blockDim.x) {
+            const int64_t z = T * tsize + x;
+            C f[kAccBatch + 2];
+#pragma unroll
+            for (int j = 0; j < kAccBatch + 2; ++j) {
+                if (j < a.m + 2 && a.fb[j]) {
+                    f[j] = ((const C*)a.fb[j])[z];
+                } else {
+                    f[j].x = 0;
+                    f[j].y = 0;
+                }
+            }
+            C p;
+            if (a.mode == 1) {
+                p = pb[z];
+            } else {
+                p.x = 0;
+                p.y = 0;
+            }
+            const C ps = psi[z];
+            R D = 0;
+            if (any_pair) {
+                const int64_t e = Abase + Wlo[x & 31] + Whi[(x >> 5) & 63] + __ldg(a.elow + x);
+                D = (R)(int)(e >> 32) * s_hi + (R)(uint32_t)(e & 0xffffffffll) * s_lo;
+            }
+            R g = 0, hs = 0;
+#pragma unroll
+            for (int i = 0; i < kAccBatch; ++i) {
+                if (i >= a.m) break;
+                const C u = ((const C*)a.bbar[i])[z];
+                const R cr = (R)a.cc_re[i], ci = (R)a.cc_im[i];
+                p.x += cr * u.x - ci * u.y;
+                p.y += cr * u.y + ci * u.x;
+                if (a.w[i] != 0.0) {
+                    const R w = (R)a.w[i];
+                    const C v = f[i + 1];
+                    g += w * (u.x * v.x + u.y * v.y);
+                    // c_k = conj(cc): c_k psi = (cr x + ci y, cr y - ci x)
+                    const R wD = w * D;
+                    const R xr = (f[i].x + f[i + 2].x) - (cr * ps.x + ci * ps.y) - wD * v.x;
+                    const R xi = (f[i].y + f[i + 2].y) - (cr * ps.y - ci * ps.x) - wD * v.y;
+                    hs += u.x * xr + u.y * xi;
+                }
+            }
+            pb[z] = p;
+            if (any_pair) {
+                Gs[z] += g;
+                hsum += hs;
+            }
+        }
+    }
+    if (any_pair) block_accumulate((double)hsum, a.slots);
+}
 
-template <>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_acc<float>(AccArgs a) {
-    const int64_t N = (int64_t)1 << a.n;
-    const float2* psi = (const float2*)a.psi;
-    float2* pb = (float2*)a.psibar;
+// FP32 variant of k_adj_acc: each thread takes two neighbouring amplitudes per
+// iteration (16-byte loads), which doubles the bytes in flight per load and halves
+// the load instructions; the arithmetic is the same.
+__global__ void __launch_bounds__(kAdjThreads) k_adj_acc_f32x2(AccArgs a) {
+    __shared__ int64_t Wlo[32], Whi[64];
+    const int M = a.M;
+    const int64_t tsize = (int64_t)1 << M;
+    const int64_t ntiles = (int64_t)1 << (a.n - M);
+    const float4* psi = (const float4*)a.psi;
+    float4* pb = (float4*)a.psibar;
     float2* Gs = (float2*)a.Gs;
     bool any_pair = false;
 #pragma unroll
     for (int i = 0; i < kAccBatch; ++i) any_pair |= (i < a.m) && a.w[i] != 0.0;
-    FF hs{0.f, 0.f};
-    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
-        float2 f[kAccBatch + 2];
-#pragma unroll
-        for (int j = 0; j < kAccBatch + 2; ++j)
-            f[j] = (j < a.m + 2 && a.fb[j]) ? ((const float2*)a.fb[j])[z] : make_float2(0.f, 0.f);
-        float2 p = a.mode == 1 ? pb[z] : make_float2(0.f, 0.f);
-        const float2 ps = psi[z];
-        float gs = 0.f, gc = 0.f;   // sum_i w_i Re(conj(u_i) b_{k+1}), compensated
-        float ts = 0.f, tc = 0.f;   // sum_i Re(conj(u_i) (b_k + b_{k+2} - c_k psi)), compensated
-#pragma unroll
-        for (int i = 0; i < kAccBatch; ++i) {
-            if (i >= a.m) break;
-            const float2 u = ((const float2*)a.bbar[i])[z];
-            const float cr = (float)a.cc_re[i], ci = (float)a.cc_im[i];
-            p.x += cr * u.x - ci * u.y;
-            p.y += cr * u.y + ci * u.x;
-            if (a.w[i] != 0.0) {
-                const float w = (float)a.w[i];
-                dot2_step(w * u.x, f[i + 1].x, gs, gc);
-                dot2_step(w * u.y, f[i + 1].y, gs, gc);
-                // c_k psi with c_k = conj(cc): (cr x + ci y, cr y - ci x), as hi + lo
-                float qx = 0.f, qxl = 0.f, qy = 0.f, qyl = 0.f;
-                dot2_step(cr, ps.x, qx, qxl);
-                dot2_step(ci, ps.y, qx, qxl);
-                dot2_step(cr, ps.y, qy, qyl);
-                dot2_step(-ci, ps.x, qy, qyl);
-                dot2_step(u.x, f[i].x, ts, tc);
-                dot2_step(u.y, f[i].y, ts, tc);
-                dot2_step(u.x, f[i + 2].x, ts, tc);
-                dot2_step(u.y, f[i + 2].y, ts, tc);
-                dot2_step(-u.x, qx, ts, tc);
-                dot2_step(-u.y, qy, ts, tc);
-                tc -= u.x * qxl + u.y * qyl;
-            }
-        }
-        pb[z] = p;
+    const float s_hi = (float)ldexp(1.0, 32 - a.Q), s_lo = (float)ldexp(1.0, -a.Q);
+    const int t = threadIdx.x;
+    float hsum = 0.f;
+    for (int64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
+        const int64_t* row = a.tiles + T * (M + 1);
         if (any_pair) {
-            const float2 go = Gs[z];
-            FF g{go.x, go.y};
-            g = ff_add(g, gs, gc);
-            Gs[z] = make_float2(g.h, g.l);
-            hs = ff_add(hs, ts, tc);
-        }
-    }
-    if (any_pair) block_accumulate((double)hs.h + (double)hs.l, a.slots);
-}
-
-template <>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_acc<double>(AccArgs a) {
-    const int64_t N = (int64_t)1 << a.n;
-    const double2* psi = (const double2*)a.psi;
-    double2* pb = (double2*)a.psibar;
-    double* Gs = (double*)a.Gs;
-    bool any_pair = false;
-#pragma unroll
-    for (int i = 0; i < kAccBatch; ++i) any_pair |= (i < a.m) && a.w[i] != 0.0;
-    double hsum = 0.0;
-    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
-        double2 f[kAccBatch + 2];
-#pragma unroll
-        for (int j = 0; j < kAccBatch + 2; ++j)
-            f[j] = (j < a.m + 2 && a.fb[j]) ? ((const double2*)a.fb[j])[z] : make_double2(0.0, 0.0);
-        double2 p = a.mode == 1 ? pb[z] : make_double2(0.0, 0.0);
-        const double2 ps = psi[z];
-        double g = 0.0;
-#pragma unroll
-        for (int i = 0; i < kAccBatch; ++i) {
-            if (i >= a.m) break;
-            const double2 u = ((const double2*)a.bbar[i])[z];
-            const double cr = a.cc_re[i], ci = a.cc_im[i];
-            p.x += cr * u.x - ci * u.y;
-            p.y += cr * u.y + ci * u.x;
-            if (a.w[i] != 0.0) {
-                g += a.w[i] * (u.x * f[i + 1].x + u.y * f[i + 1].y);
-                const double sx = f[i].x + f[i + 2].x - (cr * ps.x + ci * ps.y);
-                const double sy = f[i].y + f[i + 2].y - (cr * ps.y - ci * ps.x);
-                hsum += u.x * sx + u.y * sy;
+            __syncthreads();
+            if (t < 96) {
+                const int lo = t < 32 ? 0 : 5, hi = t < 32 ? 5 : 11;
+                const int x = t < 32 ? t : (t - 32) << 5;
+                int64_t v = 0;
+                for (int i = lo; i < hi && i < M; ++i) v += sgn_sel((x >> i) & 1, __ldg(row + i));
+                if (t < 32) Wlo[t] = v;
+                else Whi[t - 32] = v;
             }
+            __syncthreads();
         }
-        pb[z] = p;
-        if (any_pair) Gs[z] += g;
+        const int64_t Abase = any_pair ? __ldg(row + M) : 0;
+        for (int64_t x = 2 * t; x < tsize; x += 2 * blockDim.x) {
+            const int64_t z2 = (T * tsize + x) >> 1;  // float4 index of amplitudes z, z + 1
+            float4 f[kAccBatch + 2];
+#pragma unroll
+            for (int j = 0; j < kAccBatch + 2; ++j)
+                f[j] = (j < a.m + 2 && a.fb[j]) ? ((const float4*)a.fb[j])[z2] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 u[kAccBatch];
+#pragma unroll
+            for (int i = 0; i < kAccBatch; ++i)
+                u[i] = (i < a.m) ? ((const float4*)a.bbar[i])[z2] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 p = a.mode == 1 ? pb[z2] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 ps = psi[z2];
+            float2 gz = any_pair ? Gs[z2] : make_float2(0.f, 0.f);
+            float D0 = 0.f, D1 = 0.f;
+            if (any_pair) {
+                const int64_t e0 = Abase + Wlo[x & 31] + Whi[(x >> 5) & 63] + __ldg(a.elow + x);
+                const int64_t e1 = Abase + Wlo[(x + 1) & 31] + Whi[((x + 1) >> 5) & 63] + __ldg(a.elow + x + 1);
+                D0 = (float)(int)(e0 >> 32) * s_hi + (float)(uint32_t)(e0 & 0xffffffffll) * s_lo;
+                D1 = (float)(int)(e1 >> 32) * s_hi + (float)(uint32_t)(e1 & 0xffffffffll) * s_lo;
+            }
+#pragma unroll
+            for (int i = 0; i < kAccBatch; ++i) {
+                if (i >= a.m) break;
+                const float cr = (float)a.cc_re[i], ci = (float)a.cc_im[i];
+                const float4 uu = u[i];
+                p.x += cr * uu.x - ci * uu.y;
+                p.y += cr * uu.y + ci * uu.x;
+                p.z += cr * uu.z - ci * uu.w;
+                p.w += cr * uu.w + ci * uu.z;
+                if (a.w[i] != 0.0) {
+                    const float w = (float)a.w[i];
+                    const float4 v = f[i + 1], f0 = f[i], f2 = f[i + 2];
+                    gz.x += w * (uu.x * v.x + uu.y * v.y);
+                    gz.y += w * (uu.z * v.z + uu.w * v.w);
+                    // c_k = conj(cc): c_k psi = (cr x + ci y, cr y - ci x)
+                    const float wD0 = w * D0, wD1 = w * D1;
+                    const float xr0 = (f0.x + f2.x) - (cr * ps.x + ci * ps.y) - wD0 * v.x;
+                    const float xi0 = (f0.y + f2.y) - (cr * ps.y - ci * ps.x) - wD0 * v.y;
+                    const float xr1 = (f0.z + f2.z) - (cr * ps.z + ci * ps.w) - wD1 * v.z;
+                    const float xi1 = (f0.w + f2.w) - (cr * ps.w - ci * ps.z) - wD1 * v.w;
+                    hsum += (uu.x * xr0 + uu.y * xi0) + (uu.z * xr1 + uu.w * xi1);
+                }
+            }
+            pb[z2] = p;
+            if (any_pair) Gs[z2] = gz;
+        }
     }
-    if (any_pair) block_accumulate(hsum, a.slots);
+    if (any_pair) block_accumulate((double)hsum, a.slots);
 }
 
-// End of a segment: G(z) += Gs(z)/r (FP64) and slots += sum_z D(z) Gs(z), with
-// D = (E - c)/r from the segment's fixed-point tables. Gs is a float-float pair
-// (FP32 path) or a double.
+unsigned grid_tiles(int n, int M) {
+    const int64_t nt = (int64_t)1 << (n - M);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(nt, kRedBlocks));
+}
+
+// End of a segment: G(z) += Gs(z)/r (FP64).
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) k_fold(int n, int M, int Q, const int64_t* tiles, const int64_t* elow,
-                                                      const R* __restrict__ Gs, double inv_r, double* G,
-                                                      double* slots) {
-    const int64_t N = (int64_t)1 << n;
-    const double sc = ldexp(1.0, -Q);
-    constexpr int kW = sizeof(R) == 4 ? 2 : 1;
-    double acc = 0.0;
-    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
-        double g = (double)Gs[kW * z];
-        if (kW == 2) g += (double)Gs[kW * z + 1];
-        acc += __ll2double_rn(energy_fx(M, tiles, elow, (uint64_t)z)) * sc * g;
-        G[z] += g * inv_r;
-    }
-    block_accumulate(acc, slots);
+__global__ void __launch_bounds__(kAdjThreads) k_fold(int64_t N, const R* __restrict__ Gs, double inv_r, double* G) {
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x)
+        G[z] += (double)Gs[z] * inv_r;
 }
 
 // Fallback for gamma = 0, where (Ht - D)/gamma is not available: the flip sums of
@@ -394,6 +431,49 @@ __global__ void k_sum_slots(const double* slots, int nb, int count, double* out)
     }
 }
 
+// Phase gauge on the device. rec holds <ybar, H y_s> (re, im) and <ybar, y_s>
+// (re, im) of this segment; bt holds <ybar_T, y_T> (copied from the first segment
+// processed). Writes rot = e^{-i th} with th = arg(bt) - arg(<ybar, y_s>), and
+// rec[4] = dL/dt_s = Im(e^{i th} <ybar, H y_s>).
+__global__ void k_gauge(double* rec, double* bt, int first, double* rot) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (first) {
+        bt[0] = rec[2];
+        bt[1] = rec[3];
+    }
+    double th = 0.0;
+    if (hypot(rec[2], rec[3]) > 1e-300 && hypot(bt[0], bt[1]) > 1e-300)
+        th = atan2(bt[1], bt[0]) - atan2(rec[3], rec[2]);
+    const double c = cos(th), s = sin(th);
+    rot[0] = c;
+    rot[1] = -s;
+    rec[4] = s * rec[0] + c * rec[1];
+}
+
+// rot = e^{-i th0}, th0 = arg(bt) - arg(b0) (1 when either is ~0).
+__global__ void k_gauge_final(const double* b0, const double* bt, double* rot) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double th = 0.0;
+    if (hypot(b0[0], b0[1]) > 1e-300 && hypot(bt[0], bt[1]) > 1e-300) th = atan2(bt[1], bt[0]) - atan2(b0[1], b0[0]);
+    rot[0] = cos(th);
+    rot[1] = -sin(th);
+}
+
+// v *= rot[0] + i rot[1] (rot on the device).
+template <typename R>
+__global__ void __launch_bounds__(kAdjThreads) k_rotate(int64_t N, void* v_, const double* rot) {
+    using C = typename Cx<R>::T;
+    C* v = (C*)v_;
+    const R cr = (R)rot[0], ci = (R)rot[1];
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
+        const C x = v[z];
+        C o;
+        o.x = cr * x.x - ci * x.y;
+        o.y = cr * x.y + ci * x.x;
+        v[z] = o;
+    }
+}
+
 unsigned grid_n(int64_t N) {
     int64_t b = (N + kAdjThreads - 1) / kAdjThreads;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, kRedBlocks));
@@ -404,6 +484,11 @@ unsigned grid_n(int64_t N) {
 // per element), reduction slots, gradient outputs, then a pool of state vectors that
 // holds either every b_k of a segment or a ring of 6 plus anchor pairs.
 constexpr int kRing = kAccBatch + 2;
+// per-segment results stay on the device and are read back every kRecBatch segments:
+// record = <ybar,Hy> (2), <ybar,y> (2), dL/dt, hsum, flip sum, unused
+constexpr int kRecBatch = 64;
+constexpr int kRecLen = 8;
+constexpr int kOutGauge = 8;  // bt (2), rot (2), <psibar_0, psi_0> (2)
 struct AdjLayout {
     Layout fwd;
     size_t ring[kRing];
@@ -433,7 +518,7 @@ AdjLayout adj_layout(int n, int prec) {
     A.slots = off;
     off = a256(off + 4 * (size_t)kRedBlocks * sizeof(double));
     A.outs = off;
-    off = a256(off + ((size_t)n * n + n + 16) * sizeof(double));
+    off = a256(off + ((size_t)n * n + n + 16 + kOutGauge + kRecBatch * kRecLen) * sizeof(double));
     A.pool = off;
     A.total_fixed = off;
     return A;
@@ -508,7 +593,13 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
     runner.flags = C.flags();
     runner.fused = fused_supported(n, precision) && n > (precision == CHEB_FP32 ? kSmallMaxF32 : kSmallMaxF64);
     if (runner.fused) runner.plan = fused_plan(n, precision);
-    std::complex<double> BT(0.0, 0.0);
+    double* gauge = outs + (size_t)n * n + n + 16;
+    double* bt = gauge;       // <ybar_T, y_T>
+    double* rot = gauge + 2;  // e^{-i th} of the current segment
+    double* b0 = gauge + 4;   // <psibar_0, psi_0>
+    double* recs = gauge + kOutGauge;
+    std::vector<double> seg_r(S, 1.0);
+    std::vector<int> seg_K(S, 0);
     for (int s = S - 1; s >= 0; --s) {
         double r = 0.5 * (emax - emin) + std::fabs(gamma_s[s]) * n;
         if (!(r > 0)) r = 1.0;
@@ -525,8 +616,12 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
         if (slices != 1) return CHEB_ERR_UNSUPPORTED;
         const void* psi_s = (const unsigned char*)boundaries + (size_t)s * vb;
         const void* y_s = (s == S - 1) ? psi_T : (const unsigned char*)boundaries + (size_t)(s + 1) * vb;
-        // <ybar, H y_s> and the gauge invariant <ybar, y_s>
-        double theta = 0.0;
+        // <ybar, H y_s> and the gauge invariant <ybar, y_s> into this segment's record;
+        // the gauge rotation of ybar happens on the device (no host round trip)
+        const int q = (S - 1 - s) % kRecBatch;
+        double* rec = recs + (size_t)q * kRecLen;
+        seg_r[s] = r;
+        seg_K[s] = K;
         {
             CUDA_TRY(cudaMemsetAsync(slots, 0, 4 * kRedBlocks * sizeof(double), s0));
             note_launch(kKindReduce);
@@ -534,21 +629,35 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
                 k_dt<float><<<gb, kAdjThreads, 0, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), c, r, gamma_s[s], grad, y_s, slots);
             else
                 k_dt<double><<<gb, kAdjThreads, 0, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), c, r, gamma_s[s], grad, y_s, slots);
-            k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 4, outs);
-            double v4[4];
-            CUDA_TRY(cudaMemcpyAsync(v4, outs, sizeof(v4), cudaMemcpyDeviceToHost, s0));
-            CUDA_TRY(cudaStreamSynchronize(s0));
-            const std::complex<double> Ah(v4[0], v4[1]), Bs(v4[2], v4[3]);
-            if (s == S - 1) BT = Bs;
-            if (std::abs(BT) > 1e-300 && std::abs(Bs) > 1e-300) theta = std::arg(BT) - std::arg(Bs);
-            gt[s] = (std::polar(1.0, theta) * Ah).imag();
-            // the gauge moves into ybar: Re(e^{i th} conj(u) x) = Re(conj(e^{-i th} u) x)
-            if (theta != 0.0) launch_scale(precision, N, grad, grad, std::cos(theta), -std::sin(theta), s0);
+            k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 4, rec);
+            k_gauge<<<1, 32, 0, s0>>>(rec, bt, s == S - 1 ? 1 : 0, rot);
+            // Re(e^{i th} conj(u) x) = Re(conj(e^{-i th} u) x): the gauge moves into ybar
+            if (precision == CHEB_FP32) k_rotate<float><<<gb, kAdjThreads, 0, s0>>>(N, grad, rot);
+            else k_rotate<double><<<gb, kAdjThreads, 0, s0>>>(N, grad, rot);
+            CUDA_TRY(cudaMemsetAsync(rec + 5, 0, 2 * sizeof(double), s0));
         }
+        auto flush = [&]() -> cheb_status_t {  // read back the records of segments s .. s + q
+            std::vector<double> h((size_t)(q + 1) * kRecLen);
+            CUDA_TRY(cudaMemcpyAsync(h.data(), recs, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s0));
+            CUDA_TRY(cudaStreamSynchronize(s0));
+            for (int i = 0; i <= q; ++i) {
+                const int sg = S - 1 - ((S - 1 - s) - q + i);
+                const double* v = h.data() + (size_t)i * kRecLen;
+                gt[sg] = v[4];
+                // hsum = sum_k w_k Re <bbar_k, (Ht - D) b_{k+1}> = gamma dL/dgamma
+                if (seg_K[sg] == 0) gg[sg] = 0.0;
+                else if (gamma_s[sg] == 0.0) gg[sg] = v[6] / seg_r[sg];
+                else gg[sg] = v[5] / gamma_s[sg];
+            }
+            return CHEB_OK;
+        };
         if (K == 0) {
             // y = c_0 psi: psibar = conj(c_0) ybar, no operator dependence
             launch_scale(precision, N, grad, grad, coef[0].real(), -coef[0].imag(), s0);
-            gg[s] = 0.0;
+            if (q == kRecBatch - 1 || s == 0) {
+                st = flush();
+                if (st != CHEB_OK) return st;
+            }
             continue;
         }
         // Where the b_k live: all of them in the pool (store), or a ring of kRing
@@ -646,6 +755,10 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
             x.n = n;
             x.m = k1 - k0 + 1;
             x.mode = (k0 == 0) ? 2 : 1;
+            x.M = Mt;
+            x.Q = F.Q;
+            x.tiles = C.tiles();
+            x.elow = C.elow();
             x.psi = psi_s;
             x.psibar = grad;
             x.Gs = Gs;
@@ -660,8 +773,8 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
             for (int j = 0; j < x.m + 2; ++j) x.fb[j] = bk(k0 + j);
             note_launch(kKindReduce);
             const int pi = prof_begin(kKindReduce, s0);
-            if (precision == CHEB_FP32) k_adj_acc<float><<<gb, kAdjThreads, 0, s0>>>(x);
-            else k_adj_acc<double><<<gb, kAdjThreads, 0, s0>>>(x);
+            if (precision == CHEB_FP32) k_adj_acc_f32x2<<<grid_tiles(n, Mt), kAdjThreads, 0, s0>>>(x);
+            else k_adj_acc<double><<<grid_tiles(n, Mt), kAdjThreads, 0, s0>>>(x);
             prof_end(pi, s0);
             CUDA_TRY(cudaGetLastError());
             if (use_flip) {
@@ -676,20 +789,17 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
                 }
             }
         }
-        // slots: [0] hsum, [1] flip sums (gamma = 0), [2] sum_z D Gs
+        // slots: [0] hsum, [1] flip sums (gamma = 0) -> record [5..6]
         note_launch(kKindReduce);
         if (precision == CHEB_FP32)
-            k_fold<float><<<gb, kAdjThreads, 0, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), (const float*)Gs, 1.0 / r,
-                                                      (double*)(ws + A.G), slots + 2 * kRedBlocks);
+            k_fold<float><<<gb, kAdjThreads, 0, s0>>>(N, (const float*)Gs, 1.0 / r, (double*)(ws + A.G));
         else
-            k_fold<double><<<gb, kAdjThreads, 0, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), (const double*)Gs, 1.0 / r,
-                                                       (double*)(ws + A.G), slots + 2 * kRedBlocks);
-        k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 3, outs + 4);
-        double v3[3];
-        CUDA_TRY(cudaMemcpyAsync(v3, outs + 4, sizeof(v3), cudaMemcpyDeviceToHost, s0));
-        CUDA_TRY(cudaStreamSynchronize(s0));
-        // hsum - sum_z D(z) Gs(z) = sum_k w_k Re <bbar_k, (Ht - D) b_{k+1}> = gamma dL/dgamma
-        gg[s] = use_flip ? v3[1] / r : (v3[0] - v3[2]) / gamma_s[s];
+            k_fold<double><<<gb, kAdjThreads, 0, s0>>>(N, (const double*)Gs, 1.0 / r, (double*)(ws + A.G));
+        k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 2, rec + 5);
+        if (q == kRecBatch - 1 || s == 0) {
+            st = flush();
+            if (st != CHEB_OK) return st;
+        }
     }
     // the returned psibar carries the accumulated relative phase drift; remove it
     {
@@ -699,15 +809,10 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
             k_dot<float><<<gb, kAdjThreads, 0, s0>>>(n, grad, boundaries, slots);
         else
             k_dot<double><<<gb, kAdjThreads, 0, s0>>>(n, grad, boundaries, slots);
-        k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 2, outs + 4);
-        double v2[2];
-        CUDA_TRY(cudaMemcpyAsync(v2, outs + 4, sizeof(v2), cudaMemcpyDeviceToHost, s0));
-        CUDA_TRY(cudaStreamSynchronize(s0));
-        const std::complex<double> B0(v2[0], v2[1]);
-        if (std::abs(BT) > 1e-300 && std::abs(B0) > 1e-300) {
-            const double th0 = std::arg(BT) - std::arg(B0);
-            launch_scale(precision, N, grad, grad, std::cos(th0), -std::sin(th0), s0);
-        }
+        k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 2, b0);
+        k_gauge_final<<<1, 32, 0, s0>>>(b0, bt, rot);
+        if (precision == CHEB_FP32) k_rotate<float><<<gb, kAdjThreads, 0, s0>>>(N, grad, rot);
+        else k_rotate<double><<<gb, kAdjThreads, 0, s0>>>(N, grad, rot);
     }
     // dh, dJ from G (already divided by r per segment)
     const int nblk = n + n * (n - 1) / 2;
