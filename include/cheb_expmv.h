@@ -269,6 +269,16 @@ cheb_status_t cheb_get_fused_split(int n, int* l, int* h);
  *   coeffs: HOST array of 2*(K+1) doubles (re, im), 0 <= K <= 65536.
  * Errors: INVALID_ARG, WORKSPACE, CUDA, UNSUPPORTED.
  */
+/*
+ * Monomial to Chebyshev basis (the two bases of Sec. II.B): given
+ * p(x) = sum_{m=0}^{K} a_m x^m, writes c with p(x) = sum_{k=0}^{K} c_k T_k(x), so that
+ * cheb_poly_apply evaluates a polynomial given in the monomial basis by the Clenshaw
+ * recurrence. Exact up to rounding (computed in long double, O(K^2)).
+ *   monomial, chebyshev: HOST arrays of 2*(K+1) doubles (re, im); may not alias.
+ * Errors: INVALID_ARG (K < 0 or > 65536, null pointers, non-finite input).
+ */
+cheb_status_t cheb_monomial_to_chebyshev(int K, const double* monomial, double* chebyshev);
+
 cheb_status_t cheb_poly_apply(int n, const double* h, const double* J, double gamma,
                               double center, double radius, int K, const double* coeffs,
                               void* psi, cheb_precision_t precision, int path, void* workspace,

@@ -364,6 +364,25 @@ void oracle_clenshaw(int n, const double* D, double g, int K, const double* coef
     }
 }
 
+// A polynomial given in the monomial basis (the other basis of Sec. II.B), by its
+// definition: y = sum_{m=0}^{K} a_m Ht^m psi, with the powers formed by repeated
+// matvecs (no basis change, no recurrence).
+void oracle_monomial_apply(int n, const double* D, double g, int K, const double* a,
+                           const double* psi_in, double* y_out) {
+    const int64_t N = (int64_t)1 << n;
+    const cplx* psi = reinterpret_cast<const cplx*>(psi_in);
+    cplx* y = reinterpret_cast<cplx*>(y_out);
+    std::vector<cplx> pw(psi, psi + N), nx(N);   // pw = Ht^m psi
+    for (int64_t z = 0; z < N; ++z) y[z] = cplx(0.0, 0.0);
+    for (int m = 0; m <= K; ++m) {
+        const cplx am(a[2 * m], a[2 * m + 1]);
+        for (int64_t z = 0; z < N; ++z) y[z] += am * pw[z];
+        if (m == K) break;
+        apply_ht(n, D, g, pw.data(), nx.data());
+        pw.swap(nx);
+    }
+}
+
 // Evaluation-error bound of Sec. II.B.3 for a run whose per-step norms are given:
 //   sum_k  u ||b_k|| + u ||c_k psi - b_{k+2}|| + sqrt(d) gamma_d ||b_{k+1}||,
 //   gamma_d = d u / (1 - d u),  d = n + 1 nonzeros per column (Sec. I).

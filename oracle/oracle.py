@@ -13,10 +13,11 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 What pins each function (tests/test_oracle_pins.py, tests/test_oracle_cf.py):
   energies/bounds      brute force vs a numpy-vectorised restatement at n<=12;
                        symmetric-spectrum shift (Sec. II.A) vs dense eigvalsh
-  bessel_j             scipy.special.jv; J_0^2 + 2 sum J_m^2 = 1; three-term
-                       recurrence; golden values (tests/golden/bessel_*.txt)
+  bessel_j             scipy.special.jv and 40-digit mpmath; J_0^2 + 2 sum J_m^2 = 1;
+                       three-term recurrence
   cheb_coeffs          scalar series vs exp(-i a cos theta) (Eq. cheb is exact);
-                       tail rule vs brute-force error; K(a) growth (Fig. 1 shape)
+                       tail rule vs brute-force error; K(a) growth (Fig. 1 shape);
+                       the paper's 151-term count (tests/golden/paper_term_counts.txt)
   cf_coeffs            equioscillation at >= K+2 points with |error| ~ |lambda|;
                        error below the Chebyshev error of the same degree
   clenshaw / expmv     dense eigh exp(-itH) at n<=10; H_P = 0 closed form
@@ -24,6 +25,8 @@ What pins each function (tests/test_oracle_pins.py, tests/test_oracle_cf.py):
                        phases; norm preservation; group property; truncation
                        bound; Walsh-Hadamard check of H_G
   eval_bound           bound >= observed FP64 error (Sec. II.B.3)
+  monomial_apply       dense matrix polynomial (numpy matrix powers) at n <= 6
+  anneal               ordered product of dense segment exponentials (eigh)
   dense gradients      central finite differences; closed form dL/dt
 """
 from __future__ import annotations
@@ -71,6 +74,8 @@ def lib():
             L.oracle_cf_coeffs.restype = ctypes.c_int
             L.oracle_clenshaw.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int, _dp,
                                           _dp, _dp, _dp]
+            L.oracle_monomial_apply.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]
+            L.oracle_monomial_apply.restype = None
             L.oracle_eval_bound.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double]
             L.oracle_eval_bound.restype = ctypes.c_double
             L.oracle_expmv.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
@@ -172,6 +177,19 @@ def clenshaw(D, g: float, coeffs, psi, with_norms: bool = False):
     lib().oracle_clenshaw(n, _p(D), float(g), K, _p(c), _p(x), _p(y), _p(norms))
     out = y.view(np.complex128)
     return (out, norms) if with_norms else out
+
+
+def monomial_apply(D, g: float, a, psi):
+    """y = sum_m a_m Ht^m psi by repeated matvecs (the definition), Ht = diag(D) + g sum_j X_j."""
+    D = _f64(D)
+    n = int(np.log2(D.shape[0]))
+    assert D.shape[0] == 1 << n
+    c = _c128_view(a)
+    K = c.shape[0] // 2 - 1
+    x = _c128_view(psi)
+    y = np.empty(2 << n)
+    lib().oracle_monomial_apply(n, _p(D), float(g), K, _p(c), _p(x), _p(y))
+    return y.view(np.complex128)
 
 
 def eval_bound(n: int, norms, u: float) -> float:

@@ -51,6 +51,7 @@ SIGNATURES = {
                                 c_int, c_void_p, c_size_t, c_void_p, ctypes.POINTER(Info)]),
     "cheb_poly_apply": (c_int, [c_int, _dp, _dp, c_double, c_double, c_double, c_int, _dp, c_void_p, c_int,
                                 c_int, c_void_p, c_size_t, c_void_p]),
+    "cheb_monomial_to_chebyshev": (c_int, [c_int, _dp, _dp]),
     "cheb_energy": (c_int, [c_int, _dp, _dp, c_void_p, c_int, c_void_p, c_size_t, c_void_p, _dp, _dp]),
     "cheb_set_fused_split": (c_int, [c_int, c_int, c_int]),
     "cheb_get_fused_split": (c_int, [c_int, _ip, _ip]),

@@ -286,6 +286,22 @@ def energy_grad(h, J, psi):
     return e.value, g, gh, gJ
 
 
+def monomial_to_chebyshev(a):
+    """Chebyshev coefficients c of p(x) = sum_m a_m x^m (cheb_monomial_to_chebyshev)."""
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+    out = np.empty_like(a)
+    K = a.shape[0] - 1
+    _lib.check(_lib.lib().cheb_monomial_to_chebyshev(K, _dp(a.view(np.float64)), _dp(out.view(np.float64))),
+               "cheb_monomial_to_chebyshev")
+    return out
+
+
+def poly_apply_monomial(h, J, gamma: float, center: float, radius: float, a, psi, path: str = "auto"):
+    """psi <- sum_m a_m ((H - center)/radius)^m psi in place: the monomial coefficients are
+    converted to the Chebyshev basis on the host and evaluated by the Clenshaw recurrence."""
+    poly_apply(h, J, gamma, center, radius, monomial_to_chebyshev(a), psi, path=path)
+
+
 def poly_apply(h, J, gamma: float, center: float, radius: float, coeffs, psi, path: str = "auto"):
     """psi <- sum_m c_m T_m((H - center)/radius) psi in place on the GPU."""
     h, J = _f64(h), _f64(J)

@@ -294,6 +294,21 @@ cheb_status_t cheb_coefficients(double a, double phase_re, double phase_im, doub
     return CHEB_OK;
 }
 
+cheb_status_t cheb_monomial_to_chebyshev(int K, const double* monomial, double* chebyshev) {
+    if (K < 0 || K > kMaxK || !monomial || !chebyshev) return CHEB_ERR_INVALID_ARG;
+    std::vector<std::complex<double>> a(K + 1), c(K + 1);
+    for (int m = 0; m <= K; ++m) {
+        a[m] = std::complex<double>(monomial[2 * m], monomial[2 * m + 1]);
+        if (!std::isfinite(monomial[2 * m]) || !std::isfinite(monomial[2 * m + 1])) return CHEB_ERR_INVALID_ARG;
+    }
+    monomial_to_chebyshev(K, a.data(), c.data());
+    for (int k = 0; k <= K; ++k) {
+        chebyshev[2 * k] = c[k].real();
+        chebyshev[2 * k + 1] = c[k].imag();
+    }
+    return CHEB_OK;
+}
+
 size_t cheb_workspace_bytes(int n, cheb_precision_t precision) {
     if (n < 1 || n > kMaxQubits) return 0;
     if (precision != CHEB_FP32 && precision != CHEB_FP64) return 0;

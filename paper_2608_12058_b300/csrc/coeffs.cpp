@@ -287,4 +287,29 @@ int make_coefficients(double a, std::complex<double> phase, double tol, int meth
     return K;
 }
 
+// Monomial -> Chebyshev basis (Sec. II.B, the two bases of the series): with
+// P_m = x^m = sum_k p_{m,k} T_k, the next power follows from x T_0 = T_1 and
+// x T_k = (T_{k+1} + T_{k-1}) / 2; c = sum_m a_m P_m. Long double, O(K^2).
+void monomial_to_chebyshev(int K, const std::complex<double>* a, std::complex<double>* c) {
+    std::vector<long double> P(K + 2, 0.0L), Q(K + 2, 0.0L);
+    std::vector<long double> cr(K + 1, 0.0L), ci(K + 1, 0.0L);
+    P[0] = 1.0L;  // x^0 = T_0
+    for (int m = 0; m <= K; ++m) {
+        const long double ar = a[m].real(), ai = a[m].imag();
+        for (int k = 0; k <= m; ++k) {
+            cr[k] += ar * P[k];
+            ci[k] += ai * P[k];
+        }
+        if (m == K) break;
+        std::fill(Q.begin(), Q.end(), 0.0L);
+        Q[1] += P[0];
+        for (int k = 1; k <= m; ++k) {
+            Q[k + 1] += 0.5L * P[k];
+            Q[k - 1] += 0.5L * P[k];
+        }
+        P.swap(Q);
+    }
+    for (int k = 0; k <= K; ++k) c[k] = std::complex<double>((double)cr[k], (double)ci[k]);
+}
+
 }  // namespace cheb

@@ -125,3 +125,10 @@ def config_anneal(n: int = 22, S: int = 64, seed: int = 0) -> Anneal:
     h, J = sk_instance(n, seed, "normal")
     gam = np.linspace(2.0, 0.05, S) + np.random.default_rng(1).normal(0.0, 0.05, S)
     return Anneal(n, h, J, gam, np.full(S, 0.5))
+
+
+def monomial_polynomial(degree: int = 50, seed: int = 0) -> np.ndarray:
+    """Coefficients a_0..a_degree of a polynomial in the monomial basis, standard normal
+    draws from default_rng(seed) (the random polynomials of the paper's Fig. 4 and
+    Fig. 6 runtime workloads)."""
+    return np.random.default_rng(seed).standard_normal(degree + 1)

@@ -152,3 +152,29 @@ def test_expmv_rejects_bad_arguments_before_touching_the_device():
                         None, None) == 1
     assert L.cheb_expmv(n, dp(h), dp(J), 1.0, float("inf"), fake, 0, 1e-6, 0, 0, fake, ws, None, None) == 1
     assert L.cheb_expmv(n, dp(h), dp(J), 1.0, 1.0, fake, 0, 1e-6, 0, -1, fake, ws, None, None) == 1
+
+
+@pytest.mark.parametrize("K,seed", [(0, 0), (1, 1), (7, 2), (50, 3), (120, 4)])
+def test_monomial_to_chebyshev(K, seed):
+    """The host basis change agrees with numpy's poly2cheb and gives the same values
+    as the monomial form on [-1, 1] (Chebyshev series summed by numpy's chebval)."""
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal(K + 1) + 1j * rng.standard_normal(K + 1)
+    c = api.monomial_to_chebyshev(a)
+    ref = np.polynomial.chebyshev.poly2cheb(a.real) + 1j * np.polynomial.chebyshev.poly2cheb(a.imag)
+    assert np.max(np.abs(c - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+    x = np.linspace(-1, 1, 97)
+    pv = np.polynomial.polynomial.polyval(x, a)
+    cv = np.polynomial.chebyshev.chebval(x, c)
+    assert np.max(np.abs(pv - cv)) <= 1e-12 * max(1.0, np.max(np.abs(pv)))
+
+
+def test_monomial_to_chebyshev_rejects_bad_input():
+    L = _lib.lib()
+    buf = np.zeros(4)
+    out = np.zeros(4)
+    dp = lambda x: x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert L.cheb_monomial_to_chebyshev(-1, dp(buf), dp(out)) == 1
+    assert L.cheb_monomial_to_chebyshev(1, None, dp(out)) == 1
+    buf[1] = np.nan
+    assert L.cheb_monomial_to_chebyshev(1, dp(buf), dp(out)) == 1

@@ -171,6 +171,29 @@ def test_poly_apply_matches_oracle_clenshaw(cuda_lib, oracle, prec):
     assert _rel(y, ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,seed", [(5, 11), (10, 12), (16, 13), (20, 14)])
+def test_monomial_polynomial_matches_oracle(cuda_lib, oracle, prec, n, seed):
+    """The Fig. 4 / Fig. 6 workload: a degree-50 polynomial with N(0,1) coefficients in
+    the monomial basis, applied to Ht = (H - c)/r of an SK instance. The product converts
+    to the Chebyshev basis on the host and runs the Clenshaw kernels; the oracle sums
+    a_m Ht^m psi by repeated matvecs."""
+    torch = _torch()
+    from paper_2608_12058_b300 import api
+
+    h, J = I.sk_instance(n, seed)
+    a = I.monomial_polynomial(50, seed)
+    emin, emax, center, r = oracle.bounds(h, J, 0.9)
+    D = (oracle.energies(h, J) - center) / r
+    psi = I.random_state(n, seed + 100)
+    ref = oracle.monomial_apply(D, 0.9 / r, a, psi)
+    dt = torch.complex64 if prec == "fp32" else torch.complex128
+    x = torch.from_numpy(psi).to(dt).cuda()
+    api.poly_apply_monomial(h, J, 0.9, center, r, a, x)
+    y = x.cpu().numpy().astype(np.complex128)
+    assert _rel(y, ref) <= TOL[prec]
+
+
 SPLITS = [
     # n, l, h: L2 partner bits of the low pass and strided bits (11 + l + h = n);
     # h > 9 runs two strided passes

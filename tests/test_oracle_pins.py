@@ -346,6 +346,11 @@ def test_dense_gradients_vs_finite_differences(oracle):
         E_[i, j] = eps
         fd = (loss(h, J + E_, gam, t, psi) - loss(h, J - E_, gam, t, psi)) / (2 * eps)
         assert abs(fd - g["J"][i, j]) < 1e-7
+    # closed form dL/dt = 2 Re <y| H_P (-i H) |y> for L = <y|H_P|y>
+    y = oracle.dense_expmv(h, J, gam, t, psi)
+    H = oracle.dense_hamiltonian(h, J, gam)
+    E = oracle.energies(h, J)
+    assert abs(2.0 * np.real(np.vdot(y, E * (-1j * (H @ y)))) - g["t"]) < 1e-10
     # psi0 gradient (PyTorch convention: 2 dL/d conj(psi)) along a random direction
     d = I.random_state(n, 53)
     fd = (loss(h, J, gam, t, psi + eps * d) - loss(h, J, gam, t, psi - eps * d)) / (2 * eps)
@@ -366,3 +371,22 @@ def test_anneal_matches_dense_product(oracle):
         np.testing.assert_allclose(st, ref, atol=1e-12)
         ref = oracle.dense_expmv(h, J, g, t, ref)
     assert np.linalg.norm(y - ref) < 1e-12
+
+
+# Polynomials in the monomial basis (Sec. II.B; the Fig. 4 / Fig. 6 workloads)
+
+@pytest.mark.parametrize("n,seed", [(4, 0), (6, 3)])
+def test_monomial_apply_matches_dense_matrix_powers(oracle, n, seed):
+    """sum_m a_m Ht^m psi by repeated matvecs equals the dense matrix polynomial
+    (numpy matrix powers of the explicit Ht), degree 50, N(0,1) coefficients."""
+    h, J = I.sk_instance(n, seed)
+    gam = 0.7
+    E = oracle.energies(h, J)
+    c = 0.5 * (E.max() + E.min())
+    r = 0.5 * (E.max() - E.min()) + gam * n
+    a = I.monomial_polynomial(50, seed) * (1.0 + 0.5j)
+    psi = I.random_state(n, seed + 1)
+    y = oracle.monomial_apply((E - c) / r, gam / r, a, psi)
+    Ht = (oracle.dense_hamiltonian(h, J, gam) - c * np.eye(1 << n)) / r
+    ref = sum(a[m] * (np.linalg.matrix_power(Ht, m) @ psi) for m in range(a.shape[0]))
+    assert np.linalg.norm(y - ref) <= 1e-12 * np.linalg.norm(ref)
