@@ -46,7 +46,7 @@ typedef enum {
     CHEB_ERR_UNSUPPORTED = 6    /* valid but outside what this build handles */
 } cheb_status_t;
 
-typedef enum { CHEB_METHOD_CHEBYSHEV = 0, CHEB_METHOD_CF = 1 } cheb_method_t;
+typedef enum { CHEB_METHOD_CHEBYSHEV = 0, CHEB_METHOD_CF = 1, CHEB_METHOD_REMEZ = 2 } cheb_method_t;
 typedef enum { CHEB_FP32 = 0, CHEB_FP64 = 1 } cheb_precision_t;
 
 /* Kernel path for the Clenshaw steps. AUTO picks the fastest available path for
@@ -75,10 +75,12 @@ const char* cheb_status_string(cheb_status_t status);
 const char* cheb_version(void);
 
 /*
- * Host coefficient generator (Sec. II.B.1, Eq. cheb, Eq. TruncError; Sec. II.C for CF).
+ * Host coefficient generator (Sec. II.B.1, Eq. cheb, Eq. TruncError; Sec. II.C for CF and Remez).
  * Coefficients of f(x) = exp(-i a x) * phase on [-1, 1] in the Chebyshev basis,
- * c_0 = J_0(a) * phase, c_m = 2 (-i)^m J_m(a) * phase (CHEB_METHOD_CHEBYSHEV), or the
- * Caratheodory-Fejer near-minimax correction of that series (CHEB_METHOD_CF).
+ * c_0 = J_0(a) * phase, c_m = 2 (-i)^m J_m(a) * phase (CHEB_METHOD_CHEBYSHEV), the
+ * Caratheodory-Fejer near-minimax correction of that series (CHEB_METHOD_CF), or the
+ * minimax polynomials of cos(a x) and sin(a x) from the Remez exchange
+ * (CHEB_METHOD_REMEZ, Sec. II.C; err_bound = hypot of their minimax errors).
  * K is the smallest degree whose truncation bound sum_{m>K} |c_m| (Chebyshev) or
  * CF error estimate is <= tol.
  *   coeffs:  HOST buffer of 2*(max_K+1) doubles, receives (re, im) of c_0..c_K.

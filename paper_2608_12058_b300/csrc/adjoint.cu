@@ -563,7 +563,8 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
     if (!finite_all(h, n) || !finite_all(J, (size_t)n * n) || !finite_all(gamma_s, S) || !finite_all(t_s, S))
         return CHEB_ERR_INVALID_ARG;
     if (!(tol > 0) || !std::isfinite(tol)) return CHEB_ERR_INVALID_ARG;
-    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF) return CHEB_ERR_INVALID_ARG;
+    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF && method != CHEB_METHOD_REMEZ)
+        return CHEB_ERR_INVALID_ARG;
     if (((uintptr_t)boundaries | (uintptr_t)psi_T | (uintptr_t)grad) & 15) return CHEB_ERR_INVALID_ARG;
     AdjLayout A = adj_layout(n, precision);
     if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < A.total_fixed) return CHEB_ERR_WORKSPACE;

@@ -24,7 +24,8 @@ extern "C" cheb_status_t cheb_anneal(int n, const double* h, const double* J, in
     if (boundaries && ((uintptr_t)boundaries & 15) != 0) return CHEB_ERR_INVALID_ARG;
     if (!finite_all(gamma_s, S) || !finite_all(t_s, S) || !(tol > 0) || !std::isfinite(tol))
         return CHEB_ERR_INVALID_ARG;
-    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF) return CHEB_ERR_INVALID_ARG;
+    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF && method != CHEB_METHOD_REMEZ)
+        return CHEB_ERR_INVALID_ARG;
     Ctx C{n, precision, make_layout(n, precision), (unsigned char*)workspace, (cudaStream_t)stream};
     CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), C.s));
     double emin = 0, emax = 0;

@@ -207,7 +207,8 @@ cheb_status_t expmv_impl(int n, const double* h, const double* J, double gamma, 
     if (st != CHEB_OK) return st;
     if (!psi || ((uintptr_t)psi & 15) != 0) return CHEB_ERR_INVALID_ARG;
     if (!std::isfinite(gamma) || !std::isfinite(t) || !(tol > 0) || !std::isfinite(tol)) return CHEB_ERR_INVALID_ARG;
-    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF) return CHEB_ERR_INVALID_ARG;
+    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF && method != CHEB_METHOD_REMEZ)
+        return CHEB_ERR_INVALID_ARG;
     if (splits < 0 || path < 0 || path > 2) return CHEB_ERR_INVALID_ARG;
     Ctx C{n, prec, make_layout(n, prec), (unsigned char*)ws, (cudaStream_t)stream};
     CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), C.s));
@@ -280,7 +281,8 @@ cheb_status_t cheb_coefficients(double a, double phase_re, double phase_im, doub
     if (!std::isfinite(a) || !(tol > 0) || !std::isfinite(tol) || !coeffs || !K || max_K < 0)
         return CHEB_ERR_INVALID_ARG;
     if (!std::isfinite(phase_re) || !std::isfinite(phase_im)) return CHEB_ERR_INVALID_ARG;
-    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF) return CHEB_ERR_INVALID_ARG;
+    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF && method != CHEB_METHOD_REMEZ)
+        return CHEB_ERR_INVALID_ARG;
     std::vector<std::complex<double>> c;
     double err = 0;
     int k = make_coefficients(a, std::complex<double>(phase_re, phase_im), tol, method, max_K, c, &err);

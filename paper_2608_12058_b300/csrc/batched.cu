@@ -95,7 +95,8 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
     if (!batch_layout(B, n, precision, BL)) return CHEB_ERR_INVALID_ARG;
     if (!offsets || !h_cat || !J_cat || !gamma || !t || !psi_cat) return CHEB_ERR_INVALID_ARG;
     if (!(tol > 0) || !std::isfinite(tol)) return CHEB_ERR_INVALID_ARG;
-    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF) return CHEB_ERR_INVALID_ARG;
+    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF && method != CHEB_METHOD_REMEZ)
+        return CHEB_ERR_INVALID_ARG;
     if (!workspace || ((uintptr_t)workspace & 255) != 0 || ws_bytes < BL.total) return CHEB_ERR_WORKSPACE;
     const size_t cb = precision == CHEB_FP32 ? 8 : 16;
     std::vector<size_t> hoff(B), joff(B);

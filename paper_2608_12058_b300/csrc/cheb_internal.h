@@ -12,6 +12,7 @@ namespace cheb {
 void bessel_jn(double a, int mmax, std::vector<double>& out);
 double cf_correct_real(const std::vector<double>& a, int K, std::vector<double>& p);
 // method: 0 Chebyshev, 1 CF. Returns K or -1 (K would exceed max_K).
+double remez_real(bool odd, double a, int K, std::vector<double>& p);
 void monomial_to_chebyshev(int K, const std::complex<double>* a, std::complex<double>* c);
 int make_coefficients(double a, std::complex<double> phase, double tol, int method, int max_K,
                       std::vector<std::complex<double>>& c, double* err_bound);

@@ -238,6 +238,169 @@ double cf_correct_real(const std::vector<double>& a, int K, std::vector<double>&
 }
 
 // ---------------------------------------------------------------------------
+// Remez exchange (Sec. II.C, first method): the best uniform approximation of degree
+// <= K to f(x) = cos(a x) (odd = false) or sin(a x) (odd = true) on [-1, 1]. By
+// symmetry the best approximation of an even (odd) function is even (odd), so the
+// exchange runs in that subspace, spanned by phi_j = T_{2j} (T_{2j+1}), j = 0..J, on
+// [0, 1], where it satisfies the Haar condition (for the odd space on (0, 1]: x = 0
+// is a common zero of f and p). Each round solves p(x_i) + (-1)^i E = f(x_i) on a
+// reference of J + 2 increasing points (dense elimination with partial pivoting) and
+// moves the reference to the extrema of f - p, one per run of constant sign (found on
+// a Chebyshev-spaced grid, refined by golden section). Stops when max |f - p| is
+// within a factor 1 + 1e-7 of |E| (by de la Vallee Poussin's bound the minimax error
+// lies between the two, so p is minimax to that factor; tighter is below the rounding
+// of f - p at the largest degrees).
+// Returns max |f - p| and the Chebyshev coefficients p_0..p_K; -1 on failure.
+namespace {
+
+// Gaussian elimination with partial pivoting (A is m x m, row-major); false if singular.
+bool solve_dense(int m, std::vector<long double>& A, std::vector<long double>& b) {
+    for (int c = 0; c < m; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < m; ++r)
+            if (fabsl(A[(size_t)r * m + c]) > fabsl(A[(size_t)piv * m + c])) piv = r;
+        if (A[(size_t)piv * m + c] == 0.0L) return false;
+        if (piv != c) {
+            for (int k = 0; k < m; ++k) std::swap(A[(size_t)c * m + k], A[(size_t)piv * m + k]);
+            std::swap(b[c], b[piv]);
+        }
+        const long double d = A[(size_t)c * m + c];
+        for (int r = c + 1; r < m; ++r) {
+            const long double f = A[(size_t)r * m + c] / d;
+            if (f == 0.0L) continue;
+            for (int k = c; k < m; ++k) A[(size_t)r * m + k] -= f * A[(size_t)c * m + k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int c = m - 1; c >= 0; --c) {
+        long double acc = b[c];
+        for (int k = c + 1; k < m; ++k) acc -= A[(size_t)c * m + k] * b[k];
+        b[c] = acc / A[(size_t)c * m + c];
+    }
+    return true;
+}
+
+}  // namespace
+
+double remez_real(bool odd, double a_in, int K, std::vector<double>& p) {
+    const long double a = a_in, pi = 3.141592653589793238462643383279502884L;
+    auto f = [&](long double t) { return odd ? sinl(a * t) : cosl(a * t); };
+    const int par = odd ? 1 : 0;
+    const int J = odd ? (K - 1) / 2 : K / 2;  // highest index j with 2j + par <= K
+    p.assign(K + 1, 0.0);
+    // phi_j(x) = T_{2j+par}(x) for j = 0..J at one point, by the three-term recurrence
+    auto basis = [&](long double x, std::vector<long double>& out) {
+        long double t0 = 1.0L, t1 = x;
+        int deg = 0;
+        for (int j = 0; j <= J; ++j) {
+            const int want = 2 * j + par;
+            while (deg < want) {
+                const long double t2 = 2.0L * x * t1 - t0;
+                t0 = t1;
+                t1 = t2;
+                ++deg;
+            }
+            out[j] = t0;
+        }
+    };
+    const int G = 8 * (J + 2) + 64;
+    std::vector<long double> tg(G + 1);
+    for (int g = 0; g <= G; ++g) tg[g] = cosl(pi * (G - g) / (2.0L * G));  // 0 .. 1, increasing
+    if (J < 0) {  // no odd term allowed (K = 0): p = 0
+        long double m0 = 0.0L;
+        for (int g = 0; g <= G; ++g) m0 = std::max(m0, fabsl(f(tg[g])));
+        return (double)m0;
+    }
+    const int m = J + 2;
+    std::vector<long double> x(m), c(J + 1, 0.0L), phi(J + 1);
+    // initial reference: extrema of T_{2J+2+par} in [0, 1] (those > 0 for odd f)
+    for (int i = 0; i < m; ++i) x[i] = cosl(pi * (m - 1 - i) / (2.0L * m - 2.0L + 2.0L * par));
+    auto P = [&](long double t) {
+        basis(t, phi);
+        long double acc = 0.0L;
+        for (int j = 0; j <= J; ++j) acc += c[j] * phi[j];
+        return acc;
+    };
+    long double emax = 0.0L;
+    for (int it = 0; it < 60; ++it) {
+        std::vector<long double> A((size_t)m * m), b(m);
+        for (int i = 0; i < m; ++i) {
+            basis(x[i], phi);
+            for (int j = 0; j <= J; ++j) A[(size_t)i * m + j] = phi[j];
+            A[(size_t)i * m + J + 1] = (i & 1) ? -1.0L : 1.0L;
+            b[i] = f(x[i]);
+        }
+        if (!solve_dense(m, A, b)) return -1.0;
+        for (int j = 0; j <= J; ++j) c[j] = b[j];
+        const long double E = b[J + 1];
+        auto err = [&](long double t) { return f(t) - P(t); };
+        std::vector<long double> eg(G + 1);
+        long double gmax = 0.0L;
+        for (int g = 0; g <= G; ++g) {
+            eg[g] = err(tg[g]);
+            gmax = std::max(gmax, fabsl(eg[g]));
+        }
+        if (gmax <= 1e-17L) {  // f is (up to rounding) in the space
+            emax = gmax;
+            break;
+        }
+        // extrema, one per run of constant sign (the odd error vanishes at x = 0: skip it)
+        std::vector<long double> ex, ev;
+        int g = odd ? 1 : 0;
+        while (g <= G) {
+            const bool pos = eg[g] >= 0.0L;
+            int best = g, h = g;
+            while (h <= G && ((eg[h] >= 0.0L) == pos)) {
+                if (fabsl(eg[h]) > fabsl(eg[best])) best = h;
+                ++h;
+            }
+            long double lo = tg[std::max(best - 1, g)], hi = tg[std::min(best + 1, h - 1)];
+            long double xb = tg[best], eb = eg[best];
+            if (hi > lo) {
+                const long double gr = 0.6180339887498948482L;
+                long double c1 = hi - gr * (hi - lo), c2 = lo + gr * (hi - lo);
+                long double f1 = fabsl(err(c1)), f2 = fabsl(err(c2));
+                for (int r = 0; r < 24; ++r) {  // the error is flat at its extremum
+                    if (f1 > f2) {
+                        hi = c2;
+                        c2 = c1;
+                        f2 = f1;
+                        c1 = hi - gr * (hi - lo);
+                        f1 = fabsl(err(c1));
+                    } else {
+                        lo = c1;
+                        c1 = c2;
+                        f1 = f2;
+                        c2 = lo + gr * (hi - lo);
+                        f2 = fabsl(err(c2));
+                    }
+                }
+                const long double xc = 0.5L * (lo + hi), ec = err(xc);
+                if (fabsl(ec) > fabsl(eb) && ((ec >= 0.0L) == pos)) {
+                    xb = xc;
+                    eb = ec;
+                }
+            }
+            ex.push_back(xb);
+            ev.push_back(eb);
+            g = h;
+        }
+        if ((int)ex.size() < m) return -1.0;
+        size_t lo_i = 0, hi_i = ex.size();  // keep m alternating extrema: drop the smaller end
+        while (hi_i - lo_i > (size_t)m) {
+            if (fabsl(ev[lo_i]) < fabsl(ev[hi_i - 1])) ++lo_i;
+            else --hi_i;
+        }
+        emax = 0.0L;
+        for (size_t i = 0; i < ev.size(); ++i) emax = std::max(emax, fabsl(ev[i]));
+        for (int i = 0; i < m; ++i) x[i] = ex[lo_i + i];
+        if (emax - fabsl(E) <= 1e-7L * emax) break;
+    }
+    for (int j = 0; j <= J; ++j) p[2 * j + par] = (double)c[j];
+    return (double)emax;
+}
+
+// ---------------------------------------------------------------------------
 int make_coefficients(double a, std::complex<double> phase, double tol, int method, int max_K,
                       std::vector<std::complex<double>>& c, double* err_bound) {
     const int T = table_length(a);
@@ -267,6 +430,31 @@ int make_coefficients(double a, std::complex<double> phase, double tol, int meth
     for (int m = 0; m <= T; ++m) {
         double v = (m == 0 ? 1.0 : 2.0) * jm[m] * (((m >> 1) & 1) ? -1.0 : 1.0);
         if (m & 1) as[m] = v; else ac[m] = v;
+    }
+    if (method == 2) {
+        // Remez: the degree comes from the CF estimate of the minimax error (cheap);
+        // the exchange then runs at that degree, and one degree more while its
+        // combined error hypot(E_cos, E_sin) exceeds tol (the Chebyshev degree always
+        // suffices: the minimax error is below the series' truncation error).
+        std::vector<double> qc, qs;
+        const int Kcheb = K;
+        while (K > 0) {
+            const double lc2 = cf_correct_real(ac, K - 1, qc), ls2 = cf_correct_real(as, K - 1, qs);
+            if (!(std::hypot(lc2, ls2) <= tol)) break;
+            --K;
+        }
+        std::vector<double> pc, ps;
+        for (;; ++K) {
+            const double ec = remez_real(false, a, K, pc), es = remez_real(true, a, K, ps);
+            if (ec < 0 || es < 0) return -1;
+            err = std::hypot(ec, es);
+            if (err <= tol || K >= Kcheb) break;
+        }
+        if (K > max_K) return -1;
+        c.resize(K + 1);
+        for (int m = 0; m <= K; ++m) c[m] = std::complex<double>(pc[m], -ps[m]) * phase;
+        if (err_bound) *err_bound = err;
+        return K;
     }
     std::vector<double> pc, ps, qc, qs;
     double lc = cf_correct_real(ac, K, pc), ls = cf_correct_real(as, K, ps);

@@ -90,6 +90,22 @@ def test_cf_method_matches_oracle(cuda_lib, oracle, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_remez_method_matches_dense_exponential(cuda_lib, oracle, prec):
+    """Remez minimax coefficients (the product's host generator; the oracle has no
+    Remez) through the GPU path agree with the dense exp(-itH) psi to within the
+    series tolerance plus the precision's rounding."""
+    n = 9
+    h, J = I.sk_instance(n, 79)
+    psi = I.random_state(n, 80)
+    tol = 1e-10 if prec == "fp64" else 2.0 ** -23
+    ref = oracle.dense_expmv(h, J, 0.9, 5.0, psi)
+    y, info = _run(h, J, 0.9, 5.0, psi, prec, tol, method="remez")
+    _, cinfo = oracle.expmv(h, J, 0.9, 5.0, psi, tol, method="cf")
+    assert info["K"] == cinfo["K"]
+    assert _rel(y, ref) <= tol + TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("n", [9, 14])
 def test_time_splits_match_oracle(cuda_lib, oracle, prec, n):
     h, J = I.sk_instance(n, 90 + n)

@@ -82,3 +82,69 @@ def test_cf_expmv_matches_dense(oracle):
     y, info = oracle.expmv(h, J, 0.9, 4.0, psi, 1e-10, method="cf")
     ref = oracle.dense_expmv(h, J, 0.9, 4.0, psi)
     assert np.linalg.norm(y - ref) <= 1e-10 + info["eval_bound"]
+
+
+# Remez exchange (Sec. II.C): the product's host generator, pinned by the
+# alternation theorem (a certificate of optimality) and against the oracle's CF.
+
+def _alternation_count(e, level):
+    """Number of alternating-sign extrema of the sampled error e (increasing abscissae)
+    whose size is at least `level` (one per run of constant sign; qualifying runs of
+    the same sign in a row count once)."""
+    count, last = 0, 0
+    run_sign, run_max = None, 0.0
+    for v in np.append(e, 0.0):
+        s = 1 if v > 0 else (-1 if v < 0 else 0)
+        if s != run_sign:
+            if run_sign and run_max >= level and run_sign != last:
+                count += 1
+                last = run_sign
+            run_sign, run_max = s, 0.0
+        run_max = max(run_max, abs(v))
+    return count
+
+
+@pytest.mark.parametrize("a,tol", [(3.0, 1e-8), (20.0, 1e-10), (30.5, 1e-9), (100.0, 1e-9), (430.0, 2.0 ** -23)])
+def test_remez_equioscillates(a, tol):
+    """cos(ax) and sin(ax) parts each equioscillate: at least J+2 alternating extrema
+    of equal size on [0, 1] (J+1 = dimension of the even/odd subspace of degree <= K),
+    which by the alternation theorem makes each the unique minimax polynomial."""
+    from paper_2608_12058_b300 import api
+
+    c, err = api.coefficients(a, tol, "remez")
+    K = c.shape[0] - 1
+    ld = np.longdouble  # the error curves are evaluated in extended precision
+    pc, ps = c.real.astype(ld), (-c.imag).astype(ld)
+    x = np.cos(np.linspace(ld(np.pi) / 2, ld(0.0), 400001, dtype=ld))  # [0, 1], increasing
+    ec = np.cos(ld(a) * x) - np.polynomial.chebyshev.chebval(x, pc)
+    es = np.sin(ld(a) * x) - np.polynomial.chebyshev.chebval(x, ps)
+    Jc, Js = K // 2, (K - 1) // 2
+    # the odd error vanishes at x = 0, which is not an extremum. The margin covers the
+    # rounding of the coefficients to FP64 (de la Vallee Poussin: alternation at level
+    # (1 - d) E puts the minimax error within a factor 1 - d of E)
+    for e, J, q in ((ec, Jc, pc), (es[1:], Js, ps)):
+        E = np.max(np.abs(e))
+        d = max(1e-3, 10 * np.finfo(np.float64).eps * float(np.sum(np.abs(q))) / float(E))
+        assert d < 0.05
+        assert _alternation_count(e, E * (1 - d)) >= J + 2
+    Ec, Es = float(np.max(np.abs(ec))), float(np.max(np.abs(es)))
+    assert np.hypot(Ec, Es) <= tol * (1 + 1e-6)
+    assert abs(np.hypot(Ec, Es) - err) <= 1e-5 * err
+
+
+@pytest.mark.parametrize("a,tol", [(20.0, 1e-10), (60.0, 1e-9), (430.0, 2.0 ** -23)])
+def test_remez_agrees_with_oracle_cf_and_beats_chebyshev(oracle, a, tol):
+    """The Remez degree equals the oracle's CF degree and its minimax error matches the
+    CF estimate |lambda| (CF is near-best) while staying below the truncation bound of
+    the Chebyshev series of the same degree."""
+    from paper_2608_12058_b300 import api
+
+    cr, er = api.coefficients(a, tol, "remez")
+    cf, Kcf, ecf = oracle.cf_coeffs(a, tol)
+    K = cr.shape[0] - 1
+    assert K == Kcf
+    assert abs(er - ecf) <= 1e-3 * ecf
+    # Chebyshev series of the same degree: sup error <= its tail sum_{m>K} 2|J_m(a)|
+    J = oracle.bessel_j(a, int(a) + 200)
+    tail = 2.0 * np.sum(np.abs(J[K + 1:]))
+    assert er <= tail
