@@ -171,6 +171,41 @@ cheb_status_t cheb_anneal(int n, const double* h, const double* J, int S, const 
                           size_t workspace_bytes, void* stream, cheb_info_t* infos);
 
 /*
+ * General piecewise-constant schedule H_s = b_s diag(E) + a_s sum_j X_j (the usual
+ * annealing form A(t) H_X + B(t) H_P sampled per segment; cheb_anneal is b_s = 1):
+ * psi <- exp(-i t_s H_s) psi for s = 0..S-1. b_s may be zero or negative: b_s H_P
+ * has centre b_s c and half-width |b_s| (Emax - Emin)/2, from one spectral scan.
+ *   a_s, b_s, t_s: HOST arrays of S doubles. Other arguments as cheb_anneal; the
+ *   energy in infos is that of the segment's diagonal part b_s H_P.
+ * Errors: as cheb_anneal.
+ */
+cheb_status_t cheb_anneal_general(int n, const double* h, const double* J, int S, const double* a_s,
+                                  const double* b_s, const double* t_s, void* psi,
+                                  cheb_precision_t precision, double tol, cheb_method_t method,
+                                  void* boundaries, void* workspace, size_t workspace_bytes,
+                                  void* stream, cheb_info_t* infos);
+
+/*
+ * Time-dependent evolution i dpsi/dt = H(t) psi with H(t) = A(t) sum_j X_j + B(t) H_P
+ * by the fourth-order commutator-free Magnus integrator that Sec. III.B builds on:
+ * per step of length dt_m, with Gauss-Legendre nodes t1,2 = t + (1/2 -+ sqrt(3)/6) dt_m,
+ *   psi <- exp(-i dt (w1 H(t1) + w2 H(t2))) exp(-i dt (w2 H(t1) + w1 H(t2))) psi,
+ *   w1 = 1/4 - sqrt(3)/6, w2 = 1/4 + sqrt(3)/6
+ * (the right factor first). Each factor is one segment of cheb_anneal_general.
+ *   dt:     HOST array of `steps` step lengths.
+ *   nodes:  HOST array of 4*steps doubles: A(t1), B(t1), A(t2), B(t2) per step.
+ *   tol:    truncation budget of all 2*steps exponentials together (the integrator's
+ *           own O(dt^5) local error is the caller's choice of steps).
+ *   infos:  nullable HOST array of 2*steps cheb_info_t (one per exponential).
+ * Workspace: cheb_workspace_bytes(n, precision). Errors: INVALID_ARG (steps < 1,
+ * null or non-finite dt/nodes), otherwise as cheb_anneal.
+ */
+cheb_status_t cheb_magnus4(int n, const double* h, const double* J, int steps, const double* dt,
+                           const double* nodes, void* psi, cheb_precision_t precision, double tol,
+                           cheb_method_t method, void* workspace, size_t workspace_bytes, void* stream,
+                           cheb_info_t* infos);
+
+/*
  * Batched independent instances (Sec. III.A batches many small problems per launch):
  * psi_i <- exp(-i t_i H_i) psi_i for i = 0..B-1, each with its own n_i, couplings,
  * gamma_i and t_i, and its own spectral interval and polynomial (the paper pads the

@@ -59,6 +59,10 @@ SIGNATURES = {
                                    c_void_p, ctypes.POINTER(Info)]),
     "cheb_anneal": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, c_void_p, c_int, c_double, c_int, c_void_p,
                             c_void_p, c_size_t, c_void_p, ctypes.POINTER(Info)]),
+    "cheb_anneal_general": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, _dp, c_void_p, c_int, c_double, c_int,
+                                    c_void_p, c_void_p, c_size_t, c_void_p, ctypes.POINTER(Info)]),
+    "cheb_magnus4": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, c_void_p, c_int, c_double, c_int, c_void_p, c_size_t,
+                             c_void_p, ctypes.POINTER(Info)]),
     "cheb_batched_workspace_bytes": (c_size_t, [c_int, _ip, c_int]),
     "cheb_expmv_batched": (c_int, [c_int, _ip, ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp, _dp, c_void_p, c_int,
                                    c_double, c_int, c_void_p, c_size_t, c_void_p, ctypes.POINTER(Info)]),

@@ -158,6 +158,91 @@ def anneal(h, J, gammas, ts, psi, tol: Optional[float] = None, method: str = "ch
     return [x.as_dict() for x in infos] if info else None
 
 
+def anneal_general(h, J, a_s, b_s, ts, psi, tol: Optional[float] = None, method: str = "chebyshev",
+                   boundaries=None, info: bool = True):
+    """psi <- prod_s exp(-i t_s (b_s H_P + a_s sum_j X_j)) psi in place (cheb_anneal_general)."""
+    h, J = _f64(h), _f64(J)
+    a_s, b_s, ts = _f64(a_s), _f64(b_s), _f64(ts)
+    n = h.shape[0]
+    S = a_s.shape[0]
+    assert b_s.shape[0] == S and ts.shape[0] == S
+    _check_state(psi, n)
+    prec = precision_of(psi)
+    if tol is None:
+        tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+    bptr = None
+    if boundaries is not None:
+        if boundaries.dtype != psi.dtype or tuple(boundaries.shape) != (S, 1 << n) or not boundaries.is_contiguous():
+            raise ValueError("boundaries must be a contiguous (S, 2^n) tensor of psi's dtype")
+        bptr = ctypes.c_void_p(boundaries.data_ptr())
+    ws = workspace(n, prec, psi.device)
+    p, nb = _ws_ptr(ws)
+    infos = (_lib.Info * S)() if info else None
+    code = _lib.lib().cheb_anneal_general(n, _dp(h), _dp(J), S, _dp(a_s), _dp(b_s), _dp(ts),
+                                          ctypes.c_void_p(psi.data_ptr()), PREC[prec], float(tol), METHOD[method],
+                                          bptr, ctypes.c_void_p(p), nb, _stream_ptr(psi.device), infos)
+    _lib.check(code, "cheb_anneal_general")
+    return [x.as_dict() for x in infos] if info else None
+
+
+def magnus4_nodes(A, B, T: float, steps: int):
+    """Sample the schedule for cheb_magnus4: equal steps dt = T/steps of [0, T] and, per
+    step, (A(t1), B(t1), A(t2), B(t2)) at t1,2 = t + (1/2 -+ sqrt(3)/6) dt."""
+    dt = T / steps
+    nodes = np.empty((steps, 4))
+    for m in range(steps):
+        t1 = m * dt + (0.5 - np.sqrt(3.0) / 6.0) * dt
+        t2 = m * dt + (0.5 + np.sqrt(3.0) / 6.0) * dt
+        nodes[m] = (A(t1), B(t1), A(t2), B(t2))
+    return np.full(steps, dt), nodes
+
+
+def magnus4(h, J, dt, nodes, psi, tol: Optional[float] = None, method: str = "chebyshev", info: bool = False):
+    """psi <- the fourth-order commutator-free Magnus propagator of H(t) = A(t) sum_j X_j +
+    B(t) H_P, in place (cheb_magnus4); dt, nodes as from magnus4_nodes."""
+    h, J = _f64(h), _f64(J)
+    dt = _f64(dt)
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1))
+    n = h.shape[0]
+    steps = dt.shape[0]
+    assert nodes.shape[0] == 4 * steps
+    _check_state(psi, n)
+    prec = precision_of(psi)
+    if tol is None:
+        tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+    ws = workspace(n, prec, psi.device)
+    p, nb = _ws_ptr(ws)
+    infos = (_lib.Info * (2 * steps))() if info else None
+    code = _lib.lib().cheb_magnus4(n, _dp(h), _dp(J), steps, _dp(dt), _dp(nodes), ctypes.c_void_p(psi.data_ptr()),
+                                   PREC[prec], float(tol), METHOD[method], ctypes.c_void_p(p), nb,
+                                   _stream_ptr(psi.device), infos)
+    _lib.check(code, "cheb_magnus4")
+    return [x.as_dict() for x in infos] if info else None
+
+
+def magnus4_adaptive(h, J, A, B, T: float, psi, tol: float, steps0: int = 8, method: str = "chebyshev"):
+    """psi <- psi(T) with the number of equal Magnus steps chosen a posteriori for an
+    integration error of about tol: runs with M and 2M steps estimate the error of the
+    2M run as |y_M - y_2M| / 15 (fourth order), and the step count is raised by the
+    factor (estimate / tol)^(1/4) when needed. Returns the number of steps used."""
+    import torch
+
+    y1, y2 = psi.clone(), psi.clone()
+    dt, nd = magnus4_nodes(A, B, T, steps0)
+    magnus4(h, J, dt, nd, y1, method=method)
+    dt, nd = magnus4_nodes(A, B, T, 2 * steps0)
+    magnus4(h, J, dt, nd, y2, method=method)
+    est = float(torch.linalg.vector_norm(y1 - y2)) / 15.0
+    M = 2 * steps0
+    if est > tol:
+        M = int(np.ceil(M * (est / tol) ** 0.25 * 1.1))
+        dt, nd = magnus4_nodes(A, B, T, M)
+        y2.copy_(psi)
+        magnus4(h, J, dt, nd, y2, method=method)
+    psi.copy_(y2)
+    return M
+
+
 def batch_offsets(ns):
     """Contiguous layout of a batch: element offset of each state (padded to even)."""
     off, cur = [], 0

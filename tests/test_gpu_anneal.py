@@ -45,3 +45,74 @@ def test_anneal_single_segment_is_expmv(cuda_lib):
     api.anneal(h, J, [0.8], [2.5], x1, tol=1e-12)
     api.expmv(h, J, 0.8, 2.5, x2, tol=1e-12)
     assert torch.equal(x1, x2)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [7, 14])
+def test_anneal_general_matches_oracle(cuda_lib, oracle, prec, n):
+    """Segments b_s H_P + a_s sum_j X_j (b_s of both signs and zero) against the oracle."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    h, J = I.sk_instance(n, 40 + n)
+    psi = I.random_state(n, 41 + n)
+    a_s = np.array([1.2, 0.0, -0.4, 0.8, 0.3])
+    b_s = np.array([0.3, 1.1, -0.7, 0.0, 2.0])
+    ts = np.array([0.6, 0.4, 0.9, 0.5, 0.7])
+    tol = 1e-12 if prec == "fp64" else 2.0 ** -23
+    ref = oracle.anneal_general(h, J, a_s, b_s, ts, psi, tol)
+    dt = torch.complex64 if prec == "fp32" else torch.complex128
+    x = torch.from_numpy(psi).to(dt).cuda()
+    api.anneal_general(h, J, a_s, b_s, ts, x, tol=tol, info=False)
+    y = x.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) <= (1e-12 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,steps", [(8, 6), (16, 4)])
+def test_magnus4_matches_oracle(cuda_lib, oracle, prec, n, steps):
+    """cheb_magnus4 against the oracle's Magnus integrator on the same Gauss-node samples
+    of a smooth annealing schedule."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    T = 2.0
+    h, J = I.sk_instance(n, 50 + n)
+    psi = I.random_state(n, 51 + n)
+    A = lambda t: 1.5 * (1 - t / T) + 0.3 * np.sin(3 * t)
+    B = lambda t: t / T + 0.2 * np.cos(2 * t)
+    dt, nodes = api.magnus4_nodes(A, B, T, steps)
+    dto, nodeso = oracle.magnus4_nodes(A, B, T, steps)
+    tol = 1e-12 if prec == "fp64" else 2.0 ** -23
+    ref = oracle.magnus4(h, J, dto, nodeso, psi, tol)
+    dtype = torch.complex64 if prec == "fp32" else torch.complex128
+    x = torch.from_numpy(psi).to(dtype).cuda()
+    infos = api.magnus4(h, J, dt, nodes, x, tol=tol, info=True)
+    assert len(infos) == 2 * steps
+    y = x.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) <= (1e-12 if prec == "fp64" else 1e-5)
+
+
+def test_magnus4_adaptive_reaches_tolerance(cuda_lib, oracle):
+    """The a-posteriori step count meets the requested integration error against an
+    ODE solution of the dense system (FP64, n = 6)."""
+    import torch
+    from scipy.integrate import solve_ivp
+
+    from paper_2608_12058_b300 import api
+
+    n, T = 6, 2.0
+    h, J = I.sk_instance(n, 63)
+    psi = I.random_state(n, 64)
+    A = lambda t: 1.5 * (1 - t / T) + 0.3 * np.sin(3 * t)
+    B = lambda t: t / T + 0.2 * np.cos(2 * t)
+    HP = np.diag(oracle.energies(h, J))
+    HX = oracle.dense_hamiltonian(np.zeros(n), np.zeros((n, n)), 1.0)
+    sol = solve_ivp(lambda t, y: -1j * (A(t) * HX + B(t) * HP) @ y, (0, T), psi, method="DOP853",
+                    rtol=1e-13, atol=1e-13)
+    x = torch.from_numpy(psi).cuda()
+    M = api.magnus4_adaptive(h, J, A, B, T, x, tol=1e-8)
+    err = np.linalg.norm(x.cpu().numpy() - sol.y[:, -1])
+    assert M >= 16 and err <= 3e-8
