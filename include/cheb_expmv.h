@@ -49,11 +49,21 @@ typedef enum {
 typedef enum { CHEB_METHOD_CHEBYSHEV = 0, CHEB_METHOD_CF = 1, CHEB_METHOD_REMEZ = 2 } cheb_method_t;
 typedef enum { CHEB_FP32 = 0, CHEB_FP64 = 1 } cheb_precision_t;
 
-/* Kernel path for the Clenshaw steps. AUTO picks the fastest available path for
- * (n, precision); PLAIN forces the one-pass kernel that reads every bit-flip
+/* Kernel path for the Clenshaw steps. AUTO picks the fastest path measured for
+ * (n, precision): the whole run in one CTA's shared memory for n <= 13 (FP32) or 12
+ * (FP64), the plain kernel up to n = 19 (FP32) and for FP64, the fused kernels above;
+ * batches run instances of n = 14..17 (FP32) or 13..16 (FP64) on clusters. PLAIN forces the one-pass kernel that reads every bit-flip
  * partner from global memory (the reference GPU path); FUSED forces the
- * shared-memory tiled kernels (FP32, n >= 13 only). */
-typedef enum { CHEB_PATH_AUTO = 0, CHEB_PATH_PLAIN = 1, CHEB_PATH_FUSED = 2 } cheb_path_t;
+ * shared-memory tiled kernels (FP32, n >= 11 only); CLUSTER forces the whole run on
+ * one thread-block cluster with the vectors in distributed shared memory (FP32
+ * n = 14..17, FP64 n = 13..16; UNSUPPORTED elsewhere or if the device has no room
+ * for such a cluster). */
+typedef enum {
+    CHEB_PATH_AUTO = 0,
+    CHEB_PATH_PLAIN = 1,
+    CHEB_PATH_FUSED = 2,
+    CHEB_PATH_CLUSTER = 3
+} cheb_path_t;
 
 typedef struct {
     int K;               /* polynomial degree per time slice (matvecs per slice) */

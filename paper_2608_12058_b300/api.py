@@ -15,7 +15,7 @@ from . import _lib
 
 PREC = {"fp32": 0, "fp64": 1}
 METHOD = {"chebyshev": 0, "cf": 1, "remez": 2}
-PATH = {"auto": 0, "plain": 1, "fused": 2}
+PATH = {"auto": 0, "plain": 1, "fused": 2, "cluster": 3}
 
 _ws_cache = {}
 

@@ -135,8 +135,35 @@ cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::c
                               psi, C.s));
         return CHEB_OK;
     }
+    const int csb = cluster_slice_bits(C.prec);
+    if (path == CHEB_PATH_CLUSTER && C.n > csb && C.n <= csb + 4) {
+        // whole run on one cluster; its descriptor goes to the reduction scratch, which
+        // the run does not otherwise use
+        CUDA_TRY(cudaMemcpyAsync(C.ws + C.L.coef, c.data(), c.size() * sizeof(std::complex<double>),
+                                 cudaMemcpyHostToDevice, C.s));
+        SmallDesc d{};
+        d.n = C.n;
+        d.K = K;
+        d.Q = Q;
+        d.g = g;
+        d.coef = (const double*)(C.ws + C.L.coef);
+        d.tiles = C.tiles();
+        d.elow = C.elow();
+        d.psi = psi;
+        SmallDesc* dd = (SmallDesc*)C.part();
+        CUDA_TRY(cudaMemcpyAsync(dd, &d, sizeof(d), cudaMemcpyHostToDevice, C.s));
+        const cudaError_t e = launch_cluster_batched(C.prec, C.n, 1, dd, C.s);
+        if (e == cudaSuccess) return CHEB_OK;
+        (void)cudaGetLastError();
+        return e == cudaErrorNotSupported ? CHEB_ERR_UNSUPPORTED : CHEB_ERR_CUDA;
+    } else if (path == CHEB_PATH_CLUSTER) {
+        return CHEB_ERR_UNSUPPORTED;
+    }
+    // AUTO: below 2^20 amplitudes (L2-resident vectors) a step is launch-bound and the
+    // one-launch plain kernel is faster than the two-pass fused step (measured)
     bool fused = false;
-    if (path == CHEB_PATH_FUSED || path == CHEB_PATH_AUTO) fused = fused_supported(C.n, C.prec);
+    if (path == CHEB_PATH_FUSED || (path == CHEB_PATH_AUTO && C.n > kPlainMaxF32))
+        fused = fused_supported(C.n, C.prec);
     if (path == CHEB_PATH_FUSED && !fused) return CHEB_ERR_UNSUPPORTED;
     unsigned char* B[2] = {C.ws + C.L.b0, C.ws + C.L.b1};
     launch_scale(C.prec, N, psi, B[1], c[K].real(), c[K].imag(), C.s);
@@ -209,7 +236,7 @@ cheb_status_t expmv_impl(int n, const double* h, const double* J, double gamma, 
     if (!std::isfinite(gamma) || !std::isfinite(t) || !(tol > 0) || !std::isfinite(tol)) return CHEB_ERR_INVALID_ARG;
     if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF && method != CHEB_METHOD_REMEZ)
         return CHEB_ERR_INVALID_ARG;
-    if (splits < 0 || path < 0 || path > 2) return CHEB_ERR_INVALID_ARG;
+    if (splits < 0 || path < 0 || path > 3) return CHEB_ERR_INVALID_ARG;
     Ctx C{n, prec, make_layout(n, prec), (unsigned char*)ws, (cudaStream_t)stream};
     CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), C.s));
     double emin = 0, emax = 0;
@@ -349,7 +376,7 @@ cheb_status_t cheb_poly_apply(int n, const double* h, const double* J, double ga
     if (!psi || ((uintptr_t)psi & 15) != 0 || !coeffs) return CHEB_ERR_INVALID_ARG;
     if (!std::isfinite(gamma) || !std::isfinite(center) || !(radius > 0) || !std::isfinite(radius))
         return CHEB_ERR_INVALID_ARG;
-    if (K < 0 || K > kMaxK || path < 0 || path > 2) return CHEB_ERR_INVALID_ARG;
+    if (K < 0 || K > kMaxK || path < 0 || path > 3) return CHEB_ERR_INVALID_ARG;
     if (!finite_all(coeffs, 2 * (size_t)(K + 1))) return CHEB_ERR_INVALID_ARG;
     Ctx C{n, precision, make_layout(n, precision), (unsigned char*)workspace, (cudaStream_t)stream};
     CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), C.s));

@@ -6,9 +6,10 @@
 //  1. Spectral bounds of all instances, one host synchronisation.
 //  2. Host: centre, radius, fixed-point tables and coefficients per instance.
 //  3. Instances small enough for one CTA's shared memory (n <= 13 FP32, <= 12
-//     FP64) run in a single launch, one CTA each. Larger instances run their
-//     Clenshaw step loops on a pool of streams, longest first, joined back into
-//     the caller's stream.
+//     FP64) run in a single launch, one CTA each; the next four sizes run whole on
+//     a thread-block cluster each (cluster.cu), one launch per size. Larger
+//     instances run their Clenshaw step loops on a pool of streams, longest first,
+//     joined back into the caller's stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -145,6 +146,11 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
     std::vector<SmallDesc> descs;
     int small_max_n = 0;
     const int small_lim = precision == CHEB_FP32 ? kSmallMaxF32 : kSmallMaxF64;
+    // mid-size instances run whole on a thread-block cluster, grouped by size
+    const int cl_sb = cluster_slice_bits(precision);
+    const int cl_lim = cl_sb + 4;
+    std::vector<std::vector<SmallDesc>> cdescs(cl_lim + 1);
+    std::vector<std::vector<int>> cidx(cl_lim + 1);
     for (int i = 0; i < B; ++i) {
         Inst& x = in[i];
         x.emin = std::ldexp((double)mm[2 * i], -qb[i]);
@@ -163,7 +169,8 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
         st = slice_coefficients(t[i], x.c, x.r, tol, method, 0, x.coef, &x.K, &x.slices, &x.err);
         if (st != CHEB_OK) return st;
         x.small = n[i] <= small_lim && x.slices == 1 && x.K > 0;
-        if (x.small) {
+        const bool clus = !x.small && n[i] > cl_sb && n[i] <= cl_lim && x.slices == 1 && x.K > 0;
+        if (x.small || clus) {
             CUDA_TRY(cudaMemcpyAsync(C.ws + C.L.coef, x.coef.data(), x.coef.size() * sizeof(std::complex<double>),
                                      cudaMemcpyHostToDevice, s0));
             SmallDesc d{};
@@ -175,19 +182,46 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
             d.tiles = C.tiles();
             d.elow = C.elow();
             d.psi = psi_i(i);
-            descs.push_back(d);
-            small_max_n = std::max(small_max_n, n[i]);
+            if (x.small) {
+                descs.push_back(d);
+                small_max_n = std::max(small_max_n, n[i]);
+            } else {
+                cdescs[n[i]].push_back(d);
+                cidx[n[i]].push_back(i);
+                x.small = true;  // handled by its cluster launch (or taken back below)
+            }
         } else if (x.K == 0) {
             for (int q = 0; q < x.slices; ++q)
                 launch_scale(precision, (int64_t)1 << n[i], psi_i(i), psi_i(i), x.coef[0].real(), x.coef[0].imag(), s0);
             x.small = true;  // done
         }
     }
-    // 3a. all small instances in one launch
+    // the stream pool forks here, so that the large instances overlap the small ones
+    cudaEvent_t fork;
+    CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(fork, s0));
+    // 3a. all small instances in one launch, mid-size ones in one cluster launch per size
+    // (the descriptor region holds B entries: small ones first, then the clustered)
+    size_t dpos = 0;
     if (!descs.empty()) {
         CUDA_TRY(cudaMemcpyAsync(ws + BL.descs, descs.data(), descs.size() * sizeof(SmallDesc), cudaMemcpyHostToDevice,
                                  s0));
         CUDA_TRY(launch_small_batched(precision, (int)descs.size(), small_max_n, (const SmallDesc*)(ws + BL.descs), s0));
+        dpos = descs.size();
+    }
+    for (int nn = cl_sb + 1; nn <= cl_lim; ++nn) {
+        if (cdescs[nn].empty()) continue;
+        const SmallDesc* dd = (const SmallDesc*)(ws + BL.descs) + dpos;
+        CUDA_TRY(cudaMemcpyAsync((void*)dd, cdescs[nn].data(), cdescs[nn].size() * sizeof(SmallDesc),
+                                 cudaMemcpyHostToDevice, s0));
+        dpos += cdescs[nn].size();
+        const cudaError_t e = launch_cluster_batched(precision, nn, (int)cdescs[nn].size(), dd, s0);
+        if (e == cudaErrorNotSupported) {
+            (void)cudaGetLastError();
+            for (int i : cidx[nn]) in[i].small = false;  // no room for such clusters: step kernels
+        } else if (e != cudaSuccess) {
+            return CHEB_ERR_CUDA;
+        }
     }
     // 3b. larger instances on the stream pool, longest first onto the least loaded stream
     std::vector<int> big;
@@ -200,9 +234,6 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
         cudaStream_t* pool = nullptr;
         cheb_status_t st = stream_pool(&pool);
         if (st != CHEB_OK) return st;
-        cudaEvent_t fork;
-        CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        CUDA_TRY(cudaEventRecord(fork, s0));
         double load[kPoolStreams] = {0};
         bool used[kPoolStreams] = {false};
         for (int i : big) {
@@ -218,7 +249,6 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
                 if (st != CHEB_OK) return st;
             }
         }
-        cudaEventDestroy(fork);
         for (int j = 0; j < kPoolStreams; ++j) {
             if (!used[j]) continue;
             cudaEvent_t join;
@@ -228,6 +258,7 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
             cudaEventDestroy(join);
         }
     }
+    cudaEventDestroy(fork);
     // 4. per-instance results
     if (infos) {
         for (int i = 0; i < B; ++i) {

@@ -69,6 +69,11 @@ struct SmallDesc {
     void* psi;             // its state, in/out
 };
 cudaError_t launch_small_batched(int prec, int count, int max_n, const SmallDesc* descs, cudaStream_t s);
+// Whole runs of instances of one size n on thread-block clusters (cluster.cu): one
+// cluster of 2^(n - SB) CTAs per instance, SB = cluster_slice_bits(prec), n - SB in
+// 1..4. Returns cudaErrorNotSupported when no such cluster fits on the device.
+int cluster_slice_bits(int prec);
+cudaError_t launch_cluster_batched(int prec, int n, int count, const SmallDesc* descs, cudaStream_t s);
 void launch_norm_energy(int prec, int n, int M, int Q, const int64_t* tiles, const int64_t* elow,
                         double c, double r, const void* psi, double* part, double* out2,
                         cudaStream_t s);

@@ -27,7 +27,10 @@ def test_mixed_batch_matches_oracle(cuda_lib, oracle, prec):
 
     from paper_2608_12058_b300 import api
 
-    ns = [1, 3, 8, 12, 13, 14, 16, 9, 15, 12]
+    # sizes of every path: one CTA per instance (n <= 13 FP32, <= 12 FP64), one
+    # thread-block cluster per instance (n = 14..17 FP32, 13..16 FP64; repeated sizes
+    # share a launch), step kernels on the stream pool (larger)
+    ns = [1, 3, 8, 12, 13, 14, 16, 9, 15, 12, 17, 14, 17]
     hs, Js, gs, ts = _batch(ns, 3)
     offs, total = api.batch_offsets(ns)
     tol = 1e-12 if prec == "fp64" else 2.0 ** -23

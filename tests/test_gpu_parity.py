@@ -89,6 +89,20 @@ def test_cf_method_matches_oracle(cuda_lib, oracle, prec):
     assert _rel(y, ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec,n", [("fp32", 14), ("fp32", 15), ("fp32", 17), ("fp64", 13), ("fp64", 16)])
+def test_cluster_path_matches_oracle(cuda_lib, oracle, prec, n):
+    """The whole run on one thread-block cluster (vectors in distributed shared memory,
+    2..16 CTAs) against the oracle, forced and through the automatic choice."""
+    h, J = I.sk_instance(n, 120 + n)
+    psi = I.random_state(n, 121 + n)
+    tol = 1e-12 if prec == "fp64" else 2.0 ** -23
+    ref, oinfo = oracle.expmv(h, J, 0.8, 3.0, psi, tol)
+    for path in ("cluster", "auto"):
+        y, info = _run(h, J, 0.8, 3.0, psi, prec, tol, path=path)
+        assert info["K"] == oinfo["K"]
+        assert _rel(y, ref) <= TOL[prec], path
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_remez_method_matches_dense_exponential(cuda_lib, oracle, prec):
     """Remez minimax coefficients (the product's host generator; the oracle has no
