@@ -157,6 +157,72 @@ def traffic_from_profile():
         return None
 
 
+def other_workloads(dev):
+    """One timed run each (after a warm-up run) of the batch and anneal workloads:
+    the 512-instance batch (n ~ U{12..20}, complex64, tol 1e-6) and the n=22,
+    64-segment anneal forward plus its full gradient (complex64)."""
+    import numpy as np
+    import torch
+
+    from paper_2608_12058_b300 import api
+    from paper_2608_12058_b300 import inputs as I
+
+    out = {}
+    b = I.config_batch()
+    offs, total = api.batch_offsets(b.ns)
+    cat = np.zeros(total, dtype=np.complex64)
+    for nn, o in zip(b.ns, offs):
+        cat[o:o + (1 << nn)] = 2.0 ** (-nn / 2)
+    x0 = torch.from_numpy(cat).to(dev)
+    x = x0.clone()
+    infos = api.expmv_batched(b.ns, b.hs, b.Js, b.gammas, b.ts, x, tol=1e-6)
+    work = float(sum((1 << nn) * i["K"] * i["time_splits"] for nn, i in zip(b.ns, infos)))
+    x.copy_(x0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    api.expmv_batched(b.ns, b.hs, b.Js, b.gammas, b.ts, x, tol=1e-6, info=False)
+    e1.record()
+    torch.cuda.synchronize()
+    bms = e0.elapsed_time(e1)
+    out["batch_512"] = {"amp_updates_per_s": work / (bms / 1e3), "ms": bms, "amp_updates": work,
+                        "workload": "512 SK instances, n ~ U{12..20}, complex64, tol 1e-6"}
+    del x, x0
+    api.release_workspaces()
+    torch.cuda.empty_cache()
+
+    a = I.config_anneal()
+    nn, S = a.n, len(a.gammas)
+    x0 = torch.full((1 << nn,), 2 ** (-nn / 2), dtype=torch.complex64, device=dev)
+    bnd = torch.empty((S, 1 << nn), dtype=torch.complex64, device=dev)
+    res = {}
+    for rep in range(2):
+        x = x0.clone()
+        torch.cuda.synchronize()
+        e0.record()
+        inf = api.anneal(a.h, a.J, a.gammas, a.ts, x, boundaries=bnd, info=(rep == 0))
+        e1.record()
+        torch.cuda.synchronize()
+        if inf is not None:
+            res["K_total"] = int(sum(i["K"] for i in inf))
+        res["forward_ms"] = e0.elapsed_time(e1)
+        _, g, _, _ = api.energy_grad(a.h, a.J, x)
+        torch.cuda.synchronize()
+        e0.record()
+        api.anneal_adjoint(a.h, a.J, a.gammas, a.ts, bnd, x, g)
+        e1.record()
+        torch.cuda.synchronize()
+        res["backward_ms"] = e0.elapsed_time(e1)
+    res["backward_over_forward"] = res["backward_ms"] / res["forward_ms"]
+    res["forward_amp_updates_per_s"] = (1 << nn) * res["K_total"] / (res["forward_ms"] / 1e3)
+    res["workload"] = "SK n=22, 64 piecewise-constant segments, complex64; backward = all gradients"
+    out["anneal_n22"] = res
+    del x, x0, bnd
+    api.release_workspaces()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -290,6 +356,9 @@ def run_ours(args, world, rank, local):
         torch.cuda.empty_cache()
         extra["fused_over_fp64_plain"] = value / world / extra["fp64_plain"]["amp_updates_per_s"]
 
+    # the other workloads of the path, measured once each (not part of `value`)
+    others = {} if (rank != 0 or args.skip_workloads) else other_workloads(dev)
+
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -338,6 +407,7 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "accuracy": acc,
         "plain_paths": extra,
+        "workloads": others,
         "final_norm2": fin[1], "final_energy": fin[0],
     }
     print(json.dumps(line), flush=True)
@@ -354,6 +424,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--skip-workloads", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
