@@ -380,39 +380,104 @@ __global__ void __launch_bounds__(kAdjThreads) k_energy_grad(int n, int M, int Q
     block_accumulate(acc, slots);
 }
 
-// dh_i = sum_z G(z) s_i(z) (blocks 0..n-1), dJ_ij = sum_z G s_i s_j (one block per
-// pair i < j); deterministic FP64 sums.
-__global__ void __launch_bounds__(kAdjThreads) k_grad_reduce(int n, const double* __restrict__ G, double* out) {
-    const int64_t N = (int64_t)1 << n;
-    int b = blockIdx.x, i = 0, j = -1;
-    if (b < n) {
-        i = b;
-    } else {
-        b -= n;
-        for (i = 0; i < n; ++i) {
-            const int cnt = n - 1 - i;
-            if (b < cnt) {
-                j = i + 1 + b;
-                break;
+// dh_i = sum_z G(z) s_i(z), dJ_ij = sum_z G(z) s_i(z) s_j(z) (i < j), written as
+// out[i] and out[n + pair(i, j)] (pairs in row order). One pass over G: with
+// z = T 2^M + x, each tile's Walsh coefficients W_T[w] = sum_x G(T, x) prod_{i in w} s_i(x)
+// come from a fast Walsh-Hadamard transform of the tile in shared memory, and
+//   sum_z G s_i      = sum_T W_T[1<<i]            (i < M),   sum_T W_T[0] s_i(T)        (i >= M)
+//   sum_z G s_i s_j  = sum_T W_T[(1<<i)|(1<<j)]   (i,j < M), sum_T W_T[1<<i] s_j(T)     (i < M <= j),
+//                      sum_T W_T[0] s_i(T) s_j(T) (M <= i, j),
+// with s_i(T) the spin of bit i - M of T. Per-block partial sums, then a fixed-order
+// sum over blocks (deterministic).
+constexpr int kMaxMoments = kMaxQubits + kMaxQubits * (kMaxQubits - 1) / 2;
+constexpr int kMomentsPerThread = (kMaxMoments + kAdjThreads - 1) / kAdjThreads;
+
+__device__ __forceinline__ void moment_pair(int n, int o, int& i, int& j) {
+    if (o < n) {
+        i = o;
+        j = -1;
+        return;
+    }
+    o -= n;
+    for (i = 0; i < n; ++i) {
+        const int cnt = n - 1 - i;
+        if (o < cnt) {
+            j = i + 1 + o;
+            return;
+        }
+        o -= cnt;
+    }
+}
+
+__global__ void __launch_bounds__(kAdjThreads) k_moments(int n, int M, const double* __restrict__ G, double* partial) {
+    extern __shared__ double W[];  // 2^M
+    const int nout = n + n * (n - 1) / 2;
+    const int64_t tsize = (int64_t)1 << M;
+    const int64_t ntiles = (int64_t)1 << (n - M);
+    double acc[kMomentsPerThread];
+    int oi[kMomentsPerThread], oj[kMomentsPerThread];
+    for (int q = 0; q < kMomentsPerThread; ++q) {
+        acc[q] = 0.0;
+        const int o = threadIdx.x + q * kAdjThreads;
+        oi[q] = -1;
+        oj[q] = -1;
+        if (o < nout) moment_pair(n, o, oi[q], oj[q]);
+    }
+    for (int64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
+        __syncthreads();  // the previous tile's coefficients are no longer read
+        for (int64_t x = threadIdx.x; x < tsize; x += blockDim.x) W[x] = G[T * tsize + x];
+        __syncthreads();
+        for (int b = 0; b < M; ++b) {
+            for (int64_t pr = threadIdx.x; pr < tsize / 2; pr += blockDim.x) {
+                const int64_t lo = ((pr >> b) << (b + 1)) | (pr & ((1 << b) - 1));
+                const int64_t hi = lo | (1 << b);
+                const double u = W[lo], v = W[hi];
+                W[lo] = u + v;
+                W[hi] = u - v;
             }
-            b -= cnt;
+            __syncthreads();
+        }
+        for (int q = 0; q < kMomentsPerThread; ++q) {
+            const int i = oi[q], j = oj[q];
+            if (i < 0) continue;
+            auto spin = [&](int k) { return ((T >> (k - M)) & 1) ? -1.0 : 1.0; };
+            double v;
+            if (j < 0) {
+                v = i < M ? W[1 << i] : W[0] * spin(i);
+            } else if (j < M) {
+                v = W[(1 << i) | (1 << j)];
+            } else if (i < M) {
+                v = W[1 << i] * spin(j);
+            } else {
+                v = W[0] * spin(i) * spin(j);
+            }
+            acc[q] += v;
         }
     }
-    double acc = 0.0;
-    for (int64_t z = threadIdx.x; z < N; z += blockDim.x) {
-        double v = G[z];
-        if ((z >> i) & 1) v = -v;
-        if (j >= 0 && ((z >> j) & 1)) v = -v;
-        acc += v;
+    for (int q = 0; q < kMomentsPerThread; ++q) {
+        const int o = threadIdx.x + q * kAdjThreads;
+        if (o < nout) partial[(size_t)blockIdx.x * nout + o] = acc[q];
     }
-    __shared__ double red[kAdjThreads];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = kAdjThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
+}
+
+__global__ void k_moments_final(int nb, int nout, const double* __restrict__ partial, double* out) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nout; o += gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int b = 0; b < nb; ++b) a += partial[(size_t)b * nout + o];
+        out[o] = a;
     }
-    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// Launch both stages on the stream; out receives n + n(n-1)/2 doubles.
+cudaError_t launch_moments(int n, const double* G, double* partial, double* out, cudaStream_t s) {
+    const int M = n < kTileBits ? n : kTileBits;
+    const int nout = n + n * (n - 1) / 2;
+    const int64_t ntiles = (int64_t)1 << (n - M);
+    const unsigned nb = (unsigned)std::min<int64_t>(ntiles, kRedBlocks);
+    note_launch(kKindReduce);
+    k_moments<<<nb, kAdjThreads, ((size_t)1 << M) * sizeof(double), s>>>(n, M, G, partial);
+    k_moments_final<<<(nout + 127) / 128, 128, 0, s>>>((int)nb, nout, partial, out);
+    return cudaGetLastError();
 }
 
 __global__ void k_sum_slots(const double* slots, int nb, int count, double* out) {
@@ -492,7 +557,7 @@ constexpr int kOutGauge = 8;  // bt (2), rot (2), <psibar_0, psi_0> (2)
 struct AdjLayout {
     Layout fwd;
     size_t ring[kRing];
-    size_t G, Gs, slots, outs, pool;
+    size_t G, Gs, slots, outs, moments, pool;
     size_t vstride;
     size_t total_fixed;
 };
@@ -519,6 +584,8 @@ AdjLayout adj_layout(int n, int prec) {
     off = a256(off + 4 * (size_t)kRedBlocks * sizeof(double));
     A.outs = off;
     off = a256(off + ((size_t)n * n + n + 16 + kOutGauge + kRecBatch * kRecLen) * sizeof(double));
+    A.moments = off;  // per-block partial sums of the dh, dJ moments
+    off = a256(off + (size_t)kRedBlocks * ((size_t)n + (size_t)n * (n - 1) / 2) * sizeof(double));
     A.pool = off;
     A.total_fixed = off;
     return A;
@@ -817,8 +884,7 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
     }
     // dh, dJ from G (already divided by r per segment)
     const int nblk = n + n * (n - 1) / 2;
-    note_launch(kKindReduce);
-    k_grad_reduce<<<nblk, kAdjThreads, 0, s0>>>(n, (const double*)(ws + A.G), outs);
+    CUDA_TRY(launch_moments(n, (const double*)(ws + A.G), (double*)(ws + A.moments), outs, s0));
     std::vector<double> red(nblk);
     CUDA_TRY(cudaMemcpyAsync(red.data(), outs, nblk * sizeof(double), cudaMemcpyDeviceToHost, s0));
     st = read_flags(C);
@@ -867,7 +933,7 @@ extern "C" cheb_status_t cheb_energy_grad(int n, const double* h, const double* 
         k_energy_grad<double><<<gb, kAdjThreads, 0, s0>>>(n, A.fwd.M, F.Q, C.tiles(), C.elow(), 0.0, 1.0, psi, grad_psi, G, slots);
     k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 1, outs + n * n + n);
     const int nblk = n + n * (n - 1) / 2;
-    k_grad_reduce<<<nblk, kAdjThreads, 0, s0>>>(n, G, outs);
+    CUDA_TRY(launch_moments(n, G, (double*)(ws + A.moments), outs, s0));
     std::vector<double> red(nblk + 1);
     CUDA_TRY(cudaMemcpyAsync(red.data(), outs, nblk * sizeof(double), cudaMemcpyDeviceToHost, s0));
     CUDA_TRY(cudaMemcpyAsync(&red[nblk], outs + n * n + n, sizeof(double), cudaMemcpyDeviceToHost, s0));

@@ -1,24 +1,29 @@
-"""Small profiling driver: a few fused Clenshaw steps on one seeded SK instance.
+"""Small profiling driver for the library's kernels on seeded SK instances.
 
     python -m paper_2608_12058_b300.prof_case N L H [STEPS]
+        STEPS fused Clenshaw steps (cheb_poly_apply with random coefficients) at n = N
+        with the bit split (L, H) (kernel names k_low and k_strided*).
+    python -m paper_2608_12058_b300.prof_case adjoint N S
+        the first S segments of the anneal schedule at n = N (complex64): forward with
+        segment-start states, energy gradient, full reverse pass (k_adj_acc_f32x2,
+        k_dt, k_fold and the step kernels of both recurrences).
+    python -m paper_2608_12058_b300.prof_case cluster N COUNT
+        a batch of COUNT instances of size N (complex64) run whole on thread-block
+        clusters (k_cluster_run).
 
-Runs cheb_poly_apply (Algorithm 2 with random coefficients) on the FP32 fused path
-with the bit split (L, H) at n = N, for use under ncu (kernel names k_low and
-k_strided). Prints the final norm so the run is checked for finiteness.
+Each mode prints a finite summary so the run is checked.
 """
 import sys
 
 import numpy as np
 
 
-def main(argv):
+def fused_steps(n, l, h, steps):
     import torch
 
     from . import api
     from . import inputs as I
 
-    n, l, h = int(argv[0]), int(argv[1]), int(argv[2])
-    steps = int(argv[3]) if len(argv) > 3 else 6
     c = I.config_family(n, 1.0, 1.0, 0, "uniform")
     x = torch.full((1 << n,), 2 ** (-n / 2), dtype=torch.complex64, device="cuda")
     api.set_fused_split(n, l, h)
@@ -29,6 +34,56 @@ def main(argv):
     nrm = float(torch.linalg.vector_norm(x))
     assert np.isfinite(nrm)
     print("ok", nrm)
+
+
+def adjoint(n, S):
+    import torch
+
+    from . import api
+    from . import inputs as I
+
+    a = I.config_anneal(n=n, S=64)
+    g_s, t_s = a.gammas[:S], a.ts[:S]
+    x = torch.full((1 << n,), 2 ** (-n / 2), dtype=torch.complex64, device="cuda")
+    bnd = torch.empty((S, 1 << n), dtype=torch.complex64, device="cuda")
+    api.anneal(a.h, a.J, g_s, t_s, x, boundaries=bnd, info=False)
+    _, g, _, _ = api.energy_grad(a.h, a.J, x)
+    out = api.anneal_adjoint(a.h, a.J, g_s, t_s, bnd, x, g)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(out["gamma"]))
+    print("ok", out["gamma"])
+
+
+def cluster(n, count):
+    import torch
+
+    from . import api
+    from . import inputs as I
+
+    ns = [n] * count
+    hs, Js = [], []
+    for i in range(count):
+        h, J = I.sk_instance(n, 700 + i)
+        hs.append(h)
+        Js.append(J)
+    gam = np.linspace(0.5, 1.5, count)
+    ts = np.full(count, 10.0)
+    offs, total = api.batch_offsets(ns)
+    x = torch.full((total,), 2 ** (-n / 2), dtype=torch.complex64, device="cuda")
+    infos = api.expmv_batched(ns, hs, Js, gam, ts, x, tol=1e-6)
+    torch.cuda.synchronize()
+    assert all(abs(i["norm"] - 1.0) < 1e-4 for i in infos)
+    print("ok", sum(i["K"] for i in infos))
+
+
+def main(argv):
+    if argv[0] == "adjoint":
+        adjoint(int(argv[1]), int(argv[2]))
+    elif argv[0] == "cluster":
+        cluster(int(argv[1]), int(argv[2]))
+    else:
+        n, l, h = int(argv[0]), int(argv[1]), int(argv[2])
+        fused_steps(n, l, h, int(argv[3]) if len(argv) > 3 else 6)
 
 
 if __name__ == "__main__":
