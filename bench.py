@@ -99,6 +99,20 @@ def dist_setup():
     return world, rank, local
 
 
+def aggregate(t_local: float, work_local: float, pg, device):
+    """Whole-job figures of N replicas: the slowest rank's time (max) and the work of all
+    ranks (sum); pg is torch.distributed (any backend) or None for a single process."""
+    if pg is None:
+        return t_local, work_local
+    import torch
+
+    t = torch.tensor([t_local], device=device, dtype=torch.float64)
+    w = torch.tensor([work_local], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(w)
+    return t.item(), w.item()
+
+
 def cpu_sample_run():
     """The oracle, as it stands, on the bounded sample; returns (amp-updates/s, seconds, info)."""
     from oracle import oracle as O
@@ -297,14 +311,7 @@ def run_ours(args, world, rank, local):
 
     t_local = ms / 1e3
     work_local = float(N) * K * args.steps
-    if pg is not None:
-        t = torch.tensor([t_local], device=dev)
-        w = torch.tensor([work_local], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        pg.all_reduce(w)
-        t_all, work_all = t.item(), w.item()
-    else:
-        t_all, work_all = t_local, work_local
+    t_all, work_all = aggregate(t_local, work_local, pg, dev)
     value = work_all / t_all
 
     # end to end: host (pinned) state in, host state out, every step
@@ -322,11 +329,7 @@ def run_ours(args, world, rank, local):
             host.copy_(psi, non_blocking=True)
         f1.record(stream)
         barrier()
-        te = f0.elapsed_time(f1) / 1e3
-        if pg is not None:
-            t = torch.tensor([te], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            te = t.item()
+        te, _ = aggregate(f0.elapsed_time(f1) / 1e3, 0.0, pg, dev)
         e2e = {"value": work_all / te, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
         del host
 

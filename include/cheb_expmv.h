@@ -359,6 +359,17 @@ typedef enum {
     CHEB_KERNEL_FUSED_HIGH = 7
 } cheb_kernel_kind_t;
 
+/*
+ * Failure-detection self-test (no counterpart in the paper). Every device-side wait of
+ * this library is bounded: it gives up after about 2 s, records a timeout in the
+ * workspace status word and lets the kernel return, and the call reports
+ * CHEB_ERR_TIMEOUT. This entry point runs that same wait, with a ~1 ms limit, on a
+ * barrier that nothing arrives on, and returns its status: CHEB_ERR_TIMEOUT is the
+ * expected answer, and the context stays usable afterwards.
+ *   workspace: DEVICE, at least 4 bytes (one int), 4-byte aligned. Synchronises.
+ */
+cheb_status_t cheb_wait_selftest(void* workspace, size_t workspace_bytes, void* stream);
+
 long long cheb_launch_count(void);
 cheb_status_t cheb_profile_enable(int on);
 cheb_status_t cheb_profile_reset(void);

@@ -71,6 +71,7 @@ SIGNATURES = {
                                     c_int, _dp, _dp, _dp, _dp, c_void_p, c_size_t, c_void_p]),
     "cheb_energy_grad": (c_int, [c_int, _dp, _dp, c_void_p, c_void_p, c_int, _dp, _dp, _dp, c_void_p, c_size_t,
                                  c_void_p]),
+    "cheb_wait_selftest": (c_int, [c_void_p, c_size_t, c_void_p]),
     "cheb_launch_count": (ctypes.c_longlong, []),
     "cheb_profile_enable": (c_int, [c_int]),
     "cheb_profile_reset": (c_int, []),

@@ -417,6 +417,17 @@ def get_fused_split(n: int):
 KERNEL_KIND = {"plain": 3, "adjoint_acc": 5, "low": 6, "high": 7}
 
 
+def wait_selftest(device=None):
+    """Run the library's bounded device wait against a barrier nothing arrives on; raises
+    ChebError with CHEB_ERR_TIMEOUT (the expected outcome) or returns if it did not time out."""
+    import torch
+
+    buf = torch.zeros(64, dtype=torch.uint8, device=device if device is not None else "cuda")
+    dev = buf.device
+    _lib.check(_lib.lib().cheb_wait_selftest(ctypes.c_void_p(buf.data_ptr()), buf.numel(), _stream_ptr(dev)),
+               "cheb_wait_selftest")
+
+
 def launch_count() -> int:
     """Kernels launched by the CUDA library so far in this process."""
     return int(_lib.lib().cheb_launch_count())

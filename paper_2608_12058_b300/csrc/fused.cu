@@ -31,6 +31,7 @@
 
 #include "cheb_internal.h"
 #include "fused.cuh"
+#include "mbar.cuh"
 
 namespace cheb {
 
@@ -46,7 +47,6 @@ constexpr int kLowThreads = kCons + 32;             // + one producer warp
 constexpr int kMaxL = 6;                            // L2 partner bits allowed in a plan
 constexpr int kMaxStrided = 9;                      // bits per strided pass
 constexpr int kW = 50;                              // per-tile energy scalars
-constexpr long long kWaitCycles = 4000000000LL;     // ~2 s at 2 GHz
 static_assert(kTF == 2 * kCons, "two float4 per consumer thread");
 
 // shared-memory map of the low pass
@@ -55,74 +55,6 @@ constexpr size_t kWOff = kRingOff + (size_t)kNP * kTB;
 constexpr size_t kBarOff = kWOff + (size_t)kNS * kW * sizeof(int64_t);
 constexpr size_t kAbortOff = kBarOff + (size_t)(2 * kNS + 2 * kNP) * sizeof(uint64_t);
 constexpr size_t kLowSmem = kAbortOff + 16;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait. Gives up after kWaitCycles, or as soon as another thread of the CTA
-// has given up (abort != 0); a timeout is reported through the flags word.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* flags, volatile int* abort) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*abort) return false;
-        if (clock64() - t0 > kWaitCycles) {
-            atomicOr(flags, kFlagTimeout);
-            *abort = 1;
-            return false;
-        }
-    }
-    return true;
-}
-
-// Bounded wait that ignores the abort flag (used to let issued copies land).
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, int* flags) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
-            atomicOr(flags, kFlagTimeout);
-            return;
-        }
-    }
-}
 
 __device__ __forceinline__ int64_t sel(uint32_t bit, int64_t v) { return bit ? -v : v; }
 
