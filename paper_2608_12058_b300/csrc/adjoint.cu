@@ -304,32 +304,63 @@ __global__ void __launch_bounds__(kAdjThreads) k_dg_flip(int n, const void* bbar
 }
 
 // <ybar, H y> and <ybar, y> (complex), H = diag(E) + gamma sum_j X_j, E = c + r D:
-// slots[0..3] x kRedBlocks = Re, Im of each.
+// slots[0..3] x kRedBlocks = Re, Im of each. One block per tile of 2^M amplitudes:
+// the tile of y is staged in shared memory for the flip partners of the low M bits
+// (the others are read from global memory), E comes from the tile's shared energy
+// partial sums, the flip sums are formed in the vector precision and the products
+// and sums in FP64.
 template <typename R>
 __global__ void __launch_bounds__(kAdjThreads) k_dt(int n, int M, int Q, const int64_t* tiles, const int64_t* elow,
                                                     double c, double r, double gamma, const void* ybar_v,
                                                     const void* y_v, double* slots) {
     using C = typename Cx<R>::T;
-    const int64_t N = (int64_t)1 << n;
+    extern __shared__ __align__(16) unsigned char dt_smem[];
+    C* ty = (C*)dt_smem;  // 2^M
+    __shared__ int64_t Wlo[32], Whi[64];
+    const int64_t tsize = (int64_t)1 << M;
+    const int64_t ntiles = (int64_t)1 << (n - M);
     const C* yb = (const C*)ybar_v;
     const C* y = (const C*)y_v;
     const double sc = ldexp(1.0, -Q);
+    const int t = threadIdx.x;
     double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
-    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
-        const double E = c + r * (__ll2double_rn(energy_fx(M, tiles, elow, (uint64_t)z)) * sc);
-        double sx = 0, sy = 0;
-        for (int j = 0; j < n; ++j) {
-            const C v = y[z ^ ((int64_t)1 << j)];
-            sx += v.x;
-            sy += v.y;
+    for (int64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
+        const int64_t* row = tiles + T * (M + 1);
+        __syncthreads();
+        if (t < 96) {
+            const int lo = t < 32 ? 0 : 5, hi = t < 32 ? 5 : 11;
+            const int x = t < 32 ? t : (t - 32) << 5;
+            int64_t v = 0;
+            for (int i = lo; i < hi && i < M; ++i) v += sgn_sel((x >> i) & 1, __ldg(row + i));
+            if (t < 32) Wlo[t] = v;
+            else Whi[t - 32] = v;
         }
-        const C v = y[z];
-        const double hx = E * v.x + gamma * sx, hy = E * v.y + gamma * sy;
-        const C u = yb[z];
-        ar += (double)u.x * hx + (double)u.y * hy;
-        ai += (double)u.x * hy - (double)u.y * hx;
-        br += (double)u.x * v.x + (double)u.y * v.y;
-        bi += (double)u.x * v.y - (double)u.y * v.x;
+        for (int64_t x = t; x < tsize; x += blockDim.x) ty[x] = y[T * tsize + x];
+        __syncthreads();
+        const int64_t A = __ldg(row + M);
+        for (int64_t x = t; x < tsize; x += blockDim.x) {
+            const int64_t z = T * tsize + x;
+            const int64_t e = A + Wlo[x & 31] + Whi[(x >> 5) & 63] + __ldg(elow + x);
+            const double E = c + r * (__ll2double_rn(e) * sc);
+            R sx = 0, sy = 0;
+            for (int j = 0; j < M; ++j) {
+                const C v = ty[x ^ ((int64_t)1 << j)];
+                sx += v.x;
+                sy += v.y;
+            }
+            for (int j = M; j < n; ++j) {
+                const C v = y[z ^ ((int64_t)1 << j)];
+                sx += v.x;
+                sy += v.y;
+            }
+            const C v = ty[x];
+            const double hx = E * v.x + gamma * (double)sx, hy = E * v.y + gamma * (double)sy;
+            const C u = yb[z];
+            ar += (double)u.x * hx + (double)u.y * hy;
+            ai += (double)u.x * hy - (double)u.y * hx;
+            br += (double)u.x * v.x + (double)u.y * v.y;
+            bi += (double)u.x * v.y - (double)u.y * v.x;
+        }
     }
     block_accumulate(ar, slots);
     block_accumulate(ai, slots + kRedBlocks);
@@ -693,10 +724,13 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
         {
             CUDA_TRY(cudaMemsetAsync(slots, 0, 4 * kRedBlocks * sizeof(double), s0));
             note_launch(kKindReduce);
+            const size_t dsm = ((size_t)1 << Mt) * A.fwd.cbytes;
             if (precision == CHEB_FP32)
-                k_dt<float><<<gb, kAdjThreads, 0, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), c, r, gamma_s[s], grad, y_s, slots);
+                k_dt<float><<<grid_tiles(n, Mt), kAdjThreads, dsm, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), c, r,
+                                                                        gamma_s[s], grad, y_s, slots);
             else
-                k_dt<double><<<gb, kAdjThreads, 0, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), c, r, gamma_s[s], grad, y_s, slots);
+                k_dt<double><<<grid_tiles(n, Mt), kAdjThreads, dsm, s0>>>(n, Mt, F.Q, C.tiles(), C.elow(), c, r,
+                                                                         gamma_s[s], grad, y_s, slots);
             k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 4, rec);
             k_gauge<<<1, 32, 0, s0>>>(rec, bt, s == S - 1 ? 1 : 0, rot);
             // Re(e^{i th} conj(u) x) = Re(conj(e^{-i th} u) x): the gauge moves into ybar
