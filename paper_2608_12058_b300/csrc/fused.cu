@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
     const bool need_slot = a.slot_coeff != 0.f;
+    const bool need_psi = a.ck_re != 0.f || a.ck_im != 0.f;  // c_k = 0: the adjoint chain
 
     if (t == 0) {
         for (int i = 0; i < kNS; ++i) {
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
 
     if (warp == kCons / 32) {
         // ---------------- producer warp ----------------
-        const uint32_t stage_bytes = (need_slot ? 3u : 2u) * kTB;
+        const uint32_t stage_bytes = (1u + (need_psi ? 1u : 0u) + (need_slot ? 1u : 0u)) * kTB;
         int last_s[kNS], last_p[kNP];
         for (int i = 0; i < kNS; ++i) last_s[i] = -1;
         for (int i = 0; i < kNP; ++i) last_p[i] = -1;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
                 unsigned char* d = smem + (size_t)s * 3 * kTB;
                 mbar_expect_tx(&full_s[s], stage_bytes);
                 tma_load_1d(d, a.b1 + T * kTF, kTB, &full_s[s]);
-                tma_load_1d(d + kTB, a.psi + T * kTF, kTB, &full_s[s]);
+                if (need_psi) tma_load_1d(d + kTB, a.psi + T * kTF, kTB, &full_s[s]);
                 if (need_slot) tma_load_1d(d + 2 * kTB, a.slot + T * kTF, kTB, &full_s[s]);
                 last_s[s] = k;
                 for (int j = 0; j < a.l; ++j, ++pj) {
@@ -297,7 +298,8 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
         const int64_t up = W[48], um = W[49];
         const int64_t e00 = base + up + K00, e01 = base + um + K01;
         const int64_t e10 = base - um + K10, e11 = base - up + K11;
-        const float4 ps0 = spsi[t], ps1 = spsi[t + kCons];
+        const float4 ps0 = need_psi ? spsi[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 ps1 = need_psi ? spsi[t + kCons] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 q0 = need_slot ? sslot[t] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 q1 = need_slot ? sslot[t + kCons] : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncwarp();
