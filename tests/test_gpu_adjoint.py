@@ -174,3 +174,43 @@ def test_regenerated_and_stored_forward_vectors_agree(cuda_lib, n, dtype_name, t
             ref = outs[0][key]
             assert np.linalg.norm(o[key] - ref) <= tol * np.linalg.norm(ref), key
         assert np.linalg.norm(pb - psibars[0]) <= tol * np.linalg.norm(psibars[0])
+
+
+def test_adjoint_special_segments_vs_finite_differences(cuda_lib):
+    """Segments the general formulas do not cover: gamma_s = 0 (dL/dgamma from explicit
+    flip sums), a negative gamma_s, and a segment of duration 0 (degree K = 0)."""
+    import torch
+
+    from paper_2608_12058_b300 import autograd as AG
+
+    n = 7
+    h, J = I.sk_instance(n, 88)
+    gammas = np.array([1.1, 0.0, -0.6, 0.8])
+    ts = np.array([0.7, 0.5, 0.4, 0.0])
+    psi0 = I.random_state(n, 89)
+    th, tJ, tg, tT = _params(h, J, gammas, ts)
+    x = torch.from_numpy(psi0).cuda().requires_grad_(True)
+    L = AG.energy(AG.anneal(x, th, tJ, tg, tT, tol=1e-13), th, tJ)
+    L.backward()
+    eps = 1e-6
+
+    def loss(g_, t_):
+        return _energy_after(h, J, g_, t_, psi0, torch.complex128)
+
+    for s in range(len(gammas)):
+        gp, gm = gammas.copy(), gammas.copy()
+        gp[s] += eps
+        gm[s] -= eps
+        assert abs((loss(gp, ts) - loss(gm, ts)) / (2 * eps) - tg.grad[s].item()) < 1e-7, ("gamma", s)
+    for s in range(len(ts) - 1):  # a negative duration is not a valid input
+        tp, tm = ts.copy(), ts.copy()
+        tp[s] += eps
+        tm[s] -= eps
+        assert abs((loss(gammas, tp) - loss(gammas, tm)) / (2 * eps) - tT.grad[s].item()) < 1e-7, ("t", s)
+    # the zero-length segment: one-sided second-order difference at t = 0
+    e1 = 1e-5
+    t1, t2 = ts.copy(), ts.copy()
+    t1[-1] += e1
+    t2[-1] += 2 * e1
+    fd = (-3 * loss(gammas, ts) + 4 * loss(gammas, t1) - loss(gammas, t2)) / (2 * e1)
+    assert abs(fd - tT.grad[-1].item()) < 1e-6, "t at 0"
