@@ -282,6 +282,21 @@ cheb_status_t cheb_anneal_adjoint(int n, const double* h, const double* J, int S
                                   cheb_method_t method, double* grad_gamma, double* grad_t,
                                   double* grad_h, double* grad_J, void* workspace,
                                   size_t workspace_bytes, void* stream);
+/*
+ * The adjoint of cheb_anneal_general (segments H_s = b_s H_P + a_s sum_j X_j): as
+ * cheb_anneal_adjoint, plus dL/db_s = sum_z G_s(z) E(z) / r_s with G_s = dL/dDt on the
+ * segment and r_s its (frozen) radius; dh, dJ collect b_s / r_s times the moments of
+ * each G_s. boundaries are the segment starts written by cheb_anneal_general.
+ *   grad_a, grad_b, grad_t: HOST, S doubles each (nullable); other arguments as
+ *   cheb_anneal_adjoint (same workspace).
+ */
+cheb_status_t cheb_anneal_general_adjoint(int n, const double* h, const double* J, int S,
+                                          const double* a_s, const double* b_s, const double* t_s,
+                                          const void* boundaries, const void* psi_T, void* grad,
+                                          cheb_precision_t precision, double tol, cheb_method_t method,
+                                          double* grad_a, double* grad_b, double* grad_t, double* grad_h,
+                                          double* grad_J, void* workspace, size_t workspace_bytes,
+                                          void* stream);
 cheb_status_t cheb_energy_grad(int n, const double* h, const double* J, const void* psi,
                                void* grad_psi, cheb_precision_t precision, double* energy,
                                double* grad_h, double* grad_J, void* workspace,

@@ -351,6 +351,34 @@ def anneal_adjoint(h, J, gammas, ts, boundaries, psi_T, grad, tol: Optional[floa
     return {"gamma": gg, "t": gt, "h": gh, "J": gJ}
 
 
+def anneal_general_adjoint(h, J, a_s, b_s, ts, boundaries, psi_T, grad, tol: Optional[float] = None,
+                           method: str = "chebyshev", store_vectors: Optional[int] = None):
+    """Gradients through cheb_anneal_general (see cheb_anneal_general_adjoint); grad holds
+    dL/dpsi_T on entry and dL/dpsi_0 on return. Returns dict: a, b, t (S), h (n), J (n x n)."""
+    h, J = _f64(h), _f64(J)
+    a_s, b_s, ts = _f64(a_s), _f64(b_s), _f64(ts)
+    n, S = h.shape[0], a_s.shape[0]
+    prec = precision_of(psi_T)
+    if tol is None:
+        tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+    for x in (boundaries, psi_T, grad):
+        if not x.is_cuda or not x.is_contiguous() or x.dtype != psi_T.dtype:
+            raise ValueError("boundaries, psi_T and grad must be contiguous CUDA tensors of one complex dtype")
+    if store_vectors is None:
+        store_vectors = _auto_store_vectors(n, prec, psi_T.device,
+                                            _degree_upper_bound(np.abs(b_s).max() * h, np.abs(b_s).max() * J,
+                                                                a_s, ts, tol, method))
+    ws = _adjoint_workspace(n, prec, psi_T.device, store_vectors)
+    p, nb = _ws_ptr(ws)
+    ga, gb, gt, gh, gJ = np.zeros(S), np.zeros(S), np.zeros(S), np.zeros(n), np.zeros((n, n))
+    code = _lib.lib().cheb_anneal_general_adjoint(
+        n, _dp(h), _dp(J), S, _dp(a_s), _dp(b_s), _dp(ts), ctypes.c_void_p(boundaries.data_ptr()),
+        ctypes.c_void_p(psi_T.data_ptr()), ctypes.c_void_p(grad.data_ptr()), PREC[prec], float(tol), METHOD[method],
+        _dp(ga), _dp(gb), _dp(gt), _dp(gh), _dp(gJ), ctypes.c_void_p(p), nb, _stream_ptr(psi_T.device))
+    _lib.check(code, "cheb_anneal_general_adjoint")
+    return {"a": ga, "b": gb, "t": gt, "h": gh, "J": gJ}
+
+
 def energy_grad(h, J, psi):
     """(energy, dL/dpsi = 2 H_P psi as a new tensor, dL/dh, dL/dJ) for L = <psi|H_P|psi>."""
     import torch

@@ -1,6 +1,8 @@
 """torch.autograd.Function wrappers of the CUDA forward and adjoint entry points.
 
     psi_T = anneal(psi0, h, J, gammas, ts)        # differentiable in all five
+    psi_T = anneal_general(psi0, h, J, a_s, b_s, ts)    # segments b_s H_P + a_s sum X_j
+    psi_T = magnus4(psi0, h, J, dt, nodes)        # time-dependent H(t), Magnus steps
     L = energy(psi_T, h, J)                       # <psi|H_P|psi>, differentiable
     L.backward()
 
@@ -47,6 +49,34 @@ class AnnealFn(torch.autograd.Function):
         return g, dh, dJ, dg, dt, None, None, None
 
 
+class AnnealGeneralFn(torch.autograd.Function):
+    """psi_T = prod_s exp(-i t_s (b_s H_P + a_s sum_j X_j)) psi0, differentiable in psi0, h,
+    J, a_s, b_s and t_s (cheb_anneal_general / cheb_anneal_general_adjoint)."""
+
+    @staticmethod
+    def forward(ctx, psi0, h, J, a_s, b_s, ts, tol, method, store_vectors):
+        hn, Jn, an, bn, tn = _np(h), _np(J), _np(a_s), _np(b_s), _np(ts)
+        S = an.shape[0]
+        y = psi0.detach().clone().contiguous()
+        bnd = torch.empty((S, y.numel()), dtype=y.dtype, device=y.device)
+        api.anneal_general(hn, Jn, an, bn, tn, y, tol=tol, method=method, boundaries=bnd, info=False)
+        ctx.save_for_backward(bnd, y)
+        ctx.params = (hn, Jn, an, bn, tn, tol, method, store_vectors)
+        ctx.dev = (h.device, J.device, a_s.device, b_s.device, ts.device)
+        return y
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        bnd, y = ctx.saved_tensors
+        hn, Jn, an, bn, tn, tol, method, store_vectors = ctx.params
+        g = grad_out.detach().to(y.dtype).contiguous().clone()
+        out = api.anneal_general_adjoint(hn, Jn, an, bn, tn, bnd, y, g, tol=tol, method=method,
+                                         store_vectors=store_vectors)
+        conv = lambda key, dev: torch.from_numpy(out[key]).to(dev)
+        return (g, conv("h", ctx.dev[0]), conv("J", ctx.dev[1]), conv("a", ctx.dev[2]), conv("b", ctx.dev[3]),
+                conv("t", ctx.dev[4]), None, None, None)
+
+
 class EnergyFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, psi, h, J):
@@ -72,6 +102,25 @@ def expmv(psi0, h, J, gamma, t, tol=None, method="chebyshev", store_vectors=None
     g = gamma.reshape(1) if isinstance(gamma, torch.Tensor) else torch.tensor([float(gamma)], dtype=torch.float64)
     tt = t.reshape(1) if isinstance(t, torch.Tensor) else torch.tensor([float(t)], dtype=torch.float64)
     return AnnealFn.apply(psi0, h, J, g, tt, tol, method, store_vectors)
+
+
+def anneal_general(psi0, h, J, a_s, b_s, ts, tol=None, method="chebyshev", store_vectors=None):
+    return AnnealGeneralFn.apply(psi0, h, J, a_s, b_s, ts, tol, method, store_vectors)
+
+
+def magnus4(psi0, h, J, dt, nodes, tol=None, method="chebyshev", store_vectors=None):
+    """Differentiable fourth-order commutator-free Magnus propagation (as api.magnus4):
+    dt (steps) and nodes (steps x 4: A(t1), B(t1), A(t2), B(t2)) are float64 tensors. The
+    two exponentials of a step are segments of anneal_general whose coefficients are the
+    Gauss-node combinations below, so gradients reach dt and every node value."""
+    w1 = 0.25 - 3.0 ** 0.5 / 6.0
+    w2 = 0.25 + 3.0 ** 0.5 / 6.0
+    A1, B1, A2, B2 = nodes[:, 0], nodes[:, 1], nodes[:, 2], nodes[:, 3]
+    # per step: first w2 H(t1) + w1 H(t2), then w1 H(t1) + w2 H(t2)
+    a_s = torch.stack([w2 * A1 + w1 * A2, w1 * A1 + w2 * A2], dim=1).reshape(-1)
+    b_s = torch.stack([w2 * B1 + w1 * B2, w1 * B1 + w2 * B2], dim=1).reshape(-1)
+    ts = torch.stack([dt, dt], dim=1).reshape(-1)
+    return AnnealGeneralFn.apply(psi0, h, J, a_s, b_s, ts, tol, method, store_vectors)
 
 
 def energy(psi, h, J):

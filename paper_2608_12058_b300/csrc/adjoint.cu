@@ -273,11 +273,21 @@ unsigned grid_tiles(int n, int M) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(nt, kRedBlocks));
 }
 
-// End of a segment: G(z) += Gs(z)/r (FP64).
+// End of a segment: G(z) += fac Gs(z) (FP64; fac = b_s / r_s) and, when the unscaled
+// energy tables are given, slots += sum_z Gs(z) E(z) (for dL/db_s of general segments).
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) k_fold(int64_t N, const R* __restrict__ Gs, double inv_r, double* G) {
-    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x)
-        G[z] += (double)Gs[z] * inv_r;
+__global__ void __launch_bounds__(kAdjThreads) k_fold(int n, const R* __restrict__ Gs, double fac, double* G,
+                                                      int M, int Q0, const int64_t* tiles0, const int64_t* elow0,
+                                                      double* slots) {
+    const int64_t N = (int64_t)1 << n;
+    const double sc = ldexp(1.0, -Q0);
+    double acc = 0.0;
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
+        const double g = (double)Gs[z];
+        G[z] += g * fac;
+        if (tiles0) acc += g * (__ll2double_rn(energy_fx(M, tiles0, elow0, (uint64_t)z)) * sc);
+    }
+    if (tiles0) block_accumulate(acc, slots);
 }
 
 // Fallback for gamma = 0, where (Ht - D)/gamma is not available: the flip sums of
@@ -588,7 +598,7 @@ constexpr int kOutGauge = 8;  // bt (2), rot (2), <psibar_0, psi_0> (2)
 struct AdjLayout {
     Layout fwd;
     size_t ring[kRing];
-    size_t G, Gs, slots, outs, moments, pool;
+    size_t G, Gs, slots, outs, jq0, tiles0, elow0, moments, pool;
     size_t vstride;
     size_t total_fixed;
 };
@@ -615,6 +625,12 @@ AdjLayout adj_layout(int n, int prec) {
     off = a256(off + 4 * (size_t)kRedBlocks * sizeof(double));
     A.outs = off;
     off = a256(off + ((size_t)n * n + n + 16 + kOutGauge + kRecBatch * kRecLen) * sizeof(double));
+    A.jq0 = off;  // unscaled fixed-point couplings and their energy tables (general segments)
+    off = a256(off + ((size_t)n * n + n + 1) * sizeof(int64_t));
+    A.tiles0 = off;
+    off = a256(off + ((size_t)1 << (n - A.fwd.M)) * (A.fwd.M + 1) * sizeof(int64_t));
+    A.elow0 = off;
+    off = a256(off + ((size_t)1 << A.fwd.M) * sizeof(int64_t));
     A.moments = off;  // per-block partial sums of the dh, dJ moments
     off = a256(off + (size_t)kRedBlocks * ((size_t)n + (size_t)n * (n - 1) / 2) * sizeof(double));
     A.pool = off;
@@ -648,17 +664,22 @@ extern "C" size_t cheb_adjoint_workspace_bytes(int n, cheb_precision_t precision
     return A.total_fixed + (size_t)store_vectors * A.vstride;
 }
 
-// Gradient of a loss on the output of a schedule (S = 1: a single exp(-itH) psi).
-extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const double* J, int S, const double* gamma_s,
-                                             const double* t_s, const void* boundaries, const void* psi_T,
-                                             void* grad, cheb_precision_t precision, double tol,
-                                             cheb_method_t method, double* grad_gamma, double* grad_t,
-                                             double* grad_h, double* grad_J, void* workspace, size_t ws_bytes,
-                                             void* stream) {
+namespace {
+
+// Gradient of a loss on the output of a schedule of segments H_s = b_s H_P + gamma_s
+// sum_j X_j (b_s = 1 when b_s is null; S = 1: a single exp(-itH) psi). With the centre
+// b_s c and radius r_s = |b_s| (Emax - Emin)/2 + |gamma_s| n frozen, D_s = (b_s E - b_s c)/r_s,
+// so dL/db_s = sum_z G_s(z) E(z) / r_s and dh, dJ collect b_s / r_s times the moments of G_s.
+cheb_status_t adjoint_impl(int n, const double* h, const double* J, int S, const double* b_s,
+                           const double* gamma_s, const double* t_s, const void* boundaries, const void* psi_T,
+                           void* grad, cheb_precision_t precision, double tol, cheb_method_t method,
+                           double* grad_gamma, double* grad_b, double* grad_t, double* grad_h, double* grad_J,
+                           void* workspace, size_t ws_bytes, void* stream) {
     if (n < 1 || n > kMaxQubits || S < 1 || !h || !J || !gamma_s || !t_s || !boundaries || !psi_T || !grad)
         return CHEB_ERR_INVALID_ARG;
     if (precision != CHEB_FP32 && precision != CHEB_FP64) return CHEB_ERR_INVALID_ARG;
-    if (!finite_all(h, n) || !finite_all(J, (size_t)n * n) || !finite_all(gamma_s, S) || !finite_all(t_s, S))
+    if (!finite_all(h, n) || !finite_all(J, (size_t)n * n) || !finite_all(gamma_s, S) || !finite_all(t_s, S) ||
+        (b_s && !finite_all(b_s, S)))
         return CHEB_ERR_INVALID_ARG;
     if (!(tol > 0) || !std::isfinite(tol)) return CHEB_ERR_INVALID_ARG;
     if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF && method != CHEB_METHOD_REMEZ)
@@ -678,8 +699,20 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
     double emin = 0, emax = 0;
     cheb_status_t st = bounds_impl(C, h, J, &emin, &emax);
     if (st != CHEB_OK) return st;
-    const double c = 0.5 * (emax + emin);
+    const double c0 = 0.5 * (emax + emin);
     const double tol_s = tol / S;
+    // unscaled energy tables for dL/db_s (general segments only)
+    int Q0 = 0;
+    if (b_s && grad_b) {
+        FixedOp F0 = make_fixed(n, h, J, 0.0, 1.0);
+        Q0 = F0.Q;
+        CUDA_TRY(cudaMemcpyAsync(ws + A.jq0, F0.jq.data(), F0.jq.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                 s0));
+        launch_tables(n, A.fwd.M, (const int64_t*)(ws + A.jq0), (int64_t*)(ws + A.tiles0), (int64_t*)(ws + A.elow0),
+                      s0);
+        CUDA_TRY(cudaGetLastError());
+    }
+    std::vector<double> hb(n), Jb((size_t)n * n), gb_out(S, 0.0);
     double* slots = (double*)(ws + A.slots);
     double* outs = (double*)(ws + A.outs);
     unsigned char* pool = ws + A.pool;
@@ -700,10 +733,14 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
     std::vector<double> seg_r(S, 1.0);
     std::vector<int> seg_K(S, 0);
     for (int s = S - 1; s >= 0; --s) {
-        double r = 0.5 * (emax - emin) + std::fabs(gamma_s[s]) * n;
+        const double bsc = b_s ? b_s[s] : 1.0;
+        const double c = bsc * c0;
+        double r = std::fabs(bsc) * 0.5 * (emax - emin) + std::fabs(gamma_s[s]) * n;
         if (!(r > 0)) r = 1.0;
         const double g = gamma_s[s] / r;
-        FixedOp F = make_fixed(n, h, J, c, r, precision == CHEB_FP32 ? kMaxQF32 : 62);
+        for (int i = 0; i < n; ++i) hb[i] = bsc * h[i];
+        for (size_t qq = 0; qq < (size_t)n * n; ++qq) Jb[qq] = bsc * J[qq];
+        FixedOp F = make_fixed(n, hb.data(), Jb.data(), c, r, precision == CHEB_FP32 ? kMaxQF32 : 62);
         if (F.Q < 24) return CHEB_ERR_UNSUPPORTED;
         st = upload_tables(C, F);
         if (st != CHEB_OK) return st;
@@ -736,7 +773,7 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
             // Re(e^{i th} conj(u) x) = Re(conj(e^{-i th} u) x): the gauge moves into ybar
             if (precision == CHEB_FP32) k_rotate<float><<<gb, kAdjThreads, 0, s0>>>(N, grad, rot);
             else k_rotate<double><<<gb, kAdjThreads, 0, s0>>>(N, grad, rot);
-            CUDA_TRY(cudaMemsetAsync(rec + 5, 0, 2 * sizeof(double), s0));
+            CUDA_TRY(cudaMemsetAsync(rec + 5, 0, 3 * sizeof(double), s0));
         }
         auto flush = [&]() -> cheb_status_t {  // read back the records of segments s .. s + q
             std::vector<double> h((size_t)(q + 1) * kRecLen);
@@ -750,6 +787,7 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
                 if (seg_K[sg] == 0) gg[sg] = 0.0;
                 else if (gamma_s[sg] == 0.0) gg[sg] = v[6] / seg_r[sg];
                 else gg[sg] = v[5] / gamma_s[sg];
+                gb_out[sg] = seg_K[sg] == 0 ? 0.0 : v[7] / seg_r[sg];
             }
             return CHEB_OK;
         };
@@ -891,13 +929,17 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
                 }
             }
         }
-        // slots: [0] hsum, [1] flip sums (gamma = 0) -> record [5..6]
+        // slots: [0] hsum, [1] flip sums (gamma = 0), [2] sum_z Gs E (general) -> record [5..7]
         note_launch(kKindReduce);
+        const int64_t* t0p = (b_s && grad_b) ? (const int64_t*)(ws + A.tiles0) : nullptr;
+        const int64_t* e0p = (const int64_t*)(ws + A.elow0);
         if (precision == CHEB_FP32)
-            k_fold<float><<<gb, kAdjThreads, 0, s0>>>(N, (const float*)Gs, 1.0 / r, (double*)(ws + A.G));
+            k_fold<float><<<gb, kAdjThreads, 0, s0>>>(n, (const float*)Gs, bsc / r, (double*)(ws + A.G), Mt, Q0, t0p,
+                                                      e0p, slots + 2 * kRedBlocks);
         else
-            k_fold<double><<<gb, kAdjThreads, 0, s0>>>(N, (const double*)Gs, 1.0 / r, (double*)(ws + A.G));
-        k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 2, rec + 5);
+            k_fold<double><<<gb, kAdjThreads, 0, s0>>>(n, (const double*)Gs, bsc / r, (double*)(ws + A.G), Mt, Q0,
+                                                       t0p, e0p, slots + 2 * kRedBlocks);
+        k_sum_slots<<<1, 256, 0, s0>>>(slots, gb, 3, rec + 5);
         if (q == kRecBatch - 1 || s == 0) {
             st = flush();
             if (st != CHEB_OK) return st;
@@ -925,6 +967,8 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
     if (st != CHEB_OK) return st;
     if (grad_gamma)
         for (int s = 0; s < S; ++s) grad_gamma[s] = gg[s];
+    if (grad_b)
+        for (int s = 0; s < S; ++s) grad_b[s] = gb_out[s];
     if (grad_t)
         for (int s = 0; s < S; ++s) grad_t[s] = gt[s];
     if (grad_h)
@@ -936,6 +980,30 @@ extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const doubl
             for (int j = i + 1; j < n; ++j) grad_J[(size_t)i * n + j] = red[b++];
     }
     return CHEB_OK;
+}
+
+}  // namespace
+
+extern "C" cheb_status_t cheb_anneal_adjoint(int n, const double* h, const double* J, int S, const double* gamma_s,
+                                             const double* t_s, const void* boundaries, const void* psi_T,
+                                             void* grad, cheb_precision_t precision, double tol,
+                                             cheb_method_t method, double* grad_gamma, double* grad_t,
+                                             double* grad_h, double* grad_J, void* workspace, size_t ws_bytes,
+                                             void* stream) {
+    return adjoint_impl(n, h, J, S, nullptr, gamma_s, t_s, boundaries, psi_T, grad, precision, tol, method,
+                        grad_gamma, nullptr, grad_t, grad_h, grad_J, workspace, ws_bytes, stream);
+}
+
+extern "C" cheb_status_t cheb_anneal_general_adjoint(int n, const double* h, const double* J, int S,
+                                                     const double* a_s, const double* b_s, const double* t_s,
+                                                     const void* boundaries, const void* psi_T, void* grad,
+                                                     cheb_precision_t precision, double tol, cheb_method_t method,
+                                                     double* grad_a, double* grad_b, double* grad_t,
+                                                     double* grad_h, double* grad_J, void* workspace,
+                                                     size_t ws_bytes, void* stream) {
+    if (!b_s) return CHEB_ERR_INVALID_ARG;
+    return adjoint_impl(n, h, J, S, b_s, a_s, t_s, boundaries, psi_T, grad, precision, tol, method, grad_a, grad_b,
+                        grad_t, grad_h, grad_J, workspace, ws_bytes, stream);
 }
 
 // Loss L = <psi|H_P|psi>: value, dL/dpsi (torch convention: 2 H_P psi), dL/dh, dL/dJ.

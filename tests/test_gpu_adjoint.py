@@ -214,3 +214,90 @@ def test_adjoint_special_segments_vs_finite_differences(cuda_lib):
     t2[-1] += 2 * e1
     fd = (-3 * loss(gammas, ts) + 4 * loss(gammas, t1) - loss(gammas, t2)) / (2 * e1)
     assert abs(fd - tT.grad[-1].item()) < 1e-6, "t at 0"
+
+
+def _general_energy(h, J, a_s, b_s, ts, psi0):
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    x = torch.from_numpy(psi0).cuda()
+    api.anneal_general(h, J, a_s, b_s, ts, x, tol=1e-13, info=False)
+    return api.energy(h, J, x)[0]
+
+
+def test_general_segments_gradients_vs_finite_differences(cuda_lib):
+    """Segments b_s H_P + a_s sum_j X_j (b_s = 0, a_s = 0 and negative values included):
+    dL/da_s, dL/db_s, dL/dt_s, dL/dh, dL/dJ against central differences (FP64)."""
+    import torch
+
+    from paper_2608_12058_b300 import autograd as AG
+
+    n = 6
+    h, J = I.sk_instance(n, 93)
+    a_s = np.array([1.1, 0.0, -0.6, 0.8])
+    b_s = np.array([0.5, 1.2, -0.8, 0.0])
+    ts = np.array([0.6, 0.5, 0.4, 0.7])
+    psi0 = I.random_state(n, 94)
+    t = lambda v: torch.tensor(np.asarray(v, dtype=np.float64), requires_grad=True)
+    th, tJ, ta, tb, tt = t(h), t(J), t(a_s), t(b_s), t(ts)
+    x = torch.from_numpy(psi0).cuda()
+    L = AG.energy(AG.anneal_general(x, th, tJ, ta, tb, tt, tol=1e-13), th, tJ)
+    L.backward()
+    eps = 1e-6
+    base = {"h": h, "J": J, "a": a_s, "b": b_s, "t": ts}
+    grads = {"h": th.grad.numpy(), "J": tJ.grad.numpy(), "a": ta.grad.numpy(), "b": tb.grad.numpy(),
+             "t": tt.grad.numpy()}
+    picks = [("a", 0), ("a", 1), ("a", 2), ("a", 3), ("b", 0), ("b", 1), ("b", 2), ("b", 3),
+             ("t", 0), ("t", 1), ("t", 2), ("t", 3), ("h", 2), ("J", (1, 4))]
+    for key, idx in picks:
+        vals = []
+        for sgn in (1, -1):
+            v = {k: np.array(val, dtype=np.float64) for k, val in base.items()}
+            v[key][idx] += sgn * eps
+            vals.append(_general_energy(v["h"], v["J"], v["a"], v["b"], v["t"], psi0))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        assert abs(fd - grads[key][idx]) < 1e-7, (key, idx, fd, grads[key][idx])
+
+
+def test_magnus4_schedule_parameter_gradients(cuda_lib):
+    """Gradients of the energy after Magnus propagation with respect to the parameters
+    of a smooth schedule A(t) = p0 (1 - t/T) + p2 sin t, B(t) = p1 t/T (torch composes
+    the node values and the segment weights; the library supplies the segment adjoint)."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+    from paper_2608_12058_b300 import autograd as AG
+
+    n, T, steps = 6, 2.0, 5
+    h, J = I.sk_instance(n, 95)
+    psi0 = I.random_state(n, 96)
+    p = torch.tensor([1.4, 0.9, 0.3], dtype=torch.float64, requires_grad=True)
+
+    def nodes_of(pv):
+        dt = T / steps
+        m = torch.arange(steps, dtype=torch.float64)
+        t1 = m * dt + (0.5 - 3 ** 0.5 / 6) * dt
+        t2 = m * dt + (0.5 + 3 ** 0.5 / 6) * dt
+        A = lambda tt: pv[0] * (1 - tt / T) + pv[2] * torch.sin(tt)
+        B = lambda tt: pv[1] * tt / T
+        return torch.full((steps,), dt, dtype=torch.float64), torch.stack([A(t1), B(t1), A(t2), B(t2)], dim=1)
+
+    dt, nodes = nodes_of(p)
+    th, tJ = torch.tensor(h), torch.tensor(J)
+    L = AG.energy(AG.magnus4(torch.from_numpy(psi0).cuda(), th, tJ, dt, nodes, tol=1e-13), th, tJ)
+    L.backward()
+
+    def loss(pv):
+        d, nd = nodes_of(torch.tensor(pv, dtype=torch.float64))
+        x = torch.from_numpy(psi0).cuda()
+        api.magnus4(h, J, d.numpy(), nd.numpy(), x, tol=1e-13)
+        return api.energy(h, J, x)[0]
+
+    eps = 1e-6
+    for i in range(3):
+        pp, pm = p.detach().numpy().copy(), p.detach().numpy().copy()
+        pp[i] += eps
+        pm[i] -= eps
+        fd = (loss(pp) - loss(pm)) / (2 * eps)
+        assert abs(fd - p.grad[i].item()) < 1e-7, (i, fd, p.grad[i].item())
