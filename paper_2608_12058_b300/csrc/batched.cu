@@ -47,6 +47,14 @@ cheb_status_t stream_pool(cudaStream_t** out) {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// An event destroyed when the call returns, on every path.
+struct ScopedEvent {
+    cudaEvent_t e = nullptr;
+    ~ScopedEvent() {
+        if (e) cudaEventDestroy(e);
+    }
+};
+
 struct BatchLayout {
     size_t res_i64 = 0;   // 2 int64 per instance: energy bounds
     size_t res_f64 = 0;   // 2 double per instance: norm^2, energy
@@ -197,9 +205,10 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
         }
     }
     // the stream pool forks here, so that the large instances overlap the small ones
-    cudaEvent_t fork;
-    CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    CUDA_TRY(cudaEventRecord(fork, s0));
+    ScopedEvent fork_ev;
+    CUDA_TRY(cudaEventCreateWithFlags(&fork_ev.e, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(fork_ev.e, s0));
+    const cudaEvent_t fork = fork_ev.e;
     // 3a. all small instances in one launch, mid-size ones in one cluster launch per size
     // (the descriptor region holds B entries: small ones first, then the clustered)
     size_t dpos = 0;
@@ -251,14 +260,12 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
         }
         for (int j = 0; j < kPoolStreams; ++j) {
             if (!used[j]) continue;
-            cudaEvent_t join;
-            CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-            CUDA_TRY(cudaEventRecord(join, pool[j]));
-            CUDA_TRY(cudaStreamWaitEvent(s0, join, 0));
-            cudaEventDestroy(join);
+            ScopedEvent join;
+            CUDA_TRY(cudaEventCreateWithFlags(&join.e, cudaEventDisableTiming));
+            CUDA_TRY(cudaEventRecord(join.e, pool[j]));
+            CUDA_TRY(cudaStreamWaitEvent(s0, join.e, 0));
         }
     }
-    cudaEventDestroy(fork);
     // 4. per-instance results
     if (infos) {
         for (int i = 0; i < B; ++i) {
