@@ -645,8 +645,9 @@ struct StepRunner {
     FusedPlan plan;
     int prec = 0;
     int* flags = nullptr;
+    void* scratch = nullptr;  // the fused kernels' scratch vectors of the forward layout
     cudaError_t run(const StepArgs& a, cudaStream_t s) const {
-        if (fused) return launch_step_fused(plan, a, nullptr, flags, s);
+        if (fused) return launch_step_fused(plan, a, scratch, flags, s);
         launch_step_plain(prec, a, s);
         return cudaGetLastError();
     }
@@ -723,6 +724,7 @@ cheb_status_t adjoint_impl(int n, const double* h, const double* J, int S, const
     StepRunner runner;
     runner.prec = precision;
     runner.flags = C.flags();
+    runner.scratch = ws + A.fwd.coef + (size_t)(kMaxK + 1) * 2 * sizeof(double);
     runner.fused = fused_supported(n, precision) && n > (precision == CHEB_FP32 ? kSmallMaxF32 : kSmallMaxF64);
     if (runner.fused) runner.plan = fused_plan(n, precision);
     double* gauge = outs + (size_t)n * n + n + 16;

@@ -89,6 +89,21 @@ def test_cf_method_matches_oracle(cuda_lib, oracle, prec):
     assert _rel(y, ref) <= TOL[prec]
 
 
+def test_two_strided_passes_match_oracle(cuda_lib, oracle):
+    """n = 25, the smallest size whose default plan has two strided passes (7 + 7 bits;
+    the n = 30 benchmark runs two of 9), against the oracle."""
+    from paper_2608_12058_b300 import api
+
+    n = 25
+    assert api.get_fused_split(n) == (0, 14)
+    h, J = I.sk_instance(n, 125)
+    psi = I.random_state(n, 126)
+    ref, oinfo = oracle.expmv(h, J, 0.9, 0.15, psi, 2.0 ** -23)
+    y, info = _run(h, J, 0.9, 0.15, psi, "fp32", 2.0 ** -23, path="fused")
+    assert info["K"] == oinfo["K"] and info["K"] > 3
+    assert _rel(y, ref) <= TOL["fp32"]
+
+
 @pytest.mark.parametrize("prec,n", [("fp32", 14), ("fp32", 15), ("fp32", 17), ("fp64", 13), ("fp64", 16)])
 def test_cluster_path_matches_oracle(cuda_lib, oracle, prec, n):
     """The whole run on one thread-block cluster (vectors in distributed shared memory,
