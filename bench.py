@@ -146,8 +146,11 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": 0, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"sk_n{SAMPLE['n']}_sample_of_n30_family", "n": SAMPLE["n"], "tol": TOL32,
-                       "method": "chebyshev"},
+            "config": {"workload": "sk_n30_g1.0_t20", "n": 30, "gamma": 1.0, "t": 20.0, "tol": TOL32,
+                       "method": "chebyshev", "parallelism": "single",
+                       "sample": (f"each step: the full oracle exp(-itH)psi of the n={SAMPLE['n']} member of the "
+                                  f"same SK family (h~U(-1,1), gamma={SAMPLE['gamma']}, t={SAMPLE['t']}, "
+                                  f"K={info['K']}), amplitude-updates/s of that run")},
             "cpu_baseline": cpu_baseline_dict(value, dt, info),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
