@@ -324,6 +324,21 @@ cheb_status_t cheb_set_fused_split(int n, int l, int h);
 cheb_status_t cheb_get_fused_split(int n, int* l, int* h);
 
 /*
+ * L2-blocked step tail of the fused FP32 step (Sec. II.D matvec, scheduled for a
+ * 126 MB L2; no counterpart in the paper). When on, the last strided pass and the low
+ * pass of each step run as one persistent launch: amplitudes are grouped by their
+ * bits [11, lo) (lo = first bit of the last strided range), and the low tiles of
+ * a group are processed right after the strided tiles of that group, so b_{k+1}
+ * and the partial sum are read back from L2 instead of DRAM. Results are identical
+ * to the separate launches (same operations in the same order per amplitude).
+ * Used for n >= 22 when the split has at least two strided passes, l <= 1 and a
+ * last range of 6..9 bits; other splits keep the separate launches.
+ * on: 0 off, 1 on (process-wide). cheb_get_fused_blocking returns the setting.
+ */
+cheb_status_t cheb_set_fused_blocking(int on);
+int cheb_get_fused_blocking(void);
+
+/*
  * General polynomial p(Ht) psi (Algorithm 2 with caller-supplied coefficients):
  * psi <- sum_{m=0}^{K} c_m T_m(Ht) psi with Ht = (H - center) / radius and
  * H = diag(E) + gamma * sum_j X_j. The caller chooses center and radius (radius > 0);
@@ -365,13 +380,15 @@ cheb_status_t cheb_energy(int n, const double* h, const double* J, const void* p
  *   returns how many launches of that kind were timed and their summed device
  *   time. cheb_profile_reset drops the records.
  * Kinds: 3 plain one-pass step, 5 adjoint accumulation (cheb_anneal_adjoint),
- * 6 fused low pass, 7 fused strided (high-bit) pass.
+ * 6 fused low pass, 7 fused strided (high-bit) pass, 8 L2-blocked step tail (last
+ * strided pass + low pass, cheb_set_fused_blocking).
  */
 typedef enum {
     CHEB_KERNEL_STEP_PLAIN = 3,
     CHEB_KERNEL_ADJOINT_ACC = 5,
     CHEB_KERNEL_FUSED_LOW = 6,
-    CHEB_KERNEL_FUSED_HIGH = 7
+    CHEB_KERNEL_FUSED_HIGH = 7,
+    CHEB_KERNEL_FUSED_TAIL = 8
 } cheb_kernel_kind_t;
 
 /*

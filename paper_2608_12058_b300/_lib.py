@@ -55,6 +55,8 @@ SIGNATURES = {
     "cheb_energy": (c_int, [c_int, _dp, _dp, c_void_p, c_int, c_void_p, c_size_t, c_void_p, _dp, _dp]),
     "cheb_set_fused_split": (c_int, [c_int, c_int, c_int]),
     "cheb_get_fused_split": (c_int, [c_int, _ip, _ip]),
+    "cheb_set_fused_blocking": (c_int, [c_int]),
+    "cheb_get_fused_blocking": (c_int, []),
     "cheb_expmv_noalloc": (c_int, [c_int, _dp, _dp, c_double, c_double, c_void_p, c_int, c_double, c_int, c_int,
                                    c_void_p, ctypes.POINTER(Info)]),
     "cheb_anneal": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, c_void_p, c_int, c_double, c_int, c_void_p,

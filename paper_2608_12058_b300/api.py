@@ -442,7 +442,17 @@ def get_fused_split(n: int):
     return l.value, h.value
 
 
-KERNEL_KIND = {"plain": 3, "adjoint_acc": 5, "low": 6, "high": 7}
+def set_fused_blocking(on: bool):
+    """Run the last strided pass and the low pass of each fused step as one L2-blocked
+    launch (True) or as separate launches (False); results are identical."""
+    _lib.check(_lib.lib().cheb_set_fused_blocking(1 if on else 0), "cheb_set_fused_blocking")
+
+
+def get_fused_blocking() -> bool:
+    return bool(_lib.lib().cheb_get_fused_blocking())
+
+
+KERNEL_KIND = {"plain": 3, "adjoint_acc": 5, "low": 6, "high": 7, "tail": 8}
 
 
 def wait_selftest(device=None):

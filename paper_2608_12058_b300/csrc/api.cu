@@ -393,6 +393,14 @@ cheb_status_t cheb_set_fused_split(int n, int l, int h) {
     return fused_set_split(n, l, h) ? CHEB_OK : CHEB_ERR_INVALID_ARG;
 }
 
+cheb_status_t cheb_set_fused_blocking(int on) {
+    if (on != 0 && on != 1) return CHEB_ERR_INVALID_ARG;
+    fused_set_blocking(on);
+    return CHEB_OK;
+}
+
+int cheb_get_fused_blocking(void) { return fused_get_blocking(); }
+
 cheb_status_t cheb_get_fused_split(int n, int* l, int* h) {
     if (!l || !h || !fused_supported(n, 0)) return CHEB_ERR_INVALID_ARG;
     FusedPlan p = fused_plan(n, 0);

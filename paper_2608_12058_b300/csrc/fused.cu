@@ -565,6 +565,480 @@ __global__ void __launch_bounds__(kLowThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// L2-blocked tail of a step: the last strided pass (bits [lo, n), lo + H = n) and the
+// low pass in one persistent launch. Amplitudes are grouped by their bits [11, lo):
+// group g holds 2^(n - lo + 11) amplitudes, 128 strided tiles (bits 4..10 of the
+// tile index free) and 2^H low tiles (bits lo..n-1 free). A low tile of group g reads
+// the partial q that the strided tiles of group g wrote, and b_{k+1} of groups g and
+// g ^ 1 that those strided tiles read; scheduling the strided tiles of group g + 1
+// between them and the low tiles of group g keeps that data in L2, so the low tiles
+// read b_{k+1} and q from L2 and their in-place write of the output replaces the
+// q lines still in L2 before they go back to DRAM.
+//
+// Work items in order: S(0) .. S(D - 1), then S(s) followed by L(s - D) for
+// s = D .. G - 1, then L(G - D) .. L(G - 1), where S(g) are the 128 strided tiles and
+// L(g) the 2^H low tiles of group g, and the lag D (host-chosen) puts several items
+// per SM between the strided tiles of a group and its low tiles. CTAs take items
+// from a global counter, so an item only ever waits for items taken before it:
+// before loading a low tile the producer waits until all 128 strided tiles of its
+// group are published (a notifier warp per CTA fences each finished tile's q stores
+// and then raises the group's count). Every wait is bounded (status flag, abort,
+// clean exit).
+//
+// Measured on B300: DRAM traffic of the tail drops from 56 to ~32.5 B per amplitude
+// (n = 26), but the combined kernel is limited by shared-memory traffic and latency
+// (a 9-bit strided tile moves ~783 KB through shared memory, a low tile ~277 KB), so
+// the step is within a few percent of the separate launches (faster at n = 28,
+// slower at n = 26 and 30); it is off by default.
+template <int H>
+struct MixedCfg {
+    static constexpr int kRows = 1 << H;
+    static constexpr int kBox = kRows < 256 ? kRows : 256;
+    static constexpr uint32_t kS = (uint32_t)kRows * 128;    // b_{k+1} of a strided tile
+    static constexpr int kP = 1 << (H - 6);                   // q chunks of 64 rows
+    static constexpr uint32_t kChunk = 64 * 128;
+    // a whole strided tile's q chunks fit the ring (a ring of 4 stalls 9-bit tiles
+    // mid-tile for one DRAM round trip); the rest of shared memory holds the stages
+    static constexpr int kSR = kP > 4 ? 8 : 4;
+    static constexpr uint32_t kStage = 4 * kTB;              // {b1, psi, q, partner} of a low tile
+    static constexpr int kNS = kSR == 8 ? 2 : 3;
+    static constexpr int kNR = 8;                             // completion records in flight
+    static constexpr size_t kRingOff = (size_t)kNS * kStage;
+    static constexpr size_t kWOff = kRingOff + (size_t)kSR * kChunk;
+    static constexpr size_t kItemOff = kWOff + (size_t)kNS * kW * sizeof(int64_t);
+    static constexpr size_t kNoteOff = kItemOff + 32;
+    static constexpr size_t kBarOff = kNoteOff + (size_t)kNR * sizeof(int64_t);
+    static constexpr size_t kAbortOff = kBarOff + (size_t)(2 * kNS + 2 * kSR + 2 * kNR) * sizeof(uint64_t);
+    static constexpr size_t kSmem = kAbortOff + 16;
+    static_assert(kS <= kStage && kNS * sizeof(int64_t) <= 32, "stage map");
+};
+
+// Consumer warps, the producer warp and a notifier warp that publishes finished
+// strided tiles (fence + count) so that the consumers never wait on a memory fence.
+constexpr int kMixedThreads = kCons + 64;
+
+struct MixedArgs {
+    StridedArgs sa;               // last strided pass: slot_in = slot = q, sgn = 1
+    LowArgs la;                   // low pass: slot = q, slot_coeff = 1, l = 0 or 1
+    unsigned long long* work;     // item counter (zero at launch)
+    unsigned* done;               // per group: strided tiles done (zero at launch)
+    int gbits;                    // lo - 11 (2^gbits groups)
+    int lag;                      // D, 1 <= D <= 2^gbits
+};
+
+constexpr int kItemStrided = 0, kItemLow = 1, kItemEnd = 2;
+
+struct MixedItem {
+    int kind;
+    int64_t g;    // group
+    int64_t idx;  // strided tile within the group (0..127) or low tile (0..2^H - 1)
+};
+
+__device__ __forceinline__ MixedItem mixed_decode(unsigned long long i, int gbits, int H, int lag) {
+    const unsigned long long G = 1ull << gbits, D = (unsigned long long)lag, NS = 128, NL = 1ull << H;
+    const unsigned long long seg = NS + NL, head = D * NS;
+    if (i < head) return {kItemStrided, (int64_t)(i / NS), (int64_t)(i % NS)};
+    const unsigned long long j = i - head, s = D + j / seg;
+    if (s < G) {
+        const unsigned long long r = j % seg;
+        return r < NS ? MixedItem{kItemStrided, (int64_t)s, (int64_t)r}
+                      : MixedItem{kItemLow, (int64_t)(s - D), (int64_t)(r - NS)};
+    }
+    const unsigned long long k = j - (G - D) * seg, g = G - D + k / NL;
+    if (g < G) return {kItemLow, (int64_t)g, (int64_t)(k % NL)};
+    return {kItemEnd, 0, 0};
+}
+
+// Bounded acquire-wait until *p >= target (same limit and abort rule as mbar_wait).
+__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target, int* flags, volatile int* abort) {
+    const long long t0 = clock64();
+    while (true) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+        if (v >= target) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            atomicOr(flags, kFlagTimeout);
+            *abort = 1;
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+// L2 eviction-priority policies and the cache-hinted bulk copies and stores of the
+// blocked tail (PTX createpolicy / .L2::cache_hint).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void tma_load_1d_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                 uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d_hint(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                                 uint64_t* bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+        "{%2, %3, %4, %5}], [%6], %7;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ void st_hint(float4* p, float4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w), "l"(pol)
+                 : "memory");
+}
+
+template <int H>
+__global__ void __launch_bounds__(kMixedThreads, 1)
+    k_mixed(const MixedArgs m, const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap) {
+    using Cfg = MixedCfg<H>;
+    static_assert(H >= 6 && H <= 9, "strided range");
+    static_assert(Cfg::kSmem <= 227 * 1024, "shared memory");
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = (uint64_t*)(smem + Cfg::kBarOff);
+    uint64_t* empty = full + Cfg::kNS;
+    uint64_t* sfull = empty + Cfg::kNS;
+    uint64_t* sempty = sfull + Cfg::kSR;
+    uint64_t* cdone = sempty + Cfg::kSR;   // a strided tile's q stores are issued (16 warps)
+    uint64_t* cempty = cdone + Cfg::kNR;   // the notifier has published that record
+    volatile int* abort = (volatile int*)(smem + Cfg::kAbortOff);
+    int64_t* wall = (int64_t*)(smem + Cfg::kWOff);
+    long long* item = (long long*)(smem + Cfg::kItemOff);
+    volatile long long* note = (volatile long long*)(smem + Cfg::kNoteOff);
+    unsigned char* ring = smem + Cfg::kRingOff;
+    const StridedArgs& a = m.sa;
+    const LowArgs& la = m.la;
+    const int t = threadIdx.x;
+    const int warp = t >> 5, lane = t & 31;
+    const bool need_psi = la.ck_re != 0.f || la.ck_im != 0.f;
+    if (t == 0) {
+        for (int i = 0; i < Cfg::kNS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kCons / 32);
+        }
+        for (int i = 0; i < Cfg::kSR; ++i) {
+            mbar_init(&sfull[i], 1);
+            mbar_init(&sempty[i], kCons / 32);
+        }
+        for (int i = 0; i < Cfg::kNR; ++i) {
+            mbar_init(&cdone[i], kCons / 32);
+            mbar_init(&cempty[i], 1);
+        }
+        *abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == kCons / 32 + 1) {
+        // ---------------- notifier warp ----------------
+        // Record j: the consumers' q stores of this CTA's j-th strided tile (or the end
+        // marker, group < 0). The mbarrier wait observes every consumer warp's stores;
+        // the GPU-scope fence then publishes them before the group count is raised.
+        if (lane != 0) return;
+        for (long long j = 0;; ++j) {
+            const int r = (int)(j % Cfg::kNR);
+            if (!mbar_wait(&cdone[r], (uint32_t)((j / Cfg::kNR) & 1), a.flags_ws, abort)) break;
+            const long long g = note[r];
+            if (g < 0) break;
+            __threadfence();
+            atomicAdd(m.done + g, 1u);
+            mbar_arrive(&cempty[r]);
+        }
+        return;
+    }
+
+    if (warp == kCons / 32) {
+        // ---------------- producer warp ----------------
+        int last[Cfg::kNS], slast[Cfg::kSR];
+        for (int i = 0; i < Cfg::kNS; ++i) last[i] = -1;
+        for (int i = 0; i < Cfg::kSR; ++i) slast[i] = -1;
+        long long cc = 0;  // q chunks issued
+        auto grab = [&]() -> unsigned long long {
+            unsigned long long v = 0;
+            if (lane == 0) v = atomicAdd(m.work, 1ull);
+            return __shfl_sync(0xffffffffu, v, 0);
+        };
+        // this lane's tile-table entries (as in k_low), loaded one item ahead
+        auto load_row = [&](int64_t Tt, int64_t* x0, int64_t* x1) {
+            const int64_t* row = la.tiles + Tt * (kLowBits + 1);
+            x0[0] = __ldg(row + kLowBits);
+#pragma unroll
+            for (int i = 1; i <= 5; ++i) x0[i] = __ldg(row + i);
+            if (lane < 16) {
+#pragma unroll
+                for (int i = 6; i <= 9; ++i) x1[i - 6] = __ldg(row + i);
+            } else {
+                x1[0] = __ldg(row + 10);
+                x1[1] = __ldg(row + 0);
+            }
+        };
+        int64_t r0[6], r1[4];
+        // the strided tiles' b_{k+1} and q are read again by the low tiles of their group
+        const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
+        unsigned long long nxt = grab();
+        MixedItem ni = mixed_decode(nxt, m.gbits, H, m.lag);
+        if (ni.kind == kItemLow) load_row(ni.g + (ni.idx << m.gbits), r0, r1);
+        for (int it = 0;; ++it) {
+            const unsigned long long cur = nxt;
+            const MixedItem ci = ni;
+            int64_t c0[6], c1[4];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) c0[i] = r0[i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) c1[i] = r1[i];
+            if (ci.kind != kItemEnd) {
+                nxt = grab();
+                ni = mixed_decode(nxt, m.gbits, H, m.lag);
+                if (ni.kind == kItemLow) load_row(ni.g + (ni.idx << m.gbits), r0, r1);
+            }
+            const int s = it % Cfg::kNS, k = it / Cfg::kNS;
+            int ok = 1;
+            if (lane == 0 && k > 0) ok = mbar_wait(&empty[s], (k - 1) & 1, a.flags_ws, abort);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            if (ci.kind == kItemEnd) {
+                if (lane == 0) {
+                    item[s] = -1;
+                    mbar_arrive(&full[s]);
+                    last[s] = k;
+                }
+                break;
+            }
+            if (ci.kind == kItemLow) {
+                int64_t* W = wall + s * kW;
+                int64_t e = c0[0];
+#pragma unroll
+                for (int i = 1; i <= 5; ++i) e += sel((lane >> (i - 1)) & 1, c0[i]);
+                W[lane] = e;
+                if (lane < 16) {
+                    int64_t f = 0;
+#pragma unroll
+                    for (int i = 6; i <= 9; ++i) f += sel((lane >> (i - 6)) & 1, c1[i - 6]);
+                    W[32 + lane] = f;
+                } else if (lane == 16) {
+                    W[48] = c1[0] + c1[1];
+                } else if (lane == 17) {
+                    W[49] = c1[0] - c1[1];
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    ok = wait_count(m.done + ci.g, 128u, a.flags_ws, abort);
+                    if (ok) {
+                        // q was written through the generic proxy by other SMs; order
+                        // those writes before this thread's bulk copies read it
+                        asm volatile("fence.proxy.async.global;" ::: "memory");
+                        __threadfence_block();
+                        const int64_t T = ci.g + (ci.idx << m.gbits);
+                        item[s] = (long long)cur;
+                        unsigned char* d = smem + (size_t)s * Cfg::kStage;
+                        const uint32_t bytes = (2u + (need_psi ? 1u : 0u) + (uint32_t)la.l) * kTB;
+                        mbar_expect_tx(&full[s], bytes);
+                        // psi and q are not read again in this step: evict them first
+                        tma_load_1d(d, la.b1 + T * kTF, kTB, &full[s]);
+                        if (need_psi) tma_load_1d_hint(d + kTB, la.psi + T * kTF, kTB, &full[s], pol_first);
+                        tma_load_1d_hint(d + 2 * kTB, la.slot + T * kTF, kTB, &full[s], pol_first);
+                        if (la.l) tma_load_1d(d + 3 * kTB, la.b1 + (T ^ 1) * kTF, kTB, &full[s]);
+                        last[s] = k;
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            } else {
+                if (lane == 0) {
+                    const int T = (int)((ci.g << 7) | ci.idx);  // tile index below the range
+                    item[s] = (long long)cur;
+                    unsigned char* d = smem + (size_t)s * Cfg::kStage;
+                    mbar_expect_tx(&full[s], Cfg::kS);
+#pragma unroll
+                    for (int c = 0; c < Cfg::kRows / Cfg::kBox; ++c)
+                        tma_load_4d_hint(d + (size_t)c * Cfg::kBox * 128, &map, 0, T, c * Cfg::kBox, 0, &full[s],
+                                         pol_last);
+                    last[s] = k;
+                    for (int p = 0; p < Cfg::kP; ++p, ++cc) {
+                        const int r = (int)(cc % Cfg::kSR);
+                        const long long kk = cc / Cfg::kSR;
+                        if (kk > 0 && !mbar_wait(&sempty[r], (int)((kk - 1) & 1), a.flags_ws, abort)) {
+                            ok = 0;
+                            break;
+                        }
+                        mbar_expect_tx(&sfull[r], Cfg::kChunk);
+                        slast[r] = (int)(kk & 1);
+                        tma_load_4d_hint(ring + (size_t)r * Cfg::kChunk, &smap, 0, T, p * 64, 0, &sfull[r], pol_last);
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            }
+        }
+        if (lane == 0) {
+            for (int i = 0; i < Cfg::kNS; ++i)
+                if (last[i] >= 0) mbar_drain(&full[i], last[i] & 1, a.flags_ws);
+            for (int i = 0; i < Cfg::kSR; ++i)
+                if (slast[i] >= 0) mbar_drain(&sfull[i], slast[i], a.flags_ws);
+        }
+        return;
+    }
+
+    // ---------------- consumer warps ----------------
+    const int u = t & 7;
+    const int rlo = t >> 3;
+    const int64_t row_stride_f4 = (int64_t)1 << (a.lo - 1);
+    const float2 g_hi = dup(a.scale_g), g_lo = dup(a.scale_glo);
+    // low-pass thread constants (every energy term that involves only bits 0..10)
+    int64_t K00, K01, K10, K11;
+    {
+        const int n = la.n;
+        const int64_t* J = la.jq;
+        const int64_t* hq = la.jq + (size_t)n * n;
+        int64_t e_tau = 0, phi0 = hq[0], phi10 = hq[10];
+        for (int i = 1; i <= 9; ++i) {
+            const uint32_t bi = (t >> (i - 1)) & 1;
+            int64_t hi = hq[i];
+            for (int j = i + 1; j <= 9; ++j) hi += sel((t >> (j - 1)) & 1, J[i * n + j]);
+            e_tau += sel(bi, hi);
+            phi0 += sel(bi, J[0 * n + i]);
+            phi10 += sel(bi, J[10 * n + i]);
+        }
+        const int64_t j0b = J[0 * n + 10];
+        K00 = e_tau + phi0 + phi10 + j0b;
+        K01 = e_tau - phi0 + phi10 - j0b;
+        K10 = e_tau + phi0 - phi10 - j0b;
+        K11 = e_tau - phi0 - phi10 + j0b;
+    }
+    const float2 ckr = dup(la.ck_re), cki_s = make_float2(-la.ck_im, la.ck_im);
+    const float2 gh = dup(la.ghi), gl = dup(la.glo), sc = dup(la.scale), cs = dup(la.slot_coeff);
+    const int scale_hi = (127 + 32 - la.Q) << 23, scale_lo = (127 - la.Q) << 23;
+    const uint64_t pol_out = policy_evict_first();
+    long long cc = 0;  // q chunks consumed
+    long long sj = 0;  // completion records sent
+    // Send record sj (group g, or -1 for the end) to the notifier once this warp's
+    // stores are issued; records are reused after the notifier has published them.
+    auto record = [&](long long g) -> bool {
+        __syncwarp();
+        bool ok = true;
+        if (lane == 0) {
+            const int r = (int)(sj % Cfg::kNR);
+            if (sj >= Cfg::kNR) ok = mbar_wait(&cempty[r], (uint32_t)(((sj / Cfg::kNR) - 1) & 1), a.flags_ws, abort);
+            if (ok) {
+                if (warp == 0) note[r] = g;
+                mbar_arrive(&cdone[r]);
+            }
+        }
+        ++sj;
+        return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    };
+    for (int it = 0;; ++it) {
+        const int s = it % Cfg::kNS;
+        if (!mbar_wait(&full[s], (it / Cfg::kNS) & 1, a.flags_ws, abort)) break;
+        const long long cur = item[s];
+        if (cur < 0) {
+            record(-1);
+            break;
+        }
+        const MixedItem ci = mixed_decode((unsigned long long)cur, m.gbits, H, m.lag);
+        const unsigned char* d = smem + (size_t)s * Cfg::kStage;
+        if (ci.kind == kItemStrided) {
+            const int64_t T = (ci.g << 7) | ci.idx;
+            const int64_t base = T * 8;  // the range is the top H bits: no tile bits above it
+            const float4* tile = (const float4*)d;
+            bool ok = true;
+#pragma unroll
+            for (int p = 0; p < Cfg::kP; ++p) {
+                Acc S;
+                S.zero();
+#pragma unroll
+                for (int b = 1; b < Cfg::kP; b <<= 1) S.add(tile[((rlo | ((p ^ b) << 6))) * 8 + u]);
+#pragma unroll
+                for (int j = 0; j < 6; ++j) S.add(tile[((rlo ^ (1 << j)) | (p << 6)) * 8 + u]);
+                float2 q0 = __ffma2_rn(g_hi, S.a, __fmul2_rn(g_lo, S.a));
+                float2 q1 = __ffma2_rn(g_hi, S.b, __fmul2_rn(g_lo, S.b));
+                const int r = (int)(cc % Cfg::kSR);
+                if (!mbar_wait(&sfull[r], (int)((cc / Cfg::kSR) & 1), a.flags_ws, abort)) {
+                    ok = false;
+                    break;
+                }
+                ++cc;
+                const float4 w = ((const float4*)(ring + (size_t)r * Cfg::kChunk))[rlo * 8 + u];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sempty[r]);
+                q0 = __fadd2_rn(lo2(w), q0);
+                q1 = __fadd2_rn(hi2(w), q1);
+                a.slot[base + (rlo | (p << 6)) * row_stride_f4 + u] = make_float4(q0.x, q0.y, q1.x, q1.y);
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            if (!record(ci.g)) break;
+        } else {
+            const int64_t T = ci.g + (ci.idx << m.gbits);
+            const float4* sb1 = (const float4*)d;
+            const float4* spsi = sb1 + kTF;
+            const float4* sslot = sb1 + 2 * kTF;
+            const float4* spart = sb1 + 3 * kTF;
+            const int64_t* W = wall + s * kW;
+            Acc S0, S1;
+            S0.zero();
+            S1.zero();
+            if (la.l) {
+                S0.add(spart[t]);
+                S1.add(spart[t + kCons]);
+            }
+            const float4 v0 = sb1[t], v1 = sb1[t + kCons];
+            S0.a = __fadd2_rn(S0.a, __fadd2_rn(hi2(v0), lo2(v1)));
+            S0.b = __fadd2_rn(S0.b, __fadd2_rn(lo2(v0), hi2(v1)));
+            S1.a = __fadd2_rn(S1.a, __fadd2_rn(hi2(v1), lo2(v0)));
+            S1.b = __fadd2_rn(S1.b, __fadd2_rn(lo2(v1), hi2(v0)));
+#pragma unroll
+            for (int jj = 0; jj < 8; jj += 2) {
+                const int pa = t ^ (1 << jj), pb = t ^ (2 << jj);
+                S0.add2(sb1[pa], sb1[pb]);
+                S1.add2(sb1[pa + kCons], sb1[pb + kCons]);
+            }
+            {
+                const int pa = t ^ (1 << 8);
+                S0.add(sb1[pa]);
+                S1.add(sb1[pa + kCons]);
+            }
+            const int64_t base = W[t & 31] + W[32 + (t >> 5)];
+            const int64_t up = W[48], um = W[49];
+            const int64_t e00 = base + up + K00, e01 = base + um + K01;
+            const int64_t e10 = base - um + K10, e11 = base - up + K11;
+            const float4 ps0 = need_psi ? spsi[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 ps1 = need_psi ? spsi[t + kCons] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 q0 = sslot[t];
+            const float4 q1 = sslot[t + kCons];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            auto dd = [&](int64_t e, float& hi, float& lo) {
+                hi = __int2float_rn((int)(e >> 32)) * __int_as_float(scale_hi);
+                lo = __uint2float_rn((unsigned)(e & 0xffffffffll)) * __int_as_float(scale_lo);
+            };
+            float dh, dl;
+            dd(e00, dh, dl);
+            const float2 o00 = combine(dh, dl, lo2(v0), gh, gl, S0.a, sc, cs, lo2(q0), ckr, cki_s, lo2(ps0));
+            dd(e01, dh, dl);
+            const float2 o01 = combine(dh, dl, hi2(v0), gh, gl, S0.b, sc, cs, hi2(q0), ckr, cki_s, hi2(ps0));
+            dd(e10, dh, dl);
+            const float2 o10 = combine(dh, dl, lo2(v1), gh, gl, S1.a, sc, cs, lo2(q1), ckr, cki_s, lo2(ps1));
+            dd(e11, dh, dl);
+            const float2 o11 = combine(dh, dl, hi2(v1), gh, gl, S1.b, sc, cs, hi2(q1), ckr, cki_s, hi2(ps1));
+            // the output is next step's b_{k+1}, not read again in this launch
+            st_hint(la.out + T * kTF + t, make_float4(o00.x, o00.y, o01.x, o01.y), pol_out);
+            st_hint(la.out + T * kTF + t + kCons, make_float4(o10.x, o10.y, o11.x, o11.y), pol_out);
+        }
+    }
+}
+
 int g_num_sms = 0;
 std::mutex g_mu;
 
@@ -614,31 +1088,38 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-template <int H>
-cudaError_t launch_strided_ws_t(const StridedArgs& a, int n, cudaStream_t s) {
-    using Cfg = StridedWsCfg<H>;
+// Tensor maps of a strided pass over bits [lo, lo + H): b_{k+1} in boxes of `box`
+// rows of the range, the slot in chunks of 64 rows (only encoded when sgn != 0).
+cudaError_t strided_maps(const StridedArgs& a, int n, int H, int box_rows, CUtensorMap* map, CUtensorMap* smap) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     // (row of 32 floats) x (rows below the range) x (rows in the range) x (rows above)
     cuuint64_t dims[4] = {32, (cuuint64_t)1 << (a.lo - 4), (cuuint64_t)1 << H, (cuuint64_t)1 << (n - a.lo - H)};
     cuuint64_t strides[3] = {128, (cuuint64_t)1 << (a.lo + 3), (cuuint64_t)1 << (a.lo + H + 3)};
-    cuuint32_t box[4] = {32, 1, (cuuint32_t)Cfg::kBox, 1};
+    cuuint32_t box[4] = {32, 1, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUtensorMap map, smap;
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)a.b1, dims, strides, box, estr,
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)a.b1, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    // slot rows in chunks of 64 rows of the range (only read when sgn != 0)
-    smap = map;
+    *smap = *map;
     if (a.sgn != 0.f) {
         cuuint32_t sbox[4] = {32, 1, 64, 1};
-        if (enc(&smap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)a.slot_in, dims, strides, sbox, estr,
+        if (enc(smap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)a.slot_in, dims, strides, sbox, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
-    cudaError_t e =
+    return cudaSuccess;
+}
+
+template <int H>
+cudaError_t launch_strided_ws_t(const StridedArgs& a, int n, cudaStream_t s) {
+    using Cfg = StridedWsCfg<H>;
+    CUtensorMap map, smap;
+    cudaError_t e = strided_maps(a, n, H, Cfg::kBox, &map, &smap);
+    if (e != cudaSuccess) return e;
+    e =
         cudaFuncSetAttribute(k_strided_ws<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(a.ntiles, num_sms());
@@ -664,6 +1145,31 @@ cudaError_t launch_strided(int H, const StridedArgs& a, int n, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+template <int H>
+cudaError_t launch_mixed_t(const MixedArgs& m, int n, cudaStream_t s) {
+    using Cfg = MixedCfg<H>;
+    CUtensorMap map, smap;
+    cudaError_t e = strided_maps(m.sa, n, H, Cfg::kBox, &map, &smap);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_mixed<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    if (e != cudaSuccess) return e;
+    note_launch(kKindMixed);
+    const int pi = prof_begin(kKindMixed, s);
+    k_mixed<H><<<(unsigned)num_sms(), kMixedThreads, Cfg::kSmem, s>>>(m, map, smap);
+    prof_end(pi, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mixed(int H, const MixedArgs& m, int n, cudaStream_t s) {
+    switch (H) {
+        case 6: return launch_mixed_t<6>(m, n, s);
+        case 7: return launch_mixed_t<7>(m, n, s);
+        case 8: return launch_mixed_t<8>(m, n, s);
+        case 9: return launch_mixed_t<9>(m, n, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 // Split h strided bits above bit lo0 into near-equal passes of 3..9 bits.
 bool make_passes(int lo0, int h, FusedPlan& p) {
     p.npass = 0;
@@ -685,7 +1191,19 @@ bool make_passes(int lo0, int h, FusedPlan& p) {
 
 }  // namespace
 
-size_t fused_scratch_bytes(int, int) { return 0; }
+// The L2-blocked tail needs an item counter and one counter per group of amplitudes
+// (at most 2^(n - 17) groups: the last strided range has at least 6 bits).
+constexpr int kMixedMinN = 22;
+size_t mixed_counter_bytes(int gbits) { return 8 + ((size_t)4 << gbits); }
+
+size_t fused_scratch_bytes(int n, int prec) {
+    if (prec != 0 || n < kMixedMinN || n > kMaxQubits) return 0;
+    return (mixed_counter_bytes(n - 17) + 255) / 256 * 256;
+}
+
+static int g_blocking = 0;
+void fused_set_blocking(int on) { g_blocking = on ? 1 : 0; }
+int fused_get_blocking() { return g_blocking; }
 
 bool fused_supported(int n, int prec) { return prec == 0 && n >= kLowBits && n <= kMaxQubits; }
 
@@ -755,7 +1273,7 @@ FusedPlan fused_plan(int n, int prec) {
     return p;
 }
 
-cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, int* flags, cudaStream_t st) {
+cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void* scratch, int* flags, cudaStream_t st) {
     if (plan.prec != 0 || plan.n != s.n || !fused_split_valid(s.n, plan.l, plan.h) || s.M != kLowBits)
         return cudaErrorInvalidValue;
     const float ghi = (float)s.g;
@@ -764,7 +1282,14 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, i
     // The strided passes build the partial q in `out` when out is a separate
     // buffer (b2 is then left intact), else in place in b2.
     float4* q = (s.out != s.psi && s.out != s.b1) ? (float4*)s.out : (float4*)s.b2;
-    for (int k = 0; k < plan.npass; ++k) {
+    // The last strided pass and the low pass run as one L2-blocked launch when enabled
+    // and the plan allows it (an earlier strided pass, at most one L2 partner bit, a
+    // last range of 6..9 bits, scratch for the counters).
+    const int lastp = plan.npass - 1;
+    const bool mixed = g_blocking && scratch != nullptr && s.n >= kMixedMinN && plan.npass >= 2 && plan.l <= 1 &&
+                       plan.hb[lastp] >= 6 && plan.hb[lastp] <= kMaxStrided && s.out != s.b1;
+    const int nsep = mixed ? lastp : plan.npass;  // strided passes launched on their own
+    for (int k = 0; k < nsep; ++k) {
         StridedArgs sa;
         sa.b1 = (const float4*)s.b1;
         sa.slot_in = (k == 0) ? (const float4*)s.b2 : q;
@@ -797,6 +1322,33 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void*, i
     la.slot_coeff = slot_coeff;
     la.ghi = ghi;
     la.glo = glo;
+    if (mixed) {
+        MixedArgs m;
+        m.sa.b1 = (const float4*)s.b1;
+        m.sa.slot_in = q;
+        m.sa.slot = q;
+        m.sa.lo = plan.lo[lastp];
+        m.sa.ntiles = (int64_t)1 << (s.n - plan.hb[lastp] - 4);
+        m.sa.scale_g = (float)s.scale * ghi;
+        m.sa.scale_glo = (float)s.scale * glo;
+        m.sa.sgn = 1.0f;
+        m.sa.flags_ws = flags;
+        m.la = la;
+        m.gbits = plan.lo[lastp] - kLowBits;
+        // about six items per SM between a group's strided tiles and its low tiles;
+        // the groups in that window (b_{k+1} and q, 2^(15 + H) bytes each) stay in L2
+        {
+            const int per_seg = 128 + (1 << plan.hb[lastp]);
+            const int want = (6 * num_sms() + per_seg - 1) / per_seg;
+            m.lag = std::min(std::max(want, 2), 8);
+            m.lag = (int)std::min<int64_t>(m.lag, (int64_t)1 << m.gbits);
+        }
+        m.work = (unsigned long long*)scratch;
+        m.done = (unsigned*)((unsigned char*)scratch + 8);
+        cudaError_t e = cudaMemsetAsync(scratch, 0, mixed_counter_bytes(m.gbits), st);
+        if (e != cudaSuccess) return e;
+        return launch_mixed(plan.hb[lastp], m, s.n, st);
+    }
     cudaError_t e = cudaFuncSetAttribute(k_low, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLowSmem);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(la.ntiles, num_sms());

@@ -16,6 +16,7 @@ enum KernelKind : int {
     kKindReduce = 5,
     kKindLow = 6,
     kKindHigh = 7,
+    kKindMixed = 8,
 };
 void note_launch(int kind);
 // Event-bracketed timing of one launch when profiling is on (prof_begin returns -1 otherwise).

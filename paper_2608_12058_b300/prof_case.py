@@ -3,6 +3,13 @@
     python -m paper_2608_12058_b300.prof_case N L H [STEPS]
         STEPS fused Clenshaw steps (cheb_poly_apply with random coefficients) at n = N
         with the bit split (L, H) (kernel names k_low and k_strided*).
+    python -m paper_2608_12058_b300.prof_case tail N L H [STEPS]
+        the same with the L2-blocked step tail on (kernel names k_strided* for the
+        earlier strided passes, k_mixed for the last strided pass + low pass).
+    python -m paper_2608_12058_b300.prof_case compare N [STEPS]
+        times STEPS fused steps at n = N (default split) with the separate launches and
+        with the L2-blocked step tail, twice each (CUDA events around the call, per-kind
+        event timing from the library), and prints ms per step and per launch.
     python -m paper_2608_12058_b300.prof_case adjoint N S
         the first S segments of the anneal schedule at n = N (complex64): forward with
         segment-start states, energy gradient, full reverse pass (k_adj_acc_f32x2,
@@ -18,7 +25,7 @@ import sys
 import numpy as np
 
 
-def fused_steps(n, l, h, steps):
+def fused_steps(n, l, h, steps, blocking=False):
     import torch
 
     from . import api
@@ -27,6 +34,7 @@ def fused_steps(n, l, h, steps):
     c = I.config_family(n, 1.0, 1.0, 0, "uniform")
     x = torch.full((1 << n,), 2 ** (-n / 2), dtype=torch.complex64, device="cuda")
     api.set_fused_split(n, l, h)
+    api.set_fused_blocking(blocking)
     rng = np.random.default_rng(0)
     coef = (rng.standard_normal(steps + 1) + 1j * rng.standard_normal(steps + 1)) / (4 * steps)
     api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef, x, path="fused")
@@ -34,6 +42,45 @@ def fused_steps(n, l, h, steps):
     nrm = float(torch.linalg.vector_norm(x))
     assert np.isfinite(nrm)
     print("ok", nrm)
+
+
+def compare(n, steps):
+    import torch
+
+    from . import api
+    from . import inputs as I
+
+    c = I.config_family(n, 1.0, 1.0, 0, "uniform")
+    x = torch.full((1 << n,), 2 ** (-n / 2), dtype=torch.complex64, device="cuda")
+    rng = np.random.default_rng(0)
+    coef = (rng.standard_normal(steps + 1) + 1j * rng.standard_normal(steps + 1)) / (4 * steps)
+    print("n", n, "split", api.get_fused_split(n), "steps", steps)
+    try:
+        for _ in range(2):
+            for blocking in (False, True):
+                api.set_fused_blocking(blocking)
+                api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef[:4], x, path="fused")  # warm-up
+                torch.cuda.synchronize()
+                api.profile_reset()
+                api.profile_enable(True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef, x, path="fused")
+                e1.record()
+                torch.cuda.synchronize()
+                api.profile_enable(False)
+                ms = e0.elapsed_time(e1)
+                assert np.isfinite(float(torch.linalg.vector_norm(x)))
+                parts = []
+                for kind in ("low", "high", "tail"):
+                    cnt, tot = api.profile_read(kind)
+                    if cnt:
+                        parts.append(f"{kind} {cnt} x {tot / cnt * 1e3:.1f} us")
+                print(f"  blocked tail {'on ' if blocking else 'off'}: {ms / steps:.3f} ms/step, "
+                      f"{(1 << n) * steps / ms * 1e3:.3e} amplitude-updates/s; " + ", ".join(parts))
+    finally:
+        api.set_fused_blocking(False)
 
 
 def adjoint(n, S):
@@ -81,6 +128,11 @@ def main(argv):
         adjoint(int(argv[1]), int(argv[2]))
     elif argv[0] == "cluster":
         cluster(int(argv[1]), int(argv[2]))
+    elif argv[0] == "compare":
+        compare(int(argv[1]), int(argv[2]) if len(argv) > 2 else 40)
+    elif argv[0] == "tail":
+        n, l, h = int(argv[1]), int(argv[2]), int(argv[3])
+        fused_steps(n, l, h, int(argv[4]) if len(argv) > 4 else 6, blocking=True)
     else:
         n, l, h = int(argv[0]), int(argv[1]), int(argv[2])
         fused_steps(n, l, h, int(argv[3]) if len(argv) > 3 else 6)
