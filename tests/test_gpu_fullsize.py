@@ -1,5 +1,6 @@
 """The full n = 30 size in the launch configuration the benchmark times (complex64,
-fused split (1, 18): the low pass plus two strided passes of 9 bits).
+fused split (2, 17): the low pass with two L2 partner bits, a strided pass of 9 bits and
+one of 8 bits in 256-byte rows).
 
 The oracle cannot hold or evolve 2^30 amplitudes in test time, so the checks are
 closed forms evaluated on sampled amplitudes and properties that hold at any size:
@@ -31,7 +32,7 @@ def _samples(seed, count=1 << 20):
 def test_n30_fused_split_is_the_benchmarked_one(cuda_lib):
     from paper_2608_12058_b300 import api
 
-    assert api.get_fused_split(N30) == (1, 18)
+    assert api.get_fused_split(N30) == (2, 17)
 
 
 def test_n30_transverse_field_closed_form(cuda_lib):

@@ -104,6 +104,24 @@ def test_two_strided_passes_match_oracle(cuda_lib, oracle):
     assert _rel(y, ref) <= TOL["fp32"]
 
 
+@pytest.mark.parametrize("n,l,h", [(24, 0, 13), (26, 0, 15)])
+def test_wide_row_passes_match_oracle(cuda_lib, oracle, n, l, h):
+    """Splits whose top strided pass (6 or 7 bits starting at bit 18 or 19) runs on rows
+    of 32 amplitudes (256 B), against the oracle (FP32)."""
+    from paper_2608_12058_b300 import api
+
+    hq, Jq = I.sk_instance(n, 400 + n)
+    psi = I.random_state(n, 401 + n)
+    ref, oinfo = oracle.expmv(hq, Jq, 0.9, 0.15, psi, 2.0 ** -23)
+    api.set_fused_split(n, l, h)
+    try:
+        y, info = _run(hq, Jq, 0.9, 0.15, psi, "fp32", 2.0 ** -23, path="fused")
+    finally:
+        api.set_fused_split(n, -1)
+    assert info["K"] == oinfo["K"] and info["K"] > 3
+    assert _rel(y, ref) <= TOL["fp32"]
+
+
 @pytest.mark.parametrize("prec,n", [("fp32", 14), ("fp32", 15), ("fp32", 17), ("fp64", 13), ("fp64", 16)])
 def test_cluster_path_matches_oracle(cuda_lib, oracle, prec, n):
     """The whole run on one thread-block cluster (vectors in distributed shared memory,
