@@ -357,6 +357,40 @@ def test_dense_gradients_vs_finite_differences(oracle):
     assert abs(fd - np.real(np.vdot(g["psi0"], d))) < 1e-7
 
 
+def test_dense_gradients_small_t_series(oracle):
+    """Gradient pins independent of finite differences. L(t) = <psi| e^{iHt} H_P e^{-iHt} |psi>
+    with H = H_P + gamma H_G expands as <H_P> + i t gamma <C> + O(t^2), C = [H_G, H_P].
+    So dL/dgamma = i t <C> - (t^2 / 2)(<[H_P, C]> + 2 gamma <[H_G, C]>) + O(t^3).
+    At t = 0 the gradients in h and J are the spin moments <s_i>, <s_i s_j> under |psi|^2."""
+    n = 4
+    h, J = I.sk_instance(n, 61)
+    psi = I.random_state(n, 62)
+    gam = 0.9
+    HP = np.diag(oracle.energies(h, J)).astype(np.complex128)
+    HG = oracle.dense_hamiltonian(np.zeros(n), np.zeros((n, n)), 1.0)
+    C = HG @ HP - HP @ HG
+
+    def ev(A):
+        return np.vdot(psi, A @ psi)
+
+    c1 = 1j * ev(C)
+    c2 = -0.5 * (ev(HP @ C - C @ HP) + 2.0 * gam * ev(HG @ C - C @ HG))
+    assert abs(c1.imag) < 1e-12 and abs(c2.imag) < 1e-12
+    for t in (1e-2, 3e-3, 1e-3):
+        g = oracle.dense_energy_gradients(h, J, gam, t, psi)
+        series = c1.real * t + c2.real * t * t
+        assert abs(g["gamma"] - series) < 50.0 * t ** 3, (t, g["gamma"], series)
+    g0 = oracle.dense_energy_gradients(h, J, gam, 0.0, psi)
+    z = np.arange(1 << n)
+    s = 1.0 - 2.0 * ((z[:, None] >> np.arange(n)[None, :]) & 1)
+    w = np.abs(psi) ** 2
+    assert np.allclose(g0["h"], s.T @ w, atol=1e-12)
+    for i in range(n):
+        for j in range(i + 1, n):
+            assert abs(g0["J"][i, j] - np.sum(w * s[:, i] * s[:, j])) < 1e-12
+    assert abs(g0["gamma"]) < 1e-12
+
+
 def test_anneal_matches_dense_product(oracle):
     """A piecewise-constant schedule is the ordered product of the segments' dense
     exponentials (eigh of each explicit H_s)."""
