@@ -123,6 +123,46 @@ def test_fused_split_table():
     assert api.get_fused_split(20) == (0, 9)
 
 
+def _passes(lo, h):
+    """Near-equal strided passes of at most 9 bits above bit lo (largest first)."""
+    if h == 0:
+        return []
+    np_ = -(-h // 9)
+    out = []
+    for k in range(np_):
+        hb = h // np_ + (1 if k < h % np_ else 0)
+        out.append((lo, hb))
+        lo += hb
+    return out
+
+
+def test_default_split_gives_the_top_range_wide_rows():
+    """Past n = 28 the default split moves one bit to the L2 partner tiles when the top
+    strided pass would otherwise be 9 bits at bit 18 or above. An 8-bit top pass there
+    runs on 256-byte rows (n = 30: 9 + 8 bits, the benchmarked split)."""
+    assert api.get_fused_split(30) == (2, 17)
+    expect = {25: (0, 14), 26: (0, 15), 27: (0, 16), 28: (0, 17), 29: (1, 17), 30: (2, 17),
+              31: (3, 17), 32: (4, 17), 33: (4, 18)}
+    for n, lh in expect.items():
+        assert api.get_fused_split(n) == lh, n
+    for n in range(25, 33):
+        l, h = api.get_fused_split(n)
+        lo, hb = _passes(11 + l, h)[-1]
+        assert lo + hb == n and not (hb == 9 and lo >= 18), (n, lo, hb)
+
+
+def test_fused_blocking_switch():
+    """The L2-blocked tail is off by default, takes 0 or 1, and reports its setting."""
+    assert api.get_fused_blocking() is False
+    assert _lib.lib().cheb_set_fused_blocking(2) == 1  # CHEB_ERR_INVALID_ARG
+    api.set_fused_blocking(True)
+    try:
+        assert api.get_fused_blocking() is True
+    finally:
+        api.set_fused_blocking(False)
+    assert api.get_fused_blocking() is False
+
+
 def test_expmv_rejects_bad_arguments_before_touching_the_device():
     L = _lib.lib()
     n = 4
