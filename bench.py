@@ -7,8 +7,14 @@ device, host coefficients, K Clenshaw steps (fused FP32 kernels), FP64 norm and
 energy. Steps are applied back to back to the evolving state (the state, 8 GB,
 and the 16 GB of Clenshaw vectors are far larger than L2, so no flush is needed).
 Prints one JSON line on rank 0. For N > 1 (torchrun) every rank runs its own
-replica of the workload (the path does not shard: see the design doc) and the value is
-the sum of the ranks' work divided by the slowest rank's time.
+replica of the workload (one instance does not shard without a full-vector exchange
+per step) and the value is the sum of the ranks' work divided by the slowest rank's
+time.
+
+Roofline: one Clenshaw step must read b_{k+1}, b_{k+2} and psi and write b_k, 32 bytes
+per amplitude in FP32; `roofline.frac` is those bytes over the measured step time
+against the measured HBM copy bandwidth. The per-kernel entries give each pass's
+DRAM efficiency against the bytes that pass itself moves.
 """
 from __future__ import annotations
 
@@ -113,25 +119,47 @@ def aggregate(t_local: float, work_local: float, pg, device):
     return t.item(), w.item()
 
 
-def cpu_sample_run():
+def cpu_sample_run(n=None):
     """The oracle, as it stands, on the bounded sample; returns (amp-updates/s, seconds, info)."""
     from oracle import oracle as O
     from paper_2608_12058_b300 import inputs as I
 
-    c = I.config_family(SAMPLE["n"], SAMPLE["gamma"], SAMPLE["t"], SAMPLE["seed"], "uniform")
-    psi = I.uniform_state(SAMPLE["n"])
+    n = SAMPLE["n"] if n is None else n
+    c = I.config_family(n, SAMPLE["gamma"], SAMPLE["t"], SAMPLE["seed"], "uniform")
+    psi = I.uniform_state(n)
     t0 = time.perf_counter()
     _, info = O.expmv(c.h, c.J, c.gamma, c.t, psi, TOL32)
     dt = time.perf_counter() - t0
-    work = (1 << SAMPLE["n"]) * info["K"]
+    work = (1 << n) * info["K"]
     return work / dt, dt, info
 
 
-def cpu_baseline_dict(value, dt, info):
-    return {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"full oracle exp(-itH)psi on the n={SAMPLE['n']} member of the n=30 SK family "
-                       f"(h~U(-1,1), gamma={SAMPLE['gamma']}, t={SAMPLE['t']}, tol 2^-23, K={info['K']}), "
-                       f"FP64 C++ with OpenMP over elements, {dt:.1f} s")}
+# single-thread sample: a smaller member of the same family (the n=20 run takes minutes
+# on one core)
+SAMPLE_1T = 16
+
+
+def cpu_single_thread():
+    """The oracle on one core (OMP_NUM_THREADS=1 in a child process) on the n=16 member."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(SAMPLE_1T)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    v, dt, K = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": v, "unit": UNIT, "cores": 1, "seconds": dt,
+            "sample": (f"full oracle exp(-itH)psi on the n={SAMPLE_1T} member of the n=30 SK family "
+                       f"(h~U(-1,1), gamma={SAMPLE['gamma']}, t={SAMPLE['t']}, tol 2^-23, K={K}), one thread")}
+
+
+def cpu_baseline_dict(value, dt, info, single=None):
+    d = {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+         "sample": (f"full oracle exp(-itH)psi on the n={SAMPLE['n']} member of the n=30 SK family "
+                    f"(h~U(-1,1), gamma={SAMPLE['gamma']}, t={SAMPLE['t']}, tol 2^-23, K={info['K']}), "
+                    f"FP64 C++ with OpenMP over elements on all {os.cpu_count()} host threads, {dt:.1f} s")}
+    if single is not None:
+        d["single_thread"] = single
+    return d
 
 
 def run_reference(args, world, rank):
@@ -237,6 +265,46 @@ def other_workloads(dev):
     del x, x0, bnd
     api.release_workspaces()
     torch.cuda.empty_cache()
+
+    # gradients at the full n=30 size: one segment of the n=30 workload at t = 1, the
+    # forward keeps its start state, the adjoint regenerates the Clenshaw vectors in a
+    # ring of 6 from one anchor pair (workspace of 8 state vectors)
+    c = I.config_n30()
+    N30 = 1 << c.n
+    store = 8
+    g_ = np.array([c.gamma])
+    t_ = np.array([1.0])
+    bnd = torch.empty((1, N30), dtype=torch.complex64, device=dev)
+    res = {}
+    for rep in range(2):
+        x = torch.full((N30,), 2 ** (-c.n / 2), dtype=torch.complex64, device=dev)
+        torch.cuda.synchronize()
+        e0.record()
+        inf = api.anneal(c.h, c.J, g_, t_, x, boundaries=bnd, info=(rep == 0))
+        e1.record()
+        torch.cuda.synchronize()
+        if inf is not None:
+            res["K"] = int(inf[0]["K"])
+        res["forward_ms"] = e0.elapsed_time(e1)
+        api.release_workspaces()
+        _, g, _, _ = api.energy_grad(c.h, c.J, x)
+        torch.cuda.empty_cache()
+        torch.cuda.synchronize()
+        e0.record()
+        api.anneal_adjoint(c.h, c.J, g_, t_, bnd, x, g, store_vectors=store)
+        e1.record()
+        torch.cuda.synchronize()
+        res["backward_ms"] = e0.elapsed_time(e1)
+        del x, g
+        torch.cuda.empty_cache()
+    res["backward_over_forward"] = res["backward_ms"] / res["forward_ms"]
+    res["adjoint_workspace_GiB"] = api.adjoint_workspace_bytes(c.n, "fp32", store) / 2 ** 30
+    res["workload"] = (f"SK n=30 (h~U(-1,1), gamma={c.gamma}), one segment t=1, complex64; backward = all "
+                       f"gradients with {store} state vectors of workspace")
+    out["adjoint_n30"] = res
+    del bnd
+    api.release_workspaces()
+    torch.cuda.empty_cache()
     return out
 
 
@@ -265,7 +333,8 @@ def run_ours(args, world, rank, local):
     cfg = I.config_n30()
     n = cfg.n
     N = 1 << n
-    # accuracy at the n=24 configuration: FP32 fused vs FP64 recurrence (same tol rule)
+    # accuracy at the n=24 configuration: FP32 fused vs FP64 recurrence (same tol rule);
+    # the FP64 GPU result is itself checked against the oracle at this size in the tests
     acc = {}
     if rank == 0 and not args.skip_accuracy:
         c24 = I.config_n24()
@@ -274,8 +343,8 @@ def run_ours(args, world, rank, local):
         i32 = api.expmv(c24.h, c24.J, c24.gamma, c24.t, x32, tol=TOL32)
         i64 = api.expmv(c24.h, c24.J, c24.gamma, c24.t, x64, tol=1e-12)
         d = torch.linalg.vector_norm(x32.to(torch.complex128) - x64).item() / torch.linalg.vector_norm(x64).item()
-        acc = {"workload": c24.name, "fp32_vs_fp64_rel_l2": d, "K_fp32": i32["K"], "K_fp64": i64["K"],
-               "bar": 1e-5}
+        acc["n24"] = {"workload": c24.name, "fp32_vs_fp64_rel_l2": d, "K_fp32": i32["K"], "K_fp64": i64["K"],
+                      "bar": 1e-5, "fp64_vs_oracle": "within 1e-12 (tests/test_gpu_accuracy.py, same workload)"}
         del x32, x64
         api.release_workspaces()
         torch.cuda.empty_cache()
@@ -325,15 +394,17 @@ def run_ours(args, world, rank, local):
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
+        e2e_steps = min(args.steps, 3)
         f0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             psi.copy_(host, non_blocking=True)
             api.expmv(cfg.h, cfg.J, cfg.gamma, cfg.t, psi, tol=TOL32, info=False)
             host.copy_(psi, non_blocking=True)
         f1.record(stream)
         barrier()
         te, _ = aggregate(f0.elapsed_time(f1) / 1e3, 0.0, pg, dev)
-        e2e = {"value": work_all / te, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
+        e2e = {"value": work_all / args.steps * e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": N * 8,
+               "d2h_bytes_per_step": N * 8, "steps": e2e_steps}
         del host
 
     # the plain one-pass FP32 and FP64 kernels on a short run of the same operator
@@ -362,6 +433,35 @@ def run_ours(args, world, rank, local):
         torch.cuda.empty_cache()
         extra["fused_over_fp64_plain"] = value / world / extra["fp64_plain"]["amp_updates_per_s"]
 
+    # accuracy of the benchmarked result: one FP32 expmv of the n=30 workload from the
+    # uniform state against the FP64 recurrence of the same problem (tol 1e-12)
+    if rank == 0 and not args.skip_accuracy:
+        del psi
+        api.release_workspaces()
+        torch.cuda.empty_cache()
+        x32 = torch.full((N,), 2 ** (-n / 2), dtype=torch.complex64, device=dev)
+        i32 = api.expmv(cfg.h, cfg.J, cfg.gamma, cfg.t, x32, tol=TOL32)
+        api.release_workspaces()
+        x64 = torch.full((N,), 2 ** (-n / 2), dtype=torch.complex128, device=dev)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        i64 = api.expmv(cfg.h, cfg.J, cfg.gamma, cfg.t, x64, tol=1e-12, path=args.fp64_path)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        api.release_workspaces()
+        torch.cuda.empty_cache()
+        ms64 = g0.elapsed_time(g1)
+        diff = x64.clone()
+        diff -= x32.to(torch.complex128)
+        d = torch.linalg.vector_norm(diff).item() / torch.linalg.vector_norm(x64).item()
+        del diff, x32, x64
+        torch.cuda.empty_cache()
+        acc["n30"] = {"workload": cfg.name, "fp32_vs_fp64_rel_l2": d, "K_fp32": i32["K"], "K_fp64": i64["K"],
+                      "bar": 1e-5, "fp64_path": args.fp64_path, "fp64_ms": ms64,
+                      "fp64_amp_updates_per_s": N * i64["K"] / (ms64 / 1e3),
+                      "fp64_vs_oracle": "the FP64 path is checked against the oracle at n=24 (K=498) in the tests"}
+
     # the other workloads of the path, measured once each (not part of `value`)
     others = {} if (rank != 0 or args.skip_workloads) else other_workloads(dev)
 
@@ -386,17 +486,32 @@ def run_ours(args, world, rank, local):
                 "algorithmic_bytes_per_amplitude": bytes_per_amp, "launches_timed": count,
                 "avg_launch_ms": avg_s * 1e3, "share": total_ms / ms}
 
-    # low pass: read b1, psi, slot, write out; strided pass: read b1, slot, write slot
+    # per pass: low pass reads b1, psi, slot and writes out (32 B/amp); a strided pass
+    # reads b1, slot and writes slot (24 B/amp)
     r_low = kernel_roof("k_low", nlow, low_ms, 32.0)
     r_str = kernel_roof("k_strided", nhigh, high_ms, 24.0)
-    cands = [r for r in (r_low, r_str) if r is not None]
-    roof = dict(max(cands, key=lambda r: r["share"]))
-    roof["other_kernels"] = [r for r in cands if r["kernel"] != roof["kernel"]]
-    # whole Clenshaw step: 32 B/amp in k_low plus 24 B/amp per strided pass
-    step_bytes = 32.0 + 24.0 * (nhigh / max(nlow, 1))
-    roof["step_alg_bytes_per_amplitude"] = step_bytes
-    roof["step_alg_GBps"] = step_bytes * N * K * args.steps / t_local / 1e9
+    kernels = [r for r in (r_low, r_str) if r is not None]
+    # the method's roofline: one Clenshaw step (its launches, timed on their stream)
+    # needs 32 B per amplitude (read b_{k+1}, b_{k+2}, psi; write b_k)
+    steps_timed = max(nlow, 1)
+    step_ms = (low_ms + high_ms) / steps_timed
+    alg = 32.0 * N
+    achieved = alg / (step_ms / 1e3) / 1e9
+    pass_bytes = 32.0 + 24.0 * (nhigh / steps_timed)
+    tr = None
+    if traffic and "k_low" in traffic and "k_strided" in traffic:
+        tr = (traffic["k_low"] + traffic["k_strided"] * (nhigh / steps_timed)) * N
+    roof = {"bound": "hbm", "kernel": "one fused Clenshaw step (k_low + strided passes)", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": tr,
+            "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": alg,
+            "algorithmic_bytes_per_amplitude": 32.0, "step_ms": step_ms, "steps_timed": steps_timed,
+            "pass_bytes_per_amplitude": pass_bytes,
+            "pass_bytes_GBps": pass_bytes * N / (step_ms / 1e3) / 1e9,
+            "kernels": kernels,
+            "note": ("frac counts the 32 B/amp a Clenshaw step must move; the step's passes move "
+                     f"{pass_bytes:.0f} B/amp, and each kernel entry gives that pass's DRAM efficiency")}
     cpu_v, cpu_dt, cpu_info = cpu_sample_run()
+    single = None if args.skip_cpu_single else cpu_single_thread()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -407,7 +522,7 @@ def run_ours(args, world, rank, local):
                    "fused_split": list(api.get_fused_split(n)), "l2": "inputs larger than L2 (24 GB working set)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
-        "cpu_baseline": cpu_baseline_dict(cpu_v, cpu_dt, cpu_info),
+        "cpu_baseline": cpu_baseline_dict(cpu_v, cpu_dt, cpu_info, single),
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -431,7 +546,14 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-workloads", action="store_true")
+    ap.add_argument("--skip-cpu-single", action="store_true")
+    ap.add_argument("--fp64-path", default="auto", choices=["auto", "plain", "fused"])
+    ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_sample:
+        v, dt, info = cpu_sample_run(args.cpu_sample)
+        print(json.dumps([v, dt, info["K"]]))
+        return
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -76,7 +76,20 @@ typedef struct {
     double trunc_bound;  /* truncation bound (Eq. TruncError) or CF estimate, summed over slices */
     double norm;         /* ||y||_2, FP64 reduction on the device */
     double energy;       /* <y|H_P|y>, FP64 reduction on the device */
+    double eval_bound;   /* a-posteriori evaluation-error bound of Sec. II.B.3 (absolute, 2-norm,
+                            summed over slices) when CHEB_FLAG_EVAL_BOUND was given, else -1 */
 } cheb_info_t;
+
+/* Flag OR-ed into the `path` argument of cheb_expmv_path: also compute the evaluation-
+ * error bound of Sec. II.B.3 (analysis of evaluation error),
+ *   sum_{k=0}^{K} u ||b_k|| + u ||c_k psi - b_{k+2}|| + sqrt(d) gamma_d ||b_{k+1}||,
+ * with b_0 = y, d = n + 1 nonzeros per column of H, gamma_d = d u / (1 - d u) and u the
+ * unit roundoff of the arithmetic (2^-24 for CHEB_FP32, 2^-53 for CHEB_FP64), from
+ * FP64 norms of every Clenshaw vector reduced on the device after each step. It needs
+ * every b_k in memory, so the run uses the step-by-step kernels (PLAIN up to n = 19,
+ * FUSED above; CLUSTER is UNSUPPORTED), costs one extra read of b_k and psi per step
+ * and synchronises once per time slice. Requires info (INVALID_ARG otherwise). */
+#define CHEB_FLAG_EVAL_BOUND 0x100
 
 /* Human-readable name of a status code (static string). */
 const char* cheb_status_string(cheb_status_t status);
@@ -150,6 +163,10 @@ cheb_status_t cheb_expmv(int n, const double* h, const double* J, double gamma, 
  *     routine. psi (device, in/out), h, J and info are as for cheb_expmv.
  *   - The first call on each device looks up the array's device address (with that
  *     device current) and caches it; make that first call before any stream capture.
+ *     The cache is keyed on the device's context, so after a context reset
+ *     (cudaDeviceReset) the next call looks the address up again.
+ *   - A device-side condition (a bounded wait that ran out) is only reported through
+ *     info: pass info to learn it.
  *   - All calls share the one array. Calls that overlap on the GPU (other streams,
  *     other host threads on the same device) race on it and must be serialised by
  *     the caller.
@@ -206,14 +223,69 @@ cheb_status_t cheb_anneal_general(int n, const double* h, const double* J, int S
  *   nodes:  HOST array of 4*steps doubles: A(t1), B(t1), A(t2), B(t2) per step.
  *   tol:    truncation budget of all 2*steps exponentials together (the integrator's
  *           own O(dt^5) local error is the caller's choice of steps).
+ *   boundaries: nullable DEVICE buffer of 2*steps states; receives the state before
+ *           each exponential (for cheb_magnus4_adjoint).
  *   infos:  nullable HOST array of 2*steps cheb_info_t (one per exponential).
  * Workspace: cheb_workspace_bytes(n, precision). Errors: INVALID_ARG (steps < 1,
  * null or non-finite dt/nodes), otherwise as cheb_anneal.
  */
 cheb_status_t cheb_magnus4(int n, const double* h, const double* J, int steps, const double* dt,
                            const double* nodes, void* psi, cheb_precision_t precision, double tol,
-                           cheb_method_t method, void* workspace, size_t workspace_bytes, void* stream,
-                           cheb_info_t* infos);
+                           cheb_method_t method, void* boundaries, void* workspace, size_t workspace_bytes,
+                           void* stream, cheb_info_t* infos);
+
+/* A schedule for the Magnus entry points: writes A(t) and B(t) of
+ * H(t) = A(t) sum_j X_j + B(t) H_P; returns 0 on success (anything else aborts the
+ * call with CHEB_ERR_INVALID_ARG). Called on the calling host thread. */
+typedef int (*cheb_schedule_fn)(double t, double* A, double* B, void* user);
+
+/*
+ * Samples a schedule for cheb_magnus4 on `steps` equal steps of [0, T]: dt[m] = T/steps
+ * and nodes[4m..4m+3] = A(t1), B(t1), A(t2), B(t2) at the Gauss-Legendre points
+ * t1,2 = m dt + (1/2 -+ sqrt(3)/6) dt.
+ *   dt, nodes: HOST outputs of steps and 4*steps doubles.
+ * Errors: INVALID_ARG (steps < 1, null pointers, non-finite T or schedule values).
+ */
+cheb_status_t cheb_magnus4_nodes(double T, int steps, cheb_schedule_fn schedule, void* user, double* dt,
+                                 double* nodes);
+
+/*
+ * Reverse-mode gradients of cheb_magnus4 (no counterpart in the paper): the adjoint of
+ * its 2*steps exponentials (cheb_anneal_general_adjoint) chained through the
+ * Gauss-node combinations, so that gradients reach every step length and node value:
+ *   dL/d dt_m = dL/dt_{2m} + dL/dt_{2m+1},
+ *   dL/dA(t1) = w2 dL/da_{2m} + w1 dL/da_{2m+1},  dL/dA(t2) = w1 dL/da_{2m} + w2 dL/da_{2m+1}
+ * (and the same for B with b_s).
+ *   boundaries: DEVICE, the 2*steps states written by cheb_magnus4.
+ *   grad: DEVICE in/out (in: dL/dpsi_T; out: dL/dpsi_0). grad_dt (steps), grad_nodes
+ *   (4*steps), grad_h (n), grad_J (n*n): HOST, nullable.
+ * Workspace and errors: as cheb_anneal_general_adjoint (cheb_adjoint_workspace_bytes).
+ */
+cheb_status_t cheb_magnus4_adjoint(int n, const double* h, const double* J, int steps, const double* dt,
+                                   const double* nodes, const void* boundaries, const void* psi_T, void* grad,
+                                   cheb_precision_t precision, double tol, cheb_method_t method, double* grad_dt,
+                                   double* grad_nodes, double* grad_h, double* grad_J, void* workspace,
+                                   size_t workspace_bytes, void* stream);
+
+/*
+ * psi <- psi(T) under H(t) = A(t) sum_j X_j + B(t) H_P with the number of equal Magnus
+ * steps chosen a posteriori (the paper selects steps from an O(1) error term whose
+ * constants it does not print; this is the step-doubling estimate instead): runs of
+ * steps0 and 2*steps0 steps estimate the integration error of the second as
+ * ||y_M - y_2M|| / 15 (fourth order), and if that exceeds tol a last run uses
+ * ceil(2 steps0 (estimate / tol)^(1/4) * 1.1) steps. Each exponential's series uses the
+ * precision's default budget (2^-23 for FP32, 1e-12 for FP64).
+ *   schedule, user: the schedule, sampled through cheb_magnus4_nodes.
+ *   steps_used: HOST out, the step count of the returned state. err_estimate: HOST out
+ *   (nullable), the estimate scaled to that step count.
+ * Workspace: cheb_magnus4_adaptive_workspace_bytes(n, precision) (the expmv workspace
+ * plus two state vectors). Synchronises the stream once. Errors: as cheb_magnus4.
+ */
+size_t cheb_magnus4_adaptive_workspace_bytes(int n, cheb_precision_t precision);
+cheb_status_t cheb_magnus4_adaptive(int n, const double* h, const double* J, double T, cheb_schedule_fn schedule,
+                                    void* user, int steps0, double tol, void* psi, cheb_precision_t precision,
+                                    cheb_method_t method, void* workspace, size_t workspace_bytes, void* stream,
+                                    int* steps_used, double* err_estimate);
 
 /*
  * Batched independent instances (Sec. III.A batches many small problems per launch):
@@ -302,8 +374,9 @@ cheb_status_t cheb_energy_grad(int n, const double* h, const double* J, const vo
                                double* grad_h, double* grad_J, void* workspace,
                                size_t workspace_bytes, void* stream);
 
-/* Same as cheb_expmv with an explicit kernel path (cheb_path_t); used to time the
- * plain one-pass GPU path against the fused path. */
+/* Same as cheb_expmv with an explicit kernel path (cheb_path_t), optionally OR-ed
+ * with CHEB_FLAG_EVAL_BOUND; used to time the plain one-pass GPU path against the
+ * fused path and to request the evaluation bound. */
 cheb_status_t cheb_expmv_path(int n, const double* h, const double* J, double gamma, double t,
                               void* psi, cheb_precision_t precision, double tol,
                               cheb_method_t method, int time_splits, int path, void* workspace,
@@ -337,6 +410,16 @@ cheb_status_t cheb_get_fused_split(int n, int* l, int* h);
  */
 cheb_status_t cheb_set_fused_blocking(int on);
 int cheb_get_fused_blocking(void);
+
+/*
+ * Compensated flip sums in the fused FP32 step (the bit-flip sum of the matrix-free
+ * matvec, Sec. II.D, whose rounding is the sqrt(d) gamma_d term of the evaluation
+ * bound, Sec. II.B.3). When on, each pass adds its flip terms with Kahan's
+ * compensated summation instead of plain FP32 adds; the partial sums of different
+ * passes are still combined in FP32. on: 0 off (default), 1 on (process-wide).
+ */
+cheb_status_t cheb_set_fused_compensated(int on);
+int cheb_get_fused_compensated(void);
 
 /*
  * General polynomial p(Ht) psi (Algorithm 2 with caller-supplied coefficients):
@@ -401,6 +484,19 @@ typedef enum {
  *   workspace: DEVICE, at least 4 bytes (one int), 4-byte aligned. Synchronises.
  */
 cheb_status_t cheb_wait_selftest(void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Device-side status of a workspace (no counterpart in the paper). A call made
+ * without an info struct does not synchronise, so a bounded wait that ran out during
+ * it is not in its return value; the condition stays recorded in the workspace's
+ * status word until the next call on that workspace starts. This entry point
+ * synchronises the stream, returns CHEB_ERR_TIMEOUT (a wait ran out), CHEB_ERR_CUDA (a
+ * launch was refused inside a kernel) or CHEB_OK, and clears the word. Valid for the
+ * workspaces of cheb_expmv, cheb_expmv_path, cheb_poly_apply, cheb_anneal,
+ * cheb_anneal_general, cheb_magnus4 and the adjoint entry points.
+ *   workspace: DEVICE, the workspace of the call to query (256-byte aligned).
+ */
+cheb_status_t cheb_workspace_status(void* workspace, size_t workspace_bytes, void* stream);
 
 long long cheb_launch_count(void);
 cheb_status_t cheb_profile_enable(int on);

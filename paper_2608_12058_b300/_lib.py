@@ -32,6 +32,7 @@ class Info(ctypes.Structure):
         ("trunc_bound", c_double),
         ("norm", c_double),
         ("energy", c_double),
+        ("eval_bound", c_double),
     ]
 
     def as_dict(self):
@@ -57,14 +58,22 @@ SIGNATURES = {
     "cheb_get_fused_split": (c_int, [c_int, _ip, _ip]),
     "cheb_set_fused_blocking": (c_int, [c_int]),
     "cheb_get_fused_blocking": (c_int, []),
+    "cheb_set_fused_compensated": (c_int, [c_int]),
+    "cheb_get_fused_compensated": (c_int, []),
     "cheb_expmv_noalloc": (c_int, [c_int, _dp, _dp, c_double, c_double, c_void_p, c_int, c_double, c_int, c_int,
                                    c_void_p, ctypes.POINTER(Info)]),
     "cheb_anneal": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, c_void_p, c_int, c_double, c_int, c_void_p,
                             c_void_p, c_size_t, c_void_p, ctypes.POINTER(Info)]),
     "cheb_anneal_general": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, _dp, c_void_p, c_int, c_double, c_int,
                                     c_void_p, c_void_p, c_size_t, c_void_p, ctypes.POINTER(Info)]),
-    "cheb_magnus4": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, c_void_p, c_int, c_double, c_int, c_void_p, c_size_t,
-                             c_void_p, ctypes.POINTER(Info)]),
+    "cheb_magnus4": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, c_void_p, c_int, c_double, c_int, c_void_p, c_void_p,
+                             c_size_t, c_void_p, ctypes.POINTER(Info)]),
+    "cheb_magnus4_nodes": (c_int, [c_double, c_int, ctypes.c_void_p, c_void_p, _dp, _dp]),
+    "cheb_magnus4_adjoint": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, c_void_p, c_void_p, c_void_p, c_int, c_double,
+                                     c_int, _dp, _dp, _dp, _dp, c_void_p, c_size_t, c_void_p]),
+    "cheb_magnus4_adaptive_workspace_bytes": (c_size_t, [c_int, c_int]),
+    "cheb_magnus4_adaptive": (c_int, [c_int, _dp, _dp, c_double, ctypes.c_void_p, c_void_p, c_int, c_double, c_void_p,
+                                      c_int, c_int, c_void_p, c_size_t, c_void_p, _ip, _dp]),
     "cheb_batched_workspace_bytes": (c_size_t, [c_int, _ip, c_int]),
     "cheb_expmv_batched": (c_int, [c_int, _ip, ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp, _dp, c_void_p, c_int,
                                    c_double, c_int, c_void_p, c_size_t, c_void_p, ctypes.POINTER(Info)]),
@@ -76,6 +85,7 @@ SIGNATURES = {
     "cheb_energy_grad": (c_int, [c_int, _dp, _dp, c_void_p, c_void_p, c_int, _dp, _dp, _dp, c_void_p, c_size_t,
                                  c_void_p]),
     "cheb_wait_selftest": (c_int, [c_void_p, c_size_t, c_void_p]),
+    "cheb_workspace_status": (c_int, [c_void_p, c_size_t, c_void_p]),
     "cheb_launch_count": (ctypes.c_longlong, []),
     "cheb_profile_enable": (c_int, [c_int]),
     "cheb_profile_reset": (c_int, []),
@@ -84,6 +94,25 @@ SIGNATURES = {
 
 STATUS = {0: "CHEB_OK", 1: "CHEB_ERR_INVALID_ARG", 2: "CHEB_ERR_WORKSPACE", 3: "CHEB_ERR_CUDA",
           4: "CHEB_ERR_TIMEOUT", 5: "CHEB_ERR_NONFINITE", 6: "CHEB_ERR_UNSUPPORTED"}
+
+
+# cheb_schedule_fn: int (*)(double t, double* A, double* B, void* user)
+ScheduleFn = ctypes.CFUNCTYPE(c_int, c_double, _dp, _dp, c_void_p)
+
+
+def schedule_callback(A, B):
+    """Wrap two Python callables A(t), B(t) as a cheb_schedule_fn (keep the returned
+    object alive for the duration of the call)."""
+
+    def fn(t, pa, pb, user):
+        try:
+            pa[0] = float(A(t))
+            pb[0] = float(B(t))
+            return 0
+        except Exception:  # any failure aborts the library call with INVALID_ARG
+            return 1
+
+    return ScheduleFn(fn)
 
 
 class ChebError(RuntimeError):

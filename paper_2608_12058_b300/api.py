@@ -108,9 +108,13 @@ def ising_bounds(h, J, device=None):
     return lo.value, hi.value
 
 
+EVAL_BOUND_FLAG = 0x100  # CHEB_FLAG_EVAL_BOUND
+
+
 def expmv(h, J, gamma: float, t: float, psi, tol: Optional[float] = None, method: str = "chebyshev",
-          time_splits: int = 0, path: str = "auto", info: bool = True):
-    """psi <- exp(-i t H) psi in place on the GPU; returns the info dict (or None)."""
+          time_splits: int = 0, path: str = "auto", info: bool = True, eval_bound: bool = False):
+    """psi <- exp(-i t H) psi in place on the GPU; returns the info dict (or None).
+    eval_bound=True also fills info["eval_bound"] (CHEB_FLAG_EVAL_BOUND)."""
     h, J = _f64(h), _f64(J)
     n = h.shape[0]
     _check_state(psi, n)
@@ -121,11 +125,12 @@ def expmv(h, J, gamma: float, t: float, psi, tol: Optional[float] = None, method
     p, nb = _ws_ptr(ws)
     inf = _lib.Info()
     code = _lib.lib().cheb_expmv_path(n, _dp(h), _dp(J), float(gamma), float(t), ctypes.c_void_p(psi.data_ptr()),
-                                      PREC[prec], float(tol), METHOD[method], int(time_splits), PATH[path],
+                                      PREC[prec], float(tol), METHOD[method], int(time_splits),
+                                      PATH[path] | (EVAL_BOUND_FLAG if eval_bound else 0),
                                       ctypes.c_void_p(p), nb, _stream_ptr(psi.device),
-                                      ctypes.byref(inf) if info else None)
+                                      ctypes.byref(inf) if (info or eval_bound) else None)
     _lib.check(code, "cheb_expmv")
-    return inf.as_dict() if info else None
+    return inf.as_dict() if (info or eval_bound) else None
 
 
 def anneal(h, J, gammas, ts, psi, tol: Optional[float] = None, method: str = "chebyshev", boundaries=None,
@@ -186,20 +191,22 @@ def anneal_general(h, J, a_s, b_s, ts, psi, tol: Optional[float] = None, method:
 
 
 def magnus4_nodes(A, B, T: float, steps: int):
-    """Sample the schedule for cheb_magnus4: equal steps dt = T/steps of [0, T] and, per
-    step, (A(t1), B(t1), A(t2), B(t2)) at t1,2 = t + (1/2 -+ sqrt(3)/6) dt."""
-    dt = T / steps
-    nodes = np.empty((steps, 4))
-    for m in range(steps):
-        t1 = m * dt + (0.5 - np.sqrt(3.0) / 6.0) * dt
-        t2 = m * dt + (0.5 + np.sqrt(3.0) / 6.0) * dt
-        nodes[m] = (A(t1), B(t1), A(t2), B(t2))
-    return np.full(steps, dt), nodes
+    """Sample the schedule for cheb_magnus4 (cheb_magnus4_nodes): equal steps of [0, T]
+    and, per step, (A(t1), B(t1), A(t2), B(t2)) at the Gauss-Legendre points."""
+    dt = np.empty(steps)
+    nodes = np.empty(4 * steps)
+    cb = _lib.schedule_callback(A, B)
+    code = _lib.lib().cheb_magnus4_nodes(float(T), int(steps), ctypes.cast(cb, ctypes.c_void_p), None, _dp(dt),
+                                         _dp(nodes))
+    _lib.check(code, "cheb_magnus4_nodes")
+    return dt, nodes.reshape(steps, 4)
 
 
-def magnus4(h, J, dt, nodes, psi, tol: Optional[float] = None, method: str = "chebyshev", info: bool = False):
+def magnus4(h, J, dt, nodes, psi, tol: Optional[float] = None, method: str = "chebyshev", info: bool = False,
+            boundaries=None):
     """psi <- the fourth-order commutator-free Magnus propagator of H(t) = A(t) sum_j X_j +
-    B(t) H_P, in place (cheb_magnus4); dt, nodes as from magnus4_nodes."""
+    B(t) H_P, in place (cheb_magnus4); dt, nodes as from magnus4_nodes. boundaries: optional
+    CUDA tensor (2*steps, 2^n) that receives the state before each exponential."""
     h, J = _f64(h), _f64(J)
     dt = _f64(dt)
     nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1))
@@ -210,37 +217,77 @@ def magnus4(h, J, dt, nodes, psi, tol: Optional[float] = None, method: str = "ch
     prec = precision_of(psi)
     if tol is None:
         tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+    bptr = None
+    if boundaries is not None:
+        if (boundaries.dtype != psi.dtype or tuple(boundaries.shape) != (2 * steps, 1 << n)
+                or not boundaries.is_contiguous()):
+            raise ValueError("boundaries must be a contiguous (2*steps, 2^n) tensor of psi's dtype")
+        bptr = ctypes.c_void_p(boundaries.data_ptr())
     ws = workspace(n, prec, psi.device)
     p, nb = _ws_ptr(ws)
     infos = (_lib.Info * (2 * steps))() if info else None
     code = _lib.lib().cheb_magnus4(n, _dp(h), _dp(J), steps, _dp(dt), _dp(nodes), ctypes.c_void_p(psi.data_ptr()),
-                                   PREC[prec], float(tol), METHOD[method], ctypes.c_void_p(p), nb,
+                                   PREC[prec], float(tol), METHOD[method], bptr, ctypes.c_void_p(p), nb,
                                    _stream_ptr(psi.device), infos)
     _lib.check(code, "cheb_magnus4")
     return [x.as_dict() for x in infos] if info else None
 
 
+def magnus4_adjoint(h, J, dt, nodes, boundaries, psi_T, grad, tol: Optional[float] = None,
+                    method: str = "chebyshev", store_vectors: Optional[int] = None):
+    """Gradients through cheb_magnus4 (cheb_magnus4_adjoint): grad holds dL/dpsi_T on entry
+    and dL/dpsi_0 on return. Returns dict: dt (steps), nodes (steps x 4), h (n), J (n x n)."""
+    h, J = _f64(h), _f64(J)
+    dt = _f64(dt)
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1))
+    n, steps = h.shape[0], dt.shape[0]
+    prec = precision_of(psi_T)
+    if tol is None:
+        tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+    for x in (boundaries, psi_T, grad):
+        if not x.is_cuda or not x.is_contiguous() or x.dtype != psi_T.dtype:
+            raise ValueError("boundaries, psi_T and grad must be contiguous CUDA tensors of one complex dtype")
+    if store_vectors is None:
+        nd = nodes.reshape(steps, 4)
+        amax = float(np.abs(nd[:, [0, 2]]).max())
+        bmax = float(np.abs(nd[:, [1, 3]]).max())
+        store_vectors = _auto_store_vectors(n, prec, psi_T.device,
+                                            _degree_upper_bound(bmax * h, bmax * J, np.array([amax]),
+                                                                np.array([float(np.abs(dt).max())]), tol, method))
+    ws = _adjoint_workspace(n, prec, psi_T.device, store_vectors)
+    p, nb = _ws_ptr(ws)
+    gdt, gnd, gh, gJ = np.zeros(steps), np.zeros(4 * steps), np.zeros(n), np.zeros((n, n))
+    code = _lib.lib().cheb_magnus4_adjoint(n, _dp(h), _dp(J), steps, _dp(dt), _dp(nodes),
+                                           ctypes.c_void_p(boundaries.data_ptr()), ctypes.c_void_p(psi_T.data_ptr()),
+                                           ctypes.c_void_p(grad.data_ptr()), PREC[prec], float(tol), METHOD[method],
+                                           _dp(gdt), _dp(gnd), _dp(gh), _dp(gJ), ctypes.c_void_p(p), nb,
+                                           _stream_ptr(psi_T.device))
+    _lib.check(code, "cheb_magnus4_adjoint")
+    return {"dt": gdt, "nodes": gnd.reshape(steps, 4), "h": gh, "J": gJ}
+
+
 def magnus4_adaptive(h, J, A, B, T: float, psi, tol: float, steps0: int = 8, method: str = "chebyshev"):
-    """psi <- psi(T) with the number of equal Magnus steps chosen a posteriori for an
-    integration error of about tol: runs with M and 2M steps estimate the error of the
-    2M run as |y_M - y_2M| / 15 (fourth order), and the step count is raised by the
-    factor (estimate / tol)^(1/4) when needed. Returns the number of steps used."""
+    """psi <- psi(T) with the number of equal Magnus steps chosen a posteriori
+    (cheb_magnus4_adaptive: step doubling, fourth-order error estimate). Returns the
+    number of steps used."""
     import torch
 
-    y1, y2 = psi.clone(), psi.clone()
-    dt, nd = magnus4_nodes(A, B, T, steps0)
-    magnus4(h, J, dt, nd, y1, method=method)
-    dt, nd = magnus4_nodes(A, B, T, 2 * steps0)
-    magnus4(h, J, dt, nd, y2, method=method)
-    est = float(torch.linalg.vector_norm(y1 - y2)) / 15.0
-    M = 2 * steps0
-    if est > tol:
-        M = int(np.ceil(M * (est / tol) ** 0.25 * 1.1))
-        dt, nd = magnus4_nodes(A, B, T, M)
-        y2.copy_(psi)
-        magnus4(h, J, dt, nd, y2, method=method)
-    psi.copy_(y2)
-    return M
+    h, J = _f64(h), _f64(J)
+    n = h.shape[0]
+    _check_state(psi, n)
+    prec = precision_of(psi)
+    need = int(_lib.lib().cheb_magnus4_adaptive_workspace_bytes(n, PREC[prec]))
+    ws = torch.empty(need + 256, dtype=torch.uint8, device=psi.device)
+    p, nb = _ws_ptr(ws)
+    cb = _lib.schedule_callback(A, B)
+    used = ctypes.c_int(0)
+    est = ctypes.c_double(0.0)
+    code = _lib.lib().cheb_magnus4_adaptive(n, _dp(h), _dp(J), float(T), ctypes.cast(cb, ctypes.c_void_p), None,
+                                            int(steps0), float(tol), ctypes.c_void_p(psi.data_ptr()), PREC[prec],
+                                            METHOD[method], ctypes.c_void_p(p), nb, _stream_ptr(psi.device),
+                                            ctypes.byref(used), ctypes.byref(est))
+    _lib.check(code, "cheb_magnus4_adaptive")
+    return used.value
 
 
 def batch_offsets(ns):
@@ -283,6 +330,11 @@ def expmv_batched(ns, hs, Js, gammas, ts, psi_cat, offsets=None, tol: Optional[f
                                          _stream_ptr(psi_cat.device), infos)
     _lib.check(code, "cheb_expmv_batched")
     return [x.as_dict() for x in infos] if info else None
+
+
+def adjoint_workspace_bytes(n: int, precision: str, store_vectors: int) -> int:
+    """Bytes of the adjoint workspace with a pool of store_vectors state vectors."""
+    return int(_lib.lib().cheb_adjoint_workspace_bytes(n, PREC[precision], max(0, store_vectors)))
 
 
 def _adjoint_workspace(n: int, prec: str, device, store_vectors: int):
@@ -450,6 +502,15 @@ def set_fused_blocking(on: bool):
 
 def get_fused_blocking() -> bool:
     return bool(_lib.lib().cheb_get_fused_blocking())
+
+
+def set_fused_compensated(on: bool):
+    """Kahan-compensated flip sums in the fused FP32 passes (True) or plain FP32 adds."""
+    _lib.check(_lib.lib().cheb_set_fused_compensated(1 if on else 0), "cheb_set_fused_compensated")
+
+
+def get_fused_compensated() -> bool:
+    return bool(_lib.lib().cheb_get_fused_compensated())
 
 
 KERNEL_KIND = {"plain": 3, "adjoint_acc": 5, "low": 6, "high": 7, "tail": 8}

@@ -8,8 +8,9 @@
 
 psi0 and psi_T are CUDA complex tensors (complex64 or complex128); h (n), J (n x n,
 upper triangle used), gammas (S) and ts (S) are float64 tensors on any device.
-Forward and backward both run in the CUDA library (cheb_anneal,
-cheb_anneal_adjoint, cheb_energy_grad); this module only moves arguments.
+Forward and backward both run in the CUDA library (cheb_anneal, cheb_magnus4,
+cheb_anneal_adjoint, cheb_magnus4_adjoint, cheb_energy_grad); this module only
+moves arguments.
 """
 from __future__ import annotations
 
@@ -108,19 +109,40 @@ def anneal_general(psi0, h, J, a_s, b_s, ts, tol=None, method="chebyshev", store
     return AnnealGeneralFn.apply(psi0, h, J, a_s, b_s, ts, tol, method, store_vectors)
 
 
+class Magnus4Fn(torch.autograd.Function):
+    """psi_T = the fourth-order Magnus propagator of H(t) = A(t) sum_j X_j + B(t) H_P applied
+    to psi0 (cheb_magnus4), differentiable in psi0, h, J, the step lengths dt and the node
+    values (cheb_magnus4_adjoint)."""
+
+    @staticmethod
+    def forward(ctx, psi0, h, J, dt, nodes, tol, method, store_vectors):
+        hn, Jn, dn, nn = _np(h), _np(J), _np(dt), _np(nodes)
+        steps = dn.shape[0]
+        y = psi0.detach().clone().contiguous()
+        bnd = torch.empty((2 * steps, y.numel()), dtype=y.dtype, device=y.device)
+        api.magnus4(hn, Jn, dn, nn, y, tol=tol, method=method, boundaries=bnd)
+        ctx.save_for_backward(bnd, y)
+        ctx.params = (hn, Jn, dn, nn, tol, method, store_vectors)
+        ctx.dev = (h.device, J.device, dt.device, nodes.device)
+        ctx.nshape = tuple(nodes.shape)
+        return y
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        bnd, y = ctx.saved_tensors
+        hn, Jn, dn, nn, tol, method, store_vectors = ctx.params
+        g = grad_out.detach().to(y.dtype).contiguous().clone()
+        out = api.magnus4_adjoint(hn, Jn, dn, nn, bnd, y, g, tol=tol, method=method, store_vectors=store_vectors)
+        conv = lambda key, dev: torch.from_numpy(out[key]).to(dev)
+        return (g, conv("h", ctx.dev[0]), conv("J", ctx.dev[1]), conv("dt", ctx.dev[2]),
+                conv("nodes", ctx.dev[3]).reshape(ctx.nshape), None, None, None)
+
+
 def magnus4(psi0, h, J, dt, nodes, tol=None, method="chebyshev", store_vectors=None):
     """Differentiable fourth-order commutator-free Magnus propagation (as api.magnus4):
-    dt (steps) and nodes (steps x 4: A(t1), B(t1), A(t2), B(t2)) are float64 tensors. The
-    two exponentials of a step are segments of anneal_general whose coefficients are the
-    Gauss-node combinations below, so gradients reach dt and every node value."""
-    w1 = 0.25 - 3.0 ** 0.5 / 6.0
-    w2 = 0.25 + 3.0 ** 0.5 / 6.0
-    A1, B1, A2, B2 = nodes[:, 0], nodes[:, 1], nodes[:, 2], nodes[:, 3]
-    # per step: first w2 H(t1) + w1 H(t2), then w1 H(t1) + w2 H(t2)
-    a_s = torch.stack([w2 * A1 + w1 * A2, w1 * A1 + w2 * A2], dim=1).reshape(-1)
-    b_s = torch.stack([w2 * B1 + w1 * B2, w1 * B1 + w2 * B2], dim=1).reshape(-1)
-    ts = torch.stack([dt, dt], dim=1).reshape(-1)
-    return AnnealGeneralFn.apply(psi0, h, J, a_s, b_s, ts, tol, method, store_vectors)
+    dt (steps) and nodes (steps x 4: A(t1), B(t1), A(t2), B(t2)) are float64 tensors;
+    gradients reach dt and every node value through cheb_magnus4_adjoint."""
+    return Magnus4Fn.apply(psi0, h, J, dt, nodes, tol, method, store_vectors)
 
 
 def energy(psi, h, J):

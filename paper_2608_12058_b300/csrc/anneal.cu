@@ -85,6 +85,7 @@ cheb_status_t anneal_impl(int n, const double* h, const double* J, int S, const 
             in.trunc_bound = err * slices;
             in.norm = std::sqrt(ne[0]);
             in.energy = ne[1];
+            in.eval_bound = -1.0;
             if (!std::isfinite(ne[0]) || !std::isfinite(ne[1])) return CHEB_ERR_NONFINITE;
         }
     }
@@ -118,23 +119,148 @@ extern "C" cheb_status_t cheb_anneal_general(int n, const double* h, const doubl
 //   w1 = 1/4 - sqrt(3)/6, w2 = 1/4 + sqrt(3)/6,
 // with H(t) = A(t) sum_j X_j + B(t) H_P, so that every factor is one segment
 // b H_P + a sum_j X_j of cheb_anneal_general.
-extern "C" cheb_status_t cheb_magnus4(int n, const double* h, const double* J, int steps, const double* dt,
-                                      const double* nodes, void* psi, cheb_precision_t precision, double tol,
-                                      cheb_method_t method, void* workspace, size_t ws_bytes, void* stream,
-                                      cheb_info_t* infos) {
-    if (steps < 1 || !dt || !nodes) return CHEB_ERR_INVALID_ARG;
-    if (!finite_all(dt, steps) || !finite_all(nodes, (size_t)4 * steps)) return CHEB_ERR_INVALID_ARG;
-    const double w1 = 0.25 - std::sqrt(3.0) / 6.0, w2 = 0.25 + std::sqrt(3.0) / 6.0;
-    std::vector<double> a(2 * (size_t)steps), b(2 * (size_t)steps), t(2 * (size_t)steps);
+namespace {
+
+const double kW1 = 0.25 - std::sqrt(3.0) / 6.0, kW2 = 0.25 + std::sqrt(3.0) / 6.0;
+
+// Segments (a_s, b_s, t_s) of the 2*steps exponentials; segment 2m is applied first.
+void magnus_segments(int steps, const double* dt, const double* nodes, std::vector<double>& a,
+                     std::vector<double>& b, std::vector<double>& t) {
+    a.resize(2 * (size_t)steps);
+    b.resize(2 * (size_t)steps);
+    t.resize(2 * (size_t)steps);
     for (int m = 0; m < steps; ++m) {
         const double A1 = nodes[4 * m + 0], B1 = nodes[4 * m + 1], A2 = nodes[4 * m + 2], B2 = nodes[4 * m + 3];
-        // applied first: w2 H(t1) + w1 H(t2); then w1 H(t1) + w2 H(t2)
-        a[2 * m] = w2 * A1 + w1 * A2;
-        b[2 * m] = w2 * B1 + w1 * B2;
-        a[2 * m + 1] = w1 * A1 + w2 * A2;
-        b[2 * m + 1] = w1 * B1 + w2 * B2;
+        a[2 * m] = kW2 * A1 + kW1 * A2;
+        b[2 * m] = kW2 * B1 + kW1 * B2;
+        a[2 * m + 1] = kW1 * A1 + kW2 * A2;
+        b[2 * m + 1] = kW1 * B1 + kW2 * B2;
         t[2 * m] = t[2 * m + 1] = dt[m];
     }
-    return anneal_impl(n, h, J, 2 * steps, b.data(), a.data(), t.data(), psi, precision, tol, method, nullptr,
+}
+
+bool magnus_args_ok(int steps, const double* dt, const double* nodes) {
+    return steps >= 1 && dt && nodes && finite_all(dt, steps) && finite_all(nodes, (size_t)4 * steps);
+}
+
+}  // namespace
+
+extern "C" cheb_status_t cheb_magnus4_nodes(double T, int steps, cheb_schedule_fn schedule, void* user, double* dt,
+                                            double* nodes) {
+    if (steps < 1 || !schedule || !dt || !nodes || !std::isfinite(T)) return CHEB_ERR_INVALID_ARG;
+    const double h = T / steps;
+    for (int m = 0; m < steps; ++m) {
+        const double t1 = m * h + (0.5 - std::sqrt(3.0) / 6.0) * h;
+        const double t2 = m * h + (0.5 + std::sqrt(3.0) / 6.0) * h;
+        dt[m] = h;
+        if (schedule(t1, &nodes[4 * m + 0], &nodes[4 * m + 1], user) != 0) return CHEB_ERR_INVALID_ARG;
+        if (schedule(t2, &nodes[4 * m + 2], &nodes[4 * m + 3], user) != 0) return CHEB_ERR_INVALID_ARG;
+    }
+    return finite_all(nodes, (size_t)4 * steps) ? CHEB_OK : CHEB_ERR_INVALID_ARG;
+}
+
+extern "C" cheb_status_t cheb_magnus4(int n, const double* h, const double* J, int steps, const double* dt,
+                                      const double* nodes, void* psi, cheb_precision_t precision, double tol,
+                                      cheb_method_t method, void* boundaries, void* workspace, size_t ws_bytes,
+                                      void* stream, cheb_info_t* infos) {
+    if (!magnus_args_ok(steps, dt, nodes)) return CHEB_ERR_INVALID_ARG;
+    std::vector<double> a, b, t;
+    magnus_segments(steps, dt, nodes, a, b, t);
+    return anneal_impl(n, h, J, 2 * steps, b.data(), a.data(), t.data(), psi, precision, tol, method, boundaries,
                        workspace, ws_bytes, stream, infos);
+}
+
+extern "C" cheb_status_t cheb_magnus4_adjoint(int n, const double* h, const double* J, int steps, const double* dt,
+                                              const double* nodes, const void* boundaries, const void* psi_T,
+                                              void* grad, cheb_precision_t precision, double tol,
+                                              cheb_method_t method, double* grad_dt, double* grad_nodes,
+                                              double* grad_h, double* grad_J, void* workspace, size_t ws_bytes,
+                                              void* stream) {
+    if (!magnus_args_ok(steps, dt, nodes)) return CHEB_ERR_INVALID_ARG;
+    std::vector<double> a, b, t;
+    magnus_segments(steps, dt, nodes, a, b, t);
+    const size_t S = 2 * (size_t)steps;
+    std::vector<double> ga(S), gb(S), gt(S);
+    cheb_status_t st = cheb_anneal_general_adjoint(n, h, J, (int)S, a.data(), b.data(), t.data(), boundaries, psi_T,
+                                                   grad, precision, tol, method, ga.data(), gb.data(), gt.data(),
+                                                   grad_h, grad_J, workspace, ws_bytes, stream);
+    if (st != CHEB_OK) return st;
+    // chain rule through the Gauss-node combinations of each step
+    for (int m = 0; m < steps; ++m) {
+        const size_t s0 = 2 * (size_t)m, s1 = s0 + 1;
+        if (grad_dt) grad_dt[m] = gt[s0] + gt[s1];
+        if (grad_nodes) {
+            grad_nodes[4 * m + 0] = kW2 * ga[s0] + kW1 * ga[s1];
+            grad_nodes[4 * m + 1] = kW2 * gb[s0] + kW1 * gb[s1];
+            grad_nodes[4 * m + 2] = kW1 * ga[s0] + kW2 * ga[s1];
+            grad_nodes[4 * m + 3] = kW1 * gb[s0] + kW2 * gb[s1];
+        }
+    }
+    return CHEB_OK;
+}
+
+extern "C" size_t cheb_magnus4_adaptive_workspace_bytes(int n, cheb_precision_t precision) {
+    const size_t base = cheb_workspace_bytes(n, precision);
+    if (base == 0) return 0;
+    const size_t vb = (((size_t)1 << n) * (precision == CHEB_FP32 ? 8 : 16) + 255) / 256 * 256;
+    return base + 2 * vb;
+}
+
+// Step count chosen a posteriori: runs with M and 2M equal steps estimate the error of
+// the 2M run as ||y_M - y_2M|| / 15 (fourth order: halving the step divides the error
+// by 16), and a final run uses M' = ceil(2M (est / tol)^(1/4) * 1.1) steps when the
+// estimate exceeds tol.
+extern "C" cheb_status_t cheb_magnus4_adaptive(int n, const double* h, const double* J, double T,
+                                               cheb_schedule_fn schedule, void* user, int steps0, double tol,
+                                               void* psi, cheb_precision_t precision, cheb_method_t method,
+                                               void* workspace, size_t ws_bytes, void* stream, int* steps_used,
+                                               double* err_estimate) {
+    if (steps0 < 1 || steps0 > (1 << 20) || !schedule || !(tol > 0) || !std::isfinite(tol) || !std::isfinite(T))
+        return CHEB_ERR_INVALID_ARG;
+    if (!psi || ((uintptr_t)psi & 15) != 0 || !steps_used) return CHEB_ERR_INVALID_ARG;
+    const size_t base = cheb_workspace_bytes(n, precision);
+    if (base == 0) return CHEB_ERR_INVALID_ARG;
+    if (!workspace || ((uintptr_t)workspace & 255) != 0 || ws_bytes < cheb_magnus4_adaptive_workspace_bytes(n, precision))
+        return CHEB_ERR_WORKSPACE;
+    const size_t vbytes = ((size_t)1 << n) * (precision == CHEB_FP32 ? 8 : 16);
+    const size_t vb = (vbytes + 255) / 256 * 256;
+    unsigned char* y1 = (unsigned char*)workspace + base;
+    unsigned char* y2 = y1 + vb;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the series of every exponential at the precision's default budget
+    const double tol_series = precision == CHEB_FP32 ? std::ldexp(1.0, -23) : 1e-12;
+    auto run = [&](int M, void* y) -> cheb_status_t {
+        std::vector<double> dt((size_t)M), nd(4 * (size_t)M);
+        cheb_status_t st = cheb_magnus4_nodes(T, M, schedule, user, dt.data(), nd.data());
+        if (st != CHEB_OK) return st;
+        CUDA_TRY(cudaMemcpyAsync(y, psi, vbytes, cudaMemcpyDeviceToDevice, s));
+        return cheb_magnus4(n, h, J, M, dt.data(), nd.data(), y, precision, tol_series, method, nullptr, workspace,
+                            base, stream, nullptr);
+    };
+    cheb_status_t st = run(steps0, y1);
+    if (st != CHEB_OK) return st;
+    st = run(2 * steps0, y2);
+    if (st != CHEB_OK) return st;
+    // ||y1 - y2||^2 as ||1 * y1 - y2||^2 of the evaluation-bound reduction
+    Ctx C{n, precision, make_layout(n, precision), (unsigned char*)workspace, s};
+    double* d = C.f64out();
+    CUDA_TRY(cudaMemsetAsync(d, 0, 2 * sizeof(double), s));
+    launch_step_norms(precision, (int64_t)1 << n, y2, y1, 1.0, 0.0, 1, d, d + 1, s);
+    double dd[2];
+    CUDA_TRY(cudaMemcpyAsync(dd, d, sizeof(dd), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const double est = std::sqrt(dd[1]) / 15.0;
+    int M = 2 * steps0;
+    double final_est = est;
+    if (est > tol) {
+        const int M2 = (int)std::ceil(M * std::pow(est / tol, 0.25) * 1.1);
+        st = run(M2, y2);
+        if (st != CHEB_OK) return st;
+        final_est = est * std::pow((double)M / M2, 4.0);  // fourth-order scaling of the estimate
+        M = M2;
+    }
+    CUDA_TRY(cudaMemcpyAsync(psi, y2, vbytes, cudaMemcpyDeviceToDevice, s));
+    *steps_used = M;
+    if (err_estimate) *err_estimate = final_est;
+    return CHEB_OK;
 }

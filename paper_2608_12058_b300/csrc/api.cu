@@ -118,14 +118,17 @@ cheb_status_t bounds_impl(Ctx& C, const double* h, const double* J, double* emin
 
 // One Clenshaw run (Algorithm 2) of the coefficients c over psi, in place.
 cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::complex<double>>& c, int Q,
-                           double g) {
+                           double g, double* step_norms) {
     const int K = (int)c.size() - 1;
     const int64_t N = (int64_t)1 << C.n;
     if (K == 0) {
         launch_scale(C.prec, N, psi, psi, c[0].real(), c[0].imag(), C.s);
         CUDA_TRY(cudaGetLastError());
+        if (step_norms) launch_step_norms(C.prec, N, psi, psi, 0, 0, 0, step_norms, nullptr, C.s);
         return CHEB_OK;
     }
+    // the evaluation bound needs every b_k in memory: step-by-step kernels only
+    if (step_norms && path == CHEB_PATH_AUTO && C.n <= kPlainMaxF32) path = CHEB_PATH_PLAIN;
     const int small_max = C.prec == 0 ? kSmallMaxF32 : kSmallMaxF64;
     if (path == CHEB_PATH_AUTO && C.n <= small_max) {
         static_assert(sizeof(std::complex<double>) == 2 * sizeof(double), "layout");
@@ -136,6 +139,7 @@ cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::c
         return CHEB_OK;
     }
     const int csb = cluster_slice_bits(C.prec);
+    if (path == CHEB_PATH_CLUSTER && step_norms) return CHEB_ERR_UNSUPPORTED;
     if (path == CHEB_PATH_CLUSTER && C.n > csb && C.n <= csb + 4) {
         // whole run on one cluster; its descriptor goes to the reduction scratch, which
         // the run does not otherwise use
@@ -167,6 +171,15 @@ cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::c
     if (path == CHEB_PATH_FUSED && !fused) return CHEB_ERR_UNSUPPORTED;
     unsigned char* B[2] = {C.ws + C.L.b0, C.ws + C.L.b1};
     launch_scale(C.prec, N, psi, B[1], c[K].real(), c[K].imag(), C.s);
+    auto norms = [&](int k, const void* bk) {
+        // ||b_k||^2, and ||c_{k-2} psi - b_k||^2 while b_k is still the b_{k+2} of step k - 2
+        if (!step_norms) return;
+        const bool wc = k >= 2;
+        const std::complex<double> cc = wc ? c[k - 2] : std::complex<double>(0.0, 0.0);
+        launch_step_norms(C.prec, N, bk, psi, cc.real(), cc.imag(), wc ? 1 : 0, step_norms + 2 * k,
+                          wc ? step_norms + 2 * (k - 2) + 1 : nullptr, C.s);
+    };
+    norms(K, B[1]);
     FusedPlan plan;
     if (fused) plan = fused_plan(C.n, C.prec);
     int cur = 1;
@@ -194,6 +207,7 @@ cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::c
         } else {
             launch_step_plain(C.prec, a, C.s);
         }
+        norms(k, a.out);
         cur ^= 1;
     }
     CUDA_TRY(cudaGetLastError());
@@ -227,6 +241,34 @@ cheb_status_t slice_coefficients(double t, double c, double r, double tol, int m
     return CHEB_OK;
 }
 
+// Unit roundoff of the arithmetic that a Clenshaw run of (prec, path) uses: FP32
+// (operator constants in float-float, flip sums in FP32) or native FP64.
+double unit_roundoff(int prec, int path) {
+    (void)path;
+    return prec == CHEB_FP32 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+}
+
+// The a-posteriori evaluation bound of Sec. II.B.3 for one Clenshaw run:
+//   sum_{k=0}^{K} u ||b_k|| + u ||c_k psi - b_{k+2}|| + sqrt(d) gamma_d ||b_{k+1}||,
+// d = n + 1 nonzeros per column of H, gamma_d = d u / (1 - d u), ||Ht||_2 <= 1,
+// b_0 = y, b_{K+1} = b_{K+2} = 0. norms2 holds ||b_k||^2 at [2k] and
+// ||c_k psi - b_{k+2}||^2 at [2k+1] for k <= K-2; for k = K-1, K, b_{k+2} = 0.
+double evaluation_bound(int n, int prec, int path, const std::vector<std::complex<double>>& c,
+                        const std::vector<double>& norms2, double psi_norm) {
+    const int K = (int)c.size() - 1;
+    const double u = unit_roundoff(prec, path);
+    const double d = n + 1.0;
+    const double gd = d * u / (1.0 - d * u);
+    double sum = 0.0;
+    for (int k = 0; k <= K; ++k) {
+        const double bk = std::sqrt(norms2[2 * (size_t)k]);
+        const double bk1 = k + 1 <= K ? std::sqrt(norms2[2 * (size_t)(k + 1)]) : 0.0;
+        const double ck = k <= K - 2 ? std::sqrt(norms2[2 * (size_t)k + 1]) : std::abs(c[k]) * psi_norm;
+        sum += u * bk + u * ck + std::sqrt(d) * gd * bk1;
+    }
+    return sum;
+}
+
 cheb_status_t expmv_impl(int n, const double* h, const double* J, double gamma, double t, void* psi,
                                 int prec, double tol, int method, int splits, int path, void* ws,
                                 size_t ws_bytes, void* stream, cheb_info_t* info) {
@@ -236,7 +278,10 @@ cheb_status_t expmv_impl(int n, const double* h, const double* J, double gamma, 
     if (!std::isfinite(gamma) || !std::isfinite(t) || !(tol > 0) || !std::isfinite(tol)) return CHEB_ERR_INVALID_ARG;
     if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF && method != CHEB_METHOD_REMEZ)
         return CHEB_ERR_INVALID_ARG;
+    const bool want_bound = (path & CHEB_FLAG_EVAL_BOUND) != 0;
+    path &= ~CHEB_FLAG_EVAL_BOUND;
     if (splits < 0 || path < 0 || path > 3) return CHEB_ERR_INVALID_ARG;
+    if (want_bound && !info) return CHEB_ERR_INVALID_ARG;
     Ctx C{n, prec, make_layout(n, prec), (unsigned char*)ws, (cudaStream_t)stream};
     CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), C.s));
     double emin = 0, emax = 0;
@@ -255,9 +300,29 @@ cheb_status_t expmv_impl(int n, const double* h, const double* J, double gamma, 
     st = slice_coefficients(t, c, r, tol, method, splits, coef, &K, &s, &err);
     if (st != CHEB_OK) return st;
     const double g = gamma / r;
+    double ebound = -1.0;
+    if (want_bound) ebound = 0.0;
     for (int q = 0; q < s; ++q) {
-        st = clenshaw_run(C, path, psi, coef, F.Q, g);
+        if (!want_bound) {
+            st = clenshaw_run(C, path, psi, coef, F.Q, g);
+            if (st != CHEB_OK) return st;
+            continue;
+        }
+        // the step norms go to the coefficient table (unused by the step-by-step
+        // kernels), ||psi||^2 next to the reduction outputs
+        double* dn = (double*)(C.ws + C.L.coef);
+        double* dpsi = C.f64out() + 2;
+        CUDA_TRY(cudaMemsetAsync(dn, 0, 2 * (size_t)(K + 1) * sizeof(double), C.s));
+        CUDA_TRY(cudaMemsetAsync(dpsi, 0, sizeof(double), C.s));
+        launch_step_norms(prec, (int64_t)1 << n, psi, psi, 0, 0, 0, dpsi, nullptr, C.s);
+        std::vector<double> hn(2 * (size_t)(K + 1));
+        double psi2 = 0;
+        CUDA_TRY(cudaMemcpyAsync(&psi2, dpsi, sizeof(double), cudaMemcpyDeviceToHost, C.s));
+        st = clenshaw_run(C, path, psi, coef, F.Q, g, dn);
         if (st != CHEB_OK) return st;
+        CUDA_TRY(cudaMemcpyAsync(hn.data(), dn, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, C.s));
+        CUDA_TRY(cudaStreamSynchronize(C.s));
+        ebound += evaluation_bound(n, prec, path, coef, hn, std::sqrt(psi2));
     }
     if (info) {
         launch_norm_energy(prec, n, C.L.M, F.Q, C.tiles(), C.elow(), c, r, psi, C.part(), C.f64out(), C.s);
@@ -277,6 +342,7 @@ cheb_status_t expmv_impl(int n, const double* h, const double* J, double gamma, 
         info->trunc_bound = err * s;
         info->norm = std::sqrt(ne[0]);
         info->energy = ne[1];
+        info->eval_bound = ebound;
         if (!std::isfinite(ne[0]) || !std::isfinite(ne[1])) return CHEB_ERR_NONFINITE;
     }
     return CHEB_OK;
@@ -401,11 +467,32 @@ cheb_status_t cheb_set_fused_blocking(int on) {
 
 int cheb_get_fused_blocking(void) { return fused_get_blocking(); }
 
+cheb_status_t cheb_set_fused_compensated(int on) {
+    if (on != 0 && on != 1) return CHEB_ERR_INVALID_ARG;
+    fused_set_compensated(on);
+    return CHEB_OK;
+}
+
+int cheb_get_fused_compensated(void) { return fused_get_compensated(); }
+
 cheb_status_t cheb_get_fused_split(int n, int* l, int* h) {
     if (!l || !h || !fused_supported(n, 0)) return CHEB_ERR_INVALID_ARG;
     FusedPlan p = fused_plan(n, 0);
     *l = p.l;
     *h = p.h;
+    return CHEB_OK;
+}
+
+cheb_status_t cheb_workspace_status(void* workspace, size_t workspace_bytes, void* stream) {
+    if (!workspace || ((uintptr_t)workspace & 255) != 0 || workspace_bytes < 256) return CHEB_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int* f = (int*)workspace;  // the status word sits at the start of every workspace layout
+    int v = 0;
+    CUDA_TRY(cudaMemcpyAsync(&v, f, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaMemsetAsync(f, 0, sizeof(int), s));
+    if (v & kFlagTimeout) return CHEB_ERR_TIMEOUT;
+    if (v & kFlagBadLaunch) return CHEB_ERR_CUDA;
     return CHEB_OK;
 }
 

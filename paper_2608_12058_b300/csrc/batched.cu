@@ -295,6 +295,7 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
             o.trunc_bound = in[i].err * in[i].slices;
             o.norm = std::sqrt(ne[2 * i]);
             o.energy = ne[2 * i + 1];
+            o.eval_bound = -1.0;
             nonfinite |= !std::isfinite(ne[2 * i]) || !std::isfinite(ne[2 * i + 1]);
         }
         if (nonfinite) return CHEB_ERR_NONFINITE;

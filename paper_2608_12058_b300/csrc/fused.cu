@@ -62,8 +62,16 @@ __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); 
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
 
-// Two complex numbers (a float4) accumulated with packed FP32x2 adds.
-struct Acc {
+// Flip-sum accumulator of two complex numbers (a float4). C = false: plain packed
+// FP32x2 adds. C = true: Kahan's compensated summation (a running correction holds
+// the low-order part that each add rounds away and feeds it into the next term), so
+// the sum of one pass's flip terms is accurate to about one rounding whatever their
+// number.
+template <bool C>
+struct AccT;
+
+template <>
+struct AccT<false> {
     float2 a, b;
     __device__ __forceinline__ void zero() { a = b = make_float2(0.f, 0.f); }
     __device__ __forceinline__ void add(float4 v) {
@@ -74,7 +82,58 @@ struct Acc {
         a = __fadd2_rn(a, __fadd2_rn(lo2(v), lo2(w)));
         b = __fadd2_rn(b, __fadd2_rn(hi2(v), hi2(w)));
     }
+    __device__ __forceinline__ float2 ra() const { return a; }
+    __device__ __forceinline__ float2 rb() const { return b; }
 };
+
+__device__ __forceinline__ float2 neg2(float2 x) { return make_float2(-x.x, -x.y); }
+
+// s + x with the correction c: y = x - c, t = s + y, c = (t - s) - y, s = t.
+__device__ __forceinline__ void kahan2(float2& s, float2& c, float2 x) {
+    const float2 y = __fadd2_rn(x, neg2(c));
+    const float2 t = __fadd2_rn(s, y);
+    c = __fadd2_rn(__fadd2_rn(t, neg2(s)), neg2(y));
+    s = t;
+}
+
+template <>
+struct AccT<true> {
+    float2 a, b, ca, cb;
+    __device__ __forceinline__ void zero() { a = b = ca = cb = make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void add(float4 v) {
+        kahan2(a, ca, lo2(v));
+        kahan2(b, cb, hi2(v));
+    }
+    __device__ __forceinline__ void add2(float4 v, float4 w) {
+        add(v);
+        add(w);
+    }
+    __device__ __forceinline__ void add_a(float2 x) { kahan2(a, ca, x); }
+    __device__ __forceinline__ void add_b(float2 x) { kahan2(b, cb, x); }
+    __device__ __forceinline__ float2 ra() const { return __fadd2_rn(a, neg2(ca)); }
+    __device__ __forceinline__ float2 rb() const { return __fadd2_rn(b, neg2(cb)); }
+};
+
+// Flips of bit 0 (the other half of the float4) and of the register bit for the two
+// float4 v0, v1 of a low-pass thread (the plain sum keeps its pairwise order).
+template <bool C>
+__device__ __forceinline__ void add_register_partners(AccT<C>& S0, AccT<C>& S1, float4 v0, float4 v1) {
+    if constexpr (!C) {
+        S0.a = __fadd2_rn(S0.a, __fadd2_rn(hi2(v0), lo2(v1)));
+        S0.b = __fadd2_rn(S0.b, __fadd2_rn(lo2(v0), hi2(v1)));
+        S1.a = __fadd2_rn(S1.a, __fadd2_rn(hi2(v1), lo2(v0)));
+        S1.b = __fadd2_rn(S1.b, __fadd2_rn(lo2(v1), hi2(v0)));
+    } else {
+        S0.add_a(hi2(v0));
+        S0.add_a(lo2(v1));
+        S0.add_b(lo2(v0));
+        S0.add_b(hi2(v1));
+        S1.add_a(hi2(v1));
+        S1.add_a(lo2(v0));
+        S1.add_b(lo2(v1));
+        S1.add_b(hi2(v0));
+    }
+}
 
 // o = scale*(d*v + g*s) + cs*q + ck*ps for one complex amplitude, float-float
 // d = dh + dl and g = gh + gl.
@@ -104,6 +163,7 @@ struct LowArgs {
     float ck_re, ck_im, scale, slot_coeff, ghi, glo;
 };
 
+template <bool C>
 __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full_s = (uint64_t*)(smem + kBarOff);
@@ -257,7 +317,7 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
         const float4* spsi = sb1 + kTF;
         const float4* sslot = sb1 + 2 * kTF;
         const int64_t* W = wall + s * kW;
-        Acc S0, S1;
+        AccT<C> S0, S1;
         S0.zero();
         S1.zero();
         // bits 11 .. 11+l-1: partner tiles from the ring
@@ -277,10 +337,7 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
         if (!ok) break;
         const float4 v0 = sb1[t], v1 = sb1[t + kCons];
         // bit 0 (other half of the float4) and bit 10 (the other register)
-        S0.a = __fadd2_rn(S0.a, __fadd2_rn(hi2(v0), lo2(v1)));
-        S0.b = __fadd2_rn(S0.b, __fadd2_rn(lo2(v0), hi2(v1)));
-        S1.a = __fadd2_rn(S1.a, __fadd2_rn(hi2(v1), lo2(v0)));
-        S1.b = __fadd2_rn(S1.b, __fadd2_rn(lo2(v1), hi2(v0)));
+        add_register_partners<C>(S0, S1, v0, v1);
         // bits 1..9: the partner thread's float4s in shared memory
 #pragma unroll
         for (int jj = 0; jj < 8; jj += 2) {
@@ -310,13 +367,13 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
         };
         float dh, dl;
         dd(e00, dh, dl);
-        const float2 o00 = combine(dh, dl, lo2(v0), gh, gl, S0.a, sc, cs, lo2(q0), ckr, cki_s, lo2(ps0));
+        const float2 o00 = combine(dh, dl, lo2(v0), gh, gl, S0.ra(), sc, cs, lo2(q0), ckr, cki_s, lo2(ps0));
         dd(e01, dh, dl);
-        const float2 o01 = combine(dh, dl, hi2(v0), gh, gl, S0.b, sc, cs, hi2(q0), ckr, cki_s, hi2(ps0));
+        const float2 o01 = combine(dh, dl, hi2(v0), gh, gl, S0.rb(), sc, cs, hi2(q0), ckr, cki_s, hi2(ps0));
         dd(e10, dh, dl);
-        const float2 o10 = combine(dh, dl, lo2(v1), gh, gl, S1.a, sc, cs, lo2(q1), ckr, cki_s, lo2(ps1));
+        const float2 o10 = combine(dh, dl, lo2(v1), gh, gl, S1.ra(), sc, cs, lo2(q1), ckr, cki_s, lo2(ps1));
         dd(e11, dh, dl);
-        const float2 o11 = combine(dh, dl, hi2(v1), gh, gl, S1.b, sc, cs, hi2(q1), ckr, cki_s, hi2(ps1));
+        const float2 o11 = combine(dh, dl, hi2(v1), gh, gl, S1.rb(), sc, cs, hi2(q1), ckr, cki_s, hi2(ps1));
         a.out[T * kTF + t] = make_float4(o00.x, o00.y, o01.x, o01.y);
         a.out[T * kTF + t + kCons] = make_float4(o10.x, o10.y, o11.x, o11.y);
     }
@@ -354,7 +411,7 @@ __device__ __forceinline__ int64_t strided_base(const StridedArgs& a, int64_t T)
     return tlo * 8 + (thi << (a.lo + H - 1));
 }
 
-template <int H>
+template <int H, bool C>
 __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const StridedArgs a) {
     using Cfg = StridedCfg<H>;
     extern __shared__ __align__(16) float4 tiles2[];  // 2 x kRows * 8 float4 (double-buffered)
@@ -398,7 +455,7 @@ __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const St
         __syncthreads();
 #pragma unroll
         for (int p = 0; p < Cfg::kP; ++p) {
-            Acc S;
+            AccT<C> S;
             S.zero();
 #pragma unroll
             for (int b = 1; b < Cfg::kP; b <<= 1) {
@@ -412,8 +469,8 @@ __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const St
             }
             const int rho = rlo | (p << Cfg::kRowBitsT);
             const int64_t idx = base + rho * row_stride_f4 + u;
-            float2 q0 = __ffma2_rn(g_hi, S.a, __fmul2_rn(g_lo, S.a));
-            float2 q1 = __ffma2_rn(g_hi, S.b, __fmul2_rn(g_lo, S.b));
+            float2 q0 = __ffma2_rn(g_hi, S.ra(), __fmul2_rn(g_lo, S.ra()));
+            float2 q1 = __ffma2_rn(g_hi, S.rb(), __fmul2_rn(g_lo, S.rb()));
             if (need_slot) {
                 q0 = __ffma2_rn(sg, lo2(w[p]), q0);
                 q1 = __ffma2_rn(sg, hi2(w[p]), q1);
@@ -473,7 +530,7 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-template <int H, int RB>
+template <int H, int RB, bool C>
 __global__ void __launch_bounds__(kLowThreads, 1)
     k_strided_ws(const StridedArgs a, const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap) {
     using Cfg = StridedWsCfg<H, RB>;
@@ -555,7 +612,7 @@ __global__ void __launch_bounds__(kLowThreads, 1)
         const float4* tile = (const float4*)(smem + (size_t)s * Cfg::kStageBytes);
 #pragma unroll
         for (int p = 0; p < Cfg::kP; ++p) {
-            Acc S;
+            AccT<C> S;
             S.zero();
             // partners in ascending bit order of the range (the same order for both
             // row widths and for the blocked tail, so all of them agree bit for bit)
@@ -563,8 +620,8 @@ __global__ void __launch_bounds__(kLowThreads, 1)
             for (int j = 0; j < Cfg::kRB; ++j) S.add(tile[((rlo ^ (1 << j)) | (p << Cfg::kRB)) * Cfg::kRowF4 + u]);
 #pragma unroll
             for (int b = 1; b < Cfg::kP; b <<= 1) S.add(tile[(rlo | ((p ^ b) << Cfg::kRB)) * Cfg::kRowF4 + u]);
-            float2 q0 = __ffma2_rn(g_hi, S.a, __fmul2_rn(g_lo, S.a));
-            float2 q1 = __ffma2_rn(g_hi, S.b, __fmul2_rn(g_lo, S.b));
+            float2 q0 = __ffma2_rn(g_hi, S.ra(), __fmul2_rn(g_lo, S.ra()));
+            float2 q1 = __ffma2_rn(g_hi, S.rb(), __fmul2_rn(g_lo, S.rb()));
             if (need_slot) {
                 const int c = it * Cfg::kP + p, r = c % Cfg::kSR;
                 if (!mbar_wait(&sfull[r], (c / Cfg::kSR) & 1, a.flags_ws, abort)) {
@@ -721,7 +778,7 @@ __device__ __forceinline__ void st_hint(float4* p, float4 v, uint64_t pol) {
                  : "memory");
 }
 
-template <int H>
+template <int H, bool C>
 __global__ void __launch_bounds__(kMixedThreads, 1)
     k_mixed(const MixedArgs m, const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap) {
     using Cfg = MixedCfg<H>;
@@ -974,14 +1031,14 @@ __global__ void __launch_bounds__(kMixedThreads, 1)
             bool ok = true;
 #pragma unroll
             for (int p = 0; p < Cfg::kP; ++p) {
-                Acc S;
+                AccT<C> S;
                 S.zero();
 #pragma unroll
                 for (int j = 0; j < 6; ++j) S.add(tile[((rlo ^ (1 << j)) | (p << 6)) * 8 + u]);
 #pragma unroll
                 for (int b = 1; b < Cfg::kP; b <<= 1) S.add(tile[((rlo | ((p ^ b) << 6))) * 8 + u]);
-                float2 q0 = __ffma2_rn(g_hi, S.a, __fmul2_rn(g_lo, S.a));
-                float2 q1 = __ffma2_rn(g_hi, S.b, __fmul2_rn(g_lo, S.b));
+                float2 q0 = __ffma2_rn(g_hi, S.ra(), __fmul2_rn(g_lo, S.ra()));
+                float2 q1 = __ffma2_rn(g_hi, S.rb(), __fmul2_rn(g_lo, S.rb()));
                 const int r = (int)(cc % Cfg::kSR);
                 if (!mbar_wait(&sfull[r], (int)((cc / Cfg::kSR) & 1), a.flags_ws, abort)) {
                     ok = false;
@@ -1006,7 +1063,7 @@ __global__ void __launch_bounds__(kMixedThreads, 1)
             const float4* sslot = sb1 + 2 * kTF;
             const float4* spart = sb1 + 3 * kTF;
             const int64_t* W = wall + s * kW;
-            Acc S0, S1;
+            AccT<C> S0, S1;
             S0.zero();
             S1.zero();
             if (la.l) {
@@ -1014,10 +1071,7 @@ __global__ void __launch_bounds__(kMixedThreads, 1)
                 S1.add(spart[t + kCons]);
             }
             const float4 v0 = sb1[t], v1 = sb1[t + kCons];
-            S0.a = __fadd2_rn(S0.a, __fadd2_rn(hi2(v0), lo2(v1)));
-            S0.b = __fadd2_rn(S0.b, __fadd2_rn(lo2(v0), hi2(v1)));
-            S1.a = __fadd2_rn(S1.a, __fadd2_rn(hi2(v1), lo2(v0)));
-            S1.b = __fadd2_rn(S1.b, __fadd2_rn(lo2(v1), hi2(v0)));
+            add_register_partners<C>(S0, S1, v0, v1);
 #pragma unroll
             for (int jj = 0; jj < 8; jj += 2) {
                 const int pa = t ^ (1 << jj), pb = t ^ (2 << jj);
@@ -1045,13 +1099,13 @@ __global__ void __launch_bounds__(kMixedThreads, 1)
             };
             float dh, dl;
             dd(e00, dh, dl);
-            const float2 o00 = combine(dh, dl, lo2(v0), gh, gl, S0.a, sc, cs, lo2(q0), ckr, cki_s, lo2(ps0));
+            const float2 o00 = combine(dh, dl, lo2(v0), gh, gl, S0.ra(), sc, cs, lo2(q0), ckr, cki_s, lo2(ps0));
             dd(e01, dh, dl);
-            const float2 o01 = combine(dh, dl, hi2(v0), gh, gl, S0.b, sc, cs, hi2(q0), ckr, cki_s, hi2(ps0));
+            const float2 o01 = combine(dh, dl, hi2(v0), gh, gl, S0.rb(), sc, cs, hi2(q0), ckr, cki_s, hi2(ps0));
             dd(e10, dh, dl);
-            const float2 o10 = combine(dh, dl, lo2(v1), gh, gl, S1.a, sc, cs, lo2(q1), ckr, cki_s, lo2(ps1));
+            const float2 o10 = combine(dh, dl, lo2(v1), gh, gl, S1.ra(), sc, cs, lo2(q1), ckr, cki_s, lo2(ps1));
             dd(e11, dh, dl);
-            const float2 o11 = combine(dh, dl, hi2(v1), gh, gl, S1.b, sc, cs, hi2(q1), ckr, cki_s, hi2(ps1));
+            const float2 o11 = combine(dh, dl, hi2(v1), gh, gl, S1.rb(), sc, cs, hi2(q1), ckr, cki_s, hi2(ps1));
             // the output is next step's b_{k+1}, not read again in this launch
             st_hint(la.out + T * kTF + t, make_float4(o00.x, o00.y, o01.x, o01.y), pol_out);
             st_hint(la.out + T * kTF + t + kCons, make_float4(o10.x, o10.y, o11.x, o11.y), pol_out);
@@ -1073,22 +1127,30 @@ int num_sms() {
     return g_num_sms;
 }
 
-template <int H>
-cudaError_t launch_strided_t(const StridedArgs& a, cudaStream_t s) {
+// Flip sums with Kahan compensation (cheb_set_fused_compensated); off by default.
+static int g_comp = 0;
+
+template <int H, bool C>
+cudaError_t launch_strided_c(const StridedArgs& a, cudaStream_t s) {
     using Cfg = StridedCfg<H>;
     const size_t smem = 2 * (size_t)Cfg::kRows * 8 * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(k_strided<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_strided<H, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_strided<H>, Cfg::kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_strided<H, C>, Cfg::kThreads, smem);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)num_sms() * per_sm);
     if (grid < 1) grid = 1;
     note_launch(kKindHigh);
     const int pi = prof_begin(kKindHigh, s);
-    k_strided<H><<<(unsigned)grid, Cfg::kThreads, smem, s>>>(a);
+    k_strided<H, C><<<(unsigned)grid, Cfg::kThreads, smem, s>>>(a);
     prof_end(pi, s);
     return cudaGetLastError();
+}
+
+template <int H>
+cudaError_t launch_strided_t(const StridedArgs& a, cudaStream_t s) {
+    return g_comp ? launch_strided_c<H, true>(a, s) : launch_strided_c<H, false>(a, s);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
@@ -1136,20 +1198,25 @@ cudaError_t strided_maps(const StridedArgs& a, int n, int H, int RB, int box_row
     return cudaSuccess;
 }
 
-template <int H, int RB>
-cudaError_t launch_strided_ws_t(const StridedArgs& a, int n, cudaStream_t s) {
+template <int H, int RB, bool C>
+cudaError_t launch_strided_ws_c(const StridedArgs& a, int n, cudaStream_t s) {
     using Cfg = StridedWsCfg<H, RB>;
     CUtensorMap map, smap;
     cudaError_t e = strided_maps(a, n, H, RB, Cfg::kBox, &map, &smap);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_strided_ws<H, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    e = cudaFuncSetAttribute(k_strided_ws<H, RB, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(a.ntiles, num_sms());
     note_launch(kKindHigh);
     const int pi = prof_begin(kKindHigh, s);
-    k_strided_ws<H, RB><<<(unsigned)grid, kLowThreads, Cfg::kSmem, s>>>(a, map, smap);
+    k_strided_ws<H, RB, C><<<(unsigned)grid, kLowThreads, Cfg::kSmem, s>>>(a, map, smap);
     prof_end(pi, s);
     return cudaGetLastError();
+}
+
+template <int H, int RB>
+cudaError_t launch_strided_ws_t(const StridedArgs& a, int n, cudaStream_t s) {
+    return g_comp ? launch_strided_ws_c<H, RB, true>(a, n, s) : launch_strided_ws_c<H, RB, false>(a, n, s);
 }
 
 // Rows of 2^RB amplitudes for a strided pass over [lo, lo + H): wide rows (RB = 5)
@@ -1180,19 +1247,24 @@ cudaError_t launch_strided(int H, int RB, const StridedArgs& a, int n, cudaStrea
     return cudaErrorInvalidValue;
 }
 
-template <int H>
-cudaError_t launch_mixed_t(const MixedArgs& m, int n, cudaStream_t s) {
+template <int H, bool C>
+cudaError_t launch_mixed_c(const MixedArgs& m, int n, cudaStream_t s) {
     using Cfg = MixedCfg<H>;
     CUtensorMap map, smap;
     cudaError_t e = strided_maps(m.sa, n, H, 4, Cfg::kBox, &map, &smap);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_mixed<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    e = cudaFuncSetAttribute(k_mixed<H, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
     if (e != cudaSuccess) return e;
     note_launch(kKindMixed);
     const int pi = prof_begin(kKindMixed, s);
-    k_mixed<H><<<(unsigned)num_sms(), kMixedThreads, Cfg::kSmem, s>>>(m, map, smap);
+    k_mixed<H, C><<<(unsigned)num_sms(), kMixedThreads, Cfg::kSmem, s>>>(m, map, smap);
     prof_end(pi, s);
     return cudaGetLastError();
+}
+
+template <int H>
+cudaError_t launch_mixed_t(const MixedArgs& m, int n, cudaStream_t s) {
+    return g_comp ? launch_mixed_c<H, true>(m, n, s) : launch_mixed_c<H, false>(m, n, s);
 }
 
 cudaError_t launch_mixed(int H, const MixedArgs& m, int n, cudaStream_t s) {
@@ -1239,6 +1311,8 @@ size_t fused_scratch_bytes(int n, int prec) {
 static int g_blocking = 0;
 void fused_set_blocking(int on) { g_blocking = on ? 1 : 0; }
 int fused_get_blocking() { return g_blocking; }
+void fused_set_compensated(int on) { g_comp = on ? 1 : 0; }
+int fused_get_compensated() { return g_comp; }
 
 bool fused_supported(int n, int prec) { return prec == 0 && n >= kLowBits && n <= kMaxQubits; }
 
@@ -1394,12 +1468,13 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void* sc
         if (e != cudaSuccess) return e;
         return launch_mixed(plan.hb[lastp], m, s.n, st);
     }
-    cudaError_t e = cudaFuncSetAttribute(k_low, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLowSmem);
+    auto kern = g_comp ? k_low<true> : k_low<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLowSmem);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(la.ntiles, num_sms());
     note_launch(kKindLow);
     const int pi = prof_begin(kKindLow, st);
-    k_low<<<(unsigned)grid, kLowThreads, kLowSmem, st>>>(la);
+    kern<<<(unsigned)grid, kLowThreads, kLowSmem, st>>>(la);
     prof_end(pi, st);
     return cudaGetLastError();
 }

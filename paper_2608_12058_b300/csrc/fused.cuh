@@ -28,6 +28,9 @@ size_t fused_scratch_bytes(int n, int prec);
 // L2-blocked step tail (the last strided pass and the low pass in one launch): on/off.
 void fused_set_blocking(int on);
 int fused_get_blocking();
+// Kahan-compensated flip sums in the fused FP32 passes: on/off (process-wide).
+void fused_set_compensated(int on);
+int fused_get_compensated();
 bool fused_split_valid(int n, int l, int h);
 // Override the split for n (l < 0 restores the default); false if invalid.
 bool fused_set_split(int n, int l, int h);

@@ -471,6 +471,57 @@ __global__ void k_sum2_final(const double* __restrict__ part, int nb, double* __
     }
 }
 
+// ---------------------------------------------------------------------------
+// Norms for the evaluation-error bound of Sec. II.B.3: out[0] += ||b||^2 and, when
+// want_c, out_c[0] += ||c psi - b||^2, accumulated in FP64 (block tree, then one
+// atomic add per block: the order of the block sums is not fixed, which only moves
+// the last bits of a bound).
+template <typename R>
+__global__ void __launch_bounds__(256) k_step_norms(int64_t N, const typename Cx<R>::T* __restrict__ b,
+                                                    const typename Cx<R>::T* __restrict__ psi, double cr,
+                                                    double ci, int want_c, double* out_b, double* out_c) {
+    __shared__ double sb[256], sc[256];
+    double ab = 0.0, ac = 0.0;
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N;
+         z += (int64_t)gridDim.x * blockDim.x) {
+        const auto v = b[z];
+        const double vx = (double)v.x, vy = (double)v.y;
+        ab += vx * vx + vy * vy;
+        if (want_c) {
+            const auto p = psi[z];
+            const double px = (double)p.x, py = (double)p.y;
+            const double dx = cr * px - ci * py - vx, dy = cr * py + ci * px - vy;
+            ac += dx * dx + dy * dy;
+        }
+    }
+    sb[threadIdx.x] = ab;
+    sc[threadIdx.x] = ac;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sb[threadIdx.x] += sb[threadIdx.x + w];
+            sc[threadIdx.x] += sc[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(out_b, sb[0]);
+        if (want_c) atomicAdd(out_c, sc[0]);
+    }
+}
+
+void launch_step_norms(int prec, int64_t N, const void* b, const void* psi, double cr, double ci, int want_c,
+                       double* out_b, double* out_c, cudaStream_t s) {
+    const unsigned nb = grid_for(N, 256, kRedBlocks);
+    note_launch(kKindReduce);
+    if (prec == 0)
+        k_step_norms<float><<<nb, 256, 0, s>>>(N, (const float2*)b, (const float2*)psi, cr, ci, want_c, out_b,
+                                               out_c);
+    else
+        k_step_norms<double><<<nb, 256, 0, s>>>(N, (const double2*)b, (const double2*)psi, cr, ci, want_c, out_b,
+                                                out_c);
+}
+
 void launch_norm_energy(int prec, int n, int M, int Q, const int64_t* tiles, const int64_t* elow,
                         double c, double r, const void* psi, double* part, double* out2, cudaStream_t s) {
     const int64_t N = (int64_t)1 << n;

@@ -75,6 +75,10 @@ cudaError_t launch_small_batched(int prec, int count, int max_n, const SmallDesc
 // 1..4. Returns cudaErrorNotSupported when no such cluster fits on the device.
 int cluster_slice_bits(int prec);
 cudaError_t launch_cluster_batched(int prec, int n, int count, const SmallDesc* descs, cudaStream_t s);
+// Evaluation-bound norms (Sec. II.B.3): *out_b += ||b||^2 and, if want_c,
+// *out_c += ||(cr + i ci) psi - b||^2, both FP64 (atomic adds; zero them first).
+void launch_step_norms(int prec, int64_t N, const void* b, const void* psi, double cr, double ci, int want_c,
+                       double* out_b, double* out_c, cudaStream_t s);
 void launch_norm_energy(int prec, int n, int M, int Q, const int64_t* tiles, const int64_t* elow,
                         double c, double r, const void* psi, double* part, double* out2,
                         cudaStream_t s);

@@ -46,8 +46,11 @@ cheb_status_t check_common(int n, const double* h, const double* J, int prec, vo
 // Exact E_min, E_max of the Ising diagonal (synchronises the stream).
 cheb_status_t bounds_impl(Ctx& C, const double* h, const double* J, double* emin, double* emax);
 // One Clenshaw run of coefficients c over psi in place, with the tables already uploaded.
+// step_norms (device, nullable): 2(K+1) zeroed doubles that receive, per k, ||b_k||^2 at
+// [2k] and ||c_k psi - b_{k+2}||^2 at [2k+1] (k <= K-2) for the evaluation bound of
+// Sec. II.B.3; the run then uses the step-by-step kernels (b_k must be visible).
 cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::complex<double>>& c, int Q,
-                           double g);
+                           double g, double* step_norms = nullptr);
 // Synchronises and maps the device status word to a status code.
 cheb_status_t read_flags(const Ctx& C);
 // Coefficients of exp(-i a x) * exp(-i ts c) for one slice, slicing t automatically

@@ -163,6 +163,38 @@ def test_fused_blocking_switch():
     assert api.get_fused_blocking() is False
 
 
+def test_fused_compensated_switch():
+    """Compensated flip sums are off by default, take 0 or 1, and report their setting."""
+    assert api.get_fused_compensated() is False
+    assert _lib.lib().cheb_set_fused_compensated(3) == 1  # CHEB_ERR_INVALID_ARG
+    api.set_fused_compensated(True)
+    try:
+        assert api.get_fused_compensated() is True
+    finally:
+        api.set_fused_compensated(False)
+    assert api.get_fused_compensated() is False
+
+
+def test_magnus4_nodes_match_the_oracle_sampler(oracle):
+    """cheb_magnus4_nodes (host only) samples A, B at the Gauss-Legendre points of each
+    step exactly as the oracle's sampler does; a failing schedule aborts the call."""
+    T, steps = 2.0, 7
+    A = lambda t: 1.5 * (1 - t / T) + 0.3 * np.sin(3 * t)
+    B = lambda t: t / T + 0.2 * np.cos(2 * t)
+    dt, nodes = api.magnus4_nodes(A, B, T, steps)
+    dto, nodeso = oracle.magnus4_nodes(A, B, T, steps)
+    np.testing.assert_allclose(dt, dto, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(nodes, np.asarray(nodeso).reshape(steps, 4), rtol=0, atol=1e-14)
+
+    def bad(t):
+        raise ValueError("schedule failure")
+
+    with pytest.raises(_lib.ChebError):
+        api.magnus4_nodes(bad, B, T, steps)
+    with pytest.raises(_lib.ChebError):
+        api.magnus4_nodes(A, lambda t: float("nan"), T, steps)
+
+
 def test_expmv_rejects_bad_arguments_before_touching_the_device():
     L = _lib.lib()
     n = 4
@@ -192,6 +224,11 @@ def test_expmv_rejects_bad_arguments_before_touching_the_device():
                         None, None) == 1
     assert L.cheb_expmv(n, dp(h), dp(J), 1.0, float("inf"), fake, 0, 1e-6, 0, 0, fake, ws, None, None) == 1
     assert L.cheb_expmv(n, dp(h), dp(J), 1.0, 1.0, fake, 0, 1e-6, 0, -1, fake, ws, None, None) == 1
+    # the evaluation bound is written into info, so it needs one
+    assert L.cheb_expmv_path(n, dp(h), dp(J), 1.0, 1.0, fake, 0, 1e-6, 0, 0, api.EVAL_BOUND_FLAG, fake, ws, None,
+                             None) == 1
+    # unknown path bits
+    assert L.cheb_expmv_path(n, dp(h), dp(J), 1.0, 1.0, fake, 0, 1e-6, 0, 0, 0x40, fake, ws, None, None) == 1
 
 
 @pytest.mark.parametrize("K,seed", [(0, 0), (1, 1), (7, 2), (50, 3), (120, 4)])

@@ -263,7 +263,8 @@ def test_general_segments_gradients_vs_finite_differences(cuda_lib):
 def test_magnus4_schedule_parameter_gradients(cuda_lib):
     """Gradients of the energy after Magnus propagation with respect to the parameters
     of a smooth schedule A(t) = p0 (1 - t/T) + p2 sin t, B(t) = p1 t/T (torch composes
-    the node values and the segment weights; the library supplies the segment adjoint)."""
+    the node values from p; cheb_magnus4_adjoint chains the Gauss-node weights and
+    supplies the segment adjoint)."""
     import torch
 
     from paper_2608_12058_b300 import api

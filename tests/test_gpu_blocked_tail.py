@@ -141,3 +141,24 @@ def test_blocked_tail_adjoint_identical(cuda_lib, split):
     assert np.array_equal(x1, x2)
     for key in ("gamma", "t", "h", "J"):
         assert np.array_equal(np.asarray(o1[key]), np.asarray(o2[key])), key
+
+
+def test_blocked_tail_bit_identical_compensated(cuda_lib, split):
+    """With compensated flip sums the blocked tail and the separate launches still
+    perform the same operations in the same order: bit-identical results."""
+    from paper_2608_12058_b300 import api
+
+    n = 26
+    split(n, 1, 14)
+    rng = np.random.default_rng(7)
+    coef = (rng.standard_normal(8) + 1j * rng.standard_normal(8)) / 32
+    api.set_fused_compensated(True)
+    try:
+        a = _poly(n, coef, True)
+        b = _poly(n, coef, False)
+        api.set_fused_compensated(False)
+        c = _poly(n, coef, False)
+    finally:
+        api.set_fused_compensated(False)
+    assert bool((a == b).all())
+    assert not bool((a == c).all())  # the switch changes the arithmetic

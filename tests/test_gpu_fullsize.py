@@ -99,3 +99,54 @@ def test_n30_workload_conserves_norm_and_energy(cuda_lib):
     # s_i s_j sums to zero), so <H> = gamma n exactly
     assert abs(x0_H - c.gamma * N30) <= 1e-5 * radius
     assert abs(y_H - x0_H) <= 2e-4 * radius
+
+
+def test_n30_adjoint_gradients(cuda_lib):
+    """Reverse-Clenshaw gradients at the full n = 30 size (one segment of the SK
+    workload, t = 0.15, K = 20): the complex64 forward keeps only its start state, the
+    adjoint regenerates the Clenshaw vectors in a ring of 6 from one anchor pair, and
+    dL/dgamma, dL/dt and dL/dh_i of L = <psi_T|H_P|psi_T> match central differences of
+    the FP64 forward map within 1e-4."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    c = I.config_n30()
+    gamma, t = np.array([c.gamma]), np.array([0.15])
+    store = 8
+    ws_bytes = int(cuda_lib.cheb_adjoint_workspace_bytes(N30, 0, store))
+    print(f"n=30 adjoint workspace ({store} state vectors): {ws_bytes / 2**30:.1f} GiB")
+    y = torch.full((1 << N30,), 2 ** (-N30 / 2), dtype=torch.complex64, device="cuda")
+    bnd = torch.empty((1, 1 << N30), dtype=torch.complex64, device="cuda")
+    infos = api.anneal(c.h, c.J, gamma, t, y, boundaries=bnd)
+    assert 10 <= infos[0]["K"] <= 40
+    api.release_workspaces()
+    e, g, gh, gJ = api.energy_grad(c.h, c.J, y)
+    torch.cuda.empty_cache()
+    out = api.anneal_adjoint(c.h, c.J, gamma, t, bnd, y, g, store_vectors=store)
+    got = {"gamma": out["gamma"][0], "t": out["t"][0], "h": out["h"][5] + gh[5]}
+    del y, bnd, g
+    api.release_workspaces()
+    torch.cuda.empty_cache()
+
+    def loss(h_, g_, t_):
+        x = torch.full((1 << N30,), 2 ** (-N30 / 2), dtype=torch.complex128, device="cuda")
+        api.anneal(h_, c.J, g_, t_, x, tol=1e-13, info=False)
+        v = api.energy(h_, c.J, x)[0]
+        del x
+        return v
+
+    eps = 1e-4
+    refs = {}
+    for key in ("gamma", "t", "h"):
+        vals = []
+        for sgn in (+1, -1):
+            h_, g_, t_ = c.h.copy(), gamma.copy(), t.copy()
+            {"gamma": g_, "t": t_, "h": h_}[key][0 if key != "h" else 5] += sgn * eps
+            vals.append(loss(h_, g_, t_))
+        refs[key] = (vals[0] - vals[1]) / (2 * eps)
+    api.release_workspaces()
+    scale = max(abs(v) for v in refs.values())
+    for key, ref in refs.items():
+        print(f"n=30 dL/d{key}: adjoint {got[key]:.8e}, central difference {ref:.8e}")
+        assert abs(got[key] - ref) <= 1e-4 * max(abs(ref), scale), (key, got[key], ref)
