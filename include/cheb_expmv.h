@@ -51,13 +51,15 @@ typedef enum { CHEB_FP32 = 0, CHEB_FP64 = 1 } cheb_precision_t;
 
 /* Kernel path for the Clenshaw steps. AUTO picks the fastest path measured for
  * (n, precision): the whole run in one CTA's shared memory for n <= 13 (FP32) or 12
- * (FP64), the plain kernel up to n = 19 (FP32) and for FP64, the fused kernels above;
- * batches run instances of n = 14..17 (FP32) or 13..16 (FP64) on clusters. PLAIN forces the one-pass kernel that reads every bit-flip
- * partner from global memory (the reference GPU path); FUSED forces the
- * shared-memory tiled kernels (FP32, n >= 11 only); CLUSTER forces the whole run on
- * one thread-block cluster with the vectors in distributed shared memory (FP32
- * n = 14..17, FP64 n = 13..16; UNSUPPORTED elsewhere or if the device has no room
- * for such a cluster). */
+ * (FP64), the plain kernel up to n = 19 (FP32) or 16 (FP64), the fused kernels above;
+ * batches run instances of n = 14..17 (FP32) or 13..16 (FP64) on clusters. PLAIN
+ * forces the one-pass kernel that reads every bit-flip partner from global memory
+ * (the reference GPU path; for FP64 it is the native FP64 recurrence); FUSED forces
+ * the shared-memory tiled kernels (n >= 11; for FP64 these keep complex128 storage and
+ * compute in float-float on the FP32 units, about 48 significant bits, see
+ * cheb_set_fused_split_fp64); CLUSTER forces the whole run on one thread-block cluster
+ * with the vectors in distributed shared memory (FP32 n = 14..17, FP64 n = 13..16;
+ * UNSUPPORTED elsewhere or if the device has no room for such a cluster). */
 typedef enum {
     CHEB_PATH_AUTO = 0,
     CHEB_PATH_PLAIN = 1,
@@ -84,11 +86,12 @@ typedef struct {
  * error bound of Sec. II.B.3 (analysis of evaluation error),
  *   sum_{k=0}^{K} u ||b_k|| + u ||c_k psi - b_{k+2}|| + sqrt(d) gamma_d ||b_{k+1}||,
  * with b_0 = y, d = n + 1 nonzeros per column of H, gamma_d = d u / (1 - d u) and u the
- * unit roundoff of the arithmetic (2^-24 for CHEB_FP32, 2^-53 for CHEB_FP64), from
- * FP64 norms of every Clenshaw vector reduced on the device after each step. It needs
- * every b_k in memory, so the run uses the step-by-step kernels (PLAIN up to n = 19,
- * FUSED above; CLUSTER is UNSUPPORTED), costs one extra read of b_k and psi per step
- * and synchronises once per time slice. Requires info (INVALID_ARG otherwise). */
+ * unit roundoff of the arithmetic (2^-24 for CHEB_FP32; 2^-47 for the float-float
+ * fused FP64 step; 2^-53 for the native FP64 kernels), from FP64 norms of every
+ * Clenshaw vector reduced on the device after each step. It needs every b_k in memory,
+ * so the whole-run shared-memory kernel is replaced by PLAIN (CLUSTER is UNSUPPORTED);
+ * it costs one extra read of b_k and psi per step and synchronises once per time
+ * slice. Requires info (INVALID_ARG otherwise). */
 #define CHEB_FLAG_EVAL_BOUND 0x100
 
 /* Human-readable name of a status code (static string). */
@@ -397,6 +400,17 @@ cheb_status_t cheb_set_fused_split(int n, int l, int h);
 cheb_status_t cheb_get_fused_split(int n, int* l, int* h);
 
 /*
+ * Bit split of the fused float-float step of the FP64 path for n qubits (n >= 11): bits
+ * [0, 10) from a shared-memory tile of 1024 complex amplitudes, bits [10, 10 + l) from
+ * L2 partner tiles, and the remaining h bits in strided passes of 6..9 bits (5..8 bits
+ * on rows of 16 amplitudes where rows lie at least 2 MB apart), at most four, with
+ * 10 + l + h = n, 0 <= l <= 6. Same conventions as cheb_set_fused_split.
+ * Errors: INVALID_ARG for an impossible split or n outside 11..33.
+ */
+cheb_status_t cheb_set_fused_split_fp64(int n, int l, int h);
+cheb_status_t cheb_get_fused_split_fp64(int n, int* l, int* h);
+
+/*
  * L2-blocked step tail of the fused FP32 step (Sec. II.D matvec, scheduled for a
  * 126 MB L2; no counterpart in the paper). When on, the last strided pass and the low
  * pass of each step run as one persistent launch: amplitudes are grouped by their
@@ -420,6 +434,44 @@ int cheb_get_fused_blocking(void);
  */
 cheb_status_t cheb_set_fused_compensated(int on);
 int cheb_get_fused_compensated(void);
+
+/*
+ * Autotuner of the Clenshaw step configuration (no counterpart in the paper). For
+ * (n, precision) it times, on the calling device and the given stream, `steps`
+ * Clenshaw steps of a synthetic problem of that size under the built-in choice and
+ * under every candidate: the plain one-pass kernel (n <= 24 FP32, <= 26 FP64) and the
+ * fused step with each valid bit split of at most 4 (FP32) or 5 (FP64) L2 partner
+ * bits, and for FP32 the L2-blocked tail where the split allows it. The fastest
+ * candidate is installed process-wide: AUTO then uses that path, split and blocking
+ * for n (cheb_set_fused_split / cheb_set_fused_split_fp64 override it again).
+ * If the environment variable CHEB_AUTOTUNE_CACHE names a file, the result is appended
+ * to it as a line "cheb-tune-1 <device name> <prec> <n> <path> <l> <h> <blocking> <ms>",
+ * and the first Clenshaw run of a process applies the lines recorded for its device.
+ *   steps: 2..64 timed steps per candidate (each candidate runs twice, the second timed).
+ *   workspace: cheb_autotune_workspace_bytes(n, precision) bytes (the expmv workspace
+ *   plus one state vector). Synchronises the stream once per candidate.
+ *   result: HOST out.
+ * Errors: INVALID_ARG (n < 14 FP32 or < 13 FP64, steps outside 2..64, null result),
+ * WORKSPACE, CUDA, TIMEOUT.
+ */
+typedef struct {
+    int path;                    /* CHEB_PATH_PLAIN or CHEB_PATH_FUSED */
+    int l, h;                    /* the split, for FUSED */
+    int blocking;                /* FP32: L2-blocked step tail on */
+    int candidates;              /* configurations timed */
+    double best_ms_per_step;     /* the chosen configuration */
+    double default_ms_per_step;  /* the built-in choice */
+} cheb_tune_result_t;
+size_t cheb_autotune_workspace_bytes(int n, cheb_precision_t precision);
+cheb_status_t cheb_autotune(int n, cheb_precision_t precision, int steps, void* workspace, size_t workspace_bytes,
+                            void* stream, cheb_tune_result_t* result);
+/* Applies the lines of an autotuner cache file recorded for `device` (a device name
+ * with spaces replaced by '_'; NULL = the current device, which needs a GPU). applied:
+ * HOST out (nullable), the number of lines applied. Host only otherwise.
+ * Errors: INVALID_ARG (null path, file not readable). */
+cheb_status_t cheb_autotune_load(const char* path, const char* device, int* applied);
+/* Drops every tuned choice and split override (the built-in choices apply again). */
+cheb_status_t cheb_autotune_reset(void);
 
 /*
  * General polynomial p(Ht) psi (Algorithm 2 with caller-supplied coefficients):

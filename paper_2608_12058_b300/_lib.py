@@ -19,6 +19,21 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [
+        ("path", ctypes.c_int),
+        ("l", ctypes.c_int),
+        ("h", ctypes.c_int),
+        ("blocking", ctypes.c_int),
+        ("candidates", ctypes.c_int),
+        ("best_ms_per_step", ctypes.c_double),
+        ("default_ms_per_step", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Info(ctypes.Structure):
     _fields_ = [
         ("K", ctypes.c_int),
@@ -56,6 +71,8 @@ SIGNATURES = {
     "cheb_energy": (c_int, [c_int, _dp, _dp, c_void_p, c_int, c_void_p, c_size_t, c_void_p, _dp, _dp]),
     "cheb_set_fused_split": (c_int, [c_int, c_int, c_int]),
     "cheb_get_fused_split": (c_int, [c_int, _ip, _ip]),
+    "cheb_set_fused_split_fp64": (c_int, [c_int, c_int, c_int]),
+    "cheb_get_fused_split_fp64": (c_int, [c_int, _ip, _ip]),
     "cheb_set_fused_blocking": (c_int, [c_int]),
     "cheb_get_fused_blocking": (c_int, []),
     "cheb_set_fused_compensated": (c_int, [c_int]),
@@ -86,6 +103,10 @@ SIGNATURES = {
                                  c_void_p]),
     "cheb_wait_selftest": (c_int, [c_void_p, c_size_t, c_void_p]),
     "cheb_workspace_status": (c_int, [c_void_p, c_size_t, c_void_p]),
+    "cheb_autotune_workspace_bytes": (c_size_t, [c_int, c_int]),
+    "cheb_autotune": (c_int, [c_int, c_int, c_int, c_void_p, c_size_t, c_void_p, ctypes.POINTER(TuneResult)]),
+    "cheb_autotune_load": (c_int, [ctypes.c_char_p, ctypes.c_char_p, _ip]),
+    "cheb_autotune_reset": (c_int, []),
     "cheb_launch_count": (ctypes.c_longlong, []),
     "cheb_profile_enable": (c_int, [c_int]),
     "cheb_profile_reset": (c_int, []),

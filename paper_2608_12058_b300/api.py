@@ -494,6 +494,50 @@ def get_fused_split(n: int):
     return l.value, h.value
 
 
+def set_fused_split_fp64(n: int, l: int, h: int = 0):
+    """Split of the float-float fused FP64 step (10 + l + h = n); l = -1 resets."""
+    _lib.check(_lib.lib().cheb_set_fused_split_fp64(int(n), int(l), int(h)), "cheb_set_fused_split_fp64")
+
+
+def get_fused_split_fp64(n: int):
+    l, h = ctypes.c_int(), ctypes.c_int()
+    _lib.check(_lib.lib().cheb_get_fused_split_fp64(int(n), ctypes.byref(l), ctypes.byref(h)),
+               "cheb_get_fused_split_fp64")
+    return l.value, h.value
+
+
+def autotune(n: int, precision: str = "fp32", steps: int = 4, device=None):
+    """Time the candidate step configurations for (n, precision) on the device and install
+    the fastest (cheb_autotune); returns the result as a dict."""
+    import torch
+
+    need = int(_lib.lib().cheb_autotune_workspace_bytes(int(n), PREC[precision]))
+    if need == 0:
+        raise ValueError(f"unsupported n={n}")
+    dev = torch.device(device if device is not None else "cuda")
+    ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+    p, nb = _ws_ptr(ws)
+    res = _lib.TuneResult()
+    code = _lib.lib().cheb_autotune(int(n), PREC[precision], int(steps), ctypes.c_void_p(p), nb, _stream_ptr(dev),
+                                    ctypes.byref(res))
+    _lib.check(code, "cheb_autotune")
+    d = res.as_dict()
+    d["path"] = {1: "plain", 2: "fused"}.get(d["path"], d["path"])
+    return d
+
+
+def autotune_load(path: str, device: Optional[str] = None) -> int:
+    """Apply the lines of an autotuner cache file recorded for `device` (default: current)."""
+    applied = ctypes.c_int(0)
+    code = _lib.lib().cheb_autotune_load(path.encode(), device.encode() if device else None, ctypes.byref(applied))
+    _lib.check(code, "cheb_autotune_load")
+    return applied.value
+
+
+def autotune_reset():
+    _lib.check(_lib.lib().cheb_autotune_reset(), "cheb_autotune_reset")
+
+
 def set_fused_blocking(on: bool):
     """Run the last strided pass and the low pass of each fused step as one L2-blocked
     launch (True) or as separate launches (False); results are identical."""

@@ -12,6 +12,7 @@
 #include "../../include/cheb_expmv.h"
 #include "cheb_internal.h"
 #include "fused.cuh"
+#include "fused_ff.cuh"
 #include "kernels.cuh"
 #include "pipeline.h"
 
@@ -119,6 +120,7 @@ cheb_status_t bounds_impl(Ctx& C, const double* h, const double* J, double* emin
 // One Clenshaw run (Algorithm 2) of the coefficients c over psi, in place.
 cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::complex<double>>& c, int Q,
                            double g, double* step_norms) {
+    autotune_cache_once();
     const int K = (int)c.size() - 1;
     const int64_t N = (int64_t)1 << C.n;
     if (K == 0) {
@@ -127,9 +129,15 @@ cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::c
         if (step_norms) launch_step_norms(C.prec, N, psi, psi, 0, 0, 0, step_norms, nullptr, C.s);
         return CHEB_OK;
     }
-    // the evaluation bound needs every b_k in memory: step-by-step kernels only
-    if (step_norms && path == CHEB_PATH_AUTO && C.n <= kPlainMaxF32) path = CHEB_PATH_PLAIN;
     const int small_max = C.prec == 0 ? kSmallMaxF32 : kSmallMaxF64;
+    // the evaluation bound needs every b_k in memory: the plain kernel replaces the
+    // whole-run shared-memory kernel
+    if (step_norms && path == CHEB_PATH_AUTO && C.n <= small_max) path = CHEB_PATH_PLAIN;
+    // a choice measured by the autotuner replaces the built-in AUTO rule
+    if (path == CHEB_PATH_AUTO && C.n > small_max) {
+        const int tp = tuned_auto_path(C.prec, C.n);
+        if (tp == CHEB_PATH_PLAIN || tp == CHEB_PATH_FUSED) path = tp;
+    }
     if (path == CHEB_PATH_AUTO && C.n <= small_max) {
         static_assert(sizeof(std::complex<double>) == 2 * sizeof(double), "layout");
         CUDA_TRY(cudaMemcpyAsync(C.ws + C.L.coef, c.data(), c.size() * sizeof(std::complex<double>),
@@ -168,20 +176,33 @@ cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::c
     bool fused = false;
     if (path == CHEB_PATH_FUSED || (path == CHEB_PATH_AUTO && C.n > kPlainMaxF32))
         fused = fused_supported(C.n, C.prec);
-    if (path == CHEB_PATH_FUSED && !fused) return CHEB_ERR_UNSUPPORTED;
+    // FP64: the float-float fused step (complex128 storage, arithmetic on the FP32 units)
+    bool ff = false;
+    if (C.prec == CHEB_FP64 && (path == CHEB_PATH_FUSED || (path == CHEB_PATH_AUTO && C.n >= kFFAutoMinF64)))
+        ff = ff_supported(C.n);
+    if (path == CHEB_PATH_FUSED && !fused && !ff) return CHEB_ERR_UNSUPPORTED;
     unsigned char* B[2] = {C.ws + C.L.b0, C.ws + C.L.b1};
-    launch_scale(C.prec, N, psi, B[1], c[K].real(), c[K].imag(), C.s);
+    if (ff) {
+        // the run works on float-float vectors: psi is converted in place, and the final
+        // step writes y back as complex128
+        CUDA_TRY(launch_to_ff(N, psi, C.s));
+        CUDA_TRY(launch_ff_scale(N, psi, B[1], c[K].real(), c[K].imag(), C.s));
+    } else {
+        launch_scale(C.prec, N, psi, B[1], c[K].real(), c[K].imag(), C.s);
+    }
     auto norms = [&](int k, const void* bk) {
         // ||b_k||^2, and ||c_{k-2} psi - b_k||^2 while b_k is still the b_{k+2} of step k - 2
         if (!step_norms) return;
         const bool wc = k >= 2;
         const std::complex<double> cc = wc ? c[k - 2] : std::complex<double>(0.0, 0.0);
-        launch_step_norms(C.prec, N, bk, psi, cc.real(), cc.imag(), wc ? 1 : 0, step_norms + 2 * k,
+        const int fmt = (ff && k > 0) ? kFormatFF : C.prec;
+        launch_step_norms(fmt, N, bk, psi, cc.real(), cc.imag(), wc ? 1 : 0, step_norms + 2 * k,
                           wc ? step_norms + 2 * (k - 2) + 1 : nullptr, C.s);
     };
     norms(K, B[1]);
     FusedPlan plan;
     if (fused) plan = fused_plan(C.n, C.prec);
+    if (ff) plan = ff_plan(C.n);
     int cur = 1;
     for (int k = K - 1; k >= 0; --k) {
         StepArgs a;
@@ -200,7 +221,9 @@ cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::c
         a.scale = (k == 0) ? 1.0 : 2.0;
         a.sgn = (k == K - 1) ? 0.0 : -1.0;
         a.g = g;
-        if (fused) {
+        if (ff) {
+            if (launch_step_ff(plan, a, C.flags(), k == 0, C.s) != cudaSuccess) return CHEB_ERR_CUDA;
+        } else if (fused) {
             cudaError_t e = launch_step_fused(plan, a, C.ws + C.L.coef + (size_t)(kMaxK + 1) * 2 * sizeof(double),
                                               C.flags(), C.s);
             if (e != cudaSuccess) return CHEB_ERR_CUDA;
@@ -241,11 +264,20 @@ cheb_status_t slice_coefficients(double t, double c, double r, double tol, int m
     return CHEB_OK;
 }
 
-// Unit roundoff of the arithmetic that a Clenshaw run of (prec, path) uses: FP32
-// (operator constants in float-float, flip sums in FP32) or native FP64.
-double unit_roundoff(int prec, int path) {
-    (void)path;
-    return prec == CHEB_FP32 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+// Unit roundoff of the arithmetic that a Clenshaw run of (n, prec, path) uses: FP32
+// (operator constants in float-float, flip sums in FP32), the float-float FP64 path,
+// or native FP64.
+double unit_roundoff(int n, int prec, int path) {
+    if (prec == CHEB_FP32) return std::ldexp(1.0, -24);
+    if (path == CHEB_PATH_AUTO && n > kSmallMaxF64) {
+        const int tp = tuned_auto_path(prec, n);
+        if (tp == CHEB_PATH_PLAIN || tp == CHEB_PATH_FUSED) path = tp;
+    }
+    // float-float (about 48 significant bits): 2^-47 bounds the relative error of its
+    // additions and products
+    if (path == CHEB_PATH_FUSED || (path == CHEB_PATH_AUTO && n >= kFFAutoMinF64 && ff_supported(n)))
+        return std::ldexp(1.0, -47);
+    return std::ldexp(1.0, -53);
 }
 
 // The a-posteriori evaluation bound of Sec. II.B.3 for one Clenshaw run:
@@ -256,7 +288,7 @@ double unit_roundoff(int prec, int path) {
 double evaluation_bound(int n, int prec, int path, const std::vector<std::complex<double>>& c,
                         const std::vector<double>& norms2, double psi_norm) {
     const int K = (int)c.size() - 1;
-    const double u = unit_roundoff(prec, path);
+    const double u = unit_roundoff(n, prec, path);
     const double d = n + 1.0;
     const double gd = d * u / (1.0 - d * u);
     double sum = 0.0;
@@ -457,6 +489,18 @@ cheb_status_t cheb_poly_apply(int n, const double* h, const double* J, double ga
 
 cheb_status_t cheb_set_fused_split(int n, int l, int h) {
     return fused_set_split(n, l, h) ? CHEB_OK : CHEB_ERR_INVALID_ARG;
+}
+
+cheb_status_t cheb_set_fused_split_fp64(int n, int l, int h) {
+    return ff_set_split(n, l, h) ? CHEB_OK : CHEB_ERR_INVALID_ARG;
+}
+
+cheb_status_t cheb_get_fused_split_fp64(int n, int* l, int* h) {
+    if (!l || !h || !ff_supported(n)) return CHEB_ERR_INVALID_ARG;
+    FusedPlan p = ff_plan(n);
+    *l = p.l;
+    *h = p.h;
+    return CHEB_OK;
 }
 
 cheb_status_t cheb_set_fused_blocking(int on) {

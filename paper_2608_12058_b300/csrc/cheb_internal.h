@@ -24,6 +24,8 @@ constexpr int kMaxK = 1 << 16;        // coefficient table length per time slice
 constexpr int kSmallMaxF32 = 13;      // whole-vector-in-SMEM kernel limits
 constexpr int kSmallMaxF64 = 12;
 constexpr int kPlainMaxF32 = 19;      // AUTO uses the one-pass kernel up to this n (FP32)
+constexpr int kFFAutoMinF64 = 17;     // AUTO uses the float-float fused step from this n (FP64)
+constexpr int kFormatFF = 2;          // vector format code of float-float vectors (kernels)
 constexpr int kRedBlocks = 1184;      // partial-sum slots for two-stage reductions (8 x 148)
 // Largest fixed-point scale for the FP32 kernels: with |Dt| <= 1 the high 32-bit
 // word of a 2^-56 fixed-point value fits a float mantissa exactly.

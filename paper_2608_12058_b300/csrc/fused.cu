@@ -521,14 +521,6 @@ __device__ __forceinline__ int64_t strided_base_rb(const StridedArgs& a, int64_t
     return tlo * (1 << (RB - 1)) + (thi << (a.lo + H - 1));
 }
 
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-        : "memory");
-}
 
 template <int H, int RB, bool C>
 __global__ void __launch_bounds__(kLowThreads, 1)
@@ -1113,6 +1105,8 @@ __global__ void __launch_bounds__(kMixedThreads, 1)
     }
 }
 
+}  // namespace
+
 int g_num_sms = 0;
 std::mutex g_mu;
 
@@ -1169,6 +1163,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     }
     return fn;
 }
+
+namespace {
 
 // Tensor maps of a strided pass over bits [lo, lo + H) with rows of 2^RB amplitudes:
 // b_{k+1} in boxes of `box` rows of the range, the slot in 8 KB chunks of 2^(10-RB)
@@ -1311,6 +1307,45 @@ size_t fused_scratch_bytes(int n, int prec) {
 static int g_blocking = 0;
 void fused_set_blocking(int on) { g_blocking = on ? 1 : 0; }
 int fused_get_blocking() { return g_blocking; }
+
+// Per-n choices of the autotuner (-1: not tuned): the blocked tail, and the AUTO path.
+static int g_block_n[kMaxQubits + 1];
+static int g_auto_path[2][kMaxQubits + 1];
+static bool g_tuned_init = false;
+
+static void tuned_init() {
+    if (!g_tuned_init) {
+        for (int i = 0; i <= kMaxQubits; ++i) g_block_n[i] = g_auto_path[0][i] = g_auto_path[1][i] = -1;
+        g_tuned_init = true;
+    }
+}
+
+void tuned_set(int prec, int n, int path, int blocking) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    tuned_init();
+    if (n < 0 || n > kMaxQubits || prec < 0 || prec > 1) return;
+    g_auto_path[prec][n] = path;
+    if (prec == 0) g_block_n[n] = blocking;
+}
+
+int tuned_auto_path(int prec, int n) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    tuned_init();
+    if (n < 0 || n > kMaxQubits || prec < 0 || prec > 1) return -1;
+    return g_auto_path[prec][n];
+}
+
+static int blocking_for(int n) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    tuned_init();
+    return (n >= 0 && n <= kMaxQubits && g_block_n[n] >= 0) ? g_block_n[n] : g_blocking;
+}
+
+bool fused_blocking_eligible(const FusedPlan& plan) {
+    const int lastp = plan.npass - 1;
+    return plan.prec == 0 && plan.n >= kMixedMinN && plan.npass >= 2 && plan.l <= 1 && plan.hb[lastp] >= 6 &&
+           plan.hb[lastp] <= kMaxStrided;
+}
 void fused_set_compensated(int on) { g_comp = on ? 1 : 0; }
 int fused_get_compensated() { return g_comp; }
 
@@ -1404,7 +1439,7 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void* sc
     // and the plan allows it (an earlier strided pass, at most one L2 partner bit, a
     // last range of 6..9 bits, scratch for the counters).
     const int lastp = plan.npass - 1;
-    const bool mixed = g_blocking && scratch != nullptr && s.n >= kMixedMinN && plan.npass >= 2 && plan.l <= 1 &&
+    const bool mixed = blocking_for(s.n) && scratch != nullptr && s.n >= kMixedMinN && plan.npass >= 2 && plan.l <= 1 &&
                        plan.hb[lastp] >= 6 && plan.hb[lastp] <= kMaxStrided && s.out != s.b1;
     const int nsep = mixed ? lastp : plan.npass;  // strided passes launched on their own
     for (int k = 0; k < nsep; ++k) {

@@ -1,5 +1,7 @@
 // Fused shared-memory Clenshaw step for the FP32 path (fused.cu).
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 
@@ -25,9 +27,16 @@ struct FusedPlan {
 };
 
 size_t fused_scratch_bytes(int n, int prec);
+// Number of SMs of the current device (cached).
+int num_sms();
 // L2-blocked step tail (the last strided pass and the low pass in one launch): on/off.
 void fused_set_blocking(int on);
 int fused_get_blocking();
+// Choices of the autotuner: per (prec, n) the AUTO path (-1 = built-in rule) and, for
+// FP32, the blocked tail (-1 = the process-wide switch).
+void tuned_set(int prec, int n, int path, int blocking);
+int tuned_auto_path(int prec, int n);
+bool fused_blocking_eligible(const FusedPlan& plan);
 // Kahan-compensated flip sums in the fused FP32 passes: on/off (process-wide).
 void fused_set_compensated(int on);
 int fused_get_compensated();
@@ -36,6 +45,8 @@ bool fused_split_valid(int n, int l, int h);
 bool fused_set_split(int n, int l, int h);
 bool fused_supported(int n, int prec);
 FusedPlan fused_plan(int n, int prec);
+// cuTensorMapEncodeTiled through the runtime's driver entry point (null if unavailable).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& a, void* scratch, int* flags,
                               cudaStream_t s);
 

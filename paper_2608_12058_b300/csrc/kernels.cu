@@ -510,11 +510,47 @@ __global__ void __launch_bounds__(256) k_step_norms(int64_t N, const typename Cx
     }
 }
 
+// The same for float-float vectors (float4: re_hi, im_hi, re_lo, im_lo).
+__global__ void __launch_bounds__(256) k_step_norms_ff(int64_t N, const float4* __restrict__ b,
+                                                       const float4* __restrict__ psi, double cr, double ci,
+                                                       int want_c, double* out_b, double* out_c) {
+    __shared__ double sb[256], sc[256];
+    double ab = 0.0, ac = 0.0;
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N;
+         z += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = b[z];
+        const double vx = (double)v.x + (double)v.z, vy = (double)v.y + (double)v.w;
+        ab += vx * vx + vy * vy;
+        if (want_c) {
+            const float4 p = psi[z];
+            const double px = (double)p.x + (double)p.z, py = (double)p.y + (double)p.w;
+            const double dx = cr * px - ci * py - vx, dy = cr * py + ci * px - vy;
+            ac += dx * dx + dy * dy;
+        }
+    }
+    sb[threadIdx.x] = ab;
+    sc[threadIdx.x] = ac;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sb[threadIdx.x] += sb[threadIdx.x + w];
+            sc[threadIdx.x] += sc[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(out_b, sb[0]);
+        if (want_c) atomicAdd(out_c, sc[0]);
+    }
+}
+
 void launch_step_norms(int prec, int64_t N, const void* b, const void* psi, double cr, double ci, int want_c,
                        double* out_b, double* out_c, cudaStream_t s) {
     const unsigned nb = grid_for(N, 256, kRedBlocks);
     note_launch(kKindReduce);
-    if (prec == 0)
+    if (prec == kFormatFF)
+        k_step_norms_ff<<<nb, 256, 0, s>>>(N, (const float4*)b, (const float4*)psi, cr, ci, want_c, out_b, out_c);
+    else if (prec == 0)
         k_step_norms<float><<<nb, 256, 0, s>>>(N, (const float2*)b, (const float2*)psi, cr, ci, want_c, out_b,
                                                out_c);
     else

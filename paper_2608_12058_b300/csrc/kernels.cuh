@@ -77,6 +77,7 @@ int cluster_slice_bits(int prec);
 cudaError_t launch_cluster_batched(int prec, int n, int count, const SmallDesc* descs, cudaStream_t s);
 // Evaluation-bound norms (Sec. II.B.3): *out_b += ||b||^2 and, if want_c,
 // *out_c += ||(cr + i ci) psi - b||^2, both FP64 (atomic adds; zero them first).
+// prec: 0 complex64, 1 complex128, kFormatFF float-float vectors.
 void launch_step_norms(int prec, int64_t N, const void* b, const void* psi, double cr, double ci, int want_c,
                        double* out_b, double* out_c, cudaStream_t s);
 void launch_norm_energy(int prec, int n, int M, int Q, const int64_t* tiles, const int64_t* elow,

@@ -4,6 +4,8 @@
 // records kFlagTimeout in the status word, and returns false; the kernel then lets
 // its issued copies land and exits, and the host reports CHEB_ERR_TIMEOUT.
 #pragma once
+#include <cuda.h>
+
 #include <cstdint>
 
 #include "cheb_internal.h"
@@ -79,6 +81,16 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, int* 
             return;
         }
     }
+}
+
+// Tiled bulk tensor copy of a 4-D box into shared memory, completing on an mbarrier.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
 }
 
 }  // namespace cheb

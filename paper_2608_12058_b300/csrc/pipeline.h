@@ -51,6 +51,8 @@ cheb_status_t bounds_impl(Ctx& C, const double* h, const double* J, double* emin
 // Sec. II.B.3; the run then uses the step-by-step kernels (b_k must be visible).
 cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::complex<double>>& c, int Q,
                            double g, double* step_norms = nullptr);
+// Applies the autotuner cache named by CHEB_AUTOTUNE_CACHE (once per process).
+void autotune_cache_once();
 // Synchronises and maps the device status word to a status code.
 cheb_status_t read_flags(const Ctx& C);
 // Coefficients of exp(-i a x) * exp(-i ts c) for one slice, slicing t automatically

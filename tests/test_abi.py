@@ -123,6 +123,56 @@ def test_fused_split_table():
     assert api.get_fused_split(20) == (0, 9)
 
 
+def test_fp64_fused_split_table():
+    """The float-float FP64 step: 10 tile bits + l partner bits + h strided bits; each pass
+    6..9 bits (5 allowed on 256-byte rows, i.e. starting at bit 17 or above); n = 30 runs
+    three partner bits and passes of 9 + 8 bits (the top one on wide rows)."""
+    for n in range(11, 34):
+        l, h = api.get_fused_split_fp64(n)
+        assert 10 + l + h == n and 0 <= l <= 5 and (h == 0 or h >= 5), (n, l, h)
+        for lo, hb in _passes(10 + l, h):
+            assert 6 <= hb <= 9 or (hb == 5 and lo >= 17), (n, lo, hb)
+    assert api.get_fused_split_fp64(30) == (3, 17)
+    assert api.get_fused_split_fp64(24) == (0, 14)
+    with pytest.raises(_lib.ChebError):
+        api.set_fused_split_fp64(20, 0, 10)  # 5 + 5 below bit 17 needs 6-bit passes
+    with pytest.raises(_lib.ChebError):
+        api.set_fused_split_fp64(20, 3, 6)  # 10 + 3 + 6 != 20
+    with pytest.raises(_lib.ChebError):
+        api.set_fused_split_fp64(10, 0, 0)
+    api.set_fused_split_fp64(20, 4, 6)
+    assert api.get_fused_split_fp64(20) == (4, 6)
+    api.set_fused_split_fp64(20, -1)
+    assert api.get_fused_split_fp64(20) == (1, 9)
+
+
+def test_autotune_cache_file(tmp_path):
+    """cheb_autotune_load applies the cache lines recorded for the named device (later
+    lines win) and skips other devices and invalid entries; cheb_autotune_reset drops
+    every choice."""
+    f = tmp_path / "tune.txt"
+    f.write_text("\n".join([
+        "cheb-tune-1 TestDev 0 26 2 2 13 0 0.9",
+        "cheb-tune-1 TestDev 0 26 2 1 14 1 0.8",     # later line for the same n wins
+        "cheb-tune-1 OtherDev 0 27 2 3 13 0 0.1",    # another device
+        "cheb-tune-1 TestDev 0 28 2 9 8 0 0.1",      # impossible split: skipped
+        "cheb-tune-1 TestDev 1 24 2 5 9 0 2.0",      # float-float split
+        "garbage line",
+    ]) + "\n")
+    try:
+        assert api.autotune_load(str(f), "TestDev") == 3
+        assert api.get_fused_split(26) == (1, 14)
+        assert api.get_fused_split(27) == (0, 16)
+        assert api.get_fused_split(28) == (0, 17)
+        assert api.get_fused_split_fp64(24) == (5, 9)
+    finally:
+        api.autotune_reset()
+    assert api.get_fused_split(26) == (0, 15)
+    assert api.get_fused_split_fp64(24) == (0, 14)
+    with pytest.raises(_lib.ChebError):
+        api.autotune_load(str(tmp_path / "missing.txt"), "TestDev")
+
+
 def _passes(lo, h):
     """Near-equal strided passes of at most 9 bits above bit lo (largest first)."""
     if h == 0:
