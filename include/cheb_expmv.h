@@ -304,11 +304,23 @@ cheb_status_t cheb_magnus4_adaptive(int n, const double* h, const double* J, dou
  *   workspace: cheb_batched_workspace_bytes(B, n, precision) bytes (256-aligned).
  *   infos:    nullable HOST array of B cheb_info_t; requesting it synchronises.
  * The spectral bounds of all instances need one synchronisation of the stream.
- * Instances with n <= 13 (FP32) or n <= 12 (FP64) run together in one launch;
- * larger ones run on an internal pool of streams joined back into `stream`.
+ * FP32 instances run in one persistent launch (cheb_set_batch_persistent); otherwise
+ * instances with n <= 13 (FP32) or n <= 12 (FP64) run together in one launch, the next
+ * four sizes on thread-block clusters, larger ones on an internal pool of streams
+ * joined back into `stream`.
  * Errors: as cheb_expmv.
  */
 size_t cheb_batched_workspace_bytes(int B, const int* n, cheb_precision_t precision);
+/* FP32 batches run as one persistent cooperative launch: one CTA per SM takes work slots
+ * from a counter, longest instance first; n <= 13 runs whole in one CTA's shared memory,
+ * larger n on a team of 1..32 CTAs (growing with n) that steps through the Clenshaw
+ * recurrence with the vectors in L2 and a bounded team barrier after every pass (a wait
+ * that runs out reports CHEB_ERR_TIMEOUT). on = 1 (default) runs two CTAs of 512
+ * threads per SM, on = 2 one CTA per SM with twice the registers per thread; on = 0
+ * selects the per-size launches and the stream pool described above (process-wide;
+ * FP64 batches always use them). */
+cheb_status_t cheb_set_batch_persistent(int on);
+int cheb_get_batch_persistent(void);
 cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* offsets, const double* h_cat,
                                  const double* J_cat, const double* gamma, const double* t,
                                  void* psi_cat, cheb_precision_t precision, double tol,

@@ -92,6 +92,8 @@ SIGNATURES = {
     "cheb_magnus4_adaptive": (c_int, [c_int, _dp, _dp, c_double, ctypes.c_void_p, c_void_p, c_int, c_double, c_void_p,
                                       c_int, c_int, c_void_p, c_size_t, c_void_p, _ip, _dp]),
     "cheb_batched_workspace_bytes": (c_size_t, [c_int, _ip, c_int]),
+    "cheb_set_batch_persistent": (c_int, [c_int]),
+    "cheb_get_batch_persistent": (c_int, []),
     "cheb_expmv_batched": (c_int, [c_int, _ip, ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp, _dp, c_void_p, c_int,
                                    c_double, c_int, c_void_p, c_size_t, c_void_p, ctypes.POINTER(Info)]),
     "cheb_adjoint_workspace_bytes": (c_size_t, [c_int, c_int, c_int]),

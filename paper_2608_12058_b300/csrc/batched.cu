@@ -5,11 +5,14 @@
 //
 //  1. Spectral bounds of all instances, one host synchronisation.
 //  2. Host: centre, radius, fixed-point tables and coefficients per instance.
-//  3. Instances small enough for one CTA's shared memory (n <= 13 FP32, <= 12
-//     FP64) run in a single launch, one CTA each; the next four sizes run whole on
-//     a thread-block cluster each (cluster.cu), one launch per size. Larger
-//     instances run their Clenshaw step loops on a pool of streams, longest first,
-//     joined back into the caller's stream.
+//  3. FP32: every instance runs in one persistent cooperative launch (batch_team.cu):
+//     CTAs take work slots longest first, small instances whole in one CTA's shared
+//     memory, larger ones on teams of CTAs with bounded team barriers.
+//     FP64 (or with cheb_set_batch_persistent(0)): instances small enough for one
+//     CTA's shared memory (n <= 13 FP32, <= 12 FP64) run in a single launch, one CTA
+//     each; the next four sizes run whole on a thread-block cluster each (cluster.cu),
+//     one launch per size. Larger instances run their Clenshaw step loops on a pool
+//     of streams, longest first, joined back into the caller's stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +22,7 @@
 #include <numeric>
 #include <vector>
 
+#include "batch_team.cuh"
 #include "kernels.cuh"
 #include "pipeline.h"
 
@@ -47,6 +51,10 @@ cheb_status_t stream_pool(cudaStream_t** out) {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// FP32 batches run as one persistent launch (batch_team.cu) with two CTAs per SM (1),
+// with one CTA per SM (2), or as per-size launches (0).
+int g_persistent = 1;
+
 // An event destroyed when the call returns, on every path.
 struct ScopedEvent {
     cudaEvent_t e = nullptr;
@@ -60,6 +68,8 @@ struct BatchLayout {
     size_t res_f64 = 0;   // 2 double per instance: norm^2, energy
     size_t res_flag = 0;  // 1 int per instance
     size_t descs = 0;     // SmallDesc per instance
+    size_t team = 0;      // TeamInst per instance (persistent launch)
+    size_t bars = 0;      // team barrier counter per instance, then the slot counter
     std::vector<size_t> inst;
     size_t total = 0;
 };
@@ -75,6 +85,10 @@ bool batch_layout(int B, const int* n, int prec, BatchLayout& L) {
     off = align256(off + sizeof(int) * (size_t)B);
     L.descs = off;
     off = align256(off + sizeof(SmallDesc) * (size_t)B);
+    L.team = off;
+    off = align256(off + sizeof(TeamInst) * (size_t)B);
+    L.bars = off;
+    off = align256(off + sizeof(unsigned) * ((size_t)B + 1));
     L.inst.resize(B);
     for (int i = 0; i < B; ++i) {
         if (n[i] < 1 || n[i] > kMaxQubits) return false;
@@ -89,6 +103,14 @@ bool batch_layout(int B, const int* n, int prec, BatchLayout& L) {
 }  // namespace cheb
 
 using namespace cheb;
+
+extern "C" cheb_status_t cheb_set_batch_persistent(int on) {
+    if (on < 0 || on > 2) return CHEB_ERR_INVALID_ARG;
+    g_persistent = on;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_get_batch_persistent(void) { return g_persistent; }
 
 extern "C" size_t cheb_batched_workspace_bytes(int B, const int* n, cheb_precision_t precision) {
     BatchLayout L;
@@ -149,6 +171,7 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
         int Q, K, slices;
         std::vector<std::complex<double>> coef;
         bool small;
+        bool team = false;
     };
     std::vector<Inst> in(B);
     std::vector<SmallDesc> descs;
@@ -176,6 +199,14 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
         if (st != CHEB_OK) return st;
         st = slice_coefficients(t[i], x.c, x.r, tol, method, 0, x.coef, &x.K, &x.slices, &x.err);
         if (st != CHEB_OK) return st;
+        if (g_persistent && precision == CHEB_FP32 && x.slices == 1 && x.K > 0) {
+            // every instance goes into the persistent launch below
+            CUDA_TRY(cudaMemcpyAsync(C.ws + C.L.coef, x.coef.data(), x.coef.size() * sizeof(std::complex<double>),
+                                     cudaMemcpyHostToDevice, s0));
+            x.small = true;
+            x.team = true;
+            continue;
+        }
         x.small = n[i] <= small_lim && x.slices == 1 && x.K > 0;
         const bool clus = !x.small && n[i] > cl_sb && n[i] <= cl_lim && x.slices == 1 && x.K > 0;
         if (x.small || clus) {
@@ -209,6 +240,49 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
     CUDA_TRY(cudaEventCreateWithFlags(&fork_ev.e, cudaEventDisableTiming));
     CUDA_TRY(cudaEventRecord(fork_ev.e, s0));
     const cudaEvent_t fork = fork_ev.e;
+    // 3. FP32: every instance in one persistent launch, longest first
+    {
+        std::vector<int> tl;
+        for (int i = 0; i < B; ++i)
+            if (in[i].team) tl.push_back(i);
+        if (!tl.empty()) {
+            std::stable_sort(tl.begin(), tl.end(), [&](int a, int b) {
+                return std::ldexp((double)in[a].K, n[a]) > std::ldexp((double)in[b].K, n[b]);
+            });
+            std::vector<TeamInst> ti(tl.size());
+            unsigned* bars = (unsigned*)(ws + BL.bars);
+            int slots = 0;
+            for (size_t q = 0; q < tl.size(); ++q) {
+                const int i = tl[q];
+                Ctx C = ctx(i, s0);
+                TeamInst& d = ti[q];
+                d.n = n[i];
+                d.K = in[i].K;
+                d.Q = in[i].Q;
+                d.team = team_size(n[i]);
+                team_split(n[i], &d.l, &d.H);
+                d.first_slot = slots;
+                d.pad = 0;
+                d.g = in[i].g;
+                d.coef = (const double2*)(C.ws + C.L.coef);
+                d.tiles = C.tiles();
+                d.elow = C.elow();
+                d.psi = (float4*)psi_i(i);
+                d.v0 = (float4*)(C.ws + C.L.b0);
+                d.v1 = (float4*)(C.ws + C.L.b1);
+                d.bar = bars + q;
+                slots += std::max(d.team, 1);
+            }
+            CUDA_TRY(cudaMemcpyAsync(ws + BL.team, ti.data(), ti.size() * sizeof(TeamInst), cudaMemcpyHostToDevice,
+                                     s0));
+            CUDA_TRY(cudaMemsetAsync(bars, 0, sizeof(unsigned) * ((size_t)B + 1), s0));
+            // the status word of the first instance's workspace collects timeouts
+            int* flags = ctx(tl[0], s0).flags();
+            const cudaError_t e = launch_batch_team((const TeamInst*)(ws + BL.team), (int)ti.size(), slots, bars + B,
+                                                    flags, g_persistent == 2 ? 1 : 2, s0);
+            if (e != cudaSuccess) return CHEB_ERR_CUDA;
+        }
+    }
     // 3a. all small instances in one launch, mid-size ones in one cluster launch per size
     // (the descriptor region holds B entries: small ones first, then the clustered)
     size_t dpos = 0;

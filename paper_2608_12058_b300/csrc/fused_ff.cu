@@ -101,9 +101,6 @@ __device__ __forceinline__ FF2 ff_add(FF2 a, FF2 b) {
     return renorm(s, ad(e, ad(a.l, b.l)));
 }
 
-__device__ __forceinline__ FF2 ff_neg(FF2 a) { return {ng(a.h), ng(a.l)}; }
-__device__ __forceinline__ FF2 ff_twice(FF2 a) { return {ad(a.h, a.h), ad(a.l, a.l)}; }
-
 // (ah + al) x: the leading product exactly (FMA error), the rest below 2^-48 relative.
 __device__ __forceinline__ FF2 ff_mul2(float ah, float al, FF2 x) {
     const float2 p = mu(dp(ah), x.h);
@@ -111,32 +108,6 @@ __device__ __forceinline__ FF2 ff_mul2(float ah, float al, FF2 x) {
     e = fm(dp(ah), x.l, e);
     e = fm(dp(al), x.h, e);
     return renorm(p, e);
-}
-
-// (a2 + a1 + a0) x for a normalised float triple (|a1| <= ulp(a2), |a0| <= ulp(a1)).
-__device__ __forceinline__ FF2 ff_mul3(float a2, float a1, float a0, FF2 x) {
-    const float2 p = mu(dp(a2), x.h);
-    float2 e = fm(dp(a2), x.h, ng(p));
-    e = fm(dp(a2), x.l, e);
-    e = fm(dp(a1), x.h, e);
-    e = fm(dp(a1), x.l, e);
-    e = fm(dp(a0), x.h, e);
-    return renorm(p, e);
-}
-
-// D x for the exact diagonal value D = d2 + d1 + d0 (three 21-bit words of the
-// fixed-point energy, not normalised, so both upper products are taken exactly).
-__device__ __forceinline__ FF2 ff_mul_energy(float d2, float d1, float d0, FF2 x) {
-    const float2 p2 = mu(dp(d2), x.h);
-    const float2 e2 = fm(dp(d2), x.h, ng(p2));
-    const float2 p1 = mu(dp(d1), x.h);
-    const float2 e1 = fm(dp(d1), x.h, ng(p1));
-    float2 s, t;
-    two_sum(p2, p1, s, t);
-    float2 e = ad(ad(e2, e1), t);
-    e = fm(dp(d0), x.h, e);
-    e = fm(dp(__fadd_rn(d2, d1)), x.l, e);
-    return renorm(s, e);
 }
 
 // (cr + i ci) (xr + i xi) with float-float cr, ci: re = cr xr - ci xi, im = cr xi + ci xr.
@@ -155,17 +126,59 @@ __device__ __forceinline__ void energy_words(int64_t e, int Q, float& d2, float&
     d0 = __int2float_rn(w0) * __int_as_float((127 - Q) << 23);
 }
 
-// Flip-sum accumulator: TwoSum chain of the hi parts, every error and lo part in c.
+// Multi-term float-float accumulator (the summation order of Ogita, Rump and Oishi's
+// Sum2): the high parts of the terms go through a TwoSum chain in s, every rounding
+// error and every low part is added into c, and the value s + c is renormalised once.
 struct FFAcc {
     float2 s, c;
     __device__ __forceinline__ void zero() { s = c = f2(0.f, 0.f); }
-    __device__ __forceinline__ void add(float4 v) {
-        float2 e;
-        two_sum(s, f2(v.x, v.y), s, e);
-        c = ad(c, ad(e, f2(v.z, v.w)));
+    __device__ __forceinline__ void start(float2 h, float2 l) {
+        s = h;
+        c = l;
     }
+    __device__ __forceinline__ void add(float2 h, float2 l) {
+        float2 e;
+        two_sum(s, h, s, e);
+        c = ad(c, ad(e, l));
+    }
+    __device__ __forceinline__ void add(float4 v) { add(f2(v.x, v.y), f2(v.z, v.w)); }
     __device__ __forceinline__ FF2 result() const { return renorm(s, c); }
 };
+
+// Adds a * x for a float-float scalar a = ah + al and an unnormalised pair x = xh + xl:
+// the leading product exactly (FMA error) into the chain, the rest as low parts.
+__device__ __forceinline__ void acc_mul2(FFAcc& A, float ah, float al, float2 xh, float2 xl) {
+    const float2 p = mu(dp(ah), xh);
+    float2 e = fm(dp(ah), xh, ng(p));
+    e = fm(dp(ah), xl, e);
+    e = fm(dp(al), xh, e);
+    A.add(p, e);
+}
+
+// Adds (a2 + a1 + a0) x for a normalised float triple.
+__device__ __forceinline__ void acc_mul3(FFAcc& A, float a2, float a1, float a0, float2 xh, float2 xl) {
+    const float2 p = mu(dp(a2), xh);
+    float2 e = fm(dp(a2), xh, ng(p));
+    e = fm(dp(a2), xl, e);
+    e = fm(dp(a1), xh, e);
+    e = fm(dp(a1), xl, e);
+    e = fm(dp(a0), xh, e);
+    A.add(p, e);
+}
+
+// Starts the accumulator with D x for the exact diagonal value D = d2 + d1 + d0 (three
+// 21-bit words, not normalised: both upper products are taken exactly).
+__device__ __forceinline__ void acc_start_energy(FFAcc& A, float d2, float d1, float d0, float2 xh, float2 xl) {
+    const float2 p2 = mu(dp(d2), xh);
+    float2 e = fm(dp(d2), xh, ng(p2));
+    const float2 p1 = mu(dp(d1), xh);
+    const float2 e1 = fm(dp(d1), xh, ng(p1));
+    e = ad(e, e1);
+    e = fm(dp(d0), xh, e);
+    e = fm(dp(__fadd_rn(d2, d1)), xl, e);
+    A.start(p2, e);
+    A.add(p1, f2(0.f, 0.f));
+}
 
 __device__ __forceinline__ int64_t sel(uint32_t bit, int64_t v) { return bit ? -v : v; }
 
@@ -332,6 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_low_ff(const LowFFArgs a) {
         K11 = e_tau - phi9 - phi10 + j910;
     }
     const bool twice = a.scale != 1.f;
+    const float gs2 = twice ? 2.f * a.g2 : a.g2, gs1 = twice ? 2.f * a.g1 : a.g1, gs0 = twice ? 2.f * a.g0 : a.g0;
     int it = 0;
     long long pj = 0;
     for (int64_t T = blockIdx.x; T < a.ntiles; T += gridDim.x, ++it) {
@@ -378,14 +392,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_low_ff(const LowFFArgs a) {
         const float4 q1 = need_slot ? sslot[t + kCons] : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_s[s]);  // this warp is done with the stage
+        // out = scale (D b_{k+1} + g S) + slot_coeff q + c_k psi: every term goes into one
+        // accumulator (scale = 2 is folded into D and g exactly), renormalised once
         auto combine = [&](int64_t e, float4 v, const FFAcc& S, float4 q, float4 ps) -> FF2 {
             float d2, d1, d0;
             energy_words(e, a.Q, d2, d1, d0);
-            FF2 h = ff_add(ff_mul_energy(d2, d1, d0, ld(v)), ff_mul3(a.g2, a.g1, a.g0, S.result()));
-            if (twice) h = ff_twice(h);
-            if (need_slot) h = ff_add(h, a.slot_coeff < 0.f ? ff_neg(ld(q)) : ld(q));
-            if (need_psi) h = ff_add(h, ff_cmul(a.crh, a.crl, a.cih, a.cil, ld(ps)));
-            return h;
+            if (twice) {
+                d2 += d2;
+                d1 += d1;
+                d0 += d0;
+            }
+            FFAcc A;
+            acc_start_energy(A, d2, d1, d0, f2(v.x, v.y), f2(v.z, v.w));
+            acc_mul3(A, gs2, gs1, gs0, S.s, S.c);
+            if (need_slot) {
+                const float2 qh = f2(q.x, q.y), ql = f2(q.z, q.w);
+                if (a.slot_coeff < 0.f)
+                    A.add(ng(qh), ng(ql));
+                else
+                    A.add(qh, ql);
+            }
+            if (need_psi) {
+                acc_mul2(A, a.crh, a.crl, f2(ps.x, ps.y), f2(ps.z, ps.w));
+                acc_mul2(A, a.cih, a.cil, f2(-ps.y, ps.x), f2(-ps.w, ps.z));  // c_im (i psi)
+            }
+            return A.result();
         };
         const FF2 o0 = combine(e0, v0, S0, q0, ps0);
         const FF2 o1 = combine(e1, v1, S1, q1, ps1);
@@ -525,7 +556,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int j = 0; j < Cfg::kRB; ++j) S.add(tile[((rlo ^ (1 << j)) | (p << Cfg::kRB)) * Cfg::kRowF4 + u]);
 #pragma unroll
             for (int b = 1; b < Cfg::kP; b <<= 1) S.add(tile[(rlo | ((p ^ b) << Cfg::kRB)) * Cfg::kRowF4 + u]);
-            FF2 q = ff_mul3(a.g2, a.g1, a.g0, S.result());
+            // q = g S + sgn slot in one accumulator, renormalised once
+            FFAcc A;
+            A.zero();
             if (need_slot) {
                 const int c = it * Cfg::kP + p, r = c % Cfg::kSR;
                 if (!mbar_wait(&sfull[r], (c / Cfg::kSR) & 1, a.flags, abort)) {
@@ -535,9 +568,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float4 w = ((const float4*)(ring + (size_t)r * Cfg::kChunkBytes))[rlo * Cfg::kRowF4 + u];
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sempty[r]);
-                q = ff_add(q, a.sgn < 0.f ? ff_neg(ld(w)) : ld(w));
+                if (a.sgn < 0.f)
+                    A.start(f2(-w.x, -w.y), f2(-w.z, -w.w));
+                else
+                    A.start(f2(w.x, w.y), f2(w.z, w.w));
             }
-            a.slot[base + (rlo | (p << Cfg::kRB)) * row_stride + u] = pk(q);
+            acc_mul3(A, a.g2, a.g1, a.g0, S.s, S.c);
+            a.slot[base + (rlo | (p << Cfg::kRB)) * row_stride + u] = pk(A.result());
         }
         if (!ok) break;
         __syncwarp();
@@ -556,15 +593,10 @@ __global__ void k_to_ff(int64_t N, double2* psi) {
     }
 }
 
-// dst = c * src (float-float in and out; the product in FP64).
-__global__ void k_ff_scale(int64_t N, const float4* src, float4* dst, double cr, double ci) {
-    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x) {
-        const float4 v = src[z];
-        const double xr = (double)v.x + (double)v.z, xi = (double)v.y + (double)v.w;
-        const double yr = cr * xr - ci * xi, yi = cr * xi + ci * xr;
-        const float rh = __double2float_rn(yr), ih = __double2float_rn(yi);
-        dst[z] = make_float4(rh, ih, __double2float_rn(yr - (double)rh), __double2float_rn(yi - (double)ih));
-    }
+// dst = c * src for float-float vectors, c = (crh + crl) + i (cih + cil).
+__global__ void k_ff_scale(int64_t N, const float4* src, float4* dst, float crh, float crl, float cih, float cil) {
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < N; z += (int64_t)gridDim.x * blockDim.x)
+        dst[z] = pk(ff_cmul(crh, crl, cih, cil, ld(src[z])));
 }
 
 unsigned grid_1d(int64_t N) {
@@ -753,8 +785,11 @@ cudaError_t launch_to_ff(int64_t N, void* psi, cudaStream_t s) {
 }
 
 cudaError_t launch_ff_scale(int64_t N, const void* src, void* dst, double cr, double ci, cudaStream_t s) {
+    float crh, crl, cih, cil;
+    split2(cr, crh, crl);
+    split2(ci, cih, cil);
     note_launch(kKindScale);
-    k_ff_scale<<<grid_1d(N), 256, 0, s>>>(N, (const float4*)src, (float4*)dst, cr, ci);
+    k_ff_scale<<<grid_1d(N), 256, 0, s>>>(N, (const float4*)src, (float4*)dst, crh, crl, cih, cil);
     return cudaGetLastError();
 }
 

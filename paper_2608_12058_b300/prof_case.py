@@ -10,6 +10,9 @@
         times STEPS fused steps at n = N (default split) with the separate launches and
         with the L2-blocked step tail, twice each (CUDA events around the call, per-kind
         event timing from the library), and prints ms per step and per launch.
+    python -m paper_2608_12058_b300.prof_case ff N L H [STEPS]
+        STEPS float-float fused steps of the FP64 path (complex128 states) at n = N with
+        the split (L, H) (kernel names k_low_ff and k_strided_ff).
     python -m paper_2608_12058_b300.prof_case adjoint N S
         the first S segments of the anneal schedule at n = N (complex64): forward with
         segment-start states, energy gradient, full reverse pass (k_adj_acc_f32x2,
@@ -39,6 +42,28 @@ def fused_steps(n, l, h, steps, blocking=False):
     coef = (rng.standard_normal(steps + 1) + 1j * rng.standard_normal(steps + 1)) / (4 * steps)
     api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef, x, path="fused")
     torch.cuda.synchronize()
+    nrm = float(torch.linalg.vector_norm(x))
+    assert np.isfinite(nrm)
+    print("ok", nrm)
+
+
+def ff_steps(n, l, h, steps):
+    """STEPS float-float fused steps of the FP64 path at n with the split (l, h)."""
+    import torch
+
+    from . import api
+    from . import inputs as I
+
+    c = I.config_family(n, 1.0, 1.0, 0, "uniform")
+    x = torch.full((1 << n,), 2 ** (-n / 2), dtype=torch.complex128, device="cuda")
+    api.set_fused_split_fp64(n, l, h)
+    rng = np.random.default_rng(0)
+    coef = (rng.standard_normal(steps + 1) + 1j * rng.standard_normal(steps + 1)) / (4 * steps)
+    try:
+        api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef, x, path="fused")
+        torch.cuda.synchronize()
+    finally:
+        api.set_fused_split_fp64(n, -1)
     nrm = float(torch.linalg.vector_norm(x))
     assert np.isfinite(nrm)
     print("ok", nrm)
@@ -130,6 +155,9 @@ def main(argv):
         cluster(int(argv[1]), int(argv[2]))
     elif argv[0] == "compare":
         compare(int(argv[1]), int(argv[2]) if len(argv) > 2 else 40)
+    elif argv[0] == "ff":
+        n, l, h = int(argv[1]), int(argv[2]), int(argv[3])
+        ff_steps(n, l, h, int(argv[4]) if len(argv) > 4 else 6)
     elif argv[0] == "tail":
         n, l, h = int(argv[1]), int(argv[2]), int(argv[3])
         fused_steps(n, l, h, int(argv[4]) if len(argv) > 4 else 6, blocking=True)

@@ -21,16 +21,19 @@ def _batch(ns, seed):
     return hs, Js, np.array(gs), np.array(ts)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_mixed_batch_matches_oracle(cuda_lib, oracle, prec):
+@pytest.mark.parametrize("prec,persistent", [("fp64", False), ("fp32", True), ("fp32", False)])
+def test_mixed_batch_matches_oracle(cuda_lib, oracle, prec, persistent):
     import torch
 
     from paper_2608_12058_b300 import api
 
-    # sizes of every path: one CTA per instance (n <= 13 FP32, <= 12 FP64), one
+    # sizes of every path. Persistent launch (FP32): one CTA per instance up to n = 13,
+    # teams of 1..32 CTAs above (n = 14, 15 without a strided pass, n >= 16 with one).
+    # Per-size launches: one CTA per instance (n <= 13 FP32, <= 12 FP64), one
     # thread-block cluster per instance (n = 14..17 FP32, 13..16 FP64; repeated sizes
     # share a launch), step kernels on the stream pool (larger)
-    ns = [1, 3, 8, 12, 13, 14, 16, 9, 15, 12, 17, 14, 17]
+    ns = [1, 3, 8, 12, 13, 14, 16, 9, 15, 12, 17, 14, 17, 18, 19, 20, 18]
+    api.set_batch_persistent(persistent)
     hs, Js, gs, ts = _batch(ns, 3)
     offs, total = api.batch_offsets(ns)
     tol = 1e-12 if prec == "fp64" else 2.0 ** -23
@@ -40,7 +43,10 @@ def test_mixed_batch_matches_oracle(cuda_lib, oracle, prec):
         cat[o:o + s.shape[0]] = s
     dt = torch.complex64 if prec == "fp32" else torch.complex128
     x = torch.from_numpy(cat).to(dt).cuda()
-    infos = api.expmv_batched(ns, hs, Js, gs, ts, x, tol=tol)
+    try:
+        infos = api.expmv_batched(ns, hs, Js, gs, ts, x, tol=tol)
+    finally:
+        api.set_batch_persistent(True)
     y = x.cpu().numpy().astype(np.complex128)
     for i, n in enumerate(ns):
         ref, oinfo = oracle.expmv(hs[i], Js[i], gs[i], ts[i], states[i], tol)
@@ -66,8 +72,13 @@ def test_full_512_instance_batch_sampled(cuda_lib, oracle):
     infos = api.expmv_batched(b.ns, b.hs, b.Js, b.gammas, b.ts, x, tol=1e-6)
     assert all(abs(i["norm"] - 1.0) < 2e-5 for i in infos)
     y = x.cpu().numpy().astype(np.complex128)
-    order = np.argsort(np.array(b.ns) * 100 + np.arange(len(b.ns)) % 100)
-    picks = list(order[:3]) + [int(np.argmax(np.array(b.ns) == 16))]
+    ns = np.array(b.ns)
+    Ks = np.array([i["K"] for i in infos])
+    order = np.argsort(ns * 100 + np.arange(len(ns)) % 100)
+    # the three smallest, one n = 16, one each of n = 18 and 19, and the largest n = 20
+    # instance (the highest degree, a team of 32 CTAs)
+    picks = list(order[:3]) + [int(np.argmax(ns == 16)), int(np.argmax(ns == 18)), int(np.argmax(ns == 19)),
+                               int(np.argmax(np.where(ns == 20, Ks, -1)))]
     for i in picks:
         n = b.ns[i]
         ref, oinfo = oracle.expmv(b.hs[i], b.Js[i], b.gammas[i], b.ts[i], I.uniform_state(n), 1e-6)
