@@ -349,6 +349,15 @@ def run_ours(args, world, rank, local):
         api.release_workspaces()
         torch.cuda.empty_cache()
 
+    # the project's autotuner times every step configuration for this size on this device
+    # and installs the fastest (AUTO then uses it); its choice is logged in the line
+    tune = {}
+    if not args.skip_autotune:
+        tune["fp32"] = api.autotune(n, "fp32", steps=3, device=dev)
+        if rank == 0 and not args.skip_accuracy:
+            tune["fp64"] = api.autotune(n, "fp64", steps=3, device=dev)
+        torch.cuda.empty_cache()
+
     psi = torch.full((N,), 2 ** (-n / 2), dtype=torch.complex64, device=dev)
     info = None
     for _ in range(args.warmup):
@@ -519,7 +528,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": cfg.name, "n": n, "gamma": cfg.gamma, "t": cfg.t, "K": info["K"],
                    "time_splits": info["time_splits"], "radius": info["radius"], "tol": TOL32,
                    "method": "chebyshev", "precision": "fp32 (complex64 vectors, float-float operator)",
-                   "fused_split": list(api.get_fused_split(n)), "l2": "inputs larger than L2 (24 GB working set)",
+                   "fused_split": list(api.get_fused_split(n)), "autotune": tune,
+                   "l2": "inputs larger than L2 (24 GB working set)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
         "cpu_baseline": cpu_baseline_dict(cpu_v, cpu_dt, cpu_info, single),
@@ -547,6 +557,7 @@ def main():
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-workloads", action="store_true")
     ap.add_argument("--skip-cpu-single", action="store_true")
+    ap.add_argument("--skip-autotune", action="store_true")
     ap.add_argument("--fp64-path", default="auto", choices=["auto", "plain", "fused"])
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()

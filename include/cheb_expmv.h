@@ -315,10 +315,10 @@ size_t cheb_batched_workspace_bytes(int B, const int* n, cheb_precision_t precis
  * from a counter, longest instance first; n <= 13 runs whole in one CTA's shared memory,
  * larger n on a team of 1..32 CTAs (growing with n) that steps through the Clenshaw
  * recurrence with the vectors in L2 and a bounded team barrier after every pass (a wait
- * that runs out reports CHEB_ERR_TIMEOUT). on = 1 (default) runs two CTAs of 512
- * threads per SM, on = 2 one CTA per SM with twice the registers per thread; on = 0
- * selects the per-size launches and the stream pool described above (process-wide;
- * FP64 batches always use them). */
+ * that runs out reports CHEB_ERR_TIMEOUT). on = 1 (default) runs one CTA of 512
+ * threads per SM; on = 2 two CTAs per SM with half the registers per thread (whole runs
+ * up to n = 12); on = 0 selects the per-size launches and the stream pool described
+ * above (process-wide; FP64 batches always use them). */
 cheb_status_t cheb_set_batch_persistent(int on);
 int cheb_get_batch_persistent(void);
 cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* offsets, const double* h_cat,

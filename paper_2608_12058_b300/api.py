@@ -291,8 +291,8 @@ def magnus4_adaptive(h, J, A, B, T: float, psi, tol: float, steps0: int = 8, met
 
 
 def set_batch_persistent(mode):
-    """FP32 batches as one persistent launch (True or 1: two CTAs per SM, the default;
-    2: one CTA per SM) or per-size launches (False or 0)."""
+    """FP32 batches as one persistent launch (True or 1: one CTA per SM, the default;
+    2: two CTAs per SM) or per-size launches (False or 0)."""
     m = int(mode) if not isinstance(mode, bool) else (1 if mode else 0)
     _lib.check(_lib.lib().cheb_set_batch_persistent(m), "cheb_set_batch_persistent")
 

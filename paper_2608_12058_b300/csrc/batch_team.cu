@@ -1,12 +1,13 @@
 // One persistent launch for a whole batch of independent FP32 instances (Sec. III.A
 // batches many problems per launch so that no instance pays for launches of its own).
 //
-// The launch has two CTAs per SM (a cooperative launch, so that every CTA is resident).
+// The launch has one CTA of 512 threads per SM (a cooperative launch, so that every CTA
+// is resident).
 // Work is a list of slots, instances sorted longest first (2^n K) by the host; a CTA
 // takes the next slot from a global counter, runs it, and takes another:
-//  * n <= 12: one slot, the whole Clenshaw run in the CTA's shared memory (psi, b_{k+1},
-//    b_{k+2}: 96 KB at n = 12, so that two CTAs of 512 threads share an SM).
-//  * n >= 13: `team` consecutive slots (1..64 CTAs, growing with n); the team runs the
+//  * n <= 13: one slot, the whole Clenshaw run in the CTA's shared memory (psi, b_{k+1},
+//    b_{k+2}: 192 KB at n = 13).
+//  * n >= 14: `team` consecutive slots (1..32 CTAs, growing with n); the team runs the
 //    instance step by step with the vectors in global memory (L2-resident at these
 //    sizes) and a bounded team barrier after every pass. A step is
 //      - for n >= 16 a strided pass over bits [11, n): tiles of 2^(n-11) rows of 16
@@ -38,9 +39,11 @@ namespace cheb {
 namespace {
 
 constexpr int kTeamThreads = 512;
-constexpr int kTileF4 = 1024;      // float4 per 2048-amplitude low tile
-constexpr int kSmallMaxTeam = 12;  // whole-run items: psi, b_{k+1}, b_{k+2} in 96 KB
-constexpr size_t kTeamSmem = 3 * ((size_t)1 << kSmallMaxTeam) * 8;  // two CTAs per SM
+constexpr int kTileF4 = 1024;  // float4 per 2048-amplitude low tile
+// Whole-run items keep psi, b_{k+1}, b_{k+2} in shared memory: up to n = 13 (192 KB) with
+// one CTA per SM, n = 12 (96 KB) with two.
+constexpr int small_max(int ctas_per_sm) { return ctas_per_sm >= 2 ? 12 : 13; }
+constexpr size_t team_smem(int ctas_per_sm) { return 3 * ((size_t)1 << small_max(ctas_per_sm)) * 8; }
 
 __device__ __forceinline__ float4 ldcg4(const float4* p) { return __ldcg(p); }
 
@@ -258,8 +261,9 @@ __device__ bool team_run(const TeamInst& I, int r, unsigned char* smem, int* fla
     return true;
 }
 
-// MB: CTAs per SM the kernel is compiled for (2: 64 registers per thread, a few spills;
-// 1: 128 registers, no spills); cheb_set_batch_persistent picks the variant.
+// MB: CTAs per SM the kernel is compiled for (1: 128 registers per thread and whole runs
+// up to n = 13, the default; 2: 64 registers, a few spills, whole runs up to n = 12);
+// cheb_set_batch_persistent picks the variant.
 template <int MB>
 __global__ void __launch_bounds__(kTeamThreads, MB)
     k_batch_team(const TeamInst* __restrict__ inst, int ninst, int nslots, unsigned* slot_counter, int* flags) {
@@ -280,7 +284,8 @@ __global__ void __launch_bounds__(kTeamThreads, MB)
         }
         const TeamInst& I = inst[lo];
         if (I.team == 0) {
-            small_run<float, 8>(I.n, I.K, I.coef, I.Q, I.tiles, I.elow, I.g, (float2*)I.psi, smem);
+            small_run<float, 1 << (small_max(MB) - 9)>(I.n, I.K, I.coef, I.Q, I.tiles, I.elow, I.g,
+                                                       (float2*)I.psi, smem);
             __syncthreads();
         } else if (!team_run(I, slot - I.first_slot, smem, flags)) {
             return;
@@ -290,10 +295,10 @@ __global__ void __launch_bounds__(kTeamThreads, MB)
 
 }  // namespace
 
-int team_size(int n) {
-    if (n <= kSmallMaxTeam) return 0;
-    const int e = n - 14;
-    return e <= 0 ? 1 : std::min(64, 1 << e);
+int team_size(int n, int ctas_per_sm) {
+    if (n <= small_max(ctas_per_sm)) return 0;
+    const int e = n - 15 + (ctas_per_sm >= 2 ? 1 : 0);
+    return e <= 0 ? 1 : std::min(32 * std::max(ctas_per_sm, 1), 1 << e);
 }
 
 void team_split(int n, int* l, int* H) {
@@ -312,18 +317,20 @@ void team_split(int n, int* l, int* H) {
 cudaError_t launch_batch_team(const TeamInst* inst, int ninst, int nslots, unsigned* slot_counter, int* flags,
                               int ctas_per_sm, cudaStream_t s) {
     if (ninst <= 0) return cudaSuccess;
-    const void* kern = ctas_per_sm >= 2 ? (const void*)k_batch_team<2> : (const void*)k_batch_team<1>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTeamSmem);
+    const int mb = ctas_per_sm >= 2 ? 2 : 1;
+    const void* kern = mb == 2 ? (const void*)k_batch_team<2> : (const void*)k_batch_team<1>;
+    const size_t smem = team_smem(mb);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTeamThreads, kTeamSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTeamThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorNotSupported;
-    per_sm = std::min(per_sm, std::max(ctas_per_sm, 1));
+    per_sm = std::min(per_sm, mb);
     const int grid = std::min(num_sms() * per_sm, nslots);
     void* args[] = {(void*)&inst, (void*)&ninst, (void*)&nslots, (void*)&slot_counter, (void*)&flags};
     note_launch(kKindSmall);
-    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kTeamThreads), args, kTeamSmem, s);
+    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kTeamThreads), args, smem, s);
 }
 
 }  // namespace cheb

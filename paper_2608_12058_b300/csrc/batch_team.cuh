@@ -25,11 +25,12 @@ struct TeamInst {
     unsigned* bar;          // team barrier counter, zero at launch
 };
 
-// CTAs of the team of an n-qubit instance (0 for the whole-run kernel).
-int team_size(int n);
+// CTAs of the team of an n-qubit instance (0 for the whole-run kernel), for a launch of
+// ctas_per_sm CTAs per SM.
+int team_size(int n, int ctas_per_sm);
 // Split of the flips: l low-pass partner bits in L2, H bits in one strided pass.
 void team_split(int n, int* l, int* H);
-// ctas_per_sm: 2 (64 registers per thread) or 1 (128 registers).
+// ctas_per_sm: 1 (128 registers per thread, the default) or 2 (64 registers).
 cudaError_t launch_batch_team(const TeamInst* inst, int ninst, int nslots, unsigned* slot_counter, int* flags,
                               int ctas_per_sm, cudaStream_t s);
 

@@ -6,8 +6,8 @@
 //  1. Spectral bounds of all instances, one host synchronisation.
 //  2. Host: centre, radius, fixed-point tables and coefficients per instance.
 //  3. FP32: every instance runs in one persistent cooperative launch (batch_team.cu):
-//     CTAs take work slots longest first, small instances whole in one CTA's shared
-//     memory, larger ones on teams of CTAs with bounded team barriers.
+//     CTAs take work slots longest first, instances up to n = 13 whole in one CTA's
+//     shared memory, larger ones on teams of CTAs with bounded team barriers.
 //     FP64 (or with cheb_set_batch_persistent(0)): instances small enough for one
 //     CTA's shared memory (n <= 13 FP32, <= 12 FP64) run in a single launch, one CTA
 //     each; the next four sizes run whole on a thread-block cluster each (cluster.cu),
@@ -51,8 +51,8 @@ cheb_status_t stream_pool(cudaStream_t** out) {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// FP32 batches run as one persistent launch (batch_team.cu) with two CTAs per SM (1),
-// with one CTA per SM (2), or as per-size launches (0).
+// FP32 batches run as one persistent launch (batch_team.cu) with one CTA per SM (1, the
+// default), with two CTAs per SM (2), or as per-size launches (0).
 int g_persistent = 1;
 
 // An event destroyed when the call returns, on every path.
@@ -259,7 +259,7 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
                 d.n = n[i];
                 d.K = in[i].K;
                 d.Q = in[i].Q;
-                d.team = team_size(n[i]);
+                d.team = team_size(n[i], g_persistent == 2 ? 2 : 1);
                 team_split(n[i], &d.l, &d.H);
                 d.first_slot = slots;
                 d.pad = 0;
@@ -279,7 +279,7 @@ extern "C" cheb_status_t cheb_expmv_batched(int B, const int* n, const int64_t* 
             // the status word of the first instance's workspace collects timeouts
             int* flags = ctx(tl[0], s0).flags();
             const cudaError_t e = launch_batch_team((const TeamInst*)(ws + BL.team), (int)ti.size(), slots, bars + B,
-                                                    flags, g_persistent == 2 ? 1 : 2, s0);
+                                                    flags, g_persistent == 2 ? 2 : 1, s0);
             if (e != cudaSuccess) return CHEB_ERR_CUDA;
         }
     }
