@@ -152,6 +152,68 @@ def cpu_single_thread():
                        f"(h~U(-1,1), gamma={SAMPLE['gamma']}, t={SAMPLE['t']}, tol 2^-23, K={K}), one thread")}
 
 
+def cpu_configs():
+    """The oracle, as it stands, on every workload of the benchmark family (bounded where a
+    full run would take hours): wall time and amplitude-updates/s on all host threads.
+    Prints one JSON line; an opt-in leg of the CPU baseline (about 10 minutes)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2608_12058_b300 import inputs as I
+
+    out = {"cores": os.cpu_count()}
+
+    def run(name, fn, work):
+        t0 = time.perf_counter()
+        extra = fn()
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": dt, "amp_updates": work(extra), "amp_updates_per_s": work(extra) / dt}
+        print(name, out[name], flush=True)
+
+    c1 = I.config_n10()
+    run("n10_full", lambda: O.expmv(c1.h, c1.J, c1.gamma, c1.t, I.uniform_state(10), 1e-12)[1],
+        lambda i: (1 << 10) * i["K"])
+    c2 = I.config_n24()
+    run("n24_full_tol1e-12", lambda: O.expmv(c2.h, c2.J, c2.gamma, c2.t, I.uniform_state(24), 1e-12)[1],
+        lambda i: (1 << 24) * i["K"])
+    b = I.config_batch()
+    idx = list(range(0, 512, 16))  # every 16th instance: 32 of the 512
+    run("batch_sample_32_of_512",
+        lambda: [O.expmv(b.hs[i], b.Js[i], b.gammas[i], b.ts[i], I.uniform_state(b.ns[i]), 1e-6)[1] for i in idx],
+        lambda infos: float(sum((1 << b.ns[i]) * inf["K"] for i, inf in zip(idx, infos))))
+    a = I.config_anneal()
+    S = len(a.gammas)
+
+    def anneal_work(_x):
+        ksum = 0
+        for g, t in zip(a.gammas, a.ts):
+            r = O.bounds(a.h, a.J, float(g))[3]
+            ksum += O.cheb_coeffs(float(t) * r, TOL32 / S)[1]
+        return float((1 << a.n) * ksum)
+
+    run("anneal_n22_forward", lambda: O.anneal(a.h, a.J, a.gammas, a.ts, I.uniform_state(a.n), TOL32), anneal_work)
+    # n = 30: brute-force energies, then five Clenshaw steps, extrapolated to the run's K
+    c3 = I.config_n30()
+    t0 = time.perf_counter()
+    E = O.energies(c3.h, c3.J)
+    t_e = time.perf_counter() - t0
+    emin, emax = float(E.min()), float(E.max())
+    cc = 0.5 * (emin + emax)
+    r = 0.5 * (emax - emin) + c3.gamma * c3.n
+    D = (E - cc) / r
+    del E
+    coef, K, _ = O.cheb_coeffs(c3.t * r, TOL32, np.exp(-1j * c3.t * cc))
+    psi = I.uniform_state(c3.n)
+    t0 = time.perf_counter()
+    O.clenshaw(D, c3.gamma / r, coef[:6], psi)
+    t5 = time.perf_counter() - t0
+    total = t_e + t5 / 5 * K
+    out["n30_extrapolated"] = {"energies_s": t_e, "five_steps_s": t5, "K": int(K), "seconds": total,
+                               "amp_updates_per_s": (1 << 30) * K / total,
+                               "note": "extrapolated: energies + 5 timed steps x K/5"}
+    print(json.dumps({"cpu_configs": out}), flush=True)
+
+
 def cpu_baseline_dict(value, dt, info, single=None):
     d = {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
          "sample": (f"full oracle exp(-itH)psi on the n={SAMPLE['n']} member of the n=30 SK family "
@@ -238,6 +300,7 @@ def other_workloads(dev):
 
     a = I.config_anneal()
     nn, S = a.n, len(a.gammas)
+    tune22 = api.autotune(nn, "fp32", steps=4, device=dev)
     x0 = torch.full((1 << nn,), 2 ** (-nn / 2), dtype=torch.complex64, device=dev)
     bnd = torch.empty((S, 1 << nn), dtype=torch.complex64, device=dev)
     res = {}
@@ -261,6 +324,7 @@ def other_workloads(dev):
     res["backward_over_forward"] = res["backward_ms"] / res["forward_ms"]
     res["forward_amp_updates_per_s"] = (1 << nn) * res["K_total"] / (res["forward_ms"] / 1e3)
     res["workload"] = "SK n=22, 64 piecewise-constant segments, complex64; backward = all gradients"
+    res["autotune"] = tune22
     out["anneal_n22"] = res
     del x, x0, bnd
     api.release_workspaces()
@@ -558,12 +622,17 @@ def main():
     ap.add_argument("--skip-workloads", action="store_true")
     ap.add_argument("--skip-cpu-single", action="store_true")
     ap.add_argument("--skip-autotune", action="store_true")
+    ap.add_argument("--cpu-configs", action="store_true",
+                    help="only time the oracle on every workload of the family (host cores, ~10 min)")
     ap.add_argument("--fp64-path", default="auto", choices=["auto", "plain", "fused"])
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_sample:
         v, dt, info = cpu_sample_run(args.cpu_sample)
         print(json.dumps([v, dt, info["K"]]))
+        return
+    if args.cpu_configs:
+        cpu_configs()
         return
     world, rank, local = dist_setup()
     if args.impl == "reference":

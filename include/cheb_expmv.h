@@ -312,12 +312,12 @@ cheb_status_t cheb_magnus4_adaptive(int n, const double* h, const double* J, dou
  */
 size_t cheb_batched_workspace_bytes(int B, const int* n, cheb_precision_t precision);
 /* FP32 batches run as one persistent cooperative launch: one CTA per SM takes work slots
- * from a counter, longest instance first; n <= 13 runs whole in one CTA's shared memory,
- * larger n on a team of 1..32 CTAs (growing with n) that steps through the Clenshaw
+ * from a counter, longest instance first; n <= 12 runs whole in one CTA's shared memory,
+ * larger n on a team of 1..64 CTAs (2^(n-14)) that steps through the Clenshaw
  * recurrence with the vectors in L2 and a bounded team barrier after every pass (a wait
  * that runs out reports CHEB_ERR_TIMEOUT). on = 1 (default) runs one CTA of 512
- * threads per SM; on = 2 two CTAs per SM with half the registers per thread (whole runs
- * up to n = 12); on = 0 selects the per-size launches and the stream pool described
+ * threads per SM; on = 2 two CTAs per SM with half the registers per thread; on = 0
+ * selects the per-size launches and the stream pool described
  * above (process-wide; FP64 batches always use them). */
 cheb_status_t cheb_set_batch_persistent(int on);
 int cheb_get_batch_persistent(void);
@@ -542,10 +542,12 @@ typedef enum {
  * Failure-detection self-test (no counterpart in the paper). Every device-side wait of
  * this library is bounded: it gives up after about 2 s, records a timeout in the
  * workspace status word and lets the kernel return, and the call reports
- * CHEB_ERR_TIMEOUT. This entry point runs that same wait, with a ~1 ms limit, on a
- * barrier that nothing arrives on, and returns its status: CHEB_ERR_TIMEOUT is the
- * expected answer, and the context stays usable afterwards.
- *   workspace: DEVICE, at least 4 bytes (one int), 4-byte aligned. Synchronises.
+ * CHEB_ERR_TIMEOUT. This entry point runs both kinds of wait, each with a ~1 ms limit,
+ * on a wait that nothing satisfies (an mbarrier that nothing arrives on, as in the TMA
+ * kernels; a team barrier whose teammate never comes, as in the persistent batch
+ * kernel), and returns CHEB_ERR_TIMEOUT when both reported their timeout (the expected
+ * answer; CHEB_OK otherwise). The context stays usable afterwards.
+ *   workspace: DEVICE, at least 16 bytes, 4-byte aligned. Synchronises.
  */
 cheb_status_t cheb_wait_selftest(void* workspace, size_t workspace_bytes, void* stream);
 

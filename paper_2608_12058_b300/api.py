@@ -572,8 +572,9 @@ KERNEL_KIND = {"plain": 3, "adjoint_acc": 5, "low": 6, "high": 7, "tail": 8}
 
 
 def wait_selftest(device=None):
-    """Run the library's bounded device wait against a barrier nothing arrives on; raises
-    ChebError with CHEB_ERR_TIMEOUT (the expected outcome) or returns if it did not time out."""
+    """Run the library's two bounded device waits (an mbarrier wait, a team barrier) against
+    waits nothing satisfies; raises ChebError with CHEB_ERR_TIMEOUT (the expected outcome)
+    or returns if they did not both time out."""
     import torch
 
     buf = torch.zeros(64, dtype=torch.uint8, device=device if device is not None else "cuda")

@@ -5,9 +5,9 @@
 // is resident).
 // Work is a list of slots, instances sorted longest first (2^n K) by the host; a CTA
 // takes the next slot from a global counter, runs it, and takes another:
-//  * n <= 13: one slot, the whole Clenshaw run in the CTA's shared memory (psi, b_{k+1},
-//    b_{k+2}: 192 KB at n = 13).
-//  * n >= 14: `team` consecutive slots (1..32 CTAs, growing with n); the team runs the
+//  * n <= 12: one slot, the whole Clenshaw run in the CTA's shared memory (psi, b_{k+1},
+//    b_{k+2}: 96 KB at n = 12).
+//  * n >= 13: `team` consecutive slots (2^(n-14) CTAs, 1..64); the team runs the
 //    instance step by step with the vectors in global memory (L2-resident at these
 //    sizes) and a bounded team barrier after every pass. A step is
 //      - for n >= 16 a strided pass over bits [11, n): tiles of 2^(n-11) rows of 16
@@ -40,16 +40,17 @@ namespace {
 
 constexpr int kTeamThreads = 512;
 constexpr int kTileF4 = 1024;  // float4 per 2048-amplitude low tile
-// Whole-run items keep psi, b_{k+1}, b_{k+2} in shared memory: up to n = 13 (192 KB) with
-// one CTA per SM, n = 12 (96 KB) with two.
-constexpr int small_max(int ctas_per_sm) { return ctas_per_sm >= 2 ? 12 : 13; }
+// Whole-run items keep psi, b_{k+1}, b_{k+2} in shared memory, up to n = 12 (96 KB); a
+// team of one CTA stepping through L2 was measured faster for n = 13 than a whole run in
+// 192 KB (whose 16 amplitudes per thread spill registers).
+constexpr int small_max(int ctas_per_sm) { return ctas_per_sm >= 2 ? 12 : 12; }
 constexpr size_t team_smem(int ctas_per_sm) { return 3 * ((size_t)1 << small_max(ctas_per_sm)) * 8; }
 
 __device__ __forceinline__ float4 ldcg4(const float4* p) { return __ldcg(p); }
 
 // Bounded team barrier: every thread's writes of this CTA are released, the CTA arrives,
 // and thread 0 waits (acquire) until `target` arrivals are counted.
-__device__ bool team_barrier(unsigned* bar, unsigned target, int* flags, int* s_ok) {
+__device__ bool team_barrier(unsigned* bar, unsigned target, int* flags, int* s_ok, long long limit = kWaitCycles) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -60,7 +61,7 @@ __device__ bool team_barrier(unsigned* bar, unsigned target, int* flags, int* s_
             unsigned v;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
             if (v >= target) break;
-            if (clock64() - t0 > kWaitCycles) {
+            if (clock64() - t0 > limit) {
                 atomicOr(flags, kFlagTimeout);
                 good = 0;
                 break;
@@ -261,9 +262,8 @@ __device__ bool team_run(const TeamInst& I, int r, unsigned char* smem, int* fla
     return true;
 }
 
-// MB: CTAs per SM the kernel is compiled for (1: 128 registers per thread and whole runs
-// up to n = 13, the default; 2: 64 registers, a few spills, whole runs up to n = 12);
-// cheb_set_batch_persistent picks the variant.
+// MB: CTAs per SM the kernel is compiled for (1: 128 registers per thread, the default;
+// 2: 64 registers, with spills); cheb_set_batch_persistent picks the variant.
 template <int MB>
 __global__ void __launch_bounds__(kTeamThreads, MB)
     k_batch_team(const TeamInst* __restrict__ inst, int ninst, int nslots, unsigned* slot_counter, int* flags) {
@@ -293,12 +293,27 @@ __global__ void __launch_bounds__(kTeamThreads, MB)
     }
 }
 
+// One CTA of a team of two: its barrier waits for a teammate that never comes.
+__global__ void k_team_barrier_selftest(unsigned* bar, int* flags, long long limit) {
+    __shared__ int s_ok;
+    team_barrier(bar, 2u, flags, &s_ok, limit);
+}
+
 }  // namespace
 
+cudaError_t launch_team_barrier_selftest(unsigned* bar, int* flags, long long limit, cudaStream_t s) {
+    note_launch(kKindReduce);
+    k_team_barrier_selftest<<<1, 32, 0, s>>>(bar, flags, limit);
+    return cudaGetLastError();
+}
+
+// Larger teams measured faster on the 512-instance workload (teams of 2^(n-14) against
+// 2^(n-15): 782 against 945 ms): more CTAs per instance keep fewer instances, and so
+// fewer vectors, in flight in L2.
 int team_size(int n, int ctas_per_sm) {
     if (n <= small_max(ctas_per_sm)) return 0;
-    const int e = n - 15 + (ctas_per_sm >= 2 ? 1 : 0);
-    return e <= 0 ? 1 : std::min(32 * std::max(ctas_per_sm, 1), 1 << e);
+    const int e = n - 14;
+    return e <= 0 ? 1 : std::min(64, 1 << e);
 }
 
 void team_split(int n, int* l, int* H) {

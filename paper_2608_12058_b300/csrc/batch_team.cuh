@@ -34,4 +34,8 @@ void team_split(int n, int* l, int* H);
 cudaError_t launch_batch_team(const TeamInst* inst, int ninst, int nslots, unsigned* slot_counter, int* flags,
                               int ctas_per_sm, cudaStream_t s);
 
+// Failure-detection self-test of the team barrier: one CTA of a team of two waits, with
+// `limit` clock cycles, for a teammate that never arrives (bar must be zero).
+cudaError_t launch_team_barrier_selftest(unsigned* bar, int* flags, long long limit, cudaStream_t s);
+
 }  // namespace cheb

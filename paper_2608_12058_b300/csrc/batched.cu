@@ -6,7 +6,7 @@
 //  1. Spectral bounds of all instances, one host synchronisation.
 //  2. Host: centre, radius, fixed-point tables and coefficients per instance.
 //  3. FP32: every instance runs in one persistent cooperative launch (batch_team.cu):
-//     CTAs take work slots longest first, instances up to n = 13 whole in one CTA's
+//     CTAs take work slots longest first, instances up to n = 12 whole in one CTA's
 //     shared memory, larger ones on teams of CTAs with bounded team barriers.
 //     FP64 (or with cheb_set_batch_persistent(0)): instances small enough for one
 //     CTA's shared memory (n <= 13 FP32, <= 12 FP64) run in a single launch, one CTA

@@ -51,7 +51,6 @@ __device__ __forceinline__ void small_run(int n, int K, const double2* __restric
     const int M = n < kTileBits ? n : kTileBits;  // same split as the workspace tables
     R dhi[PER], dlo[PER];
     const double2 cK = coef[K];
-    #pragma unroll
     for (int q = 0; q < PER; ++q) {
         const int z = threadIdx.x + q * blockDim.x;
         if (z < N) {
@@ -91,7 +90,6 @@ __device__ __forceinline__ void small_run(int n, int K, const double2* __restric
     for (int k = K - 1; k >= 0; --k) {
         const double2 ck = coef[k];
         const R sc = (k == 0) ? R(1) : R(2);
-        #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int z = threadIdx.x + q * blockDim.x;
             if (z < N) {

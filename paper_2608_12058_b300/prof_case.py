@@ -13,6 +13,10 @@
     python -m paper_2608_12058_b300.prof_case ff N L H [STEPS]
         STEPS float-float fused steps of the FP64 path (complex128 states) at n = N with
         the split (L, H) (kernel names k_low_ff and k_strided_ff).
+    python -m paper_2608_12058_b300.prof_case batch [MODE]
+        the 512-instance batch workload by size group and whole, in the batch launch
+        mode MODE (1 persistent, the default; 2 persistent with two CTAs per SM; 0
+        per-size launches).
     python -m paper_2608_12058_b300.prof_case adjoint N S
         the first S segments of the anneal schedule at n = N (complex64): forward with
         segment-start states, energy gradient, full reverse pass (k_adj_acc_f32x2,
@@ -148,6 +152,50 @@ def cluster(n, count):
     print("ok", sum(i["K"] for i in infos))
 
 
+def batch(mode):
+    """The 512-instance workload by size group (n <= 13, 14-17, 18, 19, 20) and whole, with
+    the batch launch mode MODE (cheb_set_batch_persistent); one timed run after a warm-up."""
+    import torch
+
+    from . import api
+    from . import inputs as I
+
+    api.set_batch_persistent(mode)
+    b = I.config_batch()
+    ns = np.asarray(b.ns)
+    groups = [("all", np.ones_like(ns, dtype=bool)), ("n<=13", ns <= 13), ("14-17", (ns >= 14) & (ns <= 17)),
+              ("18", ns == 18), ("19", ns == 19), ("20", ns == 20)]
+    try:
+        for name, m in groups:
+            idx = np.nonzero(m)[0]
+            sub = [int(b.ns[i]) for i in idx]
+            offs, total = api.batch_offsets(sub)
+            cat = np.zeros(total, dtype=np.complex64)
+            for nn, o in zip(sub, offs):
+                cat[o:o + (1 << nn)] = 2.0 ** (-nn / 2)
+            x0 = torch.from_numpy(cat).cuda()
+            args = ([b.hs[i] for i in idx], [b.Js[i] for i in idx], [b.gammas[i] for i in idx],
+                    [b.ts[i] for i in idx])
+            x = x0.clone()
+            infos = api.expmv_batched(sub, *args, x, tol=1e-6)
+            work = float(sum((1 << nn) * i["K"] * i["time_splits"] for nn, i in zip(sub, infos)))
+            x.copy_(x0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            api.expmv_batched(sub, *args, x, tol=1e-6, info=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            assert np.isfinite(float(torch.linalg.vector_norm(x)))
+            print(f"{name:6s} {len(idx):4d} instances {ms:9.2f} ms {work / ms * 1e3:.3e} amplitude-updates/s")
+            del x, x0
+            api.release_workspaces()
+            torch.cuda.empty_cache()
+    finally:
+        api.set_batch_persistent(1)
+
+
 def main(argv):
     if argv[0] == "adjoint":
         adjoint(int(argv[1]), int(argv[2]))
@@ -155,6 +203,8 @@ def main(argv):
         cluster(int(argv[1]), int(argv[2]))
     elif argv[0] == "compare":
         compare(int(argv[1]), int(argv[2]) if len(argv) > 2 else 40)
+    elif argv[0] == "batch":
+        batch(int(argv[1]) if len(argv) > 1 else 1)
     elif argv[0] == "ff":
         n, l, h = int(argv[1]), int(argv[2]), int(argv[3])
         ff_steps(n, l, h, int(argv[4]) if len(argv) > 4 else 6)
