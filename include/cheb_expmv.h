@@ -564,6 +564,15 @@ cheb_status_t cheb_wait_selftest(void* workspace, size_t workspace_bytes, void* 
  */
 cheb_status_t cheb_workspace_status(void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * Programmatic dependent launch of the fused step kernels (no counterpart in the paper):
+ * when on (the default), each pass is launched so that its CTAs may be scheduled while
+ * the previous pass drains; a kernel waits for its predecessor's completion (and memory)
+ * before it reads any vector the predecessor writes, so results are unchanged. Event
+ * profiling (cheb_profile_enable) launches without it. on: 0 or 1 (process-wide).
+ */
+cheb_status_t cheb_set_programmatic_launch(int on);
+
 long long cheb_launch_count(void);
 cheb_status_t cheb_profile_enable(int on);
 cheb_status_t cheb_profile_reset(void);

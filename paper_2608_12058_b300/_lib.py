@@ -109,6 +109,7 @@ SIGNATURES = {
     "cheb_autotune": (c_int, [c_int, c_int, c_int, c_void_p, c_size_t, c_void_p, ctypes.POINTER(TuneResult)]),
     "cheb_autotune_load": (c_int, [ctypes.c_char_p, ctypes.c_char_p, _ip]),
     "cheb_autotune_reset": (c_int, []),
+    "cheb_set_programmatic_launch": (c_int, [c_int]),
     "cheb_launch_count": (ctypes.c_longlong, []),
     "cheb_profile_enable": (c_int, [c_int]),
     "cheb_profile_reset": (c_int, []),

@@ -517,6 +517,11 @@ def get_fused_split_fp64(n: int):
     return l.value, h.value
 
 
+def set_programmatic_launch(on: bool):
+    """Programmatic dependent launch of the fused step kernels (on by default)."""
+    _lib.check(_lib.lib().cheb_set_programmatic_launch(1 if on else 0), "cheb_set_programmatic_launch")
+
+
 def autotune(n: int, precision: str = "fp32", steps: int = 4, device=None):
     """Time the candidate step configurations for (n, precision) on the device and install
     the fastest (cheb_autotune); returns the result as a dict."""

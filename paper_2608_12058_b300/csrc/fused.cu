@@ -190,9 +190,11 @@ __global__ void __launch_bounds__(kLowThreads, 1) k_low(const LowArgs a) {
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_trigger();
 
     if (warp == kCons / 32) {
         // ---------------- producer warp ----------------
+        pdl_wait();  // the previous step kernel's output is read from here on
         const uint32_t stage_bytes = (1u + (need_psi ? 1u : 0u) + (need_slot ? 1u : 0u)) * kTB;
         int last_s[kNS], last_p[kNP];
         for (int i = 0; i < kNS; ++i) last_s[i] = -1;
@@ -423,6 +425,8 @@ __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const St
     const float2 g_hi = dup(a.scale_g), g_lo = dup(a.scale_glo), sg = dup(a.sgn);
     float4 nxt[Cfg::kP];
     int64_t T = blockIdx.x;
+    pdl_trigger();
+    pdl_wait();
     if (T < a.ntiles) {
         const int64_t base = strided_base<H>(a, T);
 #pragma unroll
@@ -553,7 +557,9 @@ __global__ void __launch_bounds__(kLowThreads, 1)
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_trigger();
     if (warp == kCons / 32) {
+        pdl_wait();
         if (lane != 0) return;
         int last[Cfg::kNS], slast[Cfg::kSR];
         for (int i = 0; i < Cfg::kNS; ++i) last[i] = -1;
@@ -1137,9 +1143,9 @@ cudaError_t launch_strided_c(const StridedArgs& a, cudaStream_t s) {
     if (grid < 1) grid = 1;
     note_launch(kKindHigh);
     const int pi = prof_begin(kKindHigh, s);
-    k_strided<H, C><<<(unsigned)grid, Cfg::kThreads, smem, s>>>(a);
+    const cudaError_t le = launch_step_kernel(k_strided<H, C>, (unsigned)grid, Cfg::kThreads, smem, s, a);
     prof_end(pi, s);
-    return cudaGetLastError();
+    return le;
 }
 
 template <int H>
@@ -1205,9 +1211,10 @@ cudaError_t launch_strided_ws_c(const StridedArgs& a, int n, cudaStream_t s) {
     const int64_t grid = std::min<int64_t>(a.ntiles, num_sms());
     note_launch(kKindHigh);
     const int pi = prof_begin(kKindHigh, s);
-    k_strided_ws<H, RB, C><<<(unsigned)grid, kLowThreads, Cfg::kSmem, s>>>(a, map, smap);
+    const cudaError_t le =
+        launch_step_kernel(k_strided_ws<H, RB, C>, (unsigned)grid, kLowThreads, Cfg::kSmem, s, a, map, smap);
     prof_end(pi, s);
-    return cudaGetLastError();
+    return le;
 }
 
 template <int H, int RB>
@@ -1509,9 +1516,9 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void* sc
     const int64_t grid = std::min<int64_t>(la.ntiles, num_sms());
     note_launch(kKindLow);
     const int pi = prof_begin(kKindLow, st);
-    kern<<<(unsigned)grid, kLowThreads, kLowSmem, st>>>(la);
+    const cudaError_t le = launch_step_kernel(kern, (unsigned)grid, kLowThreads, kLowSmem, st, la);
     prof_end(pi, st);
-    return cudaGetLastError();
+    return le;
 }
 
 }  // namespace cheb

@@ -232,9 +232,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_low_ff(const LowFFArgs a) {
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_trigger();
 
     if (warp == kCons / 32) {
         // ---------------- producer warp ----------------
+        pdl_wait();  // the previous step kernel's output is read from here on
         const uint32_t stage_bytes = (1u + (need_psi ? 1u : 0u) + (need_slot ? 1u : 0u)) * kTB;
         int last_s[kNS], last_p[kNP];
         for (int i = 0; i < kNS; ++i) last_s[i] = -1;
@@ -500,7 +502,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_trigger();
     if (warp == kCons / 32) {
+        pdl_wait();
         if (lane != 0) return;
         int last[Cfg::kNS], slast[Cfg::kSR];
         for (int i = 0; i < Cfg::kNS; ++i) last[i] = -1;
@@ -643,9 +647,9 @@ cudaError_t launch_strided_ff_t(const StridedFFArgs& a, int n, cudaStream_t s) {
     const int64_t grid = std::min<int64_t>(a.ntiles, num_sms());
     note_launch(kKindHigh);
     const int pi = prof_begin(kKindHigh, s);
-    k_strided_ff<H, RB><<<(unsigned)grid, kThreads, Cfg::kSmem, s>>>(a, map, smap);
+    const cudaError_t le = launch_step_kernel(k_strided_ff<H, RB>, (unsigned)grid, kThreads, Cfg::kSmem, s, a, map, smap);
     prof_end(pi, s);
-    return cudaGetLastError();
+    return le;
 }
 
 // Rows of 2^RB amplitudes: 256-byte rows (RB = 4) for ranges of 5..8 bits whose rows
@@ -840,9 +844,9 @@ cudaError_t launch_step_ff(const FusedPlan& plan, const StepArgs& s, int* flags,
     const int64_t grid = std::min<int64_t>(la.ntiles, num_sms());
     note_launch(kKindLow);
     const int pi = prof_begin(kKindLow, st);
-    k_low_ff<<<(unsigned)grid, kThreads, kLowSmem, st>>>(la);
+    const cudaError_t le = launch_step_kernel(k_low_ff, (unsigned)grid, kThreads, kLowSmem, st, la);
     prof_end(pi, st);
-    return cudaGetLastError();
+    return le;
 }
 
 }  // namespace cheb

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <utility>
 
 namespace cheb {
 
@@ -19,6 +20,10 @@ enum KernelKind : int {
     kKindMixed = 8,
 };
 void note_launch(int kind);
+// Whether step kernels are launched with programmatic dependent launch (on by default;
+// off while event profiling is on, so that per-kernel event times do not overlap).
+bool pdl_enabled();
+void pdl_set(bool on);
 // Event-bracketed timing of one launch when profiling is on (prof_begin returns -1 otherwise).
 int prof_begin(int kind, cudaStream_t s);
 void prof_end(int idx, cudaStream_t s);
@@ -83,5 +88,23 @@ void launch_step_norms(int prec, int64_t N, const void* b, const void* psi, doub
 void launch_norm_energy(int prec, int n, int M, int Q, const int64_t* tiles, const int64_t* elow,
                         double c, double r, const void* psi, double* part, double* out2,
                         cudaStream_t s);
+
+// Launches kern<<<grid, block, smem, s>>>(args...) with programmatic stream serialization
+// when pdl_enabled(), else as an ordinary launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_step_kernel(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                               Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 }  // namespace cheb

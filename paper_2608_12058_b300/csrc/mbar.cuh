@@ -83,6 +83,13 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, int* 
     }
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization
+// may start while the previous kernel of the stream drains; pdl_wait() blocks the calling
+// thread until that kernel has completed and its memory is visible, and pdl_trigger()
+// lets the next kernel be scheduled early. Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Tiled bulk tensor copy of a 4-D box into shared memory, completing on an mbarrier.
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint64_t* bar) {

@@ -40,6 +40,10 @@ static cudaEvent_t take_event() {
     return e;
 }
 
+static std::atomic<bool> g_pdl_on{true};
+bool pdl_enabled() { return g_pdl_on.load(std::memory_order_relaxed) && !g_prof_on.load(std::memory_order_relaxed); }
+void pdl_set(bool on) { g_pdl_on.store(on, std::memory_order_relaxed); }
+
 int prof_begin(int kind, cudaStream_t s) {
     if (!g_prof_on.load(std::memory_order_relaxed)) return -1;
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -99,3 +103,9 @@ cheb_status_t cheb_profile_read(int kind, long long* count, double* total_ms) {
 }
 
 }  // extern "C"
+
+extern "C" cheb_status_t cheb_set_programmatic_launch(int on) {
+    if (on != 0 && on != 1) return CHEB_ERR_INVALID_ARG;
+    cheb::pdl_set(on != 0);
+    return CHEB_OK;
+}

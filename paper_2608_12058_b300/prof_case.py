@@ -17,6 +17,10 @@
         the 512-instance batch workload by size group and whole, in the batch launch
         mode MODE (1 persistent, the default; 2 persistent with two CTAs per SM; 0
         per-size launches).
+    python -m paper_2608_12058_b300.prof_case anneal
+        the n=22 64-segment anneal forward with and without programmatic dependent launch.
+    python -m paper_2608_12058_b300.prof_case l2
+        copy bandwidth of L2-resident buffers (8..96 MB).
     python -m paper_2608_12058_b300.prof_case adjoint N S
         the first S segments of the anneal schedule at n = N (complex64): forward with
         segment-start states, energy gradient, full reverse pass (k_adj_acc_f32x2,
@@ -196,6 +200,63 @@ def batch(mode):
         api.set_batch_persistent(1)
 
 
+def anneal_time(reps=3):
+    """The n=22, 64-segment anneal forward (complex64) timed with and without programmatic
+    dependent launch of the step kernels, `reps` times each after a warm-up (CUDA events)."""
+    import torch
+
+    from . import api
+    from . import inputs as I
+
+    a = I.config_anneal()
+    n = a.n
+    x0 = torch.full((1 << n,), 2 ** (-n / 2), dtype=torch.complex64, device="cuda")
+    infos = api.anneal(a.h, a.J, a.gammas, a.ts, x0.clone())
+    K = sum(i["K"] for i in infos)
+    try:
+        for on in (True, False, True, False):
+            api.set_programmatic_launch(on)
+            ts = []
+            for _ in range(reps):
+                x = x0.clone()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                api.anneal(a.h, a.J, a.gammas, a.ts, x, info=False)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = min(ts)
+            print(f"programmatic launch {'on ' if on else 'off'}: {ms:.2f} ms, {(1 << n) * K / ms * 1e3:.3e} "
+                  f"amplitude-updates/s ({K} steps, {ms / K * 1e3:.1f} us per step)")
+    finally:
+        api.set_programmatic_launch(True)
+
+
+def l2_copy():
+    """Copy bandwidth of L2-resident buffers (torch copy_ of 8..96 MB, 200 repetitions,
+    CUDA events): the roofline for the batch and anneal workloads, whose vectors stay in
+    the 126 MB L2."""
+    import torch
+
+    for mb in (8, 16, 32, 48, 64, 96):
+        n = mb * (1 << 20) // 4
+        x = torch.ones(n, dtype=torch.float32, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(10):
+            y.copy_(x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(200):
+            y.copy_(x)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(f"{mb:3d} MB: {2 * x.numel() * 4 * 200 / (ms / 1e3) / 1e9:8.1f} GB/s (read + write)")
+        del x, y
+
+
 def main(argv):
     if argv[0] == "adjoint":
         adjoint(int(argv[1]), int(argv[2]))
@@ -203,6 +264,10 @@ def main(argv):
         cluster(int(argv[1]), int(argv[2]))
     elif argv[0] == "compare":
         compare(int(argv[1]), int(argv[2]) if len(argv) > 2 else 40)
+    elif argv[0] == "anneal":
+        anneal_time()
+    elif argv[0] == "l2":
+        l2_copy()
     elif argv[0] == "batch":
         batch(int(argv[1]) if len(argv) > 1 else 1)
     elif argv[0] == "ff":

@@ -21,14 +21,15 @@ def _batch(ns, seed):
     return hs, Js, np.array(gs), np.array(ts)
 
 
-@pytest.mark.parametrize("prec,persistent", [("fp64", False), ("fp32", True), ("fp32", False)])
+@pytest.mark.parametrize("prec,persistent", [("fp64", 0), ("fp32", 1), ("fp32", 2), ("fp32", 0)])
 def test_mixed_batch_matches_oracle(cuda_lib, oracle, prec, persistent):
     import torch
 
     from paper_2608_12058_b300 import api
 
-    # sizes of every path. Persistent launch (FP32): one CTA per instance up to n = 13,
-    # teams of 1..32 CTAs above (n = 14, 15 without a strided pass, n >= 16 with one).
+    # sizes of every path. Persistent launch (FP32, one or two CTAs per SM): one CTA per
+    # instance up to n = 12, teams of 1..64 CTAs above (n = 13..15 without a strided
+    # pass, n >= 16 with one).
     # Per-size launches: one CTA per instance (n <= 13 FP32, <= 12 FP64), one
     # thread-block cluster per instance (n = 14..17 FP32, 13..16 FP64; repeated sizes
     # share a launch), step kernels on the stream pool (larger)
@@ -46,7 +47,7 @@ def test_mixed_batch_matches_oracle(cuda_lib, oracle, prec, persistent):
     try:
         infos = api.expmv_batched(ns, hs, Js, gs, ts, x, tol=tol)
     finally:
-        api.set_batch_persistent(True)
+        api.set_batch_persistent(1)
     y = x.cpu().numpy().astype(np.complex128)
     for i, n in enumerate(ns):
         ref, oinfo = oracle.expmv(hs[i], Js[i], gs[i], ts[i], states[i], tol)

@@ -295,3 +295,28 @@ def test_fused_splits_match_oracle(cuda_lib, oracle, n, l, h):
         api.set_fused_split(n, -1)
     assert info["K"] == oinfo["K"]
     assert _rel(y, ref) <= TOL["fp32"]
+
+
+@pytest.mark.parametrize("prec,n", [("fp32", 22), ("fp32", 25), ("fp64", 22)])
+def test_programmatic_launch_gives_identical_results(cuda_lib, prec, n):
+    """The fused step kernels launched with programmatic dependent launch (the default)
+    and without it give bit-identical results: each kernel waits for its predecessor
+    before reading what it wrote."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    h, J = I.sk_instance(n, 300 + n)
+    psi = I.random_state(n, 301 + n)
+    dt = torch.complex64 if prec == "fp32" else torch.complex128
+    out = []
+    for on in (True, False):
+        api.set_programmatic_launch(on)
+        try:
+            x = torch.from_numpy(psi).to(dt).cuda()
+            api.expmv(h, J, 0.9, 2.0, x, tol=2.0 ** -23 if prec == "fp32" else 1e-12, path="fused")
+            torch.cuda.synchronize()
+            out.append(x.cpu())
+        finally:
+            api.set_programmatic_launch(True)
+    assert torch.equal(out[0], out[1])
