@@ -332,7 +332,10 @@ def other_workloads(dev):
 
     # gradients at the full n=30 size: one segment of the n=30 workload at t = 1, the
     # forward keeps its start state, the adjoint regenerates the Clenshaw vectors in a
-    # ring of 6 from one anchor pair (workspace of 8 state vectors)
+    # ring of 6 from one anchor pair (workspace of 8 state vectors). Two routes: a plain
+    # forward, after which the adjoint recomputes the segment to place its anchors; and
+    # the checkpointed forward, which places them itself (the adjoint then skips that
+    # recomputation)
     c = I.config_n30()
     N30 = 1 << c.n
     store = 8
@@ -358,13 +361,32 @@ def other_workloads(dev):
         api.anneal_adjoint(c.h, c.J, g_, t_, bnd, x, g, store_vectors=store)
         e1.record()
         torch.cuda.synchronize()
+        res["backward_recompute_ms"] = e0.elapsed_time(e1)
+        del g
+        torch.cuda.empty_cache()
+        x.fill_(2 ** (-c.n / 2))
+        torch.cuda.synchronize()
+        e0.record()
+        ck = api.anneal_checkpointed(c.h, c.J, g_, t_, x, bnd, store_vectors=store)
+        e1.record()
+        torch.cuda.synchronize()
+        res["checkpointed_forward_ms"] = e0.elapsed_time(e1)
+        _, g, _, _ = api.energy_grad(c.h, c.J, x)
+        torch.cuda.synchronize()
+        e0.record()
+        api.anneal_adjoint(c.h, c.J, g_, t_, bnd, x, g, checkpoint=ck)
+        e1.record()
+        torch.cuda.synchronize()
         res["backward_ms"] = e0.elapsed_time(e1)
-        del x, g
+        del x, g, ck
         torch.cuda.empty_cache()
     res["backward_over_forward"] = res["backward_ms"] / res["forward_ms"]
+    res["backward_recompute_over_forward"] = res["backward_recompute_ms"] / res["forward_ms"]
+    res["checkpointed_forward_over_forward"] = res["checkpointed_forward_ms"] / res["forward_ms"]
     res["adjoint_workspace_GiB"] = api.adjoint_workspace_bytes(c.n, "fp32", store) / 2 ** 30
     res["workload"] = (f"SK n=30 (h~U(-1,1), gamma={c.gamma}), one segment t=1, complex64; backward = all "
-                       f"gradients with {store} state vectors of workspace")
+                       f"gradients with {store} state vectors of workspace, after the checkpointed forward "
+                       f"(backward_recompute: after a plain forward)")
     out["adjoint_n30"] = res
     del bnd
     api.release_workspaces()

@@ -384,6 +384,40 @@ cheb_status_t cheb_anneal_general_adjoint(int n, const double* h, const double* 
                                           double* grad_a, double* grad_b, double* grad_t, double* grad_h,
                                           double* grad_J, void* workspace, size_t workspace_bytes,
                                           void* stream);
+/*
+ * Forward runs that leave the adjoint's checkpoints behind (no counterpart in the
+ * paper). They compute the same schedule as cheb_anneal / cheb_anneal_general, but
+ * run the last segment on the adjoint's step runner and keep its Clenshaw vectors
+ * b_K .. b_1 in the pool of an ADJOINT workspace (every b_k when the pool holds K
+ * vectors, else the ring and anchor pairs). The next cheb_anneal_adjoint /
+ * cheb_anneal_general_adjoint call with the same workspace (pointer and size), the
+ * same n, S, schedule, couplings, precision, tol and method, psi_T = this psi and the
+ * same boundaries then skips that segment's forward recomputation; for S = 1 (one
+ * exp(-itH) psi) that is one of its three passes over the Clenshaw recurrence.
+ *   psi:        DEVICE in/out, as cheb_anneal (out = the final state psi_T).
+ *   boundaries: DEVICE, required: receives the S segment-start states.
+ *   workspace:  cheb_adjoint_workspace_bytes(n, precision, store_vectors) bytes,
+ *               256-byte aligned; between this call and the adjoint only forward
+ *               entry points may use it (they touch its leading forward workspace,
+ *               not the pool).
+ * Any adjoint call on the workspace consumes the checkpoint; arguments that differ
+ * make the adjoint recompute the segment (the result is the same either way). The
+ * record is kept on the host per workspace pointer.
+ * Errors: as cheb_anneal_adjoint (WORKSPACE when the pool is too small for the last
+ * segment, UNSUPPORTED when it needs time slicing).
+ */
+cheb_status_t cheb_anneal_checkpointed(int n, const double* h, const double* J, int S,
+                                       const double* gamma_s, const double* t_s, void* psi,
+                                       cheb_precision_t precision, double tol, cheb_method_t method,
+                                       void* boundaries, void* workspace, size_t workspace_bytes,
+                                       void* stream);
+cheb_status_t cheb_anneal_general_checkpointed(int n, const double* h, const double* J, int S,
+                                               const double* a_s, const double* b_s,
+                                               const double* t_s, void* psi,
+                                               cheb_precision_t precision, double tol,
+                                               cheb_method_t method, void* boundaries,
+                                               void* workspace, size_t workspace_bytes,
+                                               void* stream);
 cheb_status_t cheb_energy_grad(int n, const double* h, const double* J, const void* psi,
                                void* grad_psi, cheb_precision_t precision, double* energy,
                                double* grad_h, double* grad_J, void* workspace,

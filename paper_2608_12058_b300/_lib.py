@@ -101,6 +101,10 @@ SIGNATURES = {
                                     c_int, _dp, _dp, _dp, _dp, c_void_p, c_size_t, c_void_p]),
     "cheb_anneal_general_adjoint": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, _dp, c_void_p, c_void_p, c_void_p, c_int,
                                             c_double, c_int, _dp, _dp, _dp, _dp, _dp, c_void_p, c_size_t, c_void_p]),
+    "cheb_anneal_checkpointed": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, c_void_p, c_int, c_double, c_int,
+                                         c_void_p, c_void_p, c_size_t, c_void_p]),
+    "cheb_anneal_general_checkpointed": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, _dp, c_void_p, c_int, c_double,
+                                                 c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
     "cheb_energy_grad": (c_int, [c_int, _dp, _dp, c_void_p, c_void_p, c_int, _dp, _dp, _dp, c_void_p, c_size_t,
                                  c_void_p]),
     "cheb_wait_selftest": (c_int, [c_void_p, c_size_t, c_void_p]),

@@ -382,13 +382,81 @@ def _auto_store_vectors(n: int, prec: str, device, kmax: int) -> int:
     return 6 + 2 * max(1, int(np.ceil(np.sqrt(max(kmax, 1)))))
 
 
+class Checkpoint:
+    """The adjoint workspace that a checkpointed forward run filled (cheb_anneal_checkpointed);
+    pass it to anneal_adjoint / anneal_general_adjoint as checkpoint=."""
+
+    def __init__(self, workspace, store_vectors: int):
+        self.workspace = workspace
+        self.store_vectors = store_vectors
+
+
+def _checkpointed(fn, n, S, args, psi, boundaries, prec, tol, method, store_vectors, kmax):
+    _check_state(psi, n)
+    if boundaries.dtype != psi.dtype or tuple(boundaries.shape) != (S, 1 << n) or not boundaries.is_contiguous():
+        raise ValueError("boundaries must be a contiguous (S, 2^n) tensor of psi's dtype")
+    if store_vectors is None:
+        store_vectors = _auto_store_vectors(n, prec, psi.device, kmax())
+    ws = _adjoint_workspace(n, prec, psi.device, store_vectors)
+    p, nb = _ws_ptr(ws)
+    code = fn(n, *args, ctypes.c_void_p(psi.data_ptr()), PREC[prec], float(tol), METHOD[method],
+              ctypes.c_void_p(boundaries.data_ptr()), ctypes.c_void_p(p), nb, _stream_ptr(psi.device))
+    _lib.check(code, fn.__name__)
+    return Checkpoint(ws, store_vectors)
+
+
+def anneal_checkpointed(h, J, gammas, ts, psi, boundaries, tol: Optional[float] = None, method: str = "chebyshev",
+                        store_vectors: Optional[int] = None) -> Checkpoint:
+    """psi <- prod_s exp(-i t_s H(gamma_s)) psi in place, writing the segment starts to
+    boundaries and leaving the last segment's Clenshaw vectors in an adjoint workspace
+    (cheb_anneal_checkpointed); returns that Checkpoint for anneal_adjoint."""
+    h, J = _f64(h), _f64(J)
+    gammas, ts = _f64(gammas), _f64(ts)
+    n, S = h.shape[0], gammas.shape[0]
+    assert ts.shape[0] == S
+    prec = precision_of(psi)
+    if tol is None:
+        tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+    return _checkpointed(_lib.lib().cheb_anneal_checkpointed, n, S, (_dp(h), _dp(J), S, _dp(gammas), _dp(ts)), psi,
+                         boundaries, prec, tol, method, store_vectors,
+                         lambda: _degree_upper_bound(h, J, gammas, ts, tol, method))
+
+
+def anneal_general_checkpointed(h, J, a_s, b_s, ts, psi, boundaries, tol: Optional[float] = None,
+                                method: str = "chebyshev", store_vectors: Optional[int] = None) -> Checkpoint:
+    """The checkpointed form of anneal_general (cheb_anneal_general_checkpointed)."""
+    h, J = _f64(h), _f64(J)
+    a_s, b_s, ts = _f64(a_s), _f64(b_s), _f64(ts)
+    n, S = h.shape[0], a_s.shape[0]
+    assert b_s.shape[0] == S and ts.shape[0] == S
+    prec = precision_of(psi)
+    if tol is None:
+        tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+    return _checkpointed(_lib.lib().cheb_anneal_general_checkpointed, n, S,
+                         (_dp(h), _dp(J), S, _dp(a_s), _dp(b_s), _dp(ts)), psi, boundaries, prec, tol, method,
+                         store_vectors,
+                         lambda: _degree_upper_bound(np.abs(b_s).max() * h, np.abs(b_s).max() * J, a_s, ts, tol,
+                                                     method))
+
+
+def _adjoint_ws_for(n, prec, device, store_vectors, checkpoint, kmax):
+    if checkpoint is not None:
+        return checkpoint.workspace
+    if store_vectors is None:
+        store_vectors = _auto_store_vectors(n, prec, device, kmax())
+    return _adjoint_workspace(n, prec, device, store_vectors)
+
+
 def anneal_adjoint(h, J, gammas, ts, boundaries, psi_T, grad, tol: Optional[float] = None,
-                   method: str = "chebyshev", store_vectors: Optional[int] = None):
+                   method: str = "chebyshev", store_vectors: Optional[int] = None,
+                   checkpoint: Optional[Checkpoint] = None):
     """Gradients of a loss on the final state of a schedule (see cheb_anneal_adjoint).
 
     grad (CUDA tensor like psi_T) holds dL/dpsi_T on entry and dL/dpsi_0 on return.
     store_vectors: state vectors of workspace for the Clenshaw vectors b_k (>= K keeps
     all of them; fewer regenerates them from anchors; None chooses by free memory).
+    checkpoint: the result of anneal_checkpointed for this schedule, psi_T and
+    boundaries (its workspace is used, and the last segment is not recomputed).
     Returns dict of numpy arrays: gamma (S), t (S), h (n), J (n x n, upper triangle)."""
     h, J = _f64(h), _f64(J)
     gammas, ts = _f64(gammas), _f64(ts)
@@ -399,10 +467,8 @@ def anneal_adjoint(h, J, gammas, ts, boundaries, psi_T, grad, tol: Optional[floa
     for x in (boundaries, psi_T, grad):
         if not x.is_cuda or not x.is_contiguous() or x.dtype != psi_T.dtype:
             raise ValueError("boundaries, psi_T and grad must be contiguous CUDA tensors of one complex dtype")
-    if store_vectors is None:
-        store_vectors = _auto_store_vectors(n, prec, psi_T.device,
-                                            _degree_upper_bound(h, J, gammas, ts, tol, method))
-    ws = _adjoint_workspace(n, prec, psi_T.device, store_vectors)
+    ws = _adjoint_ws_for(n, prec, psi_T.device, store_vectors, checkpoint,
+                         lambda: _degree_upper_bound(h, J, gammas, ts, tol, method))
     p, nb = _ws_ptr(ws)
     gg, gt, gh, gJ = np.zeros(S), np.zeros(S), np.zeros(n), np.zeros((n, n))
     code = _lib.lib().cheb_anneal_adjoint(n, _dp(h), _dp(J), S, _dp(gammas), _dp(ts),
@@ -415,9 +481,11 @@ def anneal_adjoint(h, J, gammas, ts, boundaries, psi_T, grad, tol: Optional[floa
 
 
 def anneal_general_adjoint(h, J, a_s, b_s, ts, boundaries, psi_T, grad, tol: Optional[float] = None,
-                           method: str = "chebyshev", store_vectors: Optional[int] = None):
+                           method: str = "chebyshev", store_vectors: Optional[int] = None,
+                           checkpoint: Optional[Checkpoint] = None):
     """Gradients through cheb_anneal_general (see cheb_anneal_general_adjoint); grad holds
-    dL/dpsi_T on entry and dL/dpsi_0 on return. Returns dict: a, b, t (S), h (n), J (n x n)."""
+    dL/dpsi_T on entry and dL/dpsi_0 on return; checkpoint as in anneal_adjoint.
+    Returns dict: a, b, t (S), h (n), J (n x n)."""
     h, J = _f64(h), _f64(J)
     a_s, b_s, ts = _f64(a_s), _f64(b_s), _f64(ts)
     n, S = h.shape[0], a_s.shape[0]
@@ -427,11 +495,9 @@ def anneal_general_adjoint(h, J, a_s, b_s, ts, boundaries, psi_T, grad, tol: Opt
     for x in (boundaries, psi_T, grad):
         if not x.is_cuda or not x.is_contiguous() or x.dtype != psi_T.dtype:
             raise ValueError("boundaries, psi_T and grad must be contiguous CUDA tensors of one complex dtype")
-    if store_vectors is None:
-        store_vectors = _auto_store_vectors(n, prec, psi_T.device,
-                                            _degree_upper_bound(np.abs(b_s).max() * h, np.abs(b_s).max() * J,
-                                                                a_s, ts, tol, method))
-    ws = _adjoint_workspace(n, prec, psi_T.device, store_vectors)
+    ws = _adjoint_ws_for(n, prec, psi_T.device, store_vectors, checkpoint,
+                         lambda: _degree_upper_bound(np.abs(b_s).max() * h, np.abs(b_s).max() * J, a_s, ts, tol,
+                                                     method))
     p, nb = _ws_ptr(ws)
     ga, gb, gt, gh, gJ = np.zeros(S), np.zeros(S), np.zeros(S), np.zeros(n), np.zeros((n, n))
     code = _lib.lib().cheb_anneal_general_adjoint(

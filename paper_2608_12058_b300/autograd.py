@@ -31,7 +31,13 @@ class AnnealFn(torch.autograd.Function):
         S = gn.shape[0]
         y = psi0.detach().clone().contiguous()
         bnd = torch.empty((S, y.numel()), dtype=y.dtype, device=y.device)
-        api.anneal(hn, Jn, gn, tn, y, tol=tol, method=method, boundaries=bnd, info=False)
+        ctx.ckpt = None
+        if any(ctx.needs_input_grad[:5]):
+            # the adjoint then skips the last segment's forward recomputation
+            ctx.ckpt = api.anneal_checkpointed(hn, Jn, gn, tn, y, bnd, tol=tol, method=method,
+                                               store_vectors=store_vectors)
+        else:
+            api.anneal(hn, Jn, gn, tn, y, tol=tol, method=method, boundaries=bnd, info=False)
         ctx.save_for_backward(bnd, y)
         ctx.params = (hn, Jn, gn, tn, tol, method, store_vectors)
         ctx.dev = (h.device, J.device, gammas.device, ts.device)
@@ -42,7 +48,9 @@ class AnnealFn(torch.autograd.Function):
         bnd, y = ctx.saved_tensors
         hn, Jn, gn, tn, tol, method, store_vectors = ctx.params
         g = grad_out.detach().to(y.dtype).contiguous().clone()
-        out = api.anneal_adjoint(hn, Jn, gn, tn, bnd, y, g, tol=tol, method=method, store_vectors=store_vectors)
+        out = api.anneal_adjoint(hn, Jn, gn, tn, bnd, y, g, tol=tol, method=method, store_vectors=store_vectors,
+                                 checkpoint=ctx.ckpt)
+        ctx.ckpt = None
         dh = torch.from_numpy(out["h"]).to(ctx.dev[0])
         dJ = torch.from_numpy(out["J"]).to(ctx.dev[1])
         dg = torch.from_numpy(out["gamma"]).to(ctx.dev[2])
@@ -60,7 +68,12 @@ class AnnealGeneralFn(torch.autograd.Function):
         S = an.shape[0]
         y = psi0.detach().clone().contiguous()
         bnd = torch.empty((S, y.numel()), dtype=y.dtype, device=y.device)
-        api.anneal_general(hn, Jn, an, bn, tn, y, tol=tol, method=method, boundaries=bnd, info=False)
+        ctx.ckpt = None
+        if any(ctx.needs_input_grad[:6]):
+            ctx.ckpt = api.anneal_general_checkpointed(hn, Jn, an, bn, tn, y, bnd, tol=tol, method=method,
+                                                       store_vectors=store_vectors)
+        else:
+            api.anneal_general(hn, Jn, an, bn, tn, y, tol=tol, method=method, boundaries=bnd, info=False)
         ctx.save_for_backward(bnd, y)
         ctx.params = (hn, Jn, an, bn, tn, tol, method, store_vectors)
         ctx.dev = (h.device, J.device, a_s.device, b_s.device, ts.device)
@@ -72,7 +85,8 @@ class AnnealGeneralFn(torch.autograd.Function):
         hn, Jn, an, bn, tn, tol, method, store_vectors = ctx.params
         g = grad_out.detach().to(y.dtype).contiguous().clone()
         out = api.anneal_general_adjoint(hn, Jn, an, bn, tn, bnd, y, g, tol=tol, method=method,
-                                         store_vectors=store_vectors)
+                                         store_vectors=store_vectors, checkpoint=ctx.ckpt)
+        ctx.ckpt = None
         conv = lambda key, dev: torch.from_numpy(out[key]).to(dev)
         return (g, conv("h", ctx.dev[0]), conv("J", ctx.dev[1]), conv("a", ctx.dev[2]), conv("b", ctx.dev[3]),
                 conv("t", ctx.dev[4]), None, None, None)

@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <mutex>
 #include <vector>
 
 #include "fused.cuh"
@@ -653,6 +654,176 @@ struct StepRunner {
     }
 };
 
+StepRunner make_runner(const Ctx& C, const AdjLayout& A, int n, int precision) {
+    StepRunner R;
+    R.prec = precision;
+    R.flags = C.flags();
+    R.scratch = C.ws + A.fwd.coef + (size_t)(kMaxK + 1) * 2 * sizeof(double);
+    R.fused = fused_supported(n, precision) && n > (precision == CHEB_FP32 ? kSmallMaxF32 : kSmallMaxF64);
+    if (R.fused) R.plan = fused_plan(n, precision);
+    return R;
+}
+
+// One segment's operator and series: H_s = b_s H_P + gamma_s sum_j X_j on the frozen
+// interval (b_s c, r_s), its fixed-point tables (uploaded) and coefficients.
+struct Segment {
+    double bsc = 1.0, c = 0.0, r = 1.0, g = 0.0;
+    FixedOp F;
+    std::vector<std::complex<double>> coef;
+    int K = -1;
+};
+
+cheb_status_t segment_setup(const Ctx& C, int n, const double* h, const double* J, const double* b_s,
+                            const double* gamma_s, const double* t_s, int s, double emin, double emax, double tol_s,
+                            cheb_method_t method, Segment& G) {
+    G.bsc = b_s ? b_s[s] : 1.0;
+    G.c = G.bsc * 0.5 * (emax + emin);
+    G.r = std::fabs(G.bsc) * 0.5 * (emax - emin) + std::fabs(gamma_s[s]) * n;
+    if (!(G.r > 0)) G.r = 1.0;
+    G.g = gamma_s[s] / G.r;
+    std::vector<double> hb(n), Jb((size_t)n * n);
+    for (int i = 0; i < n; ++i) hb[i] = G.bsc * h[i];
+    for (size_t q = 0; q < (size_t)n * n; ++q) Jb[q] = G.bsc * J[q];
+    G.F = make_fixed(n, hb.data(), Jb.data(), G.c, G.r, C.prec == CHEB_FP32 ? kMaxQF32 : 62);
+    if (G.F.Q < 24) return CHEB_ERR_UNSUPPORTED;
+    cheb_status_t st = upload_tables(C, G.F);
+    if (st != CHEB_OK) return st;
+    int slices = 1;
+    double err = 0.0;
+    st = slice_coefficients(t_s[s], G.c, G.r, tol_s, method, 0, G.coef, &G.K, &slices, &err);
+    if (st != CHEB_OK) return st;
+    return slices == 1 ? CHEB_OK : CHEB_ERR_UNSUPPORTED;
+}
+
+StepArgs segment_base(const Ctx& C, const AdjLayout& A, const Segment& G) {
+    StepArgs b{};
+    b.n = C.n;
+    b.M = A.fwd.M;
+    b.Q = G.F.Q;
+    b.tiles = C.tiles();
+    b.elow = C.elow();
+    b.jq = (const int64_t*)(C.ws + A.fwd.jq);
+    b.g = G.g;
+    return b;
+}
+
+// Where the b_k of a segment of degree K live: all of them in the pool (store), or a
+// ring of kRing regenerated upward from anchor pairs (b_a, b_{a+1}) every `gap` steps.
+struct SegPool {
+    unsigned char* pool = nullptr;
+    size_t vstride = 0;
+    int K = 0;
+    bool store = true;
+    int n_anch = 0, gap = 0;
+    SegPool(unsigned char* p, size_t vs, int K_, int64_t nvec) : pool(p), vstride(vs), K(K_) {
+        store = nvec >= K;
+        if (!store) {
+            n_anch = (int)std::min<int64_t>(std::max<int64_t>(0, (nvec - kRing) / 2), 1 << 16);
+            gap = std::max(1, (K - 1 + n_anch) / (n_anch + 1));
+        }
+    }
+    static bool fits(int K, int64_t nvec) { return nvec >= K || nvec >= kRing + 2; }
+    unsigned char* bvec(int j) const {  // b_j, 1 <= j <= K
+        return store ? pool + (size_t)(j - 1) * vstride : pool + (size_t)(j % kRing) * vstride;
+    }
+    int anchor_slot(int a) const {  // anchor pair index for b_a, or -1
+        if (store || a < 1 + gap || (a - 1) % gap != 0 || a > K - 2) return -1;
+        const int m = (a - 1) / gap - 1;
+        return m < n_anch ? m : -1;
+    }
+    unsigned char* anchor_ptr(int m, int which) const { return pool + (size_t)(kRing + 2 * m + which) * vstride; }
+};
+
+// The segment's forward Clenshaw vectors b_K .. b_1 from its start state psi_s into
+// the pool (Algorithm 2's recurrence on the step kernels), saving the anchor pairs.
+// Afterwards b_1 .. b_min(K, kRing) (every b_k when storing) are in their slots.
+cheb_status_t forward_fill(const SegPool& P, const StepRunner& runner, const StepArgs& base,
+                           const std::vector<std::complex<double>>& coef, const void* psi_s, int prec, int64_t N,
+                           size_t vb, cudaStream_t s0) {
+    const int K = P.K;
+    launch_scale(prec, N, psi_s, P.bvec(K), coef[K].real(), coef[K].imag(), s0);
+    for (int j = K - 1; j >= 1; --j) {
+        StepArgs a = base;
+        a.b1 = P.bvec(j + 1);
+        a.b2 = (j + 2 <= K) ? P.bvec(j + 2) : P.bvec(j);  // not read when sgn = 0
+        a.psi = psi_s;
+        a.out = P.bvec(j);
+        a.ck_re = coef[j].real();
+        a.ck_im = coef[j].imag();
+        a.scale = 2.0;
+        a.sgn = (j + 2 <= K) ? -1.0 : 0.0;
+        if (runner.run(a, s0) != cudaSuccess) return CHEB_ERR_CUDA;
+        const int m = P.anchor_slot(j);
+        if (m >= 0) {
+            CUDA_TRY(cudaMemcpyAsync(P.anchor_ptr(m, 0), P.bvec(j), vb, cudaMemcpyDeviceToDevice, s0));
+            CUDA_TRY(cudaMemcpyAsync(P.anchor_ptr(m, 1), P.bvec(j + 1), vb, cudaMemcpyDeviceToDevice, s0));
+        }
+    }
+    return CHEB_OK;
+}
+
+// Checkpoints left by cheb_anneal(_general)_checkpointed: the last segment's pool is
+// filled, so the next adjoint call on the same workspace with the same arguments
+// skips that segment's forward recomputation. Any adjoint call on the workspace
+// consumes the record (the pool is overwritten by the adjoint).
+struct Checkpoint {
+    const void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int n = 0, S = 0, prec = 0, method = 0;
+    double tol = 0.0;
+    uint64_t hash = 0;
+    const void* psi_T = nullptr;
+    const void* boundaries = nullptr;
+    bool operator==(const Checkpoint& o) const {
+        return ws == o.ws && ws_bytes == o.ws_bytes && n == o.n && S == o.S && prec == o.prec &&
+               method == o.method && tol == o.tol && hash == o.hash && psi_T == o.psi_T &&
+               boundaries == o.boundaries;
+    }
+};
+
+std::mutex g_ck_mu;
+std::vector<Checkpoint> g_ck;
+
+// FNV-1a over the schedule and couplings (b_s absent hashes as a marker).
+uint64_t schedule_hash(int n, const double* h, const double* J, int S, const double* b_s, const double* a_s,
+                       const double* t_s) {
+    uint64_t x = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t bytes) {
+        const unsigned char* c = (const unsigned char*)p;
+        for (size_t i = 0; i < bytes; ++i) x = (x ^ c[i]) * 1099511628211ull;
+    };
+    mix(h, sizeof(double) * n);
+    mix(J, sizeof(double) * n * n);
+    mix(a_s, sizeof(double) * S);
+    mix(t_s, sizeof(double) * S);
+    const int has_b = b_s ? 1 : 0;
+    mix(&has_b, sizeof(has_b));
+    if (b_s) mix(b_s, sizeof(double) * S);
+    return x;
+}
+
+void checkpoint_put(const Checkpoint& k) {
+    std::lock_guard<std::mutex> lk(g_ck_mu);
+    g_ck.erase(std::remove_if(g_ck.begin(), g_ck.end(), [&](const Checkpoint& c) { return c.ws == k.ws; }),
+               g_ck.end());
+    g_ck.push_back(k);
+}
+
+// Removes the workspace's record; true when it matches k.
+bool checkpoint_take(const Checkpoint& k) {
+    std::lock_guard<std::mutex> lk(g_ck_mu);
+    bool hit = false;
+    for (auto it = g_ck.begin(); it != g_ck.end();) {
+        if (it->ws == k.ws) {
+            hit = hit || (*it == k);
+            it = g_ck.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return hit;
+}
+
 }  // namespace
 }  // namespace cheb
 
@@ -700,7 +871,6 @@ cheb_status_t adjoint_impl(int n, const double* h, const double* J, int S, const
     double emin = 0, emax = 0;
     cheb_status_t st = bounds_impl(C, h, J, &emin, &emax);
     if (st != CHEB_OK) return st;
-    const double c0 = 0.5 * (emax + emin);
     const double tol_s = tol / S;
     // unscaled energy tables for dL/db_s (general segments only)
     int Q0 = 0;
@@ -713,7 +883,7 @@ cheb_status_t adjoint_impl(int n, const double* h, const double* J, int S, const
                       s0);
         CUDA_TRY(cudaGetLastError());
     }
-    std::vector<double> hb(n), Jb((size_t)n * n), gb_out(S, 0.0);
+    std::vector<double> gb_out(S, 0.0);
     double* slots = (double*)(ws + A.slots);
     double* outs = (double*)(ws + A.outs);
     unsigned char* pool = ws + A.pool;
@@ -721,12 +891,20 @@ cheb_status_t adjoint_impl(int n, const double* h, const double* J, int S, const
     auto ring = [&](int k) { return ws + A.ring[k % kRing]; };  // bbar_k
     std::vector<double> gg(S), gt(S);
     const int Mt = A.fwd.M;
-    StepRunner runner;
-    runner.prec = precision;
-    runner.flags = C.flags();
-    runner.scratch = ws + A.fwd.coef + (size_t)(kMaxK + 1) * 2 * sizeof(double);
-    runner.fused = fused_supported(n, precision) && n > (precision == CHEB_FP32 ? kSmallMaxF32 : kSmallMaxF64);
-    if (runner.fused) runner.plan = fused_plan(n, precision);
+    const StepRunner runner = make_runner(C, A, n, precision);
+    // the last segment's pool may already hold its forward vectors
+    Checkpoint key;
+    key.ws = workspace;
+    key.ws_bytes = ws_bytes;
+    key.n = n;
+    key.S = S;
+    key.prec = precision;
+    key.method = method;
+    key.tol = tol;
+    key.hash = schedule_hash(n, h, J, S, b_s, gamma_s, t_s);
+    key.psi_T = psi_T;
+    key.boundaries = boundaries;
+    const bool have_ckpt = checkpoint_take(key);
     double* gauge = outs + (size_t)n * n + n + 16;
     double* bt = gauge;       // <ybar_T, y_T>
     double* rot = gauge + 2;  // e^{-i th} of the current segment
@@ -735,23 +913,13 @@ cheb_status_t adjoint_impl(int n, const double* h, const double* J, int S, const
     std::vector<double> seg_r(S, 1.0);
     std::vector<int> seg_K(S, 0);
     for (int s = S - 1; s >= 0; --s) {
-        const double bsc = b_s ? b_s[s] : 1.0;
-        const double c = bsc * c0;
-        double r = std::fabs(bsc) * 0.5 * (emax - emin) + std::fabs(gamma_s[s]) * n;
-        if (!(r > 0)) r = 1.0;
-        const double g = gamma_s[s] / r;
-        for (int i = 0; i < n; ++i) hb[i] = bsc * h[i];
-        for (size_t qq = 0; qq < (size_t)n * n; ++qq) Jb[qq] = bsc * J[qq];
-        FixedOp F = make_fixed(n, hb.data(), Jb.data(), c, r, precision == CHEB_FP32 ? kMaxQF32 : 62);
-        if (F.Q < 24) return CHEB_ERR_UNSUPPORTED;
-        st = upload_tables(C, F);
+        Segment G;
+        st = segment_setup(C, n, h, J, b_s, gamma_s, t_s, s, emin, emax, tol_s, method, G);
         if (st != CHEB_OK) return st;
-        std::vector<std::complex<double>> coef;
-        int K = -1, slices = 1;
-        double err = 0.0;
-        st = slice_coefficients(t_s[s], c, r, tol_s, method, 0, coef, &K, &slices, &err);
-        if (st != CHEB_OK) return st;
-        if (slices != 1) return CHEB_ERR_UNSUPPORTED;
+        const double bsc = G.bsc, c = G.c, r = G.r;
+        const FixedOp& F = G.F;
+        const std::vector<std::complex<double>>& coef = G.coef;
+        const int K = G.K;
         const void* psi_s = (const unsigned char*)boundaries + (size_t)s * vb;
         const void* y_s = (s == S - 1) ? psi_T : (const unsigned char*)boundaries + (size_t)(s + 1) * vb;
         // <ybar, H y_s> and the gauge invariant <ybar, y_s> into this segment's record;
@@ -802,49 +970,16 @@ cheb_status_t adjoint_impl(int n, const double* h, const double* J, int S, const
             }
             continue;
         }
-        // Where the b_k live: all of them in the pool (store), or a ring of kRing
-        // regenerated upward from anchor pairs (b_a, b_{a+1}) every `gap` steps.
-        const bool store = nvec >= K;
-        if (!store && nvec < kRing + 2) return CHEB_ERR_WORKSPACE;
-        const int n_anch = store ? 0 : (int)std::min<int64_t>((nvec - kRing) / 2, 1 << 16);
-        const int gap = store ? 0 : std::max(1, (K - 1 + n_anch) / (n_anch + 1));
-        auto bvec = [&](int j) -> unsigned char* {  // b_j, 1 <= j <= K
-            return store ? pool + (size_t)(j - 1) * A.vstride : pool + (size_t)(j % kRing) * A.vstride;
-        };
-        auto anchor_slot = [&](int a) -> int {  // anchor pair index for b_a, or -1
-            if (store || a < 1 + gap || (a - 1) % gap != 0 || a > K - 2) return -1;
-            const int m = (a - 1) / gap - 1;
-            return m < n_anch ? m : -1;
-        };
-        auto anchor_ptr = [&](int m, int which) {
-            return pool + (size_t)(kRing + 2 * m + which) * A.vstride;
-        };
-        StepArgs base{};
-        base.n = n;
-        base.M = Mt;
-        base.Q = F.Q;
-        base.tiles = C.tiles();
-        base.elow = C.elow();
-        base.jq = (const int64_t*)(ws + A.fwd.jq);
-        base.g = g;
-        // forward recomputation from psi_s down to b_1
-        launch_scale(precision, N, psi_s, bvec(K), coef[K].real(), coef[K].imag(), s0);
-        for (int j = K - 1; j >= 1; --j) {
-            StepArgs a = base;
-            a.b1 = bvec(j + 1);
-            a.b2 = (j + 2 <= K) ? bvec(j + 2) : bvec(j);  // not read when sgn = 0
-            a.psi = psi_s;
-            a.out = bvec(j);
-            a.ck_re = coef[j].real();
-            a.ck_im = coef[j].imag();
-            a.scale = 2.0;
-            a.sgn = (j + 2 <= K) ? -1.0 : 0.0;
-            if (runner.run(a, s0) != cudaSuccess) return CHEB_ERR_CUDA;
-            const int m = anchor_slot(j);
-            if (m >= 0) {
-                CUDA_TRY(cudaMemcpyAsync(anchor_ptr(m, 0), bvec(j), vb, cudaMemcpyDeviceToDevice, s0));
-                CUDA_TRY(cudaMemcpyAsync(anchor_ptr(m, 1), bvec(j + 1), vb, cudaMemcpyDeviceToDevice, s0));
-            }
+        if (!SegPool::fits(K, nvec)) return CHEB_ERR_WORKSPACE;
+        const SegPool P(pool, A.vstride, K, nvec);
+        const bool store = P.store;
+        auto bvec = [&](int j) { return P.bvec(j); };
+        const StepArgs base = segment_base(C, A, G);
+        // forward recomputation from psi_s down to b_1 (already done by a checkpointed
+        // forward for the last segment)
+        if (!(have_ckpt && s == S - 1)) {
+            st = forward_fill(P, runner, base, coef, psi_s, precision, N, vb, s0);
+            if (st != CHEB_OK) return st;
         }
         int have = store ? K : std::min(K, kRing);  // b_1 .. b_have are current
         // b_0 := y; bbar_0 = ybar moves into the ring and grad accumulates psibar
@@ -876,10 +1011,10 @@ cheb_status_t adjoint_impl(int n, const double* h, const double* J, int S, const
             // (b_{j-2}, b_{j-1}) from an anchor where there is one
             const int need = std::min(k1 + 2, K);
             for (int j = have + 1; j <= need; ++j) {
-                const int m = anchor_slot(j - 2);
+                const int m = P.anchor_slot(j - 2);
                 if (m >= 0) {
-                    CUDA_TRY(cudaMemcpyAsync(bvec(j - 2), anchor_ptr(m, 0), vb, cudaMemcpyDeviceToDevice, s0));
-                    CUDA_TRY(cudaMemcpyAsync(bvec(j - 1), anchor_ptr(m, 1), vb, cudaMemcpyDeviceToDevice, s0));
+                    CUDA_TRY(cudaMemcpyAsync(bvec(j - 2), P.anchor_ptr(m, 0), vb, cudaMemcpyDeviceToDevice, s0));
+                    CUDA_TRY(cudaMemcpyAsync(bvec(j - 1), P.anchor_ptr(m, 1), vb, cudaMemcpyDeviceToDevice, s0));
                 }
                 StepArgs a = base;
                 a.b1 = bvec(j - 1);
@@ -1006,6 +1141,111 @@ extern "C" cheb_status_t cheb_anneal_general_adjoint(int n, const double* h, con
     if (!b_s) return CHEB_ERR_INVALID_ARG;
     return adjoint_impl(n, h, J, S, b_s, a_s, t_s, boundaries, psi_T, grad, precision, tol, method, grad_a, grad_b,
                         grad_t, grad_h, grad_J, workspace, ws_bytes, stream);
+}
+
+namespace {
+
+// Forward run of a schedule for a later adjoint call: segments 0..S-2 as in
+// cheb_anneal_general, then the last segment on the adjoint's own step runner with its
+// Clenshaw vectors placed in the adjoint workspace's pool (every b_k, or the ring and
+// anchor pairs), and y = Ht b_1 - b_2 + c_0 psi_s (Algorithm 2's final step) into psi.
+cheb_status_t checkpointed_impl(int n, const double* h, const double* J, int S, const double* b_s,
+                                const double* gamma_s, const double* t_s, void* psi, cheb_precision_t precision,
+                                double tol, cheb_method_t method, void* boundaries, void* workspace, size_t ws_bytes,
+                                void* stream) {
+    if (n < 1 || n > kMaxQubits || S < 1 || !h || !J || !gamma_s || !t_s || !psi || !boundaries)
+        return CHEB_ERR_INVALID_ARG;
+    if (precision != CHEB_FP32 && precision != CHEB_FP64) return CHEB_ERR_INVALID_ARG;
+    if (!finite_all(h, n) || !finite_all(J, (size_t)n * n) || !finite_all(gamma_s, S) || !finite_all(t_s, S) ||
+        (b_s && !finite_all(b_s, S)))
+        return CHEB_ERR_INVALID_ARG;
+    if (!(tol > 0) || !std::isfinite(tol)) return CHEB_ERR_INVALID_ARG;
+    if (method != CHEB_METHOD_CHEBYSHEV && method != CHEB_METHOD_CF && method != CHEB_METHOD_REMEZ)
+        return CHEB_ERR_INVALID_ARG;
+    if (((uintptr_t)boundaries | (uintptr_t)psi) & 15) return CHEB_ERR_INVALID_ARG;
+    AdjLayout A = adj_layout(n, precision);
+    if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < A.total_fixed) return CHEB_ERR_WORKSPACE;
+    const int64_t nvec = (int64_t)std::min<size_t>((ws_bytes - A.total_fixed) / A.vstride, 1 << 20);
+    // the workspace's pool is about to change: no earlier checkpoint of it stays valid
+    Checkpoint key;
+    key.ws = workspace;
+    checkpoint_take(key);
+    cheb_status_t st = CHEB_OK;
+    if (S > 1) {
+        // the adjoint workspace starts with a forward workspace
+        st = anneal_run(n, h, J, S, b_s, gamma_s, t_s, psi, precision, tol, method, boundaries, workspace, ws_bytes,
+                        stream, nullptr, S - 1);
+        if (st != CHEB_OK) return st;
+    }
+    unsigned char* ws = (unsigned char*)workspace;
+    cudaStream_t s0 = (cudaStream_t)stream;
+    Ctx C{n, precision, A.fwd, ws, s0};
+    const int64_t N = (int64_t)1 << n;
+    const size_t vb = (size_t)N * A.fwd.cbytes;
+    CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), s0));
+    double emin = 0, emax = 0;
+    st = bounds_impl(C, h, J, &emin, &emax);
+    if (st != CHEB_OK) return st;
+    Segment G;
+    st = segment_setup(C, n, h, J, b_s, gamma_s, t_s, S - 1, emin, emax, tol / S, method, G);
+    if (st != CHEB_OK) return st;
+    unsigned char* psi_s = (unsigned char*)boundaries + (size_t)(S - 1) * vb;
+    CUDA_TRY(cudaMemcpyAsync(psi_s, psi, vb, cudaMemcpyDeviceToDevice, s0));
+    const int K = G.K;
+    if (K == 0) {
+        launch_scale(precision, N, psi_s, psi, G.coef[0].real(), G.coef[0].imag(), s0);
+    } else {
+        if (!SegPool::fits(K, nvec)) return CHEB_ERR_WORKSPACE;
+        const SegPool P(ws + A.pool, A.vstride, K, nvec);
+        const StepRunner runner = make_runner(C, A, n, precision);
+        const StepArgs base = segment_base(C, A, G);
+        st = forward_fill(P, runner, base, G.coef, psi_s, precision, N, vb, s0);
+        if (st != CHEB_OK) return st;
+        StepArgs a = base;
+        a.b1 = P.bvec(1);
+        a.b2 = K >= 2 ? P.bvec(2) : P.bvec(1);  // not read when sgn = 0
+        a.psi = psi_s;
+        a.out = psi;
+        a.ck_re = G.coef[0].real();
+        a.ck_im = G.coef[0].imag();
+        a.scale = 1.0;
+        a.sgn = K >= 2 ? -1.0 : 0.0;
+        if (runner.run(a, s0) != cudaSuccess) return CHEB_ERR_CUDA;
+    }
+    CUDA_TRY(cudaGetLastError());
+    st = read_flags(C);
+    if (st != CHEB_OK) return st;
+    key.ws_bytes = ws_bytes;
+    key.n = n;
+    key.S = S;
+    key.prec = precision;
+    key.method = method;
+    key.tol = tol;
+    key.hash = schedule_hash(n, h, J, S, b_s, gamma_s, t_s);
+    key.psi_T = psi;
+    key.boundaries = boundaries;
+    checkpoint_put(key);
+    return CHEB_OK;
+}
+
+}  // namespace
+
+extern "C" cheb_status_t cheb_anneal_checkpointed(int n, const double* h, const double* J, int S,
+                                                  const double* gamma_s, const double* t_s, void* psi,
+                                                  cheb_precision_t precision, double tol, cheb_method_t method,
+                                                  void* boundaries, void* workspace, size_t ws_bytes, void* stream) {
+    return checkpointed_impl(n, h, J, S, nullptr, gamma_s, t_s, psi, precision, tol, method, boundaries, workspace,
+                             ws_bytes, stream);
+}
+
+extern "C" cheb_status_t cheb_anneal_general_checkpointed(int n, const double* h, const double* J, int S,
+                                                          const double* a_s, const double* b_s, const double* t_s,
+                                                          void* psi, cheb_precision_t precision, double tol,
+                                                          cheb_method_t method, void* boundaries, void* workspace,
+                                                          size_t ws_bytes, void* stream) {
+    if (!b_s) return CHEB_ERR_INVALID_ARG;
+    return checkpointed_impl(n, h, J, S, b_s, a_s, t_s, psi, precision, tol, method, boundaries, workspace,
+                             ws_bytes, stream);
 }
 
 // Loss L = <psi|H_P|psi>: value, dL/dpsi (torch convention: 2 H_P psi), dL/dh, dL/dJ.

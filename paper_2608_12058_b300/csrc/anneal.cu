@@ -14,16 +14,15 @@
 
 using namespace cheb;
 
-namespace {
-
 // Segments H_s = b_s H_P + a_s sum_j X_j (b_s = 1 when b is null), psi <- exp(-i t_s H_s) psi
-// in order. b_s H_P has energies b_s E(z): its centre is b_s c and its half-width
-// |b_s| (Emax - Emin)/2, so one bounds scan serves every segment; the fixed-point
-// tables are rebuilt per segment from the scaled couplings.
-cheb_status_t anneal_impl(int n, const double* h, const double* J, int S, const double* b_s, const double* a_s,
-                          const double* t_s, void* psi, cheb_precision_t precision, double tol,
-                          cheb_method_t method, void* boundaries, void* workspace, size_t ws_bytes, void* stream,
-                          cheb_info_t* infos) {
+// in order for s < s_end (s_end < 0: all S). b_s H_P has energies b_s E(z): its centre is
+// b_s c and its half-width |b_s| (Emax - Emin)/2, so one bounds scan serves every segment;
+// the fixed-point tables are rebuilt per segment from the scaled couplings. Every segment
+// takes the tolerance tol / S.
+cheb_status_t cheb::anneal_run(int n, const double* h, const double* J, int S, const double* b_s,
+                               const double* a_s, const double* t_s, void* psi, cheb_precision_t precision,
+                               double tol, cheb_method_t method, void* boundaries, void* workspace,
+                               size_t ws_bytes, void* stream, cheb_info_t* infos, int s_end) {
     cheb_status_t st = check_common(n, h, J, precision, workspace, ws_bytes);
     if (st != CHEB_OK) return st;
     if (S < 1 || !a_s || !t_s || !psi || ((uintptr_t)psi & 15) != 0) return CHEB_ERR_INVALID_ARG;
@@ -41,7 +40,8 @@ cheb_status_t anneal_impl(int n, const double* h, const double* J, int S, const 
     const size_t vbytes = ((size_t)1 << n) * C.L.cbytes;
     const double tol_s = tol / S;
     std::vector<double> hb(n), Jb((size_t)n * n);
-    for (int s = 0; s < S; ++s) {
+    const int S_run = (s_end < 0 || s_end > S) ? S : s_end;
+    for (int s = 0; s < S_run; ++s) {
         const double b = b_s ? b_s[s] : 1.0;
         const double c = b * 0.5 * (emax + emin);
         double r = std::fabs(b) * 0.5 * (emax - emin) + std::fabs(a_s[s]) * n;
@@ -92,14 +92,12 @@ cheb_status_t anneal_impl(int n, const double* h, const double* J, int S, const 
     return CHEB_OK;
 }
 
-}  // namespace
-
 extern "C" cheb_status_t cheb_anneal(int n, const double* h, const double* J, int S, const double* gamma_s,
                                      const double* t_s, void* psi, cheb_precision_t precision, double tol,
                                      cheb_method_t method, void* boundaries, void* workspace, size_t ws_bytes,
                                      void* stream, cheb_info_t* infos) {
-    return anneal_impl(n, h, J, S, nullptr, gamma_s, t_s, psi, precision, tol, method, boundaries, workspace,
-                       ws_bytes, stream, infos);
+    return anneal_run(n, h, J, S, nullptr, gamma_s, t_s, psi, precision, tol, method, boundaries, workspace,
+                      ws_bytes, stream, infos);
 }
 
 extern "C" cheb_status_t cheb_anneal_general(int n, const double* h, const double* J, int S, const double* a_s,
@@ -108,8 +106,8 @@ extern "C" cheb_status_t cheb_anneal_general(int n, const double* h, const doubl
                                              void* boundaries, void* workspace, size_t ws_bytes, void* stream,
                                              cheb_info_t* infos) {
     if (!b_s) return CHEB_ERR_INVALID_ARG;
-    return anneal_impl(n, h, J, S, b_s, a_s, t_s, psi, precision, tol, method, boundaries, workspace, ws_bytes,
-                       stream, infos);
+    return anneal_run(n, h, J, S, b_s, a_s, t_s, psi, precision, tol, method, boundaries, workspace, ws_bytes,
+                      stream, infos);
 }
 
 // Fourth-order commutator-free Magnus step (the exponential integrator for
@@ -166,8 +164,8 @@ extern "C" cheb_status_t cheb_magnus4(int n, const double* h, const double* J, i
     if (!magnus_args_ok(steps, dt, nodes)) return CHEB_ERR_INVALID_ARG;
     std::vector<double> a, b, t;
     magnus_segments(steps, dt, nodes, a, b, t);
-    return anneal_impl(n, h, J, 2 * steps, b.data(), a.data(), t.data(), psi, precision, tol, method, boundaries,
-                       workspace, ws_bytes, stream, infos);
+    return anneal_run(n, h, J, 2 * steps, b.data(), a.data(), t.data(), psi, precision, tol, method, boundaries,
+                      workspace, ws_bytes, stream, infos);
 }
 
 extern "C" cheb_status_t cheb_magnus4_adjoint(int n, const double* h, const double* J, int steps, const double* dt,

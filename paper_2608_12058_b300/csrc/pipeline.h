@@ -55,6 +55,12 @@ cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::c
 void autotune_cache_once();
 // Synchronises and maps the device status word to a status code.
 cheb_status_t read_flags(const Ctx& C);
+// Segments s < s_end (s_end < 0: all S) of a schedule H_s = b_s H_P + a_s sum_j X_j
+// (b_s = 1 when b_s is null), each with tolerance tol / S (cheb_anneal_general).
+cheb_status_t anneal_run(int n, const double* h, const double* J, int S, const double* b_s, const double* a_s,
+                         const double* t_s, void* psi, cheb_precision_t precision, double tol,
+                         cheb_method_t method, void* boundaries, void* workspace, size_t ws_bytes, void* stream,
+                         cheb_info_t* infos, int s_end = -1);
 // Coefficients of exp(-i a x) * exp(-i ts c) for one slice, slicing t automatically
 // (splits = 0) when the degree would exceed the coefficient table.
 cheb_status_t slice_coefficients(double t, double c, double r, double tol, int method, int splits,

@@ -302,3 +302,86 @@ def test_magnus4_schedule_parameter_gradients(cuda_lib):
         pm[i] -= eps
         fd = (loss(pp) - loss(pm)) / (2 * eps)
         assert abs(fd - p.grad[i].item()) < 1e-7, (i, fd, p.grad[i].item())
+
+
+@pytest.mark.parametrize("n,dtype_name,S,sv", [(16, "complex64", 3, 8), (16, "complex64", 1, None),
+                                               (12, "complex128", 2, 8), (9, "complex64", 2, None)])
+def test_checkpointed_forward_skips_recomputation(cuda_lib, n, dtype_name, S, sv):
+    """cheb_anneal_checkpointed gives the forward result of cheb_anneal, and the adjoint
+    that uses its checkpoint returns bit for bit what the adjoint returns when it
+    recomputes the last segment itself from the same boundaries and psi_T (the pool
+    holds the same vectors either way: all b_k (sv = None), or the ring and anchors)."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    dt = getattr(torch, dtype_name)
+    a = I.config_anneal(n=n, S=S, seed=7)
+    x0 = torch.from_numpy(I.uniform_state(n)).to(dt).cuda()
+    tol = 1e-12 if dtype_name == "complex128" else 2.0 ** -23
+    y_ref = x0.clone()
+    b_ref = torch.empty((S, 1 << n), dtype=dt, device="cuda")
+    api.anneal(a.h, a.J, a.gammas, a.ts, y_ref, boundaries=b_ref)
+    y = x0.clone()
+    bnd = torch.empty((S, 1 << n), dtype=dt, device="cuda")
+    ck = api.anneal_checkpointed(a.h, a.J, a.gammas, a.ts, y, bnd, store_vectors=sv)
+    # segments before the last run on the same path as cheb_anneal
+    assert torch.equal(bnd, b_ref)
+    rel = (torch.linalg.vector_norm(y - y_ref) / torch.linalg.vector_norm(y_ref)).item()
+    assert rel <= (1e-12 if dtype_name == "complex128" else 2e-6), rel
+    _, g, _, _ = api.energy_grad(a.h, a.J, y)
+    g_ck, g_re = g.clone(), g.clone()
+    o_ck = api.anneal_adjoint(a.h, a.J, a.gammas, a.ts, bnd, y, g_ck, checkpoint=ck)
+    o_re = api.anneal_adjoint(a.h, a.J, a.gammas, a.ts, bnd, y, g_re, store_vectors=ck.store_vectors)
+    assert torch.equal(g_ck, g_re)
+    for key in ("gamma", "t", "h", "J"):
+        assert np.array_equal(o_ck[key], o_re[key]), key
+    # the checkpoint is consumed: a second adjoint call on its workspace recomputes
+    g_again = g.clone()
+    o_again = api.anneal_adjoint(a.h, a.J, a.gammas, a.ts, bnd, y, g_again, checkpoint=ck)
+    assert torch.equal(g_again, g_re)
+    assert np.array_equal(o_again["gamma"], o_re["gamma"])
+
+
+def test_checkpoint_with_other_arguments_is_not_used(cuda_lib):
+    """A checkpoint taken for one tolerance does not serve an adjoint call with another:
+    the adjoint recomputes, and its gradients equal those of a fresh workspace."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    n, S = 14, 2
+    a = I.config_anneal(n=n, S=S, seed=9)
+    y = torch.from_numpy(I.uniform_state(n)).to(torch.complex64).cuda()
+    bnd = torch.empty((S, 1 << n), dtype=torch.complex64, device="cuda")
+    ck = api.anneal_checkpointed(a.h, a.J, a.gammas, a.ts, y, bnd, tol=1e-6, store_vectors=8)
+    _, g, _, _ = api.energy_grad(a.h, a.J, y)
+    g1, g2 = g.clone(), g.clone()
+    o1 = api.anneal_adjoint(a.h, a.J, a.gammas, a.ts, bnd, y, g1, tol=2.0 ** -23, checkpoint=ck)
+    o2 = api.anneal_adjoint(a.h, a.J, a.gammas, a.ts, bnd, y, g2, tol=2.0 ** -23, store_vectors=8)
+    assert torch.equal(g1, g2)
+    assert np.array_equal(o1["h"], o2["h"])
+
+
+def test_general_checkpointed_forward_skips_recomputation(cuda_lib):
+    """The same for cheb_anneal_general_checkpointed (segments b_s H_P + a_s sum_j X_j)."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    n, S = 15, 3
+    a = I.config_anneal(n=n, S=S, seed=11)
+    b_s = np.array([0.5, -0.8, 1.2])
+    y = torch.from_numpy(I.uniform_state(n)).to(torch.complex64).cuda()
+    bnd = torch.empty((S, 1 << n), dtype=torch.complex64, device="cuda")
+    ck = api.anneal_general_checkpointed(a.h, a.J, a.gammas, b_s, a.ts, y, bnd, store_vectors=8)
+    y_ref = torch.from_numpy(I.uniform_state(n)).to(torch.complex64).cuda()
+    api.anneal_general(a.h, a.J, a.gammas, b_s, a.ts, y_ref)
+    assert (torch.linalg.vector_norm(y - y_ref) / torch.linalg.vector_norm(y_ref)).item() <= 2e-6
+    _, g, _, _ = api.energy_grad(a.h, a.J, y)
+    g1, g2 = g.clone(), g.clone()
+    o1 = api.anneal_general_adjoint(a.h, a.J, a.gammas, b_s, a.ts, bnd, y, g1, checkpoint=ck)
+    o2 = api.anneal_general_adjoint(a.h, a.J, a.gammas, b_s, a.ts, bnd, y, g2, store_vectors=8)
+    assert torch.equal(g1, g2)
+    for key in ("a", "b", "t", "h", "J"):
+        assert np.array_equal(o1[key], o2[key]), key
