@@ -466,7 +466,16 @@ cheb_status_t cheb_get_fused_split_fp64(int n, int* l, int* h);
  * to the separate launches (same operations in the same order per amplitude).
  * Used for n >= 22 when the split has at least two strided passes, l <= 1 and a
  * last range of 6..9 bits; other splits keep the separate launches.
- * on: 0 off, 1 on (process-wide). cheb_get_fused_blocking returns the setting.
+ * Mode 2 blocks the two strided passes of a split that has exactly two (ranges
+ * A = [loA, loB) and B = [loB, n) of 6..9 bits, B no wider than A and at most one bit
+ * narrower): amplitudes are grouped by their bits [4, loA), and the tiles of the
+ * upper range B of a group run right after the tiles of range A of that group, so
+ * b_{k+1} and the partial sum come back from L2: the two passes move 24 B per
+ * amplitude of DRAM traffic instead of 48. Flip sums are plain FP32 in descending bit
+ * order, as in the separate launches, so results are identical. The lag between a
+ * group's A and B tiles is one group (environment variable CHEB_PAIR_LAG: 1..16).
+ * on: 0 off, 1 the blocked tail, 2 the blocked strided pair (process-wide; the
+ * autotuner's per-n choice takes precedence). cheb_get_fused_blocking returns it.
  */
 cheb_status_t cheb_set_fused_blocking(int on);
 int cheb_get_fused_blocking(void);
@@ -487,7 +496,7 @@ int cheb_get_fused_compensated(void);
  * Clenshaw steps of a synthetic problem of that size under the built-in choice and
  * under every candidate: the plain one-pass kernel (n <= 24 FP32, <= 26 FP64) and the
  * fused step with each valid bit split of at most 4 (FP32) or 5 (FP64) L2 partner
- * bits, and for FP32 the L2-blocked tail where the split allows it. The fastest
+ * bits, and for FP32 the L2-blocked tail and strided pair where the split allows them. The fastest
  * candidate is installed process-wide: AUTO then uses that path, split and blocking
  * for n (cheb_set_fused_split / cheb_set_fused_split_fp64 override it again).
  * If the environment variable CHEB_AUTOTUNE_CACHE names a file, the result is appended
@@ -503,7 +512,7 @@ int cheb_get_fused_compensated(void);
 typedef struct {
     int path;                    /* CHEB_PATH_PLAIN or CHEB_PATH_FUSED */
     int l, h;                    /* the split, for FUSED */
-    int blocking;                /* FP32: L2-blocked step tail on */
+    int blocking;                /* FP32: 1 L2-blocked step tail, 2 L2-blocked strided pair */
     int candidates;              /* configurations timed */
     double best_ms_per_step;     /* the chosen configuration */
     double default_ms_per_step;  /* the built-in choice */
@@ -562,14 +571,16 @@ cheb_status_t cheb_energy(int n, const double* h, const double* J, const void* p
  *   time. cheb_profile_reset drops the records.
  * Kinds: 3 plain one-pass step, 5 adjoint accumulation (cheb_anneal_adjoint),
  * 6 fused low pass, 7 fused strided (high-bit) pass, 8 L2-blocked step tail (last
- * strided pass + low pass, cheb_set_fused_blocking).
+ * strided pass + low pass, cheb_set_fused_blocking(1)), 9 L2-blocked strided pair
+ * (cheb_set_fused_blocking(2)).
  */
 typedef enum {
     CHEB_KERNEL_STEP_PLAIN = 3,
     CHEB_KERNEL_ADJOINT_ACC = 5,
     CHEB_KERNEL_FUSED_LOW = 6,
     CHEB_KERNEL_FUSED_HIGH = 7,
-    CHEB_KERNEL_FUSED_TAIL = 8
+    CHEB_KERNEL_FUSED_TAIL = 8,
+    CHEB_KERNEL_FUSED_PAIR = 9
 } cheb_kernel_kind_t;
 
 /*

@@ -357,6 +357,22 @@ def _adjoint_workspace(n: int, prec: str, device, store_vectors: int):
     return torch.empty(need + 256, dtype=torch.uint8, device=device)
 
 
+def adjoint_workspace(n: int, precision: str, store_vectors: int, device=None):
+    """A device buffer for the adjoint entry points with a pool of store_vectors state
+    vectors (pass it as workspace= to reuse one allocation across calls)."""
+    import torch
+
+    if device is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    return _adjoint_workspace(n, precision, device, store_vectors)
+
+
+def _check_adjoint_ws(ws, n, prec, store_vectors):
+    need = int(_lib.lib().cheb_adjoint_workspace_bytes(n, PREC[prec], max(0, store_vectors)))
+    if not ws.is_cuda or ws.dtype.itemsize != 1 or _ws_ptr(ws)[1] < need:
+        raise ValueError("workspace must be a CUDA byte buffer of adjoint_workspace(n, precision, store_vectors)")
+
+
 def _degree_upper_bound(h, J, gammas, ts, tol: float, method: str) -> int:
     """Largest Chebyshev degree over the segments, from the 1-norm bound of the spectral
     radius (the library's r never exceeds it, and K grows with r)."""
@@ -391,13 +407,15 @@ class Checkpoint:
         self.store_vectors = store_vectors
 
 
-def _checkpointed(fn, n, S, args, psi, boundaries, prec, tol, method, store_vectors, kmax):
+def _checkpointed(fn, n, S, args, psi, boundaries, prec, tol, method, store_vectors, kmax, workspace):
     _check_state(psi, n)
     if boundaries.dtype != psi.dtype or tuple(boundaries.shape) != (S, 1 << n) or not boundaries.is_contiguous():
         raise ValueError("boundaries must be a contiguous (S, 2^n) tensor of psi's dtype")
     if store_vectors is None:
         store_vectors = _auto_store_vectors(n, prec, psi.device, kmax())
-    ws = _adjoint_workspace(n, prec, psi.device, store_vectors)
+    if workspace is not None:
+        _check_adjoint_ws(workspace, n, prec, store_vectors)
+    ws = workspace if workspace is not None else _adjoint_workspace(n, prec, psi.device, store_vectors)
     p, nb = _ws_ptr(ws)
     code = fn(n, *args, ctypes.c_void_p(psi.data_ptr()), PREC[prec], float(tol), METHOD[method],
               ctypes.c_void_p(boundaries.data_ptr()), ctypes.c_void_p(p), nb, _stream_ptr(psi.device))
@@ -406,10 +424,11 @@ def _checkpointed(fn, n, S, args, psi, boundaries, prec, tol, method, store_vect
 
 
 def anneal_checkpointed(h, J, gammas, ts, psi, boundaries, tol: Optional[float] = None, method: str = "chebyshev",
-                        store_vectors: Optional[int] = None) -> Checkpoint:
+                        store_vectors: Optional[int] = None, workspace=None) -> Checkpoint:
     """psi <- prod_s exp(-i t_s H(gamma_s)) psi in place, writing the segment starts to
     boundaries and leaving the last segment's Clenshaw vectors in an adjoint workspace
-    (cheb_anneal_checkpointed); returns that Checkpoint for anneal_adjoint."""
+    (cheb_anneal_checkpointed; workspace: an adjoint_workspace buffer to use, else a new
+    one); returns that Checkpoint for anneal_adjoint."""
     h, J = _f64(h), _f64(J)
     gammas, ts = _f64(gammas), _f64(ts)
     n, S = h.shape[0], gammas.shape[0]
@@ -419,11 +438,12 @@ def anneal_checkpointed(h, J, gammas, ts, psi, boundaries, tol: Optional[float] 
         tol = 2.0 ** -23 if prec == "fp32" else 1e-12
     return _checkpointed(_lib.lib().cheb_anneal_checkpointed, n, S, (_dp(h), _dp(J), S, _dp(gammas), _dp(ts)), psi,
                          boundaries, prec, tol, method, store_vectors,
-                         lambda: _degree_upper_bound(h, J, gammas, ts, tol, method))
+                         lambda: _degree_upper_bound(h, J, gammas, ts, tol, method), workspace)
 
 
 def anneal_general_checkpointed(h, J, a_s, b_s, ts, psi, boundaries, tol: Optional[float] = None,
-                                method: str = "chebyshev", store_vectors: Optional[int] = None) -> Checkpoint:
+                                method: str = "chebyshev", store_vectors: Optional[int] = None,
+                                workspace=None) -> Checkpoint:
     """The checkpointed form of anneal_general (cheb_anneal_general_checkpointed)."""
     h, J = _f64(h), _f64(J)
     a_s, b_s, ts = _f64(a_s), _f64(b_s), _f64(ts)
@@ -436,12 +456,15 @@ def anneal_general_checkpointed(h, J, a_s, b_s, ts, psi, boundaries, tol: Option
                          (_dp(h), _dp(J), S, _dp(a_s), _dp(b_s), _dp(ts)), psi, boundaries, prec, tol, method,
                          store_vectors,
                          lambda: _degree_upper_bound(np.abs(b_s).max() * h, np.abs(b_s).max() * J, a_s, ts, tol,
-                                                     method))
+                                                     method), workspace)
 
 
-def _adjoint_ws_for(n, prec, device, store_vectors, checkpoint, kmax):
+def _adjoint_ws_for(n, prec, device, store_vectors, checkpoint, kmax, workspace):
     if checkpoint is not None:
         return checkpoint.workspace
+    if workspace is not None:
+        _check_adjoint_ws(workspace, n, prec, 0 if store_vectors is None else store_vectors)
+        return workspace
     if store_vectors is None:
         store_vectors = _auto_store_vectors(n, prec, device, kmax())
     return _adjoint_workspace(n, prec, device, store_vectors)
@@ -449,7 +472,7 @@ def _adjoint_ws_for(n, prec, device, store_vectors, checkpoint, kmax):
 
 def anneal_adjoint(h, J, gammas, ts, boundaries, psi_T, grad, tol: Optional[float] = None,
                    method: str = "chebyshev", store_vectors: Optional[int] = None,
-                   checkpoint: Optional[Checkpoint] = None):
+                   checkpoint: Optional[Checkpoint] = None, workspace=None):
     """Gradients of a loss on the final state of a schedule (see cheb_anneal_adjoint).
 
     grad (CUDA tensor like psi_T) holds dL/dpsi_T on entry and dL/dpsi_0 on return.
@@ -457,6 +480,8 @@ def anneal_adjoint(h, J, gammas, ts, boundaries, psi_T, grad, tol: Optional[floa
     all of them; fewer regenerates them from anchors; None chooses by free memory).
     checkpoint: the result of anneal_checkpointed for this schedule, psi_T and
     boundaries (its workspace is used, and the last segment is not recomputed).
+    workspace: an adjoint_workspace buffer to use instead of a new one (its pool size
+    decides how the b_k are kept).
     Returns dict of numpy arrays: gamma (S), t (S), h (n), J (n x n, upper triangle)."""
     h, J = _f64(h), _f64(J)
     gammas, ts = _f64(gammas), _f64(ts)
@@ -468,7 +493,7 @@ def anneal_adjoint(h, J, gammas, ts, boundaries, psi_T, grad, tol: Optional[floa
         if not x.is_cuda or not x.is_contiguous() or x.dtype != psi_T.dtype:
             raise ValueError("boundaries, psi_T and grad must be contiguous CUDA tensors of one complex dtype")
     ws = _adjoint_ws_for(n, prec, psi_T.device, store_vectors, checkpoint,
-                         lambda: _degree_upper_bound(h, J, gammas, ts, tol, method))
+                         lambda: _degree_upper_bound(h, J, gammas, ts, tol, method), workspace)
     p, nb = _ws_ptr(ws)
     gg, gt, gh, gJ = np.zeros(S), np.zeros(S), np.zeros(n), np.zeros((n, n))
     code = _lib.lib().cheb_anneal_adjoint(n, _dp(h), _dp(J), S, _dp(gammas), _dp(ts),
@@ -482,7 +507,7 @@ def anneal_adjoint(h, J, gammas, ts, boundaries, psi_T, grad, tol: Optional[floa
 
 def anneal_general_adjoint(h, J, a_s, b_s, ts, boundaries, psi_T, grad, tol: Optional[float] = None,
                            method: str = "chebyshev", store_vectors: Optional[int] = None,
-                           checkpoint: Optional[Checkpoint] = None):
+                           checkpoint: Optional[Checkpoint] = None, workspace=None):
     """Gradients through cheb_anneal_general (see cheb_anneal_general_adjoint); grad holds
     dL/dpsi_T on entry and dL/dpsi_0 on return; checkpoint as in anneal_adjoint.
     Returns dict: a, b, t (S), h (n), J (n x n)."""
@@ -497,7 +522,7 @@ def anneal_general_adjoint(h, J, a_s, b_s, ts, boundaries, psi_T, grad, tol: Opt
             raise ValueError("boundaries, psi_T and grad must be contiguous CUDA tensors of one complex dtype")
     ws = _adjoint_ws_for(n, prec, psi_T.device, store_vectors, checkpoint,
                          lambda: _degree_upper_bound(np.abs(b_s).max() * h, np.abs(b_s).max() * J, a_s, ts, tol,
-                                                     method))
+                                                     method), workspace)
     p, nb = _ws_ptr(ws)
     ga, gb, gt, gh, gJ = np.zeros(S), np.zeros(S), np.zeros(S), np.zeros(n), np.zeros((n, n))
     code = _lib.lib().cheb_anneal_general_adjoint(
@@ -620,14 +645,15 @@ def autotune_reset():
     _lib.check(_lib.lib().cheb_autotune_reset(), "cheb_autotune_reset")
 
 
-def set_fused_blocking(on: bool):
-    """Run the last strided pass and the low pass of each fused step as one L2-blocked
-    launch (True) or as separate launches (False); results are identical."""
-    _lib.check(_lib.lib().cheb_set_fused_blocking(1 if on else 0), "cheb_set_fused_blocking")
+def set_fused_blocking(mode):
+    """L2-blocked launches of the fused step (cheb_set_fused_blocking): 0 / False
+    separate launches, 1 / True the last strided pass and the low pass as one launch,
+    2 the two strided passes as one launch; results are identical."""
+    _lib.check(_lib.lib().cheb_set_fused_blocking(int(mode)), "cheb_set_fused_blocking")
 
 
-def get_fused_blocking() -> bool:
-    return bool(_lib.lib().cheb_get_fused_blocking())
+def get_fused_blocking() -> int:
+    return int(_lib.lib().cheb_get_fused_blocking())
 
 
 def set_fused_compensated(on: bool):
@@ -639,7 +665,7 @@ def get_fused_compensated() -> bool:
     return bool(_lib.lib().cheb_get_fused_compensated())
 
 
-KERNEL_KIND = {"plain": 3, "adjoint_acc": 5, "low": 6, "high": 7, "tail": 8}
+KERNEL_KIND = {"plain": 3, "adjoint_acc": 5, "low": 6, "high": 7, "tail": 8, "pair": 9}
 
 
 def wait_selftest(device=None):
@@ -668,8 +694,8 @@ def profile_reset():
 
 
 def profile_read(kind: str):
-    """(launches timed, total device ms) for 'plain', 'low' or 'high' step kernels or
-    'adjoint_acc' (the adjoint's per-step accumulation)."""
+    """(launches timed, total device ms) for 'plain', 'low', 'high', 'tail' or 'pair' step
+    kernels or 'adjoint_acc' (the adjoint's per-step accumulation)."""
     c, ms = ctypes.c_longlong(), ctypes.c_double()
     _lib.check(_lib.lib().cheb_profile_read(KERNEL_KIND[kind], ctypes.byref(c), ctypes.byref(ms)),
                "cheb_profile_read")

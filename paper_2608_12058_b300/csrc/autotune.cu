@@ -52,6 +52,7 @@ std::vector<Candidate> candidates(int n, int prec) {
             fused_set_split(n, l, h);
             p = fused_plan(n, 0);
             if (fused_blocking_eligible(p)) out.push_back({CHEB_PATH_FUSED, l, h, 1});
+            if (fused_pair_eligible(p)) out.push_back({CHEB_PATH_FUSED, l, h, 2});
         }
         fused_set_split(n, -1, 0);
     } else {

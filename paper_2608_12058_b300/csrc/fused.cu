@@ -461,13 +461,14 @@ __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const St
         for (int p = 0; p < Cfg::kP; ++p) {
             AccT<C> S;
             S.zero();
+            // partners in descending bit order of the range
 #pragma unroll
-            for (int b = 1; b < Cfg::kP; b <<= 1) {
+            for (int b = Cfg::kP >> 1; b >= 1; b >>= 1) {
                 const int rho = rlo | ((p ^ b) << Cfg::kRowBitsT);
                 S.add(tile[rho * 8 + u]);
             }
 #pragma unroll
-            for (int j = 0; j < Cfg::kRowBitsT; ++j) {
+            for (int j = Cfg::kRowBitsT - 1; j >= 0; --j) {
                 const int rho = (rlo ^ (1 << j)) | (p << Cfg::kRowBitsT);
                 S.add(tile[rho * 8 + u]);
             }
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(StridedCfg<H>::kThreads, 1) k_strided(const St
 // chunks (2^(10-RB) rows, one chunk per row group p) into a second ring, so that the
 // consumers only read shared memory. 512 consumer threads (u = float4 within the
 // row, rho low bits = the rest of the thread index, rho high bits = p) form the flip
-// sums from the partner rows, in ascending bit order, and write q. Wide rows halve
+// sums from the partner rows, in descending bit order, and write q. Wide rows halve
 // the rows per byte, which pays where the range sits at large strides (rows many
 // MB apart); a 9-bit tile of wide rows would not fit, so RB = 5 takes H <= 8.
 template <int H, int RB = 4>
@@ -612,12 +613,13 @@ __global__ void __launch_bounds__(kLowThreads, 1)
         for (int p = 0; p < Cfg::kP; ++p) {
             AccT<C> S;
             S.zero();
-            // partners in ascending bit order of the range (the same order for both
-            // row widths and for the blocked tail, so all of them agree bit for bit)
+            // partners in descending bit order of the range (the same order for both
+            // row widths, the blocked tail and the blocked pair, so all of them agree
+            // bit for bit)
 #pragma unroll
-            for (int j = 0; j < Cfg::kRB; ++j) S.add(tile[((rlo ^ (1 << j)) | (p << Cfg::kRB)) * Cfg::kRowF4 + u]);
+            for (int b = Cfg::kP >> 1; b >= 1; b >>= 1) S.add(tile[(rlo | ((p ^ b) << Cfg::kRB)) * Cfg::kRowF4 + u]);
 #pragma unroll
-            for (int b = 1; b < Cfg::kP; b <<= 1) S.add(tile[(rlo | ((p ^ b) << Cfg::kRB)) * Cfg::kRowF4 + u]);
+            for (int j = Cfg::kRB - 1; j >= 0; --j) S.add(tile[((rlo ^ (1 << j)) | (p << Cfg::kRB)) * Cfg::kRowF4 + u]);
             float2 q0 = __ffma2_rn(g_hi, S.ra(), __fmul2_rn(g_lo, S.ra()));
             float2 q1 = __ffma2_rn(g_hi, S.rb(), __fmul2_rn(g_lo, S.rb()));
             if (need_slot) {
@@ -1032,9 +1034,9 @@ __global__ void __launch_bounds__(kMixedThreads, 1)
                 AccT<C> S;
                 S.zero();
 #pragma unroll
-                for (int j = 0; j < 6; ++j) S.add(tile[((rlo ^ (1 << j)) | (p << 6)) * 8 + u]);
+                for (int b = Cfg::kP >> 1; b >= 1; b >>= 1) S.add(tile[((rlo | ((p ^ b) << 6))) * 8 + u]);
 #pragma unroll
-                for (int b = 1; b < Cfg::kP; b <<= 1) S.add(tile[((rlo | ((p ^ b) << 6))) * 8 + u]);
+                for (int j = 5; j >= 0; --j) S.add(tile[((rlo ^ (1 << j)) | (p << 6)) * 8 + u]);
                 float2 q0 = __ffma2_rn(g_hi, S.ra(), __fmul2_rn(g_lo, S.ra()));
                 float2 q1 = __ffma2_rn(g_hi, S.rb(), __fmul2_rn(g_lo, S.rb()));
                 const int r = (int)(cc % Cfg::kSR);
@@ -1107,6 +1109,268 @@ __global__ void __launch_bounds__(kMixedThreads, 1)
             // the output is next step's b_{k+1}, not read again in this launch
             st_hint(la.out + T * kTF + t, make_float4(o00.x, o00.y, o01.x, o01.y), pol_out);
             st_hint(la.out + T * kTF + t + kCons, make_float4(o10.x, o10.y, o11.x, o11.y), pol_out);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2-blocked pair of strided passes: the two strided ranges of a step, A = [loA, loB)
+// and B = [loB, n), in one persistent launch, rows of 16 amplitudes (128 B). The
+// amplitudes are grouped by their bits [4, loA): group g holds 2^(4 + HA + HB)
+// amplitudes, 2^HB A-tiles (one per value of the bits of B) and 2^HA B-tiles (one per
+// value of the bits of A). A-tiles read b_{k+1} and the slot (b_{k+2}) from DRAM and
+// write q = s g S_A + sgn slot; the B-tiles of the same group, D groups later, read
+// b_{k+1} and q back from L2 and write q + s g S_B, so a step's two strided passes
+// move 24 B per amplitude of DRAM traffic instead of 48.
+//
+// Work items in order: A(0) .. A(D - 1), then A(s) followed by B(s - D) for
+// s = D .. G - 1, then B(G - D) .. B(G - 1). CTAs take items from a global counter;
+// before loading a B-tile the producer waits (bounded) until all A-tiles of its group
+// are published by the notifier warps (fence, then the group count), so an item only
+// waits on items taken before it.
+//
+// Consumers: 256 threads. In a tile of 2^H rows thread t holds column float4
+// u = t & 7 of the 2^(H-5) rows whose bits 0..4 are t >> 3: the flips of row bits
+// 5..H-1 come from registers and those of bits 0..4 from shared memory, 56 B of
+// shared-memory traffic per amplitude (the TMA fill, the own value, five partners)
+// against 96 B in the one-pass kernels. The slot is read with L2-only loads (it was
+// written by other SMs in this launch). The flip sum runs in descending bit order, as
+// in the one-pass kernels, so the pair and two separate passes agree bit for bit.
+constexpr int kPairCons = 256;
+constexpr int kPairThreads = kPairCons + 64;  // + producer warp + notifier warp
+
+template <int HA, int HB>
+struct PairCfg {
+    static constexpr int kHMax = HA > HB ? HA : HB;
+    static constexpr uint32_t kStage = (uint32_t)128 << kHMax;   // largest tile
+    static constexpr uint32_t kBytesA = (uint32_t)128 << HA;
+    static constexpr uint32_t kBytesB = (uint32_t)128 << HB;
+    static constexpr int kNSraw = (int)((200u * 1024u) / kStage);
+    static constexpr int kNS = kNSraw < 6 ? kNSraw : 6;
+    static constexpr int kNR = 8;                                 // completion records in flight
+    static constexpr size_t kItemOff = (size_t)kNS * kStage;
+    static constexpr size_t kNoteOff = kItemOff + 64;
+    static constexpr size_t kBarOff = kNoteOff + (size_t)kNR * sizeof(int64_t);
+    static constexpr size_t kAbortOff = kBarOff + (size_t)(2 * kNS + 2 * kNR) * sizeof(uint64_t);
+    static constexpr size_t kSmem = kAbortOff + 16;
+    static_assert(kNS >= 2 && kNS <= 8, "pair stages");
+};
+
+struct PairArgs {
+    const float4* b1;
+    const float4* slot_in;  // b_{k+2} (read by the A-tiles when sgn != 0)
+    float4* slot;           // receives q (may equal slot_in)
+    int loA, loB;           // loB = loA + HA, n = loB + HB
+    float scale_g, scale_glo, sgn;
+    unsigned long long* work;  // item counter (zero at launch)
+    unsigned* done;            // per group: A-tiles published (zero at launch)
+    int gbits;                 // loA - 4 (2^gbits groups)
+    int lag;                   // D, 1 <= D <= 2^gbits
+    int* flags;
+};
+
+__device__ __forceinline__ MixedItem pair_decode(unsigned long long i, int gbits, int HA, int HB, int lag) {
+    const unsigned long long G = 1ull << gbits, D = (unsigned long long)lag, NA = 1ull << HB, NB = 1ull << HA;
+    const unsigned long long seg = NA + NB, head = D * NA;
+    if (i < head) return {kItemStrided, (int64_t)(i / NA), (int64_t)(i % NA)};
+    const unsigned long long j = i - head, s = D + j / seg;
+    if (s < G) {
+        const unsigned long long r = j % seg;
+        return r < NA ? MixedItem{kItemStrided, (int64_t)s, (int64_t)r}
+                      : MixedItem{kItemLow, (int64_t)(s - D), (int64_t)(r - NA)};
+    }
+    const unsigned long long k = j - (G - D) * seg, g = G - D + k / NB;
+    if (g < G) return {kItemLow, (int64_t)g, (int64_t)(k % NB)};
+    return {kItemEnd, 0, 0};
+}
+
+__device__ __forceinline__ float4 ld_cg4(const float4* p) {
+    float4 v;
+    asm volatile("ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// One strided tile of 2^H rows (in shared memory, rows of 8 float4) on the 256
+// consumer threads: q = s g S + sgn w for the rows' amplitudes, written to slot.
+template <int H>
+__device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const float4* slot_in, float4* slot,
+                                          int64_t base, int64_t row_stride_f4, float2 g_hi, float2 g_lo, float2 sg,
+                                          bool need_slot, uint64_t pol_store) {
+    constexpr int P = 1 << (H - 5);
+    const int t = threadIdx.x;
+    const int u = t & 7, rq = t >> 3;
+    float4 v[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) v[i] = tile[(rq | (i << 5)) * 8 + u];
+    AccT<false> S[P];
+    // register bits H-1 .. 5 first (descending)
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        S[i].zero();
+#pragma unroll
+        for (int b = P >> 1; b >= 1; b >>= 1) S[i].add(v[i ^ b]);
+    }
+    float4 w[P];
+    if (need_slot) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) w[i] = ld_cg4(slot_in + base + (int64_t)(rq | (i << 5)) * row_stride_f4 + u);
+    }
+    // then row bits 4 .. 0 from shared memory
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+#pragma unroll
+        for (int j = 4; j >= 0; --j) S[i].add(tile[((rq ^ (1 << j)) | (i << 5)) * 8 + u]);
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        float2 q0 = __ffma2_rn(g_hi, S[i].ra(), __fmul2_rn(g_lo, S[i].ra()));
+        float2 q1 = __ffma2_rn(g_hi, S[i].rb(), __fmul2_rn(g_lo, S[i].rb()));
+        if (need_slot) {
+            q0 = __ffma2_rn(sg, lo2(w[i]), q0);
+            q1 = __ffma2_rn(sg, hi2(w[i]), q1);
+        }
+        st_hint(slot + base + (int64_t)(rq | (i << 5)) * row_stride_f4 + u, make_float4(q0.x, q0.y, q1.x, q1.y),
+                pol_store);
+    }
+}
+
+template <int HA, int HB>
+__global__ void __launch_bounds__(kPairThreads, 1)
+    k_pair(const PairArgs a, const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB) {
+    using Cfg = PairCfg<HA, HB>;
+    static_assert(HA >= 6 && HA <= 9 && HB >= 6 && HB <= 9, "pair ranges");
+    static_assert(Cfg::kSmem <= 227 * 1024, "shared memory");
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = (uint64_t*)(smem + Cfg::kBarOff);
+    uint64_t* empty = full + Cfg::kNS;
+    uint64_t* cdone = empty + Cfg::kNS;   // an A-tile's q stores are issued (8 warps)
+    uint64_t* cempty = cdone + Cfg::kNR;  // the notifier has published that record
+    volatile int* abort = (volatile int*)(smem + Cfg::kAbortOff);
+    long long* item = (long long*)(smem + Cfg::kItemOff);
+    volatile long long* note = (volatile long long*)(smem + Cfg::kNoteOff);
+    const int t = threadIdx.x;
+    const int warp = t >> 5, lane = t & 31;
+    const int sha = a.loA - 4;
+    if (t == 0) {
+        for (int i = 0; i < Cfg::kNS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kPairCons / 32);
+        }
+        for (int i = 0; i < Cfg::kNR; ++i) {
+            mbar_init(&cdone[i], kPairCons / 32);
+            mbar_init(&cempty[i], 1);
+        }
+        *abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == kPairCons / 32 + 1) {
+        // ---------------- notifier warp ----------------
+        if (lane != 0) return;
+        for (long long j = 0;; ++j) {
+            const int r = (int)(j % Cfg::kNR);
+            if (!mbar_wait(&cdone[r], (uint32_t)((j / Cfg::kNR) & 1), a.flags, abort)) break;
+            const long long g = note[r];
+            if (g < 0) break;
+            __threadfence();
+            atomicAdd(a.done + g, 1u);
+            mbar_arrive(&cempty[r]);
+        }
+        return;
+    }
+
+    if (warp == kPairCons / 32) {
+        // ---------------- producer warp ----------------
+        if (lane != 0) return;
+        int last[Cfg::kNS];
+        for (int i = 0; i < Cfg::kNS; ++i) last[i] = -1;
+        // the A-tiles' b_{k+1} is read again by the B-tiles of their group
+        const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
+        for (int it = 0;; ++it) {
+            const unsigned long long cur = atomicAdd(a.work, 1ull);
+            const MixedItem ci = pair_decode(cur, a.gbits, HA, HB, a.lag);
+            const int s = it % Cfg::kNS, k = it / Cfg::kNS;
+            if (k > 0 && !mbar_wait(&empty[s], (k - 1) & 1, a.flags, abort)) break;
+            unsigned char* d = smem + (size_t)s * Cfg::kStage;
+            if (ci.kind == kItemEnd) {
+                item[s] = -1;
+                mbar_arrive(&full[s]);
+                last[s] = k;
+                break;
+            }
+            if (ci.kind == kItemStrided) {
+                // A-tile: bits [4, loA) = g, bits of B = idx
+                item[s] = (long long)cur;
+                mbar_expect_tx(&full[s], Cfg::kBytesA);
+                constexpr int box = HA < 8 ? (1 << HA) : 256;
+#pragma unroll
+                for (int c = 0; c < (1 << HA) / box; ++c)
+                    tma_load_4d_hint(d + (size_t)c * box * 128, &mapA, 0, (int)ci.g, c * box, (int)ci.idx, &full[s],
+                                     pol_last);
+                last[s] = k;
+            } else {
+                if (!wait_count(a.done + ci.g, 1u << HB, a.flags, abort)) break;
+                // q of the group was written through the generic proxy by other SMs
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                item[s] = (long long)cur;
+                mbar_expect_tx(&full[s], Cfg::kBytesB);
+                constexpr int box = HB < 8 ? (1 << HB) : 256;
+                const int tlo = (int)(ci.g | (ci.idx << sha));  // bits [4, loB)
+#pragma unroll
+                for (int c = 0; c < (1 << HB) / box; ++c)
+                    tma_load_4d_hint(d + (size_t)c * box * 128, &mapB, 0, tlo, c * box, 0, &full[s], pol_first);
+                last[s] = k;
+            }
+        }
+        for (int i = 0; i < Cfg::kNS; ++i)
+            if (last[i] >= 0) mbar_drain(&full[i], last[i] & 1, a.flags);
+        return;
+    }
+
+    // ---------------- consumer warps ----------------
+    const float2 g_hi = dup(a.scale_g), g_lo = dup(a.scale_glo), sg = dup(a.sgn), one = dup(1.f);
+    const bool need_a = a.sgn != 0.f;
+    const uint64_t pol_last = policy_evict_last(), pol_first = policy_evict_first();
+    const int64_t rsA = (int64_t)1 << (a.loA - 1), rsB = (int64_t)1 << (a.loB - 1);
+    long long sj = 0;  // completion records sent
+    auto record = [&](long long g) -> bool {
+        __syncwarp();
+        bool ok = true;
+        if (lane == 0) {
+            const int r = (int)(sj % Cfg::kNR);
+            if (sj >= Cfg::kNR) ok = mbar_wait(&cempty[r], (uint32_t)(((sj / Cfg::kNR) - 1) & 1), a.flags, abort);
+            if (ok) {
+                if (warp == 0) note[r] = g;
+                mbar_arrive(&cdone[r]);
+            }
+        }
+        ++sj;
+        return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    };
+    for (int it = 0;; ++it) {
+        const int s = it % Cfg::kNS;
+        if (!mbar_wait(&full[s], (it / Cfg::kNS) & 1, a.flags, abort)) break;
+        const long long cur = item[s];
+        if (cur < 0) {
+            record(-1);
+            break;
+        }
+        const MixedItem ci = pair_decode((unsigned long long)cur, a.gbits, HA, HB, a.lag);
+        const float4* tile = (const float4*)(smem + (size_t)s * Cfg::kStage);
+        if (ci.kind == kItemStrided) {
+            const int64_t base = ci.g * 8 + (ci.idx << (a.loB - 1));
+            pair_tile<HA>(tile, a.slot_in, a.slot, base, rsA, g_hi, g_lo, sg, need_a, pol_last);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            if (!record(ci.g)) break;
+        } else {
+            const int64_t base = (ci.g | (ci.idx << sha)) * 8;
+            pair_tile<HB>(tile, a.slot, a.slot, base, rsB, g_hi, g_lo, one, true, pol_first);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
         }
     }
 }
@@ -1280,6 +1544,44 @@ cudaError_t launch_mixed(int H, const MixedArgs& m, int n, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+template <int HA, int HB>
+cudaError_t launch_pair_t(const PairArgs& a, int n, cudaStream_t s) {
+    using Cfg = PairCfg<HA, HB>;
+    CUtensorMap mapA, mapB, unused;
+    StridedArgs sa{};
+    sa.b1 = a.b1;
+    sa.sgn = 0.f;  // tensor maps of b_{k+1} only
+    sa.lo = a.loA;
+    cudaError_t e = strided_maps(sa, n, HA, 4, HA < 8 ? (1 << HA) : 256, &mapA, &unused);
+    if (e != cudaSuccess) return e;
+    sa.lo = a.loB;
+    e = strided_maps(sa, n, HB, 4, HB < 8 ? (1 << HB) : 256, &mapB, &unused);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_pair<HA, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    if (e != cudaSuccess) return e;
+    note_launch(kKindPair);
+    const int pi = prof_begin(kKindPair, s);
+    k_pair<HA, HB><<<(unsigned)num_sms(), kPairThreads, Cfg::kSmem, s>>>(a, mapA, mapB);
+    prof_end(pi, s);
+    return cudaGetLastError();
+}
+
+// The range sizes of two-pass plans (make_passes gives the first pass the extra bit).
+cudaError_t launch_pair(int HA, int HB, const PairArgs& a, int n, cudaStream_t s) {
+    switch (HA * 16 + HB) {
+        case 6 * 16 + 6: return launch_pair_t<6, 6>(a, n, s);
+        case 7 * 16 + 6: return launch_pair_t<7, 6>(a, n, s);
+        case 7 * 16 + 7: return launch_pair_t<7, 7>(a, n, s);
+        case 8 * 16 + 7: return launch_pair_t<8, 7>(a, n, s);
+        case 8 * 16 + 8: return launch_pair_t<8, 8>(a, n, s);
+        case 9 * 16 + 8: return launch_pair_t<9, 8>(a, n, s);
+        case 9 * 16 + 9: return launch_pair_t<9, 9>(a, n, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool pair_shape_ok(int HA, int HB) { return HA >= 6 && HA <= 9 && HB >= 6 && (HB == HA || HB == HA - 1); }
+
 // Split h strided bits above bit lo0 into near-equal passes of 3..9 bits.
 bool make_passes(int lo0, int h, FusedPlan& p) {
     p.npass = 0;
@@ -1301,18 +1603,32 @@ bool make_passes(int lo0, int h, FusedPlan& p) {
 
 }  // namespace
 
-// The L2-blocked tail needs an item counter and one counter per group of amplitudes
-// (at most 2^(n - 17) groups: the last strided range has at least 6 bits).
+// The L2-blocked launches need an item counter and one counter per group of
+// amplitudes: at most 2^(n - 17) groups for the blocked tail (its strided range has at
+// least 6 bits), 2^(n - 16) for the blocked pair (bits [4, loA), loA <= n - 12).
 constexpr int kMixedMinN = 22;
 size_t mixed_counter_bytes(int gbits) { return 8 + ((size_t)4 << gbits); }
 
 size_t fused_scratch_bytes(int n, int prec) {
     if (prec != 0 || n < kMixedMinN || n > kMaxQubits) return 0;
-    return (mixed_counter_bytes(n - 17) + 255) / 256 * 256;
+    return (mixed_counter_bytes(n - 16) + 255) / 256 * 256;
 }
 
+// Lag D of the blocked pair in groups (CHEB_PAIR_LAG, default 1): the B-tiles of group
+// g follow the A-tiles of group g + D.
+static int pair_lag() {
+    static int lag = 0;
+    if (lag == 0) {
+        const char* e = std::getenv("CHEB_PAIR_LAG");
+        const int v = e ? std::atoi(e) : 0;
+        lag = (v >= 1 && v <= 16) ? v : 1;
+    }
+    return lag;
+}
+
+// 0: separate launches, 1: L2-blocked tail, 2: L2-blocked strided pair.
 static int g_blocking = 0;
-void fused_set_blocking(int on) { g_blocking = on ? 1 : 0; }
+void fused_set_blocking(int mode) { g_blocking = (mode >= 0 && mode <= 2) ? mode : 0; }
 int fused_get_blocking() { return g_blocking; }
 
 // Per-n choices of the autotuner (-1: not tuned): the blocked tail, and the AUTO path.
@@ -1352,6 +1668,9 @@ bool fused_blocking_eligible(const FusedPlan& plan) {
     const int lastp = plan.npass - 1;
     return plan.prec == 0 && plan.n >= kMixedMinN && plan.npass >= 2 && plan.l <= 1 && plan.hb[lastp] >= 6 &&
            plan.hb[lastp] <= kMaxStrided;
+}
+bool fused_pair_eligible(const FusedPlan& plan) {
+    return plan.prec == 0 && plan.n >= kMixedMinN && plan.npass == 2 && pair_shape_ok(plan.hb[0], plan.hb[1]);
 }
 void fused_set_compensated(int on) { g_comp = on ? 1 : 0; }
 int fused_get_compensated() { return g_comp; }
@@ -1446,9 +1765,34 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void* sc
     // and the plan allows it (an earlier strided pass, at most one L2 partner bit, a
     // last range of 6..9 bits, scratch for the counters).
     const int lastp = plan.npass - 1;
-    const bool mixed = blocking_for(s.n) && scratch != nullptr && s.n >= kMixedMinN && plan.npass >= 2 && plan.l <= 1 &&
+    const int mode = blocking_for(s.n);
+    const bool mixed = mode == 1 && scratch != nullptr && s.n >= kMixedMinN && plan.npass >= 2 && plan.l <= 1 &&
                        plan.hb[lastp] >= 6 && plan.hb[lastp] <= kMaxStrided && s.out != s.b1;
-    const int nsep = mixed ? lastp : plan.npass;  // strided passes launched on their own
+    // The two strided passes of a two-pass plan run as one L2-blocked launch (plain
+    // flip sums only).
+    const bool pair = mode == 2 && !g_comp && scratch != nullptr && fused_pair_eligible(plan) && s.out != s.b1;
+    if (pair) {
+        PairArgs pa;
+        pa.b1 = (const float4*)s.b1;
+        pa.slot_in = (const float4*)s.b2;
+        pa.slot = q;
+        pa.loA = plan.lo[0];
+        pa.loB = plan.lo[1];
+        pa.scale_g = (float)s.scale * ghi;
+        pa.scale_glo = (float)s.scale * glo;
+        pa.sgn = (float)s.sgn;
+        pa.gbits = plan.lo[0] - 4;
+        pa.lag = (int)std::min<int64_t>(pair_lag(), (int64_t)1 << pa.gbits);
+        pa.work = (unsigned long long*)scratch;
+        pa.done = (unsigned*)((unsigned char*)scratch + 8);
+        pa.flags = flags;
+        cudaError_t e = cudaMemsetAsync(scratch, 0, mixed_counter_bytes(pa.gbits), st);
+        if (e != cudaSuccess) return e;
+        e = launch_pair(plan.hb[0], plan.hb[1], pa, s.n, st);
+        if (e != cudaSuccess) return e;
+        slot_coeff = 1.0f;
+    }
+    const int nsep = pair ? 0 : (mixed ? lastp : plan.npass);  // strided passes launched on their own
     for (int k = 0; k < nsep; ++k) {
         StridedArgs sa;
         sa.b1 = (const float4*)s.b1;

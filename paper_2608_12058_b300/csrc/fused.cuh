@@ -29,14 +29,17 @@ struct FusedPlan {
 size_t fused_scratch_bytes(int n, int prec);
 // Number of SMs of the current device (cached).
 int num_sms();
-// L2-blocked step tail (the last strided pass and the low pass in one launch): on/off.
-void fused_set_blocking(int on);
+// L2-blocked launches: 0 off, 1 the step tail (the last strided pass and the low pass in
+// one launch), 2 the strided pair (both strided passes of a two-pass plan in one launch).
+void fused_set_blocking(int mode);
 int fused_get_blocking();
 // Choices of the autotuner: per (prec, n) the AUTO path (-1 = built-in rule) and, for
 // FP32, the blocked tail (-1 = the process-wide switch).
 void tuned_set(int prec, int n, int path, int blocking);
 int tuned_auto_path(int prec, int n);
 bool fused_blocking_eligible(const FusedPlan& plan);
+// The blocked strided pair applies (two strided passes of 6..9 bits, FP32).
+bool fused_pair_eligible(const FusedPlan& plan);
 // Kahan-compensated flip sums in the fused FP32 passes: on/off (process-wide).
 void fused_set_compensated(int on);
 int fused_get_compensated();

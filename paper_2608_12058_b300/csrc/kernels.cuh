@@ -18,6 +18,7 @@ enum KernelKind : int {
     kKindLow = 6,
     kKindHigh = 7,
     kKindMixed = 8,
+    kKindPair = 9,
 };
 void note_launch(int kind);
 // Whether step kernels are launched with programmatic dependent launch (on by default;

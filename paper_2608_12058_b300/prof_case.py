@@ -6,10 +6,13 @@
     python -m paper_2608_12058_b300.prof_case tail N L H [STEPS]
         the same with the L2-blocked step tail on (kernel names k_strided* for the
         earlier strided passes, k_mixed for the last strided pass + low pass).
-    python -m paper_2608_12058_b300.prof_case compare N [STEPS]
-        times STEPS fused steps at n = N (default split) with the separate launches and
-        with the L2-blocked step tail, twice each (CUDA events around the call, per-kind
-        event timing from the library), and prints ms per step and per launch.
+    python -m paper_2608_12058_b300.prof_case pair N L H [STEPS]
+        the same with the L2-blocked strided pair (kernel names k_pair and k_low).
+    python -m paper_2608_12058_b300.prof_case compare N [STEPS [L H]]
+        times STEPS fused steps at n = N (default split, or (L, H)) with the separate
+        launches, the L2-blocked step tail and the L2-blocked strided pair, twice each
+        (CUDA events around the call; then a run with the library's per-kind event
+        timing), and prints ms per step and per launch.
     python -m paper_2608_12058_b300.prof_case ff N L H [STEPS]
         STEPS float-float fused steps of the FP64 path (complex128 states) at n = N with
         the split (L, H) (kernel names k_low_ff and k_strided_ff).
@@ -36,7 +39,7 @@ import sys
 import numpy as np
 
 
-def fused_steps(n, l, h, steps, blocking=False):
+def fused_steps(n, l, h, steps, blocking=0):
     import torch
 
     from . import api
@@ -77,43 +80,52 @@ def ff_steps(n, l, h, steps):
     print("ok", nrm)
 
 
-def compare(n, steps):
+def compare(n, steps, split=None):
+    """Step time of the fused FP32 step at n with separate launches (mode 0), the
+    L2-blocked tail (1) and the L2-blocked strided pair (2): CUDA events without
+    profiling, then a profiled run for the per-kernel split."""
     import torch
 
     from . import api
     from . import inputs as I
 
+    if split is not None:
+        api.set_fused_split(n, split[0], split[1])
     c = I.config_family(n, 1.0, 1.0, 0, "uniform")
     x = torch.full((1 << n,), 2 ** (-n / 2), dtype=torch.complex64, device="cuda")
     rng = np.random.default_rng(0)
     coef = (rng.standard_normal(steps + 1) + 1j * rng.standard_normal(steps + 1)) / (4 * steps)
     print("n", n, "split", api.get_fused_split(n), "steps", steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     try:
         for _ in range(2):
-            for blocking in (False, True):
-                api.set_fused_blocking(blocking)
+            for mode in (0, 1, 2):
+                api.set_fused_blocking(mode)
                 api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef[:4], x, path="fused")  # warm-up
                 torch.cuda.synchronize()
-                api.profile_reset()
-                api.profile_enable(True)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
                 e0.record()
                 api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef, x, path="fused")
                 e1.record()
                 torch.cuda.synchronize()
-                api.profile_enable(False)
                 ms = e0.elapsed_time(e1)
                 assert np.isfinite(float(torch.linalg.vector_norm(x)))
+                api.profile_reset()
+                api.profile_enable(True)
+                api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef, x, path="fused")
+                torch.cuda.synchronize()
+                api.profile_enable(False)
                 parts = []
-                for kind in ("low", "high", "tail"):
+                for kind in ("low", "high", "tail", "pair"):
                     cnt, tot = api.profile_read(kind)
                     if cnt:
                         parts.append(f"{kind} {cnt} x {tot / cnt * 1e3:.1f} us")
-                print(f"  blocked tail {'on ' if blocking else 'off'}: {ms / steps:.3f} ms/step, "
-                      f"{(1 << n) * steps / ms * 1e3:.3e} amplitude-updates/s; " + ", ".join(parts))
+                print(f"  blocking {mode}: {ms / steps:.3f} ms/step, "
+                      f"{(1 << n) * steps / ms * 1e3:.3e} amplitude-updates/s; profiled: " + ", ".join(parts))
     finally:
-        api.set_fused_blocking(False)
+        api.set_fused_blocking(0)
+        if split is not None:
+            api.set_fused_split(n, -1)
 
 
 def adjoint(n, S):
@@ -263,7 +275,8 @@ def main(argv):
     elif argv[0] == "cluster":
         cluster(int(argv[1]), int(argv[2]))
     elif argv[0] == "compare":
-        compare(int(argv[1]), int(argv[2]) if len(argv) > 2 else 40)
+        split = (int(argv[3]), int(argv[4])) if len(argv) > 4 else None
+        compare(int(argv[1]), int(argv[2]) if len(argv) > 2 else 40, split)
     elif argv[0] == "anneal":
         anneal_time()
     elif argv[0] == "l2":
@@ -275,7 +288,10 @@ def main(argv):
         ff_steps(n, l, h, int(argv[4]) if len(argv) > 4 else 6)
     elif argv[0] == "tail":
         n, l, h = int(argv[1]), int(argv[2]), int(argv[3])
-        fused_steps(n, l, h, int(argv[4]) if len(argv) > 4 else 6, blocking=True)
+        fused_steps(n, l, h, int(argv[4]) if len(argv) > 4 else 6, blocking=1)
+    elif argv[0] == "pair":
+        n, l, h = int(argv[1]), int(argv[2]), int(argv[3])
+        fused_steps(n, l, h, int(argv[4]) if len(argv) > 4 else 6, blocking=2)
     else:
         n, l, h = int(argv[0]), int(argv[1]), int(argv[2])
         fused_steps(n, l, h, int(argv[3]) if len(argv) > 3 else 6)

@@ -202,15 +202,19 @@ def test_default_split_gives_the_top_range_wide_rows():
 
 
 def test_fused_blocking_switch():
-    """The L2-blocked tail is off by default, takes 0 or 1, and reports its setting."""
-    assert api.get_fused_blocking() is False
-    assert _lib.lib().cheb_set_fused_blocking(2) == 1  # CHEB_ERR_INVALID_ARG
-    api.set_fused_blocking(True)
+    """The L2-blocked launches are off by default, take 0 (off), 1 (step tail) or 2
+    (strided pair), and report the setting."""
+    assert api.get_fused_blocking() == 0
+    assert _lib.lib().cheb_set_fused_blocking(3) == 1  # CHEB_ERR_INVALID_ARG
+    assert _lib.lib().cheb_set_fused_blocking(-1) == 1
     try:
-        assert api.get_fused_blocking() is True
+        api.set_fused_blocking(True)
+        assert api.get_fused_blocking() == 1
+        api.set_fused_blocking(2)
+        assert api.get_fused_blocking() == 2
     finally:
         api.set_fused_blocking(False)
-    assert api.get_fused_blocking() is False
+    assert api.get_fused_blocking() == 0
 
 
 def test_fused_compensated_switch():

@@ -162,3 +162,77 @@ def test_blocked_tail_bit_identical_compensated(cuda_lib, split):
         api.set_fused_compensated(False)
     assert bool((a == b).all())
     assert not bool((a == c).all())  # the switch changes the arithmetic
+
+
+# ---------------------------------------------------------------------------
+# The L2-blocked strided pair (cheb_set_fused_blocking(2)): both strided passes of a
+# two-pass split in one launch. The same flip sums in the same order as the separate
+# launches, so results are bit-identical; the oracle comparison uses the FP32 bar.
+
+@pytest.mark.parametrize("n,l,h", [(23, 0, 12), (25, 0, 14), (26, 1, 14)])
+def test_blocked_pair_matches_oracle(cuda_lib, oracle, split, n, l, h):
+    """Ranges of 6+6, 7+7 and 7+7 bits, against the FP64 oracle and the separate
+    launches (two launches per step instead of three)."""
+    from paper_2608_12058_b300 import api
+
+    split(n, l, h)
+    hq, Jq = I.sk_instance(n, 700 + n + l)
+    psi = I.random_state(n, 750 + n)
+    ref, oinfo = oracle.expmv(hq, Jq, 0.8, 0.25, psi, 2.0 ** -23)
+    c0 = api.launch_count()
+    y, info = _expmv(hq, Jq, 0.8, 0.25, psi, 2)
+    paired = api.launch_count() - c0
+    assert info["K"] == oinfo["K"] and info["K"] > 3
+    assert _rel(y, ref) <= 1e-5
+    c1 = api.launch_count()
+    y_sep, _ = _expmv(hq, Jq, 0.8, 0.25, psi, 0)
+    assert (api.launch_count() - c1) - paired == info["K"]
+    assert np.array_equal(y, y_sep)
+
+
+@pytest.mark.parametrize("n,l,h", [(24, 0, 13), (27, 0, 16), (28, 1, 16), (29, 0, 18), (30, 2, 17),
+                                   (30, 3, 16), (30, 4, 15)])
+def test_blocked_pair_bit_identical(cuda_lib, split, n, l, h):
+    """Range pairs 7+6, 8+8, 9+9, 9+8, 8+8 and 8+7 up to 2^30 amplitudes: the blocked
+    pair equals the separate launches bit for bit, including steps with c_k = 0 and the
+    final step alone."""
+    split(n, l, h)
+    rng = np.random.default_rng(n + l)
+    coef = (rng.standard_normal(8) + 1j * rng.standard_normal(8)) / 32
+    coef[2] = 0.0
+    coef[5] = 0.0
+    a = _poly(n, coef, 2)
+    b = _poly(n, coef, 0)
+    assert bool((a == b).all())
+    assert bool(torch_isfinite(a))
+    del a, b
+    one = np.array([0.3 + 0.1j, 0.5 - 0.2j])
+    a = _poly(n, one, 2)
+    b = _poly(n, one, 0)
+    assert bool((a == b).all())
+
+
+def test_blocked_pair_adjoint_identical(cuda_lib, split):
+    """The adjoint chain on the blocked pair gives the same gradients as on the
+    separate launches."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    n = 24
+    split(n, 0, 13)
+    a = I.config_anneal(n=n, S=3)
+    outs = []
+    for mode in (2, 0):
+        _blocking(mode)
+        x = torch.full((1 << n,), 2 ** (-n / 2), dtype=torch.complex64, device="cuda")
+        bnd = torch.empty((a.gammas.shape[0], 1 << n), dtype=torch.complex64, device="cuda")
+        api.anneal(a.h, a.J, a.gammas, a.ts, x, boundaries=bnd, info=False)
+        _, g, _, _ = api.energy_grad(a.h, a.J, x)
+        out = api.anneal_adjoint(a.h, a.J, a.gammas, a.ts, bnd, x, g)
+        torch.cuda.synchronize()
+        outs.append((x.cpu().numpy(), out))
+    (x1, o1), (x2, o2) = outs
+    assert np.array_equal(x1, x2)
+    for key in ("gamma", "t", "h", "J"):
+        assert np.array_equal(np.asarray(o1[key]), np.asarray(o2[key])), key
