@@ -473,7 +473,8 @@ cheb_status_t cheb_get_fused_split_fp64(int n, int* l, int* h);
  * b_{k+1} and the partial sum come back from L2: the two passes move 24 B per
  * amplitude of DRAM traffic instead of 48. Flip sums are plain FP32 in descending bit
  * order, as in the separate launches, so results are identical. The lag between a
- * group's A and B tiles is one group (environment variable CHEB_PAIR_LAG: 1..16).
+ * group's A and B tiles keeps about 48 MB of the two vectors live in L2 (one group of
+ * 32 MB, two of 16 MB); the environment variable CHEB_PAIR_LAG (1..16) overrides it.
  * on: 0 off, 1 the blocked tail, 2 the blocked strided pair (process-wide; the
  * autotuner's per-n choice takes precedence). cheb_get_fused_blocking returns it.
  */

@@ -1145,6 +1145,8 @@ struct PairCfg {
     static constexpr uint32_t kStage = (uint32_t)128 << kHMax;   // largest tile
     static constexpr uint32_t kBytesA = (uint32_t)128 << HA;
     static constexpr uint32_t kBytesB = (uint32_t)128 << HB;
+    // a narrower B-tile leaves room in its stage for its q rows, which then come by TMA
+    static constexpr bool kQInStage = HB < HA;
     static constexpr int kNSraw = (int)((200u * 1024u) / kStage);
     static constexpr int kNS = kNSraw < 6 ? kNSraw : 6;
     static constexpr int kNR = 8;                                 // completion records in flight
@@ -1192,12 +1194,22 @@ __device__ __forceinline__ float4 ld_cg4(const float4* p) {
     return v;
 }
 
+// Bulk prefetch of a tensor-map box into L2 (no shared memory, no completion).
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
+}
+
 // One strided tile of 2^H rows (in shared memory, rows of 8 float4) on the 256
 // consumer threads: q = s g S + sgn w for the rows' amplitudes, written to slot.
+// The slot comes from qtile (shared memory, same layout as the tile) when it is not null,
+// else from slot_in with L2-only loads.
 template <int H>
-__device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const float4* slot_in, float4* slot,
-                                          int64_t base, int64_t row_stride_f4, float2 g_hi, float2 g_lo, float2 sg,
-                                          bool need_slot, uint64_t pol_store) {
+__device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const float4* __restrict__ qtile,
+                                          const float4* slot_in, float4* slot, int64_t base, int64_t row_stride_f4,
+                                          float2 g_hi, float2 g_lo, float2 sg, bool need_slot, uint64_t pol_store) {
     constexpr int P = 1 << (H - 5);
     const int t = threadIdx.x;
     const int u = t & 7, rq = t >> 3;
@@ -1213,7 +1225,7 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const
         for (int b = P >> 1; b >= 1; b >>= 1) S[i].add(v[i ^ b]);
     }
     float4 w[P];
-    if (need_slot) {
+    if (need_slot && !qtile) {
 #pragma unroll
         for (int i = 0; i < P; ++i) w[i] = ld_cg4(slot_in + base + (int64_t)(rq | (i << 5)) * row_stride_f4 + u);
     }
@@ -1222,6 +1234,10 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const
     for (int i = 0; i < P; ++i) {
 #pragma unroll
         for (int j = 4; j >= 0; --j) S[i].add(tile[((rq ^ (1 << j)) | (i << 5)) * 8 + u]);
+    }
+    if (need_slot && qtile) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) w[i] = qtile[(rq | (i << 5)) * 8 + u];
     }
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -1238,7 +1254,8 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const
 
 template <int HA, int HB>
 __global__ void __launch_bounds__(kPairThreads, 1)
-    k_pair(const PairArgs a, const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB) {
+    k_pair(const PairArgs a, const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+           const __grid_constant__ CUtensorMap smapA, const __grid_constant__ CUtensorMap qmapB) {
     using Cfg = PairCfg<HA, HB>;
     static_assert(HA >= 6 && HA <= 9 && HB >= 6 && HB <= 9, "pair ranges");
     static_assert(Cfg::kSmem <= 227 * 1024, "shared memory");
@@ -1289,9 +1306,27 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         for (int i = 0; i < Cfg::kNS; ++i) last[i] = -1;
         // the A-tiles' b_{k+1} is read again by the B-tiles of their group
         const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
+        // the next item is taken one ahead, so the counter's round trip overlaps the
+        // current item (it is later in the order, so holding it cannot block anyone)
+        unsigned long long nxt = atomicAdd(a.work, 1ull);
+        constexpr int boxA = HA < 8 ? (1 << HA) : 256;
+        // an A-tile's slot rows (b_{k+2}, read by the consumers with L2-only loads) are
+        // prefetched from DRAM into L2 when the item is taken, a few items before use
+        auto prefetch_slot = [&](unsigned long long i) {
+            if (a.sgn == 0.f) return;
+            const MixedItem pi = pair_decode(i, a.gbits, HA, HB, a.lag);
+            if (pi.kind != kItemStrided) return;
+#pragma unroll
+            for (int c = 0; c < (1 << HA) / boxA; ++c) tma_prefetch_4d(&smapA, 0, (int)pi.g, c * boxA, (int)pi.idx);
+        };
+        prefetch_slot(nxt);
         for (int it = 0;; ++it) {
-            const unsigned long long cur = atomicAdd(a.work, 1ull);
+            const unsigned long long cur = nxt;
             const MixedItem ci = pair_decode(cur, a.gbits, HA, HB, a.lag);
+            if (ci.kind != kItemEnd) {
+                nxt = atomicAdd(a.work, 1ull);
+                prefetch_slot(nxt);
+            }
             const int s = it % Cfg::kNS, k = it / Cfg::kNS;
             if (k > 0 && !mbar_wait(&empty[s], (k - 1) & 1, a.flags, abort)) break;
             unsigned char* d = smem + (size_t)s * Cfg::kStage;
@@ -1305,10 +1340,9 @@ __global__ void __launch_bounds__(kPairThreads, 1)
                 // A-tile: bits [4, loA) = g, bits of B = idx
                 item[s] = (long long)cur;
                 mbar_expect_tx(&full[s], Cfg::kBytesA);
-                constexpr int box = HA < 8 ? (1 << HA) : 256;
 #pragma unroll
-                for (int c = 0; c < (1 << HA) / box; ++c)
-                    tma_load_4d_hint(d + (size_t)c * box * 128, &mapA, 0, (int)ci.g, c * box, (int)ci.idx, &full[s],
+                for (int c = 0; c < (1 << HA) / boxA; ++c)
+                    tma_load_4d_hint(d + (size_t)c * boxA * 128, &mapA, 0, (int)ci.g, c * boxA, (int)ci.idx, &full[s],
                                      pol_last);
                 last[s] = k;
             } else {
@@ -1316,12 +1350,16 @@ __global__ void __launch_bounds__(kPairThreads, 1)
                 // q of the group was written through the generic proxy by other SMs
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 item[s] = (long long)cur;
-                mbar_expect_tx(&full[s], Cfg::kBytesB);
+                mbar_expect_tx(&full[s], Cfg::kQInStage ? 2 * Cfg::kBytesB : Cfg::kBytesB);
                 constexpr int box = HB < 8 ? (1 << HB) : 256;
                 const int tlo = (int)(ci.g | (ci.idx << sha));  // bits [4, loB)
 #pragma unroll
-                for (int c = 0; c < (1 << HB) / box; ++c)
+                for (int c = 0; c < (1 << HB) / box; ++c) {
                     tma_load_4d_hint(d + (size_t)c * box * 128, &mapB, 0, tlo, c * box, 0, &full[s], pol_first);
+                    if (Cfg::kQInStage)
+                        tma_load_4d_hint(d + Cfg::kBytesB + (size_t)c * box * 128, &qmapB, 0, tlo, c * box, 0,
+                                         &full[s], pol_first);
+                }
                 last[s] = k;
             }
         }
@@ -1362,13 +1400,14 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         const float4* tile = (const float4*)(smem + (size_t)s * Cfg::kStage);
         if (ci.kind == kItemStrided) {
             const int64_t base = ci.g * 8 + (ci.idx << (a.loB - 1));
-            pair_tile<HA>(tile, a.slot_in, a.slot, base, rsA, g_hi, g_lo, sg, need_a, pol_last);
+            pair_tile<HA>(tile, nullptr, a.slot_in, a.slot, base, rsA, g_hi, g_lo, sg, need_a, pol_last);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
             if (!record(ci.g)) break;
         } else {
             const int64_t base = (ci.g | (ci.idx << sha)) * 8;
-            pair_tile<HB>(tile, a.slot, a.slot, base, rsB, g_hi, g_lo, one, true, pol_first);
+            const float4* qt = Cfg::kQInStage ? tile + (Cfg::kBytesB / 16) : nullptr;
+            pair_tile<HB>(tile, qt, a.slot, a.slot, base, rsB, g_hi, g_lo, one, true, pol_first);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
         }
@@ -1547,13 +1586,23 @@ cudaError_t launch_mixed(int H, const MixedArgs& m, int n, cudaStream_t s) {
 template <int HA, int HB>
 cudaError_t launch_pair_t(const PairArgs& a, int n, cudaStream_t s) {
     using Cfg = PairCfg<HA, HB>;
-    CUtensorMap mapA, mapB, unused;
+    CUtensorMap mapA, mapB, smapA, unused;
     StridedArgs sa{};
     sa.b1 = a.b1;
     sa.sgn = 0.f;  // tensor maps of b_{k+1} only
     sa.lo = a.loA;
     cudaError_t e = strided_maps(sa, n, HA, 4, HA < 8 ? (1 << HA) : 256, &mapA, &unused);
     if (e != cudaSuccess) return e;
+    // the A-tiles' slot, in the same boxes (prefetched into L2), and the B-tiles' q
+    sa.b1 = a.slot_in;
+    e = strided_maps(sa, n, HA, 4, HA < 8 ? (1 << HA) : 256, &smapA, &unused);
+    if (e != cudaSuccess) return e;
+    CUtensorMap qmapB;
+    sa.b1 = a.slot;
+    sa.lo = a.loB;
+    e = strided_maps(sa, n, HB, 4, HB < 8 ? (1 << HB) : 256, &qmapB, &unused);
+    if (e != cudaSuccess) return e;
+    sa.b1 = a.b1;
     sa.lo = a.loB;
     e = strided_maps(sa, n, HB, 4, HB < 8 ? (1 << HB) : 256, &mapB, &unused);
     if (e != cudaSuccess) return e;
@@ -1561,7 +1610,7 @@ cudaError_t launch_pair_t(const PairArgs& a, int n, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     note_launch(kKindPair);
     const int pi = prof_begin(kKindPair, s);
-    k_pair<HA, HB><<<(unsigned)num_sms(), kPairThreads, Cfg::kSmem, s>>>(a, mapA, mapB);
+    k_pair<HA, HB><<<(unsigned)num_sms(), kPairThreads, Cfg::kSmem, s>>>(a, mapA, mapB, smapA, qmapB);
     prof_end(pi, s);
     return cudaGetLastError();
 }
@@ -1614,16 +1663,20 @@ size_t fused_scratch_bytes(int n, int prec) {
     return (mixed_counter_bytes(n - 16) + 255) / 256 * 256;
 }
 
-// Lag D of the blocked pair in groups (CHEB_PAIR_LAG, default 1): the B-tiles of group
-// g follow the A-tiles of group g + D.
-static int pair_lag() {
-    static int lag = 0;
-    if (lag == 0) {
+// Lag D of the blocked pair in groups: the B-tiles of group g follow the A-tiles of group
+// g + D, so about D + 1 groups of b_{k+1} and q are live in L2. Measured at n = 28..30,
+// the best D keeps that near 48 MB: D = 1 for 32 MB groups, D = 2 for 16 MB groups (one
+// more group cost 10-27%). CHEB_PAIR_LAG (1..16) overrides the rule.
+static int pair_lag(size_t group_bytes) {
+    static int env = -1;
+    if (env < 0) {
         const char* e = std::getenv("CHEB_PAIR_LAG");
         const int v = e ? std::atoi(e) : 0;
-        lag = (v >= 1 && v <= 16) ? v : 1;
+        env = (v >= 1 && v <= 16) ? v : 0;
     }
-    return lag;
+    if (env > 0) return env;
+    const int d = (int)((size_t)48 * 1024 * 1024 / std::max<size_t>(group_bytes, 1)) - 1;
+    return std::min(std::max(d, 1), 8);
 }
 
 // 0: separate launches, 1: L2-blocked tail, 2: L2-blocked strided pair.
@@ -1782,7 +1835,8 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void* sc
         pa.scale_glo = (float)s.scale * glo;
         pa.sgn = (float)s.sgn;
         pa.gbits = plan.lo[0] - 4;
-        pa.lag = (int)std::min<int64_t>(pair_lag(), (int64_t)1 << pa.gbits);
+        const size_t group_bytes = (size_t)16 << (4 + plan.hb[0] + plan.hb[1]);  // b_{k+1} and q
+        pa.lag = (int)std::min<int64_t>(pair_lag(group_bytes), (int64_t)1 << pa.gbits);
         pa.work = (unsigned long long*)scratch;
         pa.done = (unsigned*)((unsigned char*)scratch + 8);
         pa.flags = flags;
