@@ -475,6 +475,7 @@ def run_ours(args, world, rank, local):
     ms = e0.elapsed_time(e1)
     nlow, low_ms = api.profile_read("low")
     nhigh, high_ms = api.profile_read("high")
+    npair, pair_ms = api.profile_read("pair")
     api.profile_reset()
     fin = api.energy(cfg.h, cfg.J, psi)
 
@@ -584,21 +585,25 @@ def run_ours(args, world, rank, local):
                 "avg_launch_ms": avg_s * 1e3, "share": total_ms / ms}
 
     # per pass: low pass reads b1, psi, slot and writes out (32 B/amp); a strided pass
-    # reads b1, slot and writes slot (24 B/amp)
+    # reads b1, slot and writes slot (24 B/amp); the blocked pair does both strided
+    # passes with 24 B/amp of DRAM traffic (b1 and b_{k+2} read once, q written once)
     r_low = kernel_roof("k_low", nlow, low_ms, 32.0)
     r_str = kernel_roof("k_strided", nhigh, high_ms, 24.0)
-    kernels = [r for r in (r_low, r_str) if r is not None]
+    r_pair = kernel_roof("k_pair", npair, pair_ms, 24.0)
+    kernels = [r for r in (r_low, r_str, r_pair) if r is not None]
     # the method's roofline: one Clenshaw step (its launches, timed on their stream)
     # needs 32 B per amplitude (read b_{k+1}, b_{k+2}, psi; write b_k)
     steps_timed = max(nlow, 1)
-    step_ms = (low_ms + high_ms) / steps_timed
+    step_ms = (low_ms + high_ms + pair_ms) / steps_timed
     alg = 32.0 * N
     achieved = alg / (step_ms / 1e3) / 1e9
-    pass_bytes = 32.0 + 24.0 * (nhigh / steps_timed)
+    pass_bytes = 32.0 + 24.0 * (nhigh / steps_timed) + 24.0 * (npair / steps_timed)
     tr = None
-    if traffic and "k_low" in traffic and "k_strided" in traffic:
-        tr = (traffic["k_low"] + traffic["k_strided"] * (nhigh / steps_timed)) * N
-    roof = {"bound": "hbm", "kernel": "one fused Clenshaw step (k_low + strided passes)", "achieved": achieved,
+    if traffic and "k_low" in traffic and (npair == 0 or "k_pair" in traffic) and (nhigh == 0 or "k_strided" in traffic):
+        tr = (traffic["k_low"] + traffic.get("k_strided", 0.0) * (nhigh / steps_timed)
+              + traffic.get("k_pair", 0.0) * (npair / steps_timed)) * N
+    step_kind = "k_low + the L2-blocked strided pair k_pair" if npair else "k_low + strided passes"
+    roof = {"bound": "hbm", "kernel": f"one fused Clenshaw step ({step_kind})", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": tr,
             "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": alg,
             "algorithmic_bytes_per_amplitude": 32.0, "step_ms": step_ms, "steps_timed": steps_timed,

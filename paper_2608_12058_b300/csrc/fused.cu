@@ -1129,14 +1129,16 @@ __global__ void __launch_bounds__(kMixedThreads, 1)
 // are published by the notifier warps (fence, then the group count), so an item only
 // waits on items taken before it.
 //
-// Consumers: 256 threads. In a tile of 2^H rows thread t holds column float4
-// u = t & 7 of the 2^(H-5) rows whose bits 0..4 are t >> 3: the flips of row bits
-// 5..H-1 come from registers and those of bits 0..4 from shared memory, 56 B of
-// shared-memory traffic per amplitude (the TMA fill, the own value, five partners)
-// against 96 B in the one-pass kernels. The slot is read with L2-only loads (it was
-// written by other SMs in this launch). The flip sum runs in descending bit order, as
-// in the one-pass kernels, so the pair and two separate passes agree bit for bit.
-constexpr int kPairCons = 256;
+// Consumers: 512 threads. In a tile of 2^H rows thread t holds column float4
+// u = t & 7 of the 2^(H-6) rows whose bits 0..5 are t >> 3: the flips of row bits
+// 6..H-1 come from registers and those of bits 0..5 from shared memory, 64 B of
+// shared-memory traffic per amplitude (the TMA fill, the own value, six partners)
+// against 96 B in the one-pass kernels. An A-tile's slot (b_{k+2}) is read with
+// L2-only loads; a B-tile's q, which other SMs wrote in this launch, comes by TMA into
+// the free half of its stage when B is the narrower range, else with L2-only loads.
+// The flip sum runs in descending bit order, as in the one-pass kernels, so the pair
+// and two separate passes agree bit for bit.
+constexpr int kPairCons = 512;
 constexpr int kPairThreads = kPairCons + 64;  // + producer warp + notifier warp
 
 template <int HA, int HB>
@@ -1194,14 +1196,6 @@ __device__ __forceinline__ float4 ld_cg4(const float4* p) {
     return v;
 }
 
-// Bulk prefetch of a tensor-map box into L2 (no shared memory, no completion).
-__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
-    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-                 : "memory");
-}
-
 // One strided tile of 2^H rows (in shared memory, rows of 8 float4) on the 256
 // consumer threads: q = s g S + sgn w for the rows' amplitudes, written to slot.
 // The slot comes from qtile (shared memory, same layout as the tile) when it is not null,
@@ -1210,14 +1204,14 @@ template <int H>
 __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const float4* __restrict__ qtile,
                                           const float4* slot_in, float4* slot, int64_t base, int64_t row_stride_f4,
                                           float2 g_hi, float2 g_lo, float2 sg, bool need_slot, uint64_t pol_store) {
-    constexpr int P = 1 << (H - 5);
+    constexpr int P = 1 << (H - 6);
     const int t = threadIdx.x;
     const int u = t & 7, rq = t >> 3;
     float4 v[P];
 #pragma unroll
-    for (int i = 0; i < P; ++i) v[i] = tile[(rq | (i << 5)) * 8 + u];
+    for (int i = 0; i < P; ++i) v[i] = tile[(rq | (i << 6)) * 8 + u];
     AccT<false> S[P];
-    // register bits H-1 .. 5 first (descending)
+    // register bits H-1 .. 6 first (descending)
 #pragma unroll
     for (int i = 0; i < P; ++i) {
         S[i].zero();
@@ -1227,17 +1221,17 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const
     float4 w[P];
     if (need_slot && !qtile) {
 #pragma unroll
-        for (int i = 0; i < P; ++i) w[i] = ld_cg4(slot_in + base + (int64_t)(rq | (i << 5)) * row_stride_f4 + u);
+        for (int i = 0; i < P; ++i) w[i] = ld_cg4(slot_in + base + (int64_t)(rq | (i << 6)) * row_stride_f4 + u);
     }
-    // then row bits 4 .. 0 from shared memory
+    // then row bits 5 .. 0 from shared memory
 #pragma unroll
     for (int i = 0; i < P; ++i) {
 #pragma unroll
-        for (int j = 4; j >= 0; --j) S[i].add(tile[((rq ^ (1 << j)) | (i << 5)) * 8 + u]);
+        for (int j = 5; j >= 0; --j) S[i].add(tile[((rq ^ (1 << j)) | (i << 6)) * 8 + u]);
     }
     if (need_slot && qtile) {
 #pragma unroll
-        for (int i = 0; i < P; ++i) w[i] = qtile[(rq | (i << 5)) * 8 + u];
+        for (int i = 0; i < P; ++i) w[i] = qtile[(rq | (i << 6)) * 8 + u];
     }
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -1247,7 +1241,7 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const
             q0 = __ffma2_rn(sg, lo2(w[i]), q0);
             q1 = __ffma2_rn(sg, hi2(w[i]), q1);
         }
-        st_hint(slot + base + (int64_t)(rq | (i << 5)) * row_stride_f4 + u, make_float4(q0.x, q0.y, q1.x, q1.y),
+        st_hint(slot + base + (int64_t)(rq | (i << 6)) * row_stride_f4 + u, make_float4(q0.x, q0.y, q1.x, q1.y),
                 pol_store);
     }
 }
@@ -1255,7 +1249,7 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const
 template <int HA, int HB>
 __global__ void __launch_bounds__(kPairThreads, 1)
     k_pair(const PairArgs a, const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-           const __grid_constant__ CUtensorMap smapA, const __grid_constant__ CUtensorMap qmapB) {
+           const __grid_constant__ CUtensorMap qmapB) {
     using Cfg = PairCfg<HA, HB>;
     static_assert(HA >= 6 && HA <= 9 && HB >= 6 && HB <= 9, "pair ranges");
     static_assert(Cfg::kSmem <= 227 * 1024, "shared memory");
@@ -1310,23 +1304,10 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         // current item (it is later in the order, so holding it cannot block anyone)
         unsigned long long nxt = atomicAdd(a.work, 1ull);
         constexpr int boxA = HA < 8 ? (1 << HA) : 256;
-        // an A-tile's slot rows (b_{k+2}, read by the consumers with L2-only loads) are
-        // prefetched from DRAM into L2 when the item is taken, a few items before use
-        auto prefetch_slot = [&](unsigned long long i) {
-            if (a.sgn == 0.f) return;
-            const MixedItem pi = pair_decode(i, a.gbits, HA, HB, a.lag);
-            if (pi.kind != kItemStrided) return;
-#pragma unroll
-            for (int c = 0; c < (1 << HA) / boxA; ++c) tma_prefetch_4d(&smapA, 0, (int)pi.g, c * boxA, (int)pi.idx);
-        };
-        prefetch_slot(nxt);
         for (int it = 0;; ++it) {
             const unsigned long long cur = nxt;
             const MixedItem ci = pair_decode(cur, a.gbits, HA, HB, a.lag);
-            if (ci.kind != kItemEnd) {
-                nxt = atomicAdd(a.work, 1ull);
-                prefetch_slot(nxt);
-            }
+            if (ci.kind != kItemEnd) nxt = atomicAdd(a.work, 1ull);
             const int s = it % Cfg::kNS, k = it / Cfg::kNS;
             if (k > 0 && !mbar_wait(&empty[s], (k - 1) & 1, a.flags, abort)) break;
             unsigned char* d = smem + (size_t)s * Cfg::kStage;
@@ -1586,17 +1567,14 @@ cudaError_t launch_mixed(int H, const MixedArgs& m, int n, cudaStream_t s) {
 template <int HA, int HB>
 cudaError_t launch_pair_t(const PairArgs& a, int n, cudaStream_t s) {
     using Cfg = PairCfg<HA, HB>;
-    CUtensorMap mapA, mapB, smapA, unused;
+    CUtensorMap mapA, mapB, unused;
     StridedArgs sa{};
     sa.b1 = a.b1;
     sa.sgn = 0.f;  // tensor maps of b_{k+1} only
     sa.lo = a.loA;
     cudaError_t e = strided_maps(sa, n, HA, 4, HA < 8 ? (1 << HA) : 256, &mapA, &unused);
     if (e != cudaSuccess) return e;
-    // the A-tiles' slot, in the same boxes (prefetched into L2), and the B-tiles' q
-    sa.b1 = a.slot_in;
-    e = strided_maps(sa, n, HA, 4, HA < 8 ? (1 << HA) : 256, &smapA, &unused);
-    if (e != cudaSuccess) return e;
+    // the B-tiles' q
     CUtensorMap qmapB;
     sa.b1 = a.slot;
     sa.lo = a.loB;
@@ -1610,7 +1588,7 @@ cudaError_t launch_pair_t(const PairArgs& a, int n, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     note_launch(kKindPair);
     const int pi = prof_begin(kKindPair, s);
-    k_pair<HA, HB><<<(unsigned)num_sms(), kPairThreads, Cfg::kSmem, s>>>(a, mapA, mapB, smapA, qmapB);
+    k_pair<HA, HB><<<(unsigned)num_sms(), kPairThreads, Cfg::kSmem, s>>>(a, mapA, mapB, qmapB);
     prof_end(pi, s);
     return cudaGetLastError();
 }
