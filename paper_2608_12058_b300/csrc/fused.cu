@@ -1134,8 +1134,9 @@ __global__ void __launch_bounds__(kMixedThreads, 1)
 // 6..H-1 come from registers and those of bits 0..5 from shared memory, 64 B of
 // shared-memory traffic per amplitude (the TMA fill, the own value, six partners)
 // against 96 B in the one-pass kernels. An A-tile's slot (b_{k+2}) is read with
-// L2-only loads; a B-tile's q, which other SMs wrote in this launch, comes by TMA into
-// the free half of its stage when B is the narrower range, else with L2-only loads.
+// L2-only loads, or by TMA with the tile when tiles have at most 8 bits (a stage then
+// holds both); a B-tile's q, which other SMs wrote in this launch, comes by TMA into
+// the stage when it has room (ranges of at most 8 bits, or B narrower than A).
 // The flip sum runs in descending bit order, as in the one-pass kernels, so the pair
 // and two separate passes agree bit for bit.
 constexpr int kPairCons = 512;
@@ -1144,11 +1145,18 @@ constexpr int kPairThreads = kPairCons + 64;  // + producer warp + notifier warp
 template <int HA, int HB>
 struct PairCfg {
     static constexpr int kHMax = HA > HB ? HA : HB;
-    static constexpr uint32_t kStage = (uint32_t)128 << kHMax;   // largest tile
+    static constexpr uint32_t kTileMax = (uint32_t)128 << kHMax;  // largest tile
     static constexpr uint32_t kBytesA = (uint32_t)128 << HA;
     static constexpr uint32_t kBytesB = (uint32_t)128 << HB;
-    // a narrower B-tile leaves room in its stage for its q rows, which then come by TMA
-    static constexpr bool kQInStage = HB < HA;
+    // Tiles of up to 8 bits: a stage holds a tile and its slot rows (three stages of
+    // 64 KB), so the consumers read nothing from global memory. 9-bit A-tiles fill a
+    // stage alone: their slot comes by L2-only loads; a narrower B-tile still leaves
+    // room for its q rows.
+    static constexpr bool kFull = kHMax <= 8;
+    static constexpr uint32_t kStage = kFull ? 2 * kTileMax : kTileMax;
+    static constexpr uint32_t kSlotOff = kFull ? kTileMax : kBytesB;
+    static constexpr bool kSlotInStageA = kFull;
+    static constexpr bool kQInStage = kFull || HB < HA;
     static constexpr int kNSraw = (int)((200u * 1024u) / kStage);
     static constexpr int kNS = kNSraw < 6 ? kNSraw : 6;
     static constexpr int kNR = 8;                                 // completion records in flight
@@ -1249,7 +1257,7 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const
 template <int HA, int HB>
 __global__ void __launch_bounds__(kPairThreads, 1)
     k_pair(const PairArgs a, const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-           const __grid_constant__ CUtensorMap qmapB) {
+           const __grid_constant__ CUtensorMap smapA, const __grid_constant__ CUtensorMap qmapB) {
     using Cfg = PairCfg<HA, HB>;
     static_assert(HA >= 6 && HA <= 9 && HB >= 6 && HB <= 9, "pair ranges");
     static_assert(Cfg::kSmem <= 227 * 1024, "shared memory");
@@ -1320,11 +1328,17 @@ __global__ void __launch_bounds__(kPairThreads, 1)
             if (ci.kind == kItemStrided) {
                 // A-tile: bits [4, loA) = g, bits of B = idx
                 item[s] = (long long)cur;
-                mbar_expect_tx(&full[s], Cfg::kBytesA);
+                const bool slot_tma = Cfg::kSlotInStageA && a.sgn != 0.f;
+                mbar_expect_tx(&full[s], slot_tma ? 2 * Cfg::kBytesA : Cfg::kBytesA);
 #pragma unroll
-                for (int c = 0; c < (1 << HA) / boxA; ++c)
+                for (int c = 0; c < (1 << HA) / boxA; ++c) {
                     tma_load_4d_hint(d + (size_t)c * boxA * 128, &mapA, 0, (int)ci.g, c * boxA, (int)ci.idx, &full[s],
                                      pol_last);
+                    // the slot lines become q, which the group's B-tiles read back
+                    if (slot_tma)
+                        tma_load_4d_hint(d + Cfg::kSlotOff + (size_t)c * boxA * 128, &smapA, 0, (int)ci.g, c * boxA,
+                                         (int)ci.idx, &full[s], pol_last);
+                }
                 last[s] = k;
             } else {
                 if (!wait_count(a.done + ci.g, 1u << HB, a.flags, abort)) break;
@@ -1338,7 +1352,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
                 for (int c = 0; c < (1 << HB) / box; ++c) {
                     tma_load_4d_hint(d + (size_t)c * box * 128, &mapB, 0, tlo, c * box, 0, &full[s], pol_first);
                     if (Cfg::kQInStage)
-                        tma_load_4d_hint(d + Cfg::kBytesB + (size_t)c * box * 128, &qmapB, 0, tlo, c * box, 0,
+                        tma_load_4d_hint(d + Cfg::kSlotOff + (size_t)c * box * 128, &qmapB, 0, tlo, c * box, 0,
                                          &full[s], pol_first);
                 }
                 last[s] = k;
@@ -1381,13 +1395,14 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         const float4* tile = (const float4*)(smem + (size_t)s * Cfg::kStage);
         if (ci.kind == kItemStrided) {
             const int64_t base = ci.g * 8 + (ci.idx << (a.loB - 1));
-            pair_tile<HA>(tile, nullptr, a.slot_in, a.slot, base, rsA, g_hi, g_lo, sg, need_a, pol_last);
+            const float4* st = Cfg::kSlotInStageA ? tile + (Cfg::kSlotOff / 16) : nullptr;
+            pair_tile<HA>(tile, st, a.slot_in, a.slot, base, rsA, g_hi, g_lo, sg, need_a, pol_last);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
             if (!record(ci.g)) break;
         } else {
             const int64_t base = (ci.g | (ci.idx << sha)) * 8;
-            const float4* qt = Cfg::kQInStage ? tile + (Cfg::kBytesB / 16) : nullptr;
+            const float4* qt = Cfg::kQInStage ? tile + (Cfg::kSlotOff / 16) : nullptr;
             pair_tile<HB>(tile, qt, a.slot, a.slot, base, rsB, g_hi, g_lo, one, true, pol_first);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
@@ -1574,8 +1589,11 @@ cudaError_t launch_pair_t(const PairArgs& a, int n, cudaStream_t s) {
     sa.lo = a.loA;
     cudaError_t e = strided_maps(sa, n, HA, 4, HA < 8 ? (1 << HA) : 256, &mapA, &unused);
     if (e != cudaSuccess) return e;
-    // the B-tiles' q
-    CUtensorMap qmapB;
+    // the A-tiles' slot (b_{k+2}) and the B-tiles' q in the same boxes
+    CUtensorMap smapA, qmapB;
+    sa.b1 = a.slot_in;
+    e = strided_maps(sa, n, HA, 4, HA < 8 ? (1 << HA) : 256, &smapA, &unused);
+    if (e != cudaSuccess) return e;
     sa.b1 = a.slot;
     sa.lo = a.loB;
     e = strided_maps(sa, n, HB, 4, HB < 8 ? (1 << HB) : 256, &qmapB, &unused);
@@ -1588,7 +1606,7 @@ cudaError_t launch_pair_t(const PairArgs& a, int n, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     note_launch(kKindPair);
     const int pi = prof_begin(kKindPair, s);
-    k_pair<HA, HB><<<(unsigned)num_sms(), kPairThreads, Cfg::kSmem, s>>>(a, mapA, mapB, qmapB);
+    k_pair<HA, HB><<<(unsigned)num_sms(), kPairThreads, Cfg::kSmem, s>>>(a, mapA, mapB, smapA, qmapB);
     prof_end(pi, s);
     return cudaGetLastError();
 }
