@@ -85,6 +85,16 @@ def release_workspaces():
     _ws_cache.clear()
 
 
+def check_status(n: int, precision: str, device=None):
+    """Raise if a bounded wait ran out (or a launch was refused) during an earlier call
+    that ran without an info struct on the cached workspace of (n, precision)
+    (cheb_workspace_status; synchronises, clears the recorded condition)."""
+    ws = workspace(n, precision, device)
+    p, nb = _ws_ptr(ws)
+    _lib.check(_lib.lib().cheb_workspace_status(ctypes.c_void_p(p), nb, _stream_ptr(ws.device)),
+               "cheb_workspace_status")
+
+
 def coefficients(a: float, tol: float, method: str = "chebyshev", phase: complex = 1.0, max_K: int = 1 << 16):
     """Host coefficient generator; returns (complex array c_0..c_K, err_bound)."""
     buf = np.empty(2 * (max_K + 1))

@@ -1160,8 +1160,8 @@ struct PairCfg {
     static constexpr int kNSraw = (int)((200u * 1024u) / kStage);
     static constexpr int kNS = kNSraw < 6 ? kNSraw : 6;
     static constexpr int kNR = 8;                                 // completion records in flight
-    static constexpr size_t kItemOff = (size_t)kNS * kStage;
-    static constexpr size_t kNoteOff = kItemOff + 64;
+    static constexpr size_t kItemOff = (size_t)kNS * kStage;  // per stage: kind, group, index
+    static constexpr size_t kNoteOff = kItemOff + 3 * 8 * sizeof(long long);
     static constexpr size_t kBarOff = kNoteOff + (size_t)kNR * sizeof(int64_t);
     static constexpr size_t kAbortOff = kBarOff + (size_t)(2 * kNS + 2 * kNR) * sizeof(uint64_t);
     static constexpr size_t kSmem = kAbortOff + 16;
@@ -1267,6 +1267,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     uint64_t* cdone = empty + Cfg::kNS;   // an A-tile's q stores are issued (8 warps)
     uint64_t* cempty = cdone + Cfg::kNR;  // the notifier has published that record
     volatile int* abort = (volatile int*)(smem + Cfg::kAbortOff);
+    // the producer decodes each item once: kind, group and index per stage
     long long* item = (long long*)(smem + Cfg::kItemOff);
     volatile long long* note = (volatile long long*)(smem + Cfg::kNoteOff);
     const int t = threadIdx.x;
@@ -1320,14 +1321,16 @@ __global__ void __launch_bounds__(kPairThreads, 1)
             if (k > 0 && !mbar_wait(&empty[s], (k - 1) & 1, a.flags, abort)) break;
             unsigned char* d = smem + (size_t)s * Cfg::kStage;
             if (ci.kind == kItemEnd) {
-                item[s] = -1;
+                item[3 * s] = kItemEnd;
                 mbar_arrive(&full[s]);
                 last[s] = k;
                 break;
             }
             if (ci.kind == kItemStrided) {
                 // A-tile: bits [4, loA) = g, bits of B = idx
-                item[s] = (long long)cur;
+                item[3 * s] = kItemStrided;
+                item[3 * s + 1] = ci.g;
+                item[3 * s + 2] = ci.idx;
                 const bool slot_tma = Cfg::kSlotInStageA && a.sgn != 0.f;
                 mbar_expect_tx(&full[s], slot_tma ? 2 * Cfg::kBytesA : Cfg::kBytesA);
 #pragma unroll
@@ -1344,7 +1347,9 @@ __global__ void __launch_bounds__(kPairThreads, 1)
                 if (!wait_count(a.done + ci.g, 1u << HB, a.flags, abort)) break;
                 // q of the group was written through the generic proxy by other SMs
                 asm volatile("fence.proxy.async.global;" ::: "memory");
-                item[s] = (long long)cur;
+                item[3 * s] = kItemLow;
+                item[3 * s + 1] = ci.g;
+                item[3 * s + 2] = ci.idx;
                 mbar_expect_tx(&full[s], Cfg::kQInStage ? 2 * Cfg::kBytesB : Cfg::kBytesB);
                 constexpr int box = HB < 8 ? (1 << HB) : 256;
                 const int tlo = (int)(ci.g | (ci.idx << sha));  // bits [4, loB)
@@ -1386,12 +1391,11 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     for (int it = 0;; ++it) {
         const int s = it % Cfg::kNS;
         if (!mbar_wait(&full[s], (it / Cfg::kNS) & 1, a.flags, abort)) break;
-        const long long cur = item[s];
-        if (cur < 0) {
+        const MixedItem ci = {(int)item[3 * s], item[3 * s + 1], item[3 * s + 2]};
+        if (ci.kind == kItemEnd) {
             record(-1);
             break;
         }
-        const MixedItem ci = pair_decode((unsigned long long)cur, a.gbits, HA, HB, a.lag);
         const float4* tile = (const float4*)(smem + (size_t)s * Cfg::kStage);
         if (ci.kind == kItemStrided) {
             const int64_t base = ci.g * 8 + (ci.idx << (a.loB - 1));

@@ -52,7 +52,7 @@ def fused_steps(n, l, h, steps, blocking=0):
     rng = np.random.default_rng(0)
     coef = (rng.standard_normal(steps + 1) + 1j * rng.standard_normal(steps + 1)) / (4 * steps)
     api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef, x, path="fused")
-    torch.cuda.synchronize()
+    api.check_status(n, "fp32")
     nrm = float(torch.linalg.vector_norm(x))
     assert np.isfinite(nrm)
     print("ok", nrm)
@@ -109,6 +109,7 @@ def compare(n, steps, split=None):
                 e1.record()
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1)
+                api.check_status(n, "fp32")
                 assert np.isfinite(float(torch.linalg.vector_norm(x)))
                 api.profile_reset()
                 api.profile_enable(True)
