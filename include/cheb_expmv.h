@@ -216,6 +216,37 @@ cheb_status_t cheb_anneal_general(int n, const double* h, const double* J, int S
                                   void* stream, cheb_info_t* infos);
 
 /*
+ * CUDA-graph capture of a schedule (no counterpart in the paper). cheb_anneal_graph_create
+ * runs the host side of cheb_anneal_general once (spectral scan, fixed-point couplings,
+ * series and degrees of every segment; it synchronises the stream), keeps each
+ * segment's couplings in the workspace, and captures the device work of the whole
+ * schedule into a graph: per segment the boundary copy, the table rebuild and the
+ * Clenshaw steps, on the same kernels as cheb_anneal_general. cheb_anneal_graph_launch
+ * replays it on `stream`: psi <- prod_s exp(-i t_s H_s) psi again, bit for bit what
+ * cheb_anneal_general computes from the same state.
+ *   Arguments as cheb_anneal_general (b_s null means b_s = 1, i.e. cheb_anneal).
+ *   psi, boundaries and workspace are bound into the graph: they must stay allocated
+ *   and are the buffers every replay reads and writes.
+ *   workspace: cheb_anneal_graph_workspace_bytes(n, precision, S) bytes, 256-byte
+ *   aligned, used only by this graph while it exists.
+ *   graph: HOST out; release with cheb_anneal_graph_destroy.
+ * A replay does not synchronise; its bounded waits report through the workspace's
+ * status word (cheb_workspace_status). Replays count their kernels in
+ * cheb_launch_count. Errors: as cheb_anneal_general; UNSUPPORTED while per-kernel event
+ * timing is on (cheb_profile_enable); CUDA if the capture or instantiation fails.
+ */
+typedef struct cheb_anneal_graph* cheb_anneal_graph_t;
+size_t cheb_anneal_graph_workspace_bytes(int n, cheb_precision_t precision, int S);
+cheb_status_t cheb_anneal_graph_create(int n, const double* h, const double* J, int S,
+                                       const double* a_s, const double* b_s, const double* t_s,
+                                       void* psi, cheb_precision_t precision, double tol,
+                                       cheb_method_t method, void* boundaries, void* workspace,
+                                       size_t workspace_bytes, void* stream,
+                                       cheb_anneal_graph_t* graph);
+cheb_status_t cheb_anneal_graph_launch(cheb_anneal_graph_t graph, void* stream);
+void cheb_anneal_graph_destroy(cheb_anneal_graph_t graph);
+
+/*
  * Time-dependent evolution i dpsi/dt = H(t) psi with H(t) = A(t) sum_j X_j + B(t) H_P
  * by the fourth-order commutator-free Magnus integrator that Sec. III.B builds on:
  * per step of length dt_m, with Gauss-Legendre nodes t1,2 = t + (1/2 -+ sqrt(3)/6) dt_m,

@@ -101,6 +101,11 @@ SIGNATURES = {
                                     c_int, _dp, _dp, _dp, _dp, c_void_p, c_size_t, c_void_p]),
     "cheb_anneal_general_adjoint": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, _dp, c_void_p, c_void_p, c_void_p, c_int,
                                             c_double, c_int, _dp, _dp, _dp, _dp, _dp, c_void_p, c_size_t, c_void_p]),
+    "cheb_anneal_graph_workspace_bytes": (c_size_t, [c_int, c_int, c_int]),
+    "cheb_anneal_graph_create": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, _dp, c_void_p, c_int, c_double, c_int,
+                                         c_void_p, c_void_p, c_size_t, c_void_p, ctypes.POINTER(c_void_p)]),
+    "cheb_anneal_graph_launch": (c_int, [c_void_p, c_void_p]),
+    "cheb_anneal_graph_destroy": (None, [c_void_p]),
     "cheb_anneal_checkpointed": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, c_void_p, c_int, c_double, c_int,
                                          c_void_p, c_void_p, c_size_t, c_void_p]),
     "cheb_anneal_general_checkpointed": (c_int, [c_int, _dp, _dp, c_int, _dp, _dp, _dp, c_void_p, c_int, c_double,

@@ -200,6 +200,69 @@ def anneal_general(h, J, a_s, b_s, ts, psi, tol: Optional[float] = None, method:
     return [x.as_dict() for x in infos] if info else None
 
 
+class AnnealGraph:
+    """A schedule captured into a CUDA graph (cheb_anneal_graph_create): the host side
+    runs once, launch() replays the device work on psi (and boundaries), bit for bit what
+    anneal / anneal_general computes from the same state. psi and boundaries are bound
+    into the graph; close() (or garbage collection) releases it."""
+
+    def __init__(self, h, J, gammas, ts, psi, boundaries=None, b_s=None, tol: Optional[float] = None,
+                 method: str = "chebyshev"):
+        import torch
+
+        h, J = _f64(h), _f64(J)
+        a_s, ts = _f64(gammas), _f64(ts)
+        n, S = h.shape[0], a_s.shape[0]
+        assert ts.shape[0] == S
+        _check_state(psi, n)
+        prec = precision_of(psi)
+        if tol is None:
+            tol = 2.0 ** -23 if prec == "fp32" else 1e-12
+        bptr = None
+        if boundaries is not None:
+            if (boundaries.dtype != psi.dtype or tuple(boundaries.shape) != (S, 1 << n)
+                    or not boundaries.is_contiguous()):
+                raise ValueError("boundaries must be a contiguous (S, 2^n) tensor of psi's dtype")
+            bptr = ctypes.c_void_p(boundaries.data_ptr())
+        bs = None if b_s is None else _f64(b_s)
+        need = int(_lib.lib().cheb_anneal_graph_workspace_bytes(n, PREC[prec], S))
+        self.workspace = torch.empty(need + 256, dtype=torch.uint8, device=psi.device)
+        self.psi, self.boundaries, self.n, self.prec = psi, boundaries, n, prec
+        p, nb = _ws_ptr(self.workspace)
+        handle = ctypes.c_void_p()
+        code = _lib.lib().cheb_anneal_graph_create(n, _dp(h), _dp(J), S, _dp(a_s),
+                                                   _dp(bs) if bs is not None else None, _dp(ts),
+                                                   ctypes.c_void_p(psi.data_ptr()), PREC[prec], float(tol),
+                                                   METHOD[method], bptr, ctypes.c_void_p(p), nb,
+                                                   _stream_ptr(psi.device), ctypes.byref(handle))
+        _lib.check(code, "cheb_anneal_graph_create")
+        self._handle = handle
+
+    def launch(self):
+        """Replay the schedule on the current stream (psi <- the schedule applied to psi)."""
+        if self._handle is None:
+            raise ValueError("graph released")
+        _lib.check(_lib.lib().cheb_anneal_graph_launch(self._handle, _stream_ptr(self.psi.device)),
+                   "cheb_anneal_graph_launch")
+
+    def status(self):
+        """Raise if a bounded wait ran out during a replay (synchronises)."""
+        p, nb = _ws_ptr(self.workspace)
+        _lib.check(_lib.lib().cheb_workspace_status(ctypes.c_void_p(p), nb, _stream_ptr(self.psi.device)),
+                   "cheb_workspace_status")
+
+    def close(self):
+        if getattr(self, "_handle", None) is not None:
+            _lib.lib().cheb_anneal_graph_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def magnus4_nodes(A, B, T: float, steps: int):
     """Sample the schedule for cheb_magnus4 (cheb_magnus4_nodes): equal steps of [0, T]
     and, per step, (A(t1), B(t1), A(t2), B(t2)) at the Gauss-Legendre points."""

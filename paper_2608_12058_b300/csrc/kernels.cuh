@@ -21,6 +21,9 @@ enum KernelKind : int {
     kKindPair = 9,
 };
 void note_launch(int kind);
+// count kernels that run as part of a CUDA graph replay; whether event timing is on
+void note_launches(long long count);
+bool prof_enabled();
 // Whether step kernels are launched with programmatic dependent launch (on by default;
 // off while event profiling is on, so that per-kernel event times do not overlap).
 bool pdl_enabled();

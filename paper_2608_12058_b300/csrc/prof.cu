@@ -28,6 +28,8 @@ static std::vector<ProfRec> g_recs;
 static std::vector<cudaEvent_t> g_pool;
 
 void note_launch(int) { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+bool prof_enabled() { return g_prof_on.load(std::memory_order_relaxed); }
 
 static cudaEvent_t take_event() {
     if (!g_pool.empty()) {

@@ -21,7 +21,8 @@
         mode MODE (1 persistent, the default; 2 persistent with two CTAs per SM; 0
         per-size launches).
     python -m paper_2608_12058_b300.prof_case anneal
-        the n=22 64-segment anneal forward with and without programmatic dependent launch.
+        the n=22 64-segment anneal forward with and without programmatic dependent launch,
+        and replayed from a CUDA graph.
     python -m paper_2608_12058_b300.prof_case l2
         copy bandwidth of L2-resident buffers (8..96 MB).
     python -m paper_2608_12058_b300.prof_case adjoint N S
@@ -242,6 +243,25 @@ def anneal_time(reps=3):
             ms = min(ts)
             print(f"programmatic launch {'on ' if on else 'off'}: {ms:.2f} ms, {(1 << n) * K / ms * 1e3:.3e} "
                   f"amplitude-updates/s ({K} steps, {ms / K * 1e3:.1f} us per step)")
+        # the same schedule captured into a CUDA graph and replayed
+        api.set_programmatic_launch(True)
+        x = x0.clone()
+        g = api.AnnealGraph(a.h, a.J, a.gammas, a.ts, x)
+        ts = []
+        for _ in range(reps):
+            x.copy_(x0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            g.launch()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        g.status()
+        g.close()
+        ms = min(ts)
+        print(f"graph replay (programmatic launch on): {ms:.2f} ms, {(1 << n) * K / ms * 1e3:.3e} "
+              f"amplitude-updates/s ({ms / K * 1e3:.1f} us per step)")
     finally:
         api.set_programmatic_launch(True)
 

@@ -116,3 +116,66 @@ def test_magnus4_adaptive_reaches_tolerance(cuda_lib, oracle):
     M = api.magnus4_adaptive(h, J, A, B, T, x, tol=1e-8)
     err = np.linalg.norm(x.cpu().numpy() - sol.y[:, -1])
     assert M >= 16 and err <= 3e-8
+
+
+@pytest.mark.parametrize("n,dtype_name,S", [(12, "complex64", 5), (18, "complex64", 4), (22, "complex64", 3),
+                                            (14, "complex128", 3), (20, "complex128", 2)])
+def test_anneal_graph_replays_anneal(cuda_lib, n, dtype_name, S):
+    """A schedule captured into a CUDA graph (cheb_anneal_graph_create) and replayed
+    equals cheb_anneal bit for bit, boundaries included, on every path (whole-run CTA,
+    fused FP32, float-float FP64); a second replay applies the schedule again."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    dt = getattr(torch, dtype_name)
+    a = I.config_anneal(n=n, S=S, seed=21)
+    x0 = torch.from_numpy(I.random_state(n, 22)).to(dt).cuda()
+    y_ref = x0.clone()
+    b_ref = torch.empty((S, 1 << n), dtype=dt, device="cuda")
+    api.anneal(a.h, a.J, a.gammas, a.ts, y_ref, boundaries=b_ref, info=False)
+    y2_ref = y_ref.clone()
+    api.anneal(a.h, a.J, a.gammas, a.ts, y2_ref, info=False)
+    x = x0.clone()
+    bnd = torch.empty((S, 1 << n), dtype=dt, device="cuda")
+    c0 = api.launch_count()
+    g = api.AnnealGraph(a.h, a.J, a.gammas, a.ts, x, boundaries=bnd)
+    c1 = api.launch_count()
+    try:
+        assert torch.equal(x, x0)  # capture does not run the work
+        g.launch()
+        g.status()
+        replay = api.launch_count() - c1
+        assert 0 < replay < c1 - c0  # the captured kernels, without the spectral scan
+        assert torch.equal(x, y_ref)
+        assert torch.equal(bnd, b_ref)
+        g.launch()
+        g.status()
+        assert torch.equal(x, y2_ref)
+    finally:
+        g.close()
+
+
+def test_anneal_graph_general_segments_and_slicing(cuda_lib):
+    """Segments b_s H_P + a_s sum_j X_j (cheb_anneal_general), one of them long enough to
+    be time-sliced: the replay equals the stream run."""
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    n = 10
+    a = I.config_anneal(n=n, S=3, seed=23)
+    b_s = np.array([1.0, -0.5, 0.8])
+    ts = np.array([0.5, 3000.0, 0.7])  # the middle segment exceeds the coefficient table
+    x0 = torch.from_numpy(I.random_state(n, 24)).to(torch.complex128).cuda()
+    y_ref = x0.clone()
+    inf = api.anneal_general(a.h, a.J, a.gammas, b_s, ts, y_ref, tol=1e-10)
+    assert inf[1]["time_splits"] > 1
+    x = x0.clone()
+    g = api.AnnealGraph(a.h, a.J, a.gammas, ts, x, b_s=b_s, tol=1e-10)
+    try:
+        g.launch()
+        g.status()
+        assert torch.equal(x, y_ref)
+    finally:
+        g.close()
