@@ -323,7 +323,23 @@ def other_workloads(dev):
         res["backward_ms"] = e0.elapsed_time(e1)
     res["backward_over_forward"] = res["backward_ms"] / res["forward_ms"]
     res["forward_amp_updates_per_s"] = (1 << nn) * res["K_total"] / (res["forward_ms"] / 1e3)
-    res["workload"] = "SK n=22, 64 piecewise-constant segments, complex64; backward = all gradients"
+    # the same forward captured once into a CUDA graph (host side at capture) and replayed
+    xg = x0.clone()
+    graph = api.AnnealGraph(a.h, a.J, a.gammas, a.ts, xg, boundaries=bnd)
+    for rep in range(2):
+        xg.copy_(x0)
+        torch.cuda.synchronize()
+        e0.record()
+        graph.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        res["forward_graph_ms"] = e0.elapsed_time(e1)
+    graph.status()
+    graph.close()
+    res["forward_graph_amp_updates_per_s"] = (1 << nn) * res["K_total"] / (res["forward_graph_ms"] / 1e3)
+    del xg
+    res["workload"] = ("SK n=22, 64 piecewise-constant segments, complex64; backward = all gradients; "
+                       "forward_graph: the schedule replayed from a CUDA graph (host side done at capture)")
     res["autotune"] = tune22
     out["anneal_n22"] = res
     del x, x0, bnd

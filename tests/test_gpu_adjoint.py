@@ -144,6 +144,39 @@ def test_anneal_workload_n22_gradients(cuda_lib):
         assert abs(got - ref) <= 1e-4 * max(abs(ref), scale), (which, idx, got, ref)
 
 
+def test_anneal_workload_n22_gradients_fp64_each_component(cuda_lib):
+    """The same workload with the FP64 forward and adjoint: every sampled gradient,
+    large or small, within 1e-6 of its own central finite difference (the FP32 test
+    above bounds its components by the FP32 noise floor of the largest one)."""
+    import torch
+
+    from paper_2608_12058_b300 import autograd as AG
+
+    a = I.config_anneal()
+    n = a.n
+    psi0 = I.uniform_state(n)
+    th, tJ, tg, tT = _params(a.h, a.J, a.gammas, a.ts)
+    x = torch.from_numpy(psi0).to(torch.complex128).cuda()
+    L = AG.energy(AG.anneal(x, th, tJ, tg, tT, tol=1e-13), th, tJ)
+    L.backward()
+    eps = 1e-4
+
+    def fd(which, idx):
+        vals = []
+        for sgn in (+1, -1):
+            h_, J_, g_, t_ = [np.array(v, dtype=np.float64) for v in (a.h, a.J, a.gammas, a.ts)]
+            {"gamma": g_, "t": t_, "h": h_, "J": J_}[which][idx] += sgn * eps
+            vals.append(_energy_after(h_, J_, g_, t_, psi0, torch.complex128))
+        return (vals[0] - vals[1]) / (2 * eps)
+
+    checks = [("gamma", 10, tg.grad[10].item()), ("gamma", 60, tg.grad[60].item()),
+              ("t", 31, tT.grad[31].item()), ("t", 63, tT.grad[63].item()), ("h", 3, th.grad[3].item()),
+              ("J", (2, 17), tJ.grad[2, 17].item())]
+    for which, idx, got in checks:
+        ref = fd(which, idx)
+        assert abs(got - ref) <= 1e-6 * abs(ref) + 1e-9, (which, idx, got, ref)
+
+
 @pytest.mark.parametrize("n,dtype_name,tol", [(12, "complex128", 1e-11), (16, "complex64", 2e-5)])
 def test_regenerated_and_stored_forward_vectors_agree(cuda_lib, n, dtype_name, tol):
     """The two ways of providing b_k to the adjoint - all kept, or regenerated upward
