@@ -146,8 +146,8 @@ def test_anneal_workload_n22_gradients(cuda_lib):
 
 def test_anneal_workload_n22_gradients_fp64_each_component(cuda_lib):
     """The same workload with the FP64 forward and adjoint: every sampled gradient,
-    large or small, within 1e-6 of its own central finite difference (the FP32 test
-    above bounds its components by the FP32 noise floor of the largest one)."""
+    large or small, within 1e-6 (relative) of its own central finite difference (the
+    FP32 test above bounds its components by the FP32 noise floor of the largest one)."""
     import torch
 
     from paper_2608_12058_b300 import autograd as AG
@@ -174,7 +174,9 @@ def test_anneal_workload_n22_gradients_fp64_each_component(cuda_lib):
               ("J", (2, 17), tJ.grad[2, 17].item())]
     for which, idx, got in checks:
         ref = fd(which, idx)
-        assert abs(got - ref) <= 1e-6 * abs(ref) + 1e-9, (which, idx, got, ref)
+        # the absolute term is the finite difference's own rounding: FP64 energies accurate
+        # to ~1e-13 relative (|L| ~ 10) over 2 eps
+        assert abs(got - ref) <= 1e-6 * abs(ref) + 1e-7, (which, idx, got, ref)
 
 
 @pytest.mark.parametrize("n,dtype_name,tol", [(12, "complex128", 1e-11), (16, "complex64", 2e-5)])
