@@ -36,11 +36,12 @@ struct Seg {
     double g = 0.0;
 };
 
-// Ends a capture that failed part way and drops its graph.
+// Ends a capture that failed part way, drops its graph and the capture stream.
 cheb_status_t abandon(cudaStream_t s, cheb_status_t st) {
     cudaGraph_t g = nullptr;
     cudaStreamEndCapture(s, &g);
     if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(s);
     cudaGetLastError();
     return st == CHEB_OK ? CHEB_ERR_CUDA : st;
 }
@@ -106,26 +107,36 @@ extern "C" cheb_status_t cheb_anneal_graph_create(int n, const double* h, const 
     st = read_flags(C);
     if (st != CHEB_OK) return st;
     const size_t vbytes = ((size_t)1 << n) * C.L.cbytes;
+    // capture on a private stream (the caller's may be the legacy default stream, which
+    // cannot be captured); the graph itself is launched on the caller's stream
+    cudaStream_t cs = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    C.s = cs;
     const long long launches0 = cheb_launch_count();
-    CUDA_TRY(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return CHEB_ERR_CUDA;
+    }
     for (int s = 0; s < S; ++s) {
         const Seg& G = segs[s];
         if (boundaries &&
             cudaMemcpyAsync((unsigned char*)boundaries + (size_t)s * vbytes, psi, vbytes, cudaMemcpyDeviceToDevice,
-                            s0) != cudaSuccess)
-            return abandon(s0, CHEB_ERR_CUDA);
+                            cs) != cudaSuccess)
+            return abandon(cs, CHEB_ERR_CUDA);
         if (cudaMemcpyAsync(C.ws + C.L.jq, store + (size_t)s * a256(jq_bytes(n)), jq_bytes(n),
-                            cudaMemcpyDeviceToDevice, s0) != cudaSuccess)
-            return abandon(s0, CHEB_ERR_CUDA);
-        launch_tables(n, C.L.M, (const int64_t*)(C.ws + C.L.jq), C.tiles(), C.elow(), s0);
-        if (cudaGetLastError() != cudaSuccess) return abandon(s0, CHEB_ERR_CUDA);
+                            cudaMemcpyDeviceToDevice, cs) != cudaSuccess)
+            return abandon(cs, CHEB_ERR_CUDA);
+        launch_tables(n, C.L.M, (const int64_t*)(C.ws + C.L.jq), C.tiles(), C.elow(), cs);
+        if (cudaGetLastError() != cudaSuccess) return abandon(cs, CHEB_ERR_CUDA);
         for (int q = 0; q < G.slices; ++q) {
             st = clenshaw_run(C, CHEB_PATH_AUTO, psi, G.coef, G.F.Q, G.g);
-            if (st != CHEB_OK) return abandon(s0, st);
+            if (st != CHEB_OK) return abandon(cs, st);
         }
     }
     cudaGraph_t g = nullptr;
-    if (cudaStreamEndCapture(s0, &g) != cudaSuccess || !g) {
+    const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (ce != cudaSuccess || !g) {
         cudaGetLastError();
         return CHEB_ERR_CUDA;
     }
