@@ -29,6 +29,14 @@ size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 
 size_t jq_bytes(int n) { return ((size_t)n * n + n + 1) * sizeof(int64_t); }
 
+// Per segment the store keeps the fixed-point couplings and, where the whole run is one
+// kernel that reads its coefficients from device memory (n <= 13 FP32, 12 FP64), the
+// coefficients of one time slice (at most kMaxK + 1).
+size_t seg_bytes(int n, int prec) {
+    const bool small = n <= (prec == CHEB_FP32 ? kSmallMaxF32 : kSmallMaxF64);
+    return a256(jq_bytes(n)) + (small ? a256((size_t)(kMaxK + 1) * 2 * sizeof(double)) : 0);
+}
+
 struct Seg {
     FixedOp F;
     std::vector<std::complex<double>> coef;
@@ -51,7 +59,7 @@ cheb_status_t abandon(cudaStream_t s, cheb_status_t st) {
 extern "C" size_t cheb_anneal_graph_workspace_bytes(int n, cheb_precision_t precision, int S) {
     if (n < 1 || n > kMaxQubits || S < 1) return 0;
     if (precision != CHEB_FP32 && precision != CHEB_FP64) return 0;
-    return a256(make_layout(n, precision).total) + (size_t)S * a256(jq_bytes(n));
+    return a256(make_layout(n, precision).total) + (size_t)S * seg_bytes(n, precision);
 }
 
 extern "C" cheb_status_t cheb_anneal_graph_create(int n, const double* h, const double* J, int S, const double* a_s,
@@ -100,8 +108,11 @@ extern "C" cheb_status_t cheb_anneal_graph_create(int n, const double* h, const 
         st = slice_coefficients(t_s[s], c, r, tol_s, method, 0, G.coef, &K, &G.slices, &err);
         if (st != CHEB_OK) return st;
         G.g = a_s[s] / r;
-        CUDA_TRY(cudaMemcpyAsync(store + (size_t)s * a256(jq_bytes(n)), G.F.jq.data(), jq_bytes(n),
-                                 cudaMemcpyHostToDevice, s0));
+        unsigned char* seg = store + (size_t)s * seg_bytes(n, precision);
+        CUDA_TRY(cudaMemcpyAsync(seg, G.F.jq.data(), jq_bytes(n), cudaMemcpyHostToDevice, s0));
+        if (seg_bytes(n, precision) > a256(jq_bytes(n)))
+            CUDA_TRY(cudaMemcpyAsync(seg + a256(jq_bytes(n)), G.coef.data(),
+                                     G.coef.size() * sizeof(std::complex<double>), cudaMemcpyHostToDevice, s0));
     }
     CUDA_TRY(cudaStreamSynchronize(s0));  // the host copies above are done before capture
     st = read_flags(C);
@@ -123,9 +134,10 @@ extern "C" cheb_status_t cheb_anneal_graph_create(int n, const double* h, const 
             cudaMemcpyAsync((unsigned char*)boundaries + (size_t)s * vbytes, psi, vbytes, cudaMemcpyDeviceToDevice,
                             cs) != cudaSuccess)
             return abandon(cs, CHEB_ERR_CUDA);
-        if (cudaMemcpyAsync(C.ws + C.L.jq, store + (size_t)s * a256(jq_bytes(n)), jq_bytes(n),
-                            cudaMemcpyDeviceToDevice, cs) != cudaSuccess)
+        unsigned char* seg = store + (size_t)s * seg_bytes(n, precision);
+        if (cudaMemcpyAsync(C.ws + C.L.jq, seg, jq_bytes(n), cudaMemcpyDeviceToDevice, cs) != cudaSuccess)
             return abandon(cs, CHEB_ERR_CUDA);
+        C.dev_coef = seg_bytes(n, precision) > a256(jq_bytes(n)) ? seg + a256(jq_bytes(n)) : nullptr;
         launch_tables(n, C.L.M, (const int64_t*)(C.ws + C.L.jq), C.tiles(), C.elow(), cs);
         if (cudaGetLastError() != cudaSuccess) return abandon(cs, CHEB_ERR_CUDA);
         for (int q = 0; q < G.slices; ++q) {

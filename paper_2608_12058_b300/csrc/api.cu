@@ -140,8 +140,12 @@ cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::c
     }
     if (path == CHEB_PATH_AUTO && C.n <= small_max) {
         static_assert(sizeof(std::complex<double>) == 2 * sizeof(double), "layout");
-        CUDA_TRY(cudaMemcpyAsync(C.ws + C.L.coef, c.data(), c.size() * sizeof(std::complex<double>),
-                                 cudaMemcpyHostToDevice, C.s));
+        if (C.dev_coef)
+            CUDA_TRY(cudaMemcpyAsync(C.ws + C.L.coef, C.dev_coef, c.size() * sizeof(std::complex<double>),
+                                     cudaMemcpyDeviceToDevice, C.s));
+        else
+            CUDA_TRY(cudaMemcpyAsync(C.ws + C.L.coef, c.data(), c.size() * sizeof(std::complex<double>),
+                                     cudaMemcpyHostToDevice, C.s));
         CUDA_TRY(launch_small(C.prec, C.n, K, (const double*)(C.ws + C.L.coef), Q, C.tiles(), C.elow(), g,
                               psi, C.s));
         return CHEB_OK;

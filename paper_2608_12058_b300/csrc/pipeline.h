@@ -25,6 +25,9 @@ struct Ctx {
     Layout L;
     unsigned char* ws;
     cudaStream_t s;
+    // when set, the whole-run kernel takes the run's coefficients from this device copy
+    // (a captured graph must not read host memory at replay)
+    const void* dev_coef = nullptr;
     int64_t* tiles() const { return (int64_t*)(ws + L.tiles); }
     int64_t* elow() const { return (int64_t*)(ws + L.elow); }
     int* flags() const { return (int*)(ws + L.status); }
