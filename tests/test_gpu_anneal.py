@@ -166,7 +166,7 @@ def test_anneal_graph_general_segments_and_slicing(cuda_lib):
     n = 10
     a = I.config_anneal(n=n, S=3, seed=23)
     b_s = np.array([1.0, -0.5, 0.8])
-    ts = np.array([0.5, 3000.0, 0.7])  # the middle segment exceeds the coefficient table
+    ts = np.array([0.5, 10000.0, 0.7])  # the middle segment exceeds the coefficient table
     x0 = torch.from_numpy(I.random_state(n, 24)).to(torch.complex128).cuda()
     y_ref = x0.clone()
     inf = api.anneal_general(a.h, a.J, a.gammas, b_s, ts, y_ref, tol=1e-10)
