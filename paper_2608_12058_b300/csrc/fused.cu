@@ -1135,8 +1135,7 @@ __global__ void __launch_bounds__(kMixedThreads, 1)
 // shared-memory traffic per amplitude (the TMA fill, the own value, six partners)
 // against 96 B in the one-pass kernels. An A-tile's slot (b_{k+2}) is read with
 // L2-only loads, or by TMA with the tile when tiles have at most 8 bits (a stage then
-// holds both); a B-tile's q, which other SMs wrote in this launch, comes by TMA into
-// the stage when it has room (ranges of at most 8 bits, or B narrower than A).
+// holds both); so does a B-tile's q, which other SMs wrote in this launch.
 // The flip sum runs in descending bit order, as in the one-pass kernels, so the pair
 // and two separate passes agree bit for bit.
 constexpr int kPairCons = 512;
@@ -1149,14 +1148,14 @@ struct PairCfg {
     static constexpr uint32_t kBytesA = (uint32_t)128 << HA;
     static constexpr uint32_t kBytesB = (uint32_t)128 << HB;
     // Tiles of up to 8 bits: a stage holds a tile and its slot rows (three stages of
-    // 64 KB), so the consumers read nothing from global memory. 9-bit A-tiles fill a
-    // stage alone: their slot comes by L2-only loads; a narrower B-tile still leaves
-    // room for its q rows.
+    // 64 KB), so the consumers read nothing from global memory. With 9-bit tiles a stage
+    // holds the tile alone and both slots come by L2-only loads (staging a narrower
+    // B-tile's q in the free half of its stage measured 2% slower at n=30).
     static constexpr bool kFull = kHMax <= 8;
     static constexpr uint32_t kStage = kFull ? 2 * kTileMax : kTileMax;
-    static constexpr uint32_t kSlotOff = kFull ? kTileMax : kBytesB;
+    static constexpr uint32_t kSlotOff = kTileMax;
     static constexpr bool kSlotInStageA = kFull;
-    static constexpr bool kQInStage = kFull || HB < HA;
+    static constexpr bool kQInStage = kFull;
     static constexpr int kNSraw = (int)((200u * 1024u) / kStage);
     static constexpr int kNS = kNSraw < 6 ? kNSraw : 6;
     static constexpr int kNR = 8;                                 // completion records in flight
