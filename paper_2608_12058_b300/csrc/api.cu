@@ -226,7 +226,9 @@ cheb_status_t clenshaw_run(Ctx& C, int path, void* psi, const std::vector<std::c
         a.sgn = (k == K - 1) ? 0.0 : -1.0;
         a.g = g;
         if (ff) {
-            if (launch_step_ff(plan, a, C.flags(), k == 0, C.s) != cudaSuccess) return CHEB_ERR_CUDA;
+            if (launch_step_ff(plan, a, C.ws + C.L.coef + (size_t)(kMaxK + 1) * 2 * sizeof(double), C.flags(), k == 0,
+                               C.s) != cudaSuccess)
+                return CHEB_ERR_CUDA;
         } else if (fused) {
             cudaError_t e = launch_step_fused(plan, a, C.ws + C.L.coef + (size_t)(kMaxK + 1) * 2 * sizeof(double),
                                               C.flags(), C.s);

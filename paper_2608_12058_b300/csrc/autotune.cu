@@ -58,8 +58,12 @@ std::vector<Candidate> candidates(int n, int prec) {
     } else {
         for (int l = 0; l <= 5 && 10 + l <= n; ++l) {
             const int h = n - 10 - l;
-            if (ff_split_valid(n, l, h)) out.push_back({CHEB_PATH_FUSED, l, h, 0});
+            if (!ff_split_valid(n, l, h)) continue;
+            out.push_back({CHEB_PATH_FUSED, l, h, 0});
+            ff_set_split(n, l, h);
+            if (ff_pair_eligible(ff_plan(n))) out.push_back({CHEB_PATH_FUSED, l, h, 2});
         }
+        ff_set_split(n, -1, 0);
     }
     return out;
 }
@@ -71,7 +75,7 @@ void apply(int prec, int n, const Candidate& c) {
         else
             ff_set_split(n, c.l, c.h);
     }
-    tuned_set(prec, n, c.path, prec == CHEB_FP32 ? c.blocking : -1);
+    tuned_set(prec, n, c.path, c.blocking);
 }
 
 std::string device_name() {

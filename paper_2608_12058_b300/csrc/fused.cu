@@ -32,6 +32,7 @@
 #include "cheb_internal.h"
 #include "fused.cuh"
 #include "mbar.cuh"
+#include "pair.cuh"
 
 namespace cheb {
 
@@ -727,57 +728,6 @@ __device__ __forceinline__ MixedItem mixed_decode(unsigned long long i, int gbit
     return {kItemEnd, 0, 0};
 }
 
-// Bounded acquire-wait until *p >= target (same limit and abort rule as mbar_wait).
-__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target, int* flags, volatile int* abort) {
-    const long long t0 = clock64();
-    while (true) {
-        unsigned v;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-        if (v >= target) return true;
-        if (*abort) return false;
-        if (clock64() - t0 > kWaitCycles) {
-            atomicOr(flags, kFlagTimeout);
-            *abort = 1;
-            return false;
-        }
-        __nanosleep(64);
-    }
-}
-
-// L2 eviction-priority policies and the cache-hinted bulk copies and stores of the
-// blocked tail (PTX createpolicy / .L2::cache_hint).
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ void tma_load_1d_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                                 uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
-        "%4;" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_4d_hint(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                                 uint64_t* bar, uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
-        "{%2, %3, %4, %5}], [%6], %7;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-__device__ __forceinline__ void st_hint(float4* p, float4 v, uint64_t pol) {
-    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
-                 "f"(v.w), "l"(pol)
-                 : "memory");
-}
-
 template <int H, bool C>
 __global__ void __launch_bounds__(kMixedThreads, 1)
     k_mixed(const MixedArgs m, const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap) {
@@ -1113,305 +1063,27 @@ __global__ void __launch_bounds__(kMixedThreads, 1)
     }
 }
 
-// ---------------------------------------------------------------------------
-// L2-blocked pair of strided passes: the two strided ranges of a step, A = [loA, loB)
-// and B = [loB, n), in one persistent launch, rows of 16 amplitudes (128 B). The
-// amplitudes are grouped by their bits [4, loA): group g holds 2^(4 + HA + HB)
-// amplitudes, 2^HB A-tiles (one per value of the bits of B) and 2^HA B-tiles (one per
-// value of the bits of A). A-tiles read b_{k+1} and the slot (b_{k+2}) from DRAM and
-// write q = s g S_A + sgn slot; the B-tiles of the same group, D groups later, read
-// b_{k+1} and q back from L2 and write q + s g S_B, so a step's two strided passes
-// move 24 B per amplitude of DRAM traffic instead of 48.
-//
-// Work items in order: A(0) .. A(D - 1), then A(s) followed by B(s - D) for
-// s = D .. G - 1, then B(G - D) .. B(G - 1). CTAs take items from a global counter;
-// before loading a B-tile the producer waits (bounded) until all A-tiles of its group
-// are published by the notifier warps (fence, then the group count), so an item only
-// waits on items taken before it.
-//
-// Consumers: 512 threads. In a tile of 2^H rows thread t holds column float4
-// u = t & 7 of the 2^(H-6) rows whose bits 0..5 are t >> 3: the flips of row bits
-// 6..H-1 come from registers and those of bits 0..5 from shared memory, 64 B of
-// shared-memory traffic per amplitude (the TMA fill, the own value, six partners)
-// against 96 B in the one-pass kernels. An A-tile's slot (b_{k+2}) is read with
-// L2-only loads, or by TMA with the tile when tiles have at most 8 bits (a stage then
-// holds both); so does a B-tile's q, which other SMs wrote in this launch.
-// The flip sum runs in descending bit order, as in the one-pass kernels, so the pair
-// and two separate passes agree bit for bit.
-constexpr int kPairCons = 512;
-constexpr int kPairThreads = kPairCons + 64;  // + producer warp + notifier warp
-
-template <int HA, int HB>
-struct PairCfg {
-    static constexpr int kHMax = HA > HB ? HA : HB;
-    static constexpr uint32_t kTileMax = (uint32_t)128 << kHMax;  // largest tile
-    static constexpr uint32_t kBytesA = (uint32_t)128 << HA;
-    static constexpr uint32_t kBytesB = (uint32_t)128 << HB;
-    // Tiles of up to 8 bits: a stage holds a tile and its slot rows (three stages of
-    // 64 KB), so the consumers read nothing from global memory. With 9-bit tiles a stage
-    // holds the tile alone and both slots come by L2-only loads (staging a narrower
-    // B-tile's q in the free half of its stage measured 2% slower at n=30).
-    static constexpr bool kFull = kHMax <= 8;
-    static constexpr uint32_t kStage = kFull ? 2 * kTileMax : kTileMax;
-    static constexpr uint32_t kSlotOff = kTileMax;
-    static constexpr bool kSlotInStageA = kFull;
-    static constexpr bool kQInStage = kFull;
-    static constexpr int kNSraw = (int)((200u * 1024u) / kStage);
-    static constexpr int kNS = kNSraw < 6 ? kNSraw : 6;
-    static constexpr int kNR = 8;                                 // completion records in flight
-    static constexpr size_t kItemOff = (size_t)kNS * kStage;  // per stage: kind, group, index
-    static constexpr size_t kNoteOff = kItemOff + 3 * 8 * sizeof(long long);
-    static constexpr size_t kBarOff = kNoteOff + (size_t)kNR * sizeof(int64_t);
-    static constexpr size_t kAbortOff = kBarOff + (size_t)(2 * kNS + 2 * kNR) * sizeof(uint64_t);
-    static constexpr size_t kSmem = kAbortOff + 16;
-    static_assert(kNS >= 2 && kNS <= 8, "pair stages");
-};
-
-struct PairArgs {
-    const float4* b1;
-    const float4* slot_in;  // b_{k+2} (read by the A-tiles when sgn != 0)
-    float4* slot;           // receives q (may equal slot_in)
-    int loA, loB;           // loB = loA + HA, n = loB + HB
-    float scale_g, scale_glo, sgn;
-    unsigned long long* work;  // item counter (zero at launch)
-    unsigned* done;            // per group: A-tiles published (zero at launch)
-    int gbits;                 // loA - 4 (2^gbits groups)
-    int lag;                   // D, 1 <= D <= 2^gbits
-    int* flags;
-};
-
-__device__ __forceinline__ MixedItem pair_decode(unsigned long long i, int gbits, int HA, int HB, int lag) {
-    const unsigned long long G = 1ull << gbits, D = (unsigned long long)lag, NA = 1ull << HB, NB = 1ull << HA;
-    const unsigned long long seg = NA + NB, head = D * NA;
-    if (i < head) return {kItemStrided, (int64_t)(i / NA), (int64_t)(i % NA)};
-    const unsigned long long j = i - head, s = D + j / seg;
-    if (s < G) {
-        const unsigned long long r = j % seg;
-        return r < NA ? MixedItem{kItemStrided, (int64_t)s, (int64_t)r}
-                      : MixedItem{kItemLow, (int64_t)(s - D), (int64_t)(r - NA)};
-    }
-    const unsigned long long k = j - (G - D) * seg, g = G - D + k / NB;
-    if (g < G) return {kItemLow, (int64_t)g, (int64_t)(k % NB)};
-    return {kItemEnd, 0, 0};
-}
-
-__device__ __forceinline__ float4 ld_cg4(const float4* p) {
-    float4 v;
-    asm volatile("ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p));
-    return v;
-}
-
-// One strided tile of 2^H rows (in shared memory, rows of 8 float4) on the 256
-// consumer threads: q = s g S + sgn w for the rows' amplitudes, written to slot.
-// The slot comes from qtile (shared memory, same layout as the tile) when it is not null,
-// else from slot_in with L2-only loads.
-template <int H>
-__device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, const float4* __restrict__ qtile,
-                                          const float4* slot_in, float4* slot, int64_t base, int64_t row_stride_f4,
-                                          float2 g_hi, float2 g_lo, float2 sg, bool need_slot, uint64_t pol_store) {
-    constexpr int P = 1 << (H - 6);
-    const int t = threadIdx.x;
-    const int u = t & 7, rq = t >> 3;
-    float4 v[P];
-#pragma unroll
-    for (int i = 0; i < P; ++i) v[i] = tile[(rq | (i << 6)) * 8 + u];
-    AccT<false> S[P];
-    // register bits H-1 .. 6 first (descending)
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-        S[i].zero();
-#pragma unroll
-        for (int b = P >> 1; b >= 1; b >>= 1) S[i].add(v[i ^ b]);
-    }
-    float4 w[P];
-    if (need_slot && !qtile) {
-#pragma unroll
-        for (int i = 0; i < P; ++i) w[i] = ld_cg4(slot_in + base + (int64_t)(rq | (i << 6)) * row_stride_f4 + u);
-    }
-    // then row bits 5 .. 0 from shared memory
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-#pragma unroll
-        for (int j = 5; j >= 0; --j) S[i].add(tile[((rq ^ (1 << j)) | (i << 6)) * 8 + u]);
-    }
-    if (need_slot && qtile) {
-#pragma unroll
-        for (int i = 0; i < P; ++i) w[i] = qtile[(rq | (i << 6)) * 8 + u];
-    }
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-        float2 q0 = __ffma2_rn(g_hi, S[i].ra(), __fmul2_rn(g_lo, S[i].ra()));
-        float2 q1 = __ffma2_rn(g_hi, S[i].rb(), __fmul2_rn(g_lo, S[i].rb()));
-        if (need_slot) {
-            q0 = __ffma2_rn(sg, lo2(w[i]), q0);
-            q1 = __ffma2_rn(sg, hi2(w[i]), q1);
-        }
-        st_hint(slot + base + (int64_t)(rq | (i << 6)) * row_stride_f4 + u, make_float4(q0.x, q0.y, q1.x, q1.y),
-                pol_store);
-    }
-}
-
-template <int HA, int HB>
-__global__ void __launch_bounds__(kPairThreads, 1)
-    k_pair(const PairArgs a, const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-           const __grid_constant__ CUtensorMap smapA, const __grid_constant__ CUtensorMap qmapB) {
-    using Cfg = PairCfg<HA, HB>;
-    static_assert(HA >= 6 && HA <= 9 && HB >= 6 && HB <= 9, "pair ranges");
-    static_assert(Cfg::kSmem <= 227 * 1024, "shared memory");
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* full = (uint64_t*)(smem + Cfg::kBarOff);
-    uint64_t* empty = full + Cfg::kNS;
-    uint64_t* cdone = empty + Cfg::kNS;   // an A-tile's q stores are issued (8 warps)
-    uint64_t* cempty = cdone + Cfg::kNR;  // the notifier has published that record
-    volatile int* abort = (volatile int*)(smem + Cfg::kAbortOff);
-    // the producer decodes each item once: kind, group and index per stage
-    long long* item = (long long*)(smem + Cfg::kItemOff);
-    volatile long long* note = (volatile long long*)(smem + Cfg::kNoteOff);
-    const int t = threadIdx.x;
-    const int warp = t >> 5, lane = t & 31;
-    const int sha = a.loA - 4;
-    if (t == 0) {
-        for (int i = 0; i < Cfg::kNS; ++i) {
-            mbar_init(&full[i], 1);
-            mbar_init(&empty[i], kPairCons / 32);
-        }
-        for (int i = 0; i < Cfg::kNR; ++i) {
-            mbar_init(&cdone[i], kPairCons / 32);
-            mbar_init(&cempty[i], 1);
-        }
-        *abort = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    if (warp == kPairCons / 32 + 1) {
-        // ---------------- notifier warp ----------------
-        if (lane != 0) return;
-        for (long long j = 0;; ++j) {
-            const int r = (int)(j % Cfg::kNR);
-            if (!mbar_wait(&cdone[r], (uint32_t)((j / Cfg::kNR) & 1), a.flags, abort)) break;
-            const long long g = note[r];
-            if (g < 0) break;
-            __threadfence();
-            atomicAdd(a.done + g, 1u);
-            mbar_arrive(&cempty[r]);
-        }
-        return;
-    }
-
-    if (warp == kPairCons / 32) {
-        // ---------------- producer warp ----------------
-        if (lane != 0) return;
-        int last[Cfg::kNS];
-        for (int i = 0; i < Cfg::kNS; ++i) last[i] = -1;
-        // the A-tiles' b_{k+1} is read again by the B-tiles of their group
-        const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
-        // the next item is taken one ahead, so the counter's round trip overlaps the
-        // current item (it is later in the order, so holding it cannot block anyone)
-        unsigned long long nxt = atomicAdd(a.work, 1ull);
-        constexpr int boxA = HA < 8 ? (1 << HA) : 256;
-        for (int it = 0;; ++it) {
-            const unsigned long long cur = nxt;
-            const MixedItem ci = pair_decode(cur, a.gbits, HA, HB, a.lag);
-            if (ci.kind != kItemEnd) nxt = atomicAdd(a.work, 1ull);
-            const int s = it % Cfg::kNS, k = it / Cfg::kNS;
-            if (k > 0 && !mbar_wait(&empty[s], (k - 1) & 1, a.flags, abort)) break;
-            unsigned char* d = smem + (size_t)s * Cfg::kStage;
-            if (ci.kind == kItemEnd) {
-                item[3 * s] = kItemEnd;
-                mbar_arrive(&full[s]);
-                last[s] = k;
-                break;
-            }
-            if (ci.kind == kItemStrided) {
-                // A-tile: bits [4, loA) = g, bits of B = idx
-                item[3 * s] = kItemStrided;
-                item[3 * s + 1] = ci.g;
-                item[3 * s + 2] = ci.idx;
-                const bool slot_tma = Cfg::kSlotInStageA && a.sgn != 0.f;
-                mbar_expect_tx(&full[s], slot_tma ? 2 * Cfg::kBytesA : Cfg::kBytesA);
-#pragma unroll
-                for (int c = 0; c < (1 << HA) / boxA; ++c) {
-                    tma_load_4d_hint(d + (size_t)c * boxA * 128, &mapA, 0, (int)ci.g, c * boxA, (int)ci.idx, &full[s],
-                                     pol_last);
-                    // the slot lines become q, which the group's B-tiles read back
-                    if (slot_tma)
-                        tma_load_4d_hint(d + Cfg::kSlotOff + (size_t)c * boxA * 128, &smapA, 0, (int)ci.g, c * boxA,
-                                         (int)ci.idx, &full[s], pol_last);
-                }
-                last[s] = k;
-            } else {
-                if (!wait_count(a.done + ci.g, 1u << HB, a.flags, abort)) break;
-                // q of the group was written through the generic proxy by other SMs
-                asm volatile("fence.proxy.async.global;" ::: "memory");
-                item[3 * s] = kItemLow;
-                item[3 * s + 1] = ci.g;
-                item[3 * s + 2] = ci.idx;
-                mbar_expect_tx(&full[s], Cfg::kQInStage ? 2 * Cfg::kBytesB : Cfg::kBytesB);
-                constexpr int box = HB < 8 ? (1 << HB) : 256;
-                const int tlo = (int)(ci.g | (ci.idx << sha));  // bits [4, loB)
-#pragma unroll
-                for (int c = 0; c < (1 << HB) / box; ++c) {
-                    tma_load_4d_hint(d + (size_t)c * box * 128, &mapB, 0, tlo, c * box, 0, &full[s], pol_first);
-                    if (Cfg::kQInStage)
-                        tma_load_4d_hint(d + Cfg::kSlotOff + (size_t)c * box * 128, &qmapB, 0, tlo, c * box, 0,
-                                         &full[s], pol_first);
-                }
-                last[s] = k;
-            }
-        }
-        for (int i = 0; i < Cfg::kNS; ++i)
-            if (last[i] >= 0) mbar_drain(&full[i], last[i] & 1, a.flags);
-        return;
-    }
-
-    // ---------------- consumer warps ----------------
-    const float2 g_hi = dup(a.scale_g), g_lo = dup(a.scale_glo), sg = dup(a.sgn), one = dup(1.f);
-    const bool need_a = a.sgn != 0.f;
-    const uint64_t pol_last = policy_evict_last(), pol_first = policy_evict_first();
-    const int64_t rsA = (int64_t)1 << (a.loA - 1), rsB = (int64_t)1 << (a.loB - 1);
-    long long sj = 0;  // completion records sent
-    auto record = [&](long long g) -> bool {
-        __syncwarp();
-        bool ok = true;
-        if (lane == 0) {
-            const int r = (int)(sj % Cfg::kNR);
-            if (sj >= Cfg::kNR) ok = mbar_wait(&cempty[r], (uint32_t)(((sj / Cfg::kNR) - 1) & 1), a.flags, abort);
-            if (ok) {
-                if (warp == 0) note[r] = g;
-                mbar_arrive(&cdone[r]);
-            }
-        }
-        ++sj;
-        return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+// Arithmetic of the blocked strided pair (pair.cuh) for complex64 vectors: plain FP32
+// flip sums, q = s g S (float-float s g) + sgn w, exactly as in k_strided_ws.
+struct ArithF32 {
+    static constexpr int kAmpShift = 1;  // two amplitudes per float4
+    static constexpr int kRowBits = 4;   // 16 amplitudes per 128-byte row
+    using Acc = AccT<false>;
+    struct Scale {
+        float2 ghi, glo;
     };
-    for (int it = 0;; ++it) {
-        const int s = it % Cfg::kNS;
-        if (!mbar_wait(&full[s], (it / Cfg::kNS) & 1, a.flags, abort)) break;
-        const MixedItem ci = {(int)item[3 * s], item[3 * s + 1], item[3 * s + 2]};
-        if (ci.kind == kItemEnd) {
-            record(-1);
-            break;
+    __device__ static Scale scale(const pairk::Args& a) { return {dup(a.scale_g), dup(a.scale_glo)}; }
+    __device__ static float4 finish(const Acc& S, float4 w, bool need, float sgn, const Scale& c) {
+        float2 q0 = __ffma2_rn(c.ghi, S.ra(), __fmul2_rn(c.glo, S.ra()));
+        float2 q1 = __ffma2_rn(c.ghi, S.rb(), __fmul2_rn(c.glo, S.rb()));
+        if (need) {
+            const float2 sg = dup(sgn);
+            q0 = __ffma2_rn(sg, lo2(w), q0);
+            q1 = __ffma2_rn(sg, hi2(w), q1);
         }
-        const float4* tile = (const float4*)(smem + (size_t)s * Cfg::kStage);
-        if (ci.kind == kItemStrided) {
-            const int64_t base = ci.g * 8 + (ci.idx << (a.loB - 1));
-            const float4* st = Cfg::kSlotInStageA ? tile + (Cfg::kSlotOff / 16) : nullptr;
-            pair_tile<HA>(tile, st, a.slot_in, a.slot, base, rsA, g_hi, g_lo, sg, need_a, pol_last);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
-            if (!record(ci.g)) break;
-        } else {
-            const int64_t base = (ci.g | (ci.idx << sha)) * 8;
-            const float4* qt = Cfg::kQInStage ? tile + (Cfg::kSlotOff / 16) : nullptr;
-            pair_tile<HB>(tile, qt, a.slot, a.slot, base, rsB, g_hi, g_lo, one, true, pol_first);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
-        }
+        return make_float4(q0.x, q0.y, q1.x, q1.y);
     }
-}
+};
 
 }  // namespace
 
@@ -1582,54 +1254,6 @@ cudaError_t launch_mixed(int H, const MixedArgs& m, int n, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
-template <int HA, int HB>
-cudaError_t launch_pair_t(const PairArgs& a, int n, cudaStream_t s) {
-    using Cfg = PairCfg<HA, HB>;
-    CUtensorMap mapA, mapB, unused;
-    StridedArgs sa{};
-    sa.b1 = a.b1;
-    sa.sgn = 0.f;  // tensor maps of b_{k+1} only
-    sa.lo = a.loA;
-    cudaError_t e = strided_maps(sa, n, HA, 4, HA < 8 ? (1 << HA) : 256, &mapA, &unused);
-    if (e != cudaSuccess) return e;
-    // the A-tiles' slot (b_{k+2}) and the B-tiles' q in the same boxes
-    CUtensorMap smapA, qmapB;
-    sa.b1 = a.slot_in;
-    e = strided_maps(sa, n, HA, 4, HA < 8 ? (1 << HA) : 256, &smapA, &unused);
-    if (e != cudaSuccess) return e;
-    sa.b1 = a.slot;
-    sa.lo = a.loB;
-    e = strided_maps(sa, n, HB, 4, HB < 8 ? (1 << HB) : 256, &qmapB, &unused);
-    if (e != cudaSuccess) return e;
-    sa.b1 = a.b1;
-    sa.lo = a.loB;
-    e = strided_maps(sa, n, HB, 4, HB < 8 ? (1 << HB) : 256, &mapB, &unused);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_pair<HA, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
-    if (e != cudaSuccess) return e;
-    note_launch(kKindPair);
-    const int pi = prof_begin(kKindPair, s);
-    k_pair<HA, HB><<<(unsigned)num_sms(), kPairThreads, Cfg::kSmem, s>>>(a, mapA, mapB, smapA, qmapB);
-    prof_end(pi, s);
-    return cudaGetLastError();
-}
-
-// The range sizes of two-pass plans (make_passes gives the first pass the extra bit).
-cudaError_t launch_pair(int HA, int HB, const PairArgs& a, int n, cudaStream_t s) {
-    switch (HA * 16 + HB) {
-        case 6 * 16 + 6: return launch_pair_t<6, 6>(a, n, s);
-        case 7 * 16 + 6: return launch_pair_t<7, 6>(a, n, s);
-        case 7 * 16 + 7: return launch_pair_t<7, 7>(a, n, s);
-        case 8 * 16 + 7: return launch_pair_t<8, 7>(a, n, s);
-        case 8 * 16 + 8: return launch_pair_t<8, 8>(a, n, s);
-        case 9 * 16 + 8: return launch_pair_t<9, 8>(a, n, s);
-        case 9 * 16 + 9: return launch_pair_t<9, 9>(a, n, s);
-    }
-    return cudaErrorInvalidValue;
-}
-
-bool pair_shape_ok(int HA, int HB) { return HA >= 6 && HA <= 9 && HB >= 6 && (HB == HA || HB == HA - 1); }
-
 // Split h strided bits above bit lo0 into near-equal passes of 3..9 bits.
 bool make_passes(int lo0, int h, FusedPlan& p) {
     p.npass = 0;
@@ -1658,15 +1282,16 @@ constexpr int kMixedMinN = 22;
 size_t mixed_counter_bytes(int gbits) { return 8 + ((size_t)4 << gbits); }
 
 size_t fused_scratch_bytes(int n, int prec) {
-    if (prec != 0 || n < kMixedMinN || n > kMaxQubits) return 0;
-    return (mixed_counter_bytes(n - 16) + 255) / 256 * 256;
+    if (n < kMixedMinN || n > kMaxQubits) return 0;
+    // float-float rows are 8 amplitudes: the pair's groups are bits [3, loA), one more bit
+    return (mixed_counter_bytes(prec == 0 ? n - 16 : n - 15) + 255) / 256 * 256;
 }
 
 // Lag D of the blocked pair in groups: the B-tiles of group g follow the A-tiles of group
 // g + D, so about D + 1 groups of b_{k+1} and q are live in L2. Measured at n = 28..30,
 // the best D keeps that near 48 MB: D = 1 for 32 MB groups, D = 2 for 16 MB groups (one
 // more group cost 10-27%). CHEB_PAIR_LAG (1..16) overrides the rule.
-static int pair_lag(size_t group_bytes) {
+int pair_lag(size_t group_bytes) {
     static int env = -1;
     if (env < 0) {
         const char* e = std::getenv("CHEB_PAIR_LAG");
@@ -1684,13 +1309,14 @@ void fused_set_blocking(int mode) { g_blocking = (mode >= 0 && mode <= 2) ? mode
 int fused_get_blocking() { return g_blocking; }
 
 // Per-n choices of the autotuner (-1: not tuned): the blocked tail, and the AUTO path.
-static int g_block_n[kMaxQubits + 1];
+static int g_block_n[2][kMaxQubits + 1];
 static int g_auto_path[2][kMaxQubits + 1];
 static bool g_tuned_init = false;
 
 static void tuned_init() {
     if (!g_tuned_init) {
-        for (int i = 0; i <= kMaxQubits; ++i) g_block_n[i] = g_auto_path[0][i] = g_auto_path[1][i] = -1;
+        for (int i = 0; i <= kMaxQubits; ++i)
+            g_block_n[0][i] = g_block_n[1][i] = g_auto_path[0][i] = g_auto_path[1][i] = -1;
         g_tuned_init = true;
     }
 }
@@ -1700,7 +1326,7 @@ void tuned_set(int prec, int n, int path, int blocking) {
     tuned_init();
     if (n < 0 || n > kMaxQubits || prec < 0 || prec > 1) return;
     g_auto_path[prec][n] = path;
-    if (prec == 0) g_block_n[n] = blocking;
+    g_block_n[prec][n] = blocking;
 }
 
 int tuned_auto_path(int prec, int n) {
@@ -1710,11 +1336,14 @@ int tuned_auto_path(int prec, int n) {
     return g_auto_path[prec][n];
 }
 
-static int blocking_for(int n) {
+int fused_blocking_for(int prec, int n) {
     std::lock_guard<std::mutex> lk(g_mu);
     tuned_init();
-    return (n >= 0 && n <= kMaxQubits && g_block_n[n] >= 0) ? g_block_n[n] : g_blocking;
+    if (prec < 0 || prec > 1) return 0;
+    const int m = (n >= 0 && n <= kMaxQubits && g_block_n[prec][n] >= 0) ? g_block_n[prec][n] : g_blocking;
+    return (prec == 1 && m == 1) ? 0 : m;  // the blocked tail is FP32 only
 }
+static int blocking_for(int n) { return fused_blocking_for(0, n); }
 
 bool fused_blocking_eligible(const FusedPlan& plan) {
     const int lastp = plan.npass - 1;
@@ -1722,7 +1351,7 @@ bool fused_blocking_eligible(const FusedPlan& plan) {
            plan.hb[lastp] <= kMaxStrided;
 }
 bool fused_pair_eligible(const FusedPlan& plan) {
-    return plan.prec == 0 && plan.n >= kMixedMinN && plan.npass == 2 && pair_shape_ok(plan.hb[0], plan.hb[1]);
+    return plan.prec == 0 && plan.n >= kMixedMinN && plan.npass == 2 && pairk::shape_ok(plan.hb[0], plan.hb[1]);
 }
 void fused_set_compensated(int on) { g_comp = on ? 1 : 0; }
 int fused_get_compensated() { return g_comp; }
@@ -1824,7 +1453,7 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void* sc
     // flip sums only).
     const bool pair = mode == 2 && !g_comp && scratch != nullptr && fused_pair_eligible(plan) && s.out != s.b1;
     if (pair) {
-        PairArgs pa;
+        pairk::Args pa{};
         pa.b1 = (const float4*)s.b1;
         pa.slot_in = (const float4*)s.b2;
         pa.slot = q;
@@ -1833,7 +1462,7 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void* sc
         pa.scale_g = (float)s.scale * ghi;
         pa.scale_glo = (float)s.scale * glo;
         pa.sgn = (float)s.sgn;
-        pa.gbits = plan.lo[0] - 4;
+        pa.gbits = plan.lo[0] - ArithF32::kRowBits;
         const size_t group_bytes = (size_t)16 << (4 + plan.hb[0] + plan.hb[1]);  // b_{k+1} and q
         pa.lag = (int)std::min<int64_t>(pair_lag(group_bytes), (int64_t)1 << pa.gbits);
         pa.work = (unsigned long long*)scratch;
@@ -1841,7 +1470,7 @@ cudaError_t launch_step_fused(const FusedPlan& plan, const StepArgs& s, void* sc
         pa.flags = flags;
         cudaError_t e = cudaMemsetAsync(scratch, 0, mixed_counter_bytes(pa.gbits), st);
         if (e != cudaSuccess) return e;
-        e = launch_pair(plan.hb[0], plan.hb[1], pa, s.n, st);
+        e = pairk::launch<ArithF32>(plan.hb[0], plan.hb[1], pa, s.n, st);
         if (e != cudaSuccess) return e;
         slot_coeff = 1.0f;
     }

@@ -36,6 +36,11 @@ int fused_get_blocking();
 // Choices of the autotuner: per (prec, n) the AUTO path (-1 = built-in rule) and, for
 // FP32, the blocked tail (-1 = the process-wide switch).
 void tuned_set(int prec, int n, int path, int blocking);
+// The L2-blocked mode for (prec, n): the autotuner's choice, else the process-wide switch
+// (the blocked tail, mode 1, is FP32 only).
+int fused_blocking_for(int prec, int n);
+// Lag of the blocked pair in groups for groups of `group_bytes` (b_{k+1} and q).
+int pair_lag(size_t group_bytes);
 int tuned_auto_path(int prec, int n);
 bool fused_blocking_eligible(const FusedPlan& plan);
 // The blocked strided pair applies (two strided passes of 6..9 bits, FP32).

@@ -40,6 +40,7 @@
 #include "fused.cuh"
 #include "fused_ff.cuh"
 #include "mbar.cuh"
+#include "pair.cuh"
 
 namespace cheb {
 
@@ -556,10 +557,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int p = 0; p < Cfg::kP; ++p) {
             FFAcc S;
             S.zero();
+            // partners in descending bit order of the range (as in the blocked pair, so the
+            // two agree bit for bit)
 #pragma unroll
-            for (int j = 0; j < Cfg::kRB; ++j) S.add(tile[((rlo ^ (1 << j)) | (p << Cfg::kRB)) * Cfg::kRowF4 + u]);
+            for (int b = Cfg::kP >> 1; b >= 1; b >>= 1) S.add(tile[(rlo | ((p ^ b) << Cfg::kRB)) * Cfg::kRowF4 + u]);
 #pragma unroll
-            for (int b = 1; b < Cfg::kP; b <<= 1) S.add(tile[(rlo | ((p ^ b) << Cfg::kRB)) * Cfg::kRowF4 + u]);
+            for (int j = Cfg::kRB - 1; j >= 0; --j) S.add(tile[((rlo ^ (1 << j)) | (p << Cfg::kRB)) * Cfg::kRowF4 + u]);
             // q = g S + sgn slot in one accumulator, renormalised once
             FFAcc A;
             A.zero();
@@ -585,6 +588,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&empty[s]);
     }
 }
+
+// Arithmetic of the blocked strided pair (pair.cuh) for float-float vectors: the flip
+// sum in the Sum2 accumulator, q = (s g) S + sgn w in one accumulator, exactly as in
+// k_strided_ff.
+struct ArithFF {
+    static constexpr int kAmpShift = 0;  // one amplitude per float4
+    static constexpr int kRowBits = 3;   // 8 amplitudes per 128-byte row
+    using Acc = FFAcc;
+    struct Scale {
+        float g2, g1, g0;
+    };
+    __device__ static Scale scale(const pairk::Args& a) { return {a.g2, a.g1, a.g0}; }
+    __device__ static float4 finish(const Acc& S, float4 w, bool need, float sgn, const Scale& c) {
+        FFAcc A;
+        A.zero();
+        if (need) {
+            if (sgn < 0.f)
+                A.start(f2(-w.x, -w.y), f2(-w.z, -w.w));
+            else
+                A.start(f2(w.x, w.y), f2(w.z, w.w));
+        }
+        acc_mul3(A, c.g2, c.g1, c.g0, S.s, S.c);
+        return pk(A.result());
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Conversions at the ends of a run (once per Clenshaw run, FP64 arithmetic).
@@ -797,14 +825,45 @@ cudaError_t launch_ff_scale(int64_t N, const void* src, void* dst, double cr, do
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_ff(const FusedPlan& plan, const StepArgs& s, int* flags, bool out_f64, cudaStream_t st) {
+bool ff_pair_eligible(const FusedPlan& plan) {
+    return plan.prec == 1 && plan.n >= 22 && plan.npass == 2 && pairk::shape_ok(plan.hb[0], plan.hb[1]);
+}
+
+cudaError_t launch_step_ff(const FusedPlan& plan, const StepArgs& s, void* scratch, int* flags, bool out_f64,
+                           cudaStream_t st) {
     if (plan.prec != 1 || plan.n != s.n || !ff_split_valid(s.n, plan.l, plan.h) || s.M != 11)
         return cudaErrorInvalidValue;
     float g2, g1, g0;
     split3(s.g * s.scale, g2, g1, g0);
     float slot_coeff = (float)s.sgn;
     float4* q = (s.out != s.psi && s.out != s.b1) ? (float4*)s.out : (float4*)s.b2;
-    for (int k = 0; k < plan.npass; ++k) {
+    // the two strided passes of a two-pass split as one L2-blocked launch
+    const bool pair = fused_blocking_for(1, s.n) == 2 && scratch != nullptr && ff_pair_eligible(plan) &&
+                      s.out != s.b1;
+    if (pair) {
+        pairk::Args pa{};
+        pa.b1 = (const float4*)s.b1;
+        pa.slot_in = (const float4*)s.b2;
+        pa.slot = q;
+        pa.loA = plan.lo[0];
+        pa.loB = plan.lo[1];
+        pa.g2 = g2;
+        pa.g1 = g1;
+        pa.g0 = g0;
+        pa.sgn = (float)s.sgn;
+        pa.gbits = plan.lo[0] - ArithFF::kRowBits;
+        const size_t group_bytes = (size_t)32 << (ArithFF::kRowBits + plan.hb[0] + plan.hb[1]);  // b_{k+1} and q
+        pa.lag = (int)std::min<int64_t>(pair_lag(group_bytes), (int64_t)1 << pa.gbits);
+        pa.work = (unsigned long long*)scratch;
+        pa.done = (unsigned*)((unsigned char*)scratch + 8);
+        pa.flags = flags;
+        cudaError_t e = cudaMemsetAsync(scratch, 0, 8 + ((size_t)4 << pa.gbits), st);
+        if (e != cudaSuccess) return e;
+        e = pairk::launch<ArithFF>(plan.hb[0], plan.hb[1], pa, s.n, st);
+        if (e != cudaSuccess) return e;
+        slot_coeff = 1.0f;
+    }
+    for (int k = 0; k < (pair ? 0 : plan.npass); ++k) {
         StridedFFArgs sa;
         sa.b1 = (const float4*)s.b1;
         sa.slot_in = (k == 0) ? (const float4*)s.b2 : q;

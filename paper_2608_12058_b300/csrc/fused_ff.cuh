@@ -22,6 +22,10 @@ cudaError_t launch_to_ff(int64_t N, void* psi, cudaStream_t s);
 cudaError_t launch_ff_scale(int64_t N, const void* src, void* dst, double cr, double ci, cudaStream_t s);
 // One Clenshaw step on float-float vectors b1, b2, psi; out is float-float, or complex128
 // when out_f64 (the final step).
-cudaError_t launch_step_ff(const FusedPlan& plan, const StepArgs& a, int* flags, bool out_f64, cudaStream_t s);
+// scratch (nullable): the fused scratch of the workspace (counters of the blocked pair).
+cudaError_t launch_step_ff(const FusedPlan& plan, const StepArgs& a, void* scratch, int* flags, bool out_f64,
+                           cudaStream_t s);
+// The blocked strided pair applies to the float-float step (two strided passes of 6..9 bits).
+bool ff_pair_eligible(const FusedPlan& plan);
 
 }  // namespace cheb

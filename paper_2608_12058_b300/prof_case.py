@@ -13,6 +13,9 @@
         launches, the L2-blocked step tail and the L2-blocked strided pair, twice each
         (CUDA events around the call; then a run with the library's per-kind event
         timing), and prints ms per step and per launch.
+    python -m paper_2608_12058_b300.prof_case ffcompare N [STEPS [L H]]
+        float-float (FP64 path) step time at n = N with separate launches and with the
+        L2-blocked strided pair.
     python -m paper_2608_12058_b300.prof_case ff N L H [STEPS]
         STEPS float-float fused steps of the FP64 path (complex128 states) at n = N with
         the split (L, H) (kernel names k_low_ff and k_strided_ff).
@@ -128,6 +131,43 @@ def compare(n, steps, split=None):
         api.set_fused_blocking(0)
         if split is not None:
             api.set_fused_split(n, -1)
+
+
+def ff_compare(n, steps, split=None):
+    """Step time of the float-float fused step (FP64 path) at n with separate launches
+    (mode 0) and the L2-blocked strided pair (2), CUDA events, twice each."""
+    import torch
+
+    from . import api
+    from . import inputs as I
+
+    if split is not None:
+        api.set_fused_split_fp64(n, split[0], split[1])
+    c = I.config_family(n, 1.0, 1.0, 0, "uniform")
+    x = torch.full((1 << n,), 2 ** (-n / 2), dtype=torch.complex128, device="cuda")
+    rng = np.random.default_rng(0)
+    coef = (rng.standard_normal(steps + 1) + 1j * rng.standard_normal(steps + 1)) / (4 * steps)
+    print("n", n, "fp64 split", api.get_fused_split_fp64(n), "steps", steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    try:
+        for _ in range(2):
+            for mode in (0, 2):
+                api.set_fused_blocking(mode)
+                api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef[:4], x, path="fused")  # warm-up
+                torch.cuda.synchronize()
+                e0.record()
+                api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef, x, path="fused")
+                e1.record()
+                torch.cuda.synchronize()
+                api.check_status(n, "fp64")
+                ms = e0.elapsed_time(e1)
+                print(f"  blocking {mode}: {ms / steps:.3f} ms/step, {(1 << n) * steps / ms * 1e3:.3e} "
+                      "amplitude-updates/s")
+    finally:
+        api.set_fused_blocking(0)
+        if split is not None:
+            api.set_fused_split_fp64(n, -1)
 
 
 def adjoint(n, S):
@@ -298,6 +338,9 @@ def main(argv):
     elif argv[0] == "compare":
         split = (int(argv[3]), int(argv[4])) if len(argv) > 4 else None
         compare(int(argv[1]), int(argv[2]) if len(argv) > 2 else 40, split)
+    elif argv[0] == "ffcompare":
+        split = (int(argv[3]), int(argv[4])) if len(argv) > 4 else None
+        ff_compare(int(argv[1]), int(argv[2]) if len(argv) > 2 else 10, split)
     elif argv[0] == "anneal":
         anneal_time()
     elif argv[0] == "l2":

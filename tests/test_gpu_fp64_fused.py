@@ -123,3 +123,76 @@ def test_ff_eval_bound(cuda_lib, oracle):
     print(f"n={n} float-float: eval_bound {gb:.3e} (oracle {ob:.3e}), observed {err:.3e}")
     assert abs(gb - ob) <= 1e-3 * ob
     assert err <= gb
+
+
+# ---------------------------------------------------------------------------
+# The L2-blocked strided pair on the float-float step (cheb_set_fused_blocking(2)): the
+# same Sum2 flip sums in the same order as the separate launches, so the results agree
+# bit for bit; against the oracle at the FP64 bar.
+
+@pytest.mark.parametrize("n,split", [(22, (0, 12)), (23, (0, 13)), (25, (1, 14))])
+def test_ff_blocked_pair_matches_oracle_and_separate(cuda_lib, oracle, n, split):
+    """Range pairs 6+6, 7+6 and 7+7 against the FP64 oracle and, bit for bit, against
+    the separate launches (two launches per step instead of three)."""
+    from paper_2608_12058_b300 import api
+
+    h, J = I.sk_instance(n, 640 + n)
+    psi = I.random_state(n, 641 + n)
+    ref, oinfo = oracle.expmv(h, J, 0.9, 0.3, psi, 1e-12)
+    api.set_fused_split_fp64(n, *split)
+    try:
+        api.set_fused_blocking(2)
+        c0 = api.launch_count()
+        y, info = _run(h, J, 0.9, 0.3, psi)
+        paired = api.launch_count() - c0
+        api.set_fused_blocking(0)
+        c1 = api.launch_count()
+        y_sep, _ = _run(h, J, 0.9, 0.3, psi)
+        separate = api.launch_count() - c1
+    finally:
+        api.set_fused_blocking(0)
+        api.set_fused_split_fp64(n, -1)
+    assert info["K"] == oinfo["K"] and info["K"] >= 10
+    assert separate - paired == info["K"]
+    assert np.array_equal(y, y_sep)
+    assert _rel(y, ref) <= BAR
+
+
+def _ff_poly(n, coef, mode):
+    import torch
+
+    from paper_2608_12058_b300 import api
+
+    c = I.config_family(n, 1.0, 1.0, 0, "uniform")
+    api.set_fused_blocking(mode)
+    g = torch.Generator(device="cuda").manual_seed(70 + n)
+    x = torch.randn(1 << n, dtype=torch.complex128, device="cuda", generator=g)
+    x /= torch.linalg.vector_norm(x)
+    api.poly_apply(c.h, c.J, 1.0, 0.0, 80.0, coef, x, path="fused")
+    api.check_status(n, "fp64")
+    return x
+
+
+@pytest.mark.parametrize("n,split", [(26, (0, 16)), (28, (1, 17)), (29, (2, 17))])
+def test_ff_blocked_pair_bit_identical(cuda_lib, n, split):
+    """8+8, 9+8 and 9+8 ranges up to 2^29 float-float amplitudes: the blocked pair equals
+    the separate launches bit for bit, including steps with c_k = 0 and the final step
+    alone."""
+    from paper_2608_12058_b300 import api
+
+    rng = np.random.default_rng(n)
+    coef = (rng.standard_normal(6) + 1j * rng.standard_normal(6)) / 32
+    coef[2] = 0.0
+    api.set_fused_split_fp64(n, *split)
+    try:
+        a = _ff_poly(n, coef, 2)
+        b = _ff_poly(n, coef, 0)
+        assert bool((a == b).all())
+        del a, b
+        one = np.array([0.3 + 0.1j, 0.5 - 0.2j])
+        a = _ff_poly(n, one, 2)
+        b = _ff_poly(n, one, 0)
+        assert bool((a == b).all())
+    finally:
+        api.set_fused_blocking(0)
+        api.set_fused_split_fp64(n, -1)
