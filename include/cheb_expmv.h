@@ -499,15 +499,17 @@ cheb_status_t cheb_get_fused_split_fp64(int n, int* l, int* h);
  * last range of 6..9 bits; other splits keep the separate launches.
  * Mode 2 blocks the two strided passes of a split that has exactly two (ranges
  * A = [loA, loB) and B = [loB, n) of 6..9 bits, B no wider than A and at most one bit
- * narrower): amplitudes are grouped by their bits [4, loA), and the tiles of the
- * upper range B of a group run right after the tiles of range A of that group, so
- * b_{k+1} and the partial sum come back from L2: the two passes move 24 B per
- * amplitude of DRAM traffic instead of 48. Flip sums are plain FP32 in descending bit
+ * narrower), in the FP32 step and in the float-float step of the FP64 path (n >= 22):
+ * amplitudes are grouped by their bits above a 128-byte row and below loA, and the
+ * tiles of the upper range B of a group run right after the tiles of range A of that
+ * group, so b_{k+1} and the partial sum come back from L2: the two passes move half
+ * the DRAM bytes of two separate passes (24 B per amplitude in FP32). Flip sums are plain FP32 in descending bit
  * order, as in the separate launches, so results are identical. The lag between a
  * group's A and B tiles keeps about 48 MB of the two vectors live in L2 (one group of
  * 32 MB, two of 16 MB); the environment variable CHEB_PAIR_LAG (1..16) overrides it.
- * on: 0 off, 1 the blocked tail, 2 the blocked strided pair (process-wide; the
- * autotuner's per-n choice takes precedence). cheb_get_fused_blocking returns it.
+ * on: 0 off, 1 the blocked tail (FP32 only), 2 the blocked strided pair (process-wide;
+ * the autotuner's per-(precision, n) choice takes precedence). cheb_get_fused_blocking
+ * returns it.
  */
 cheb_status_t cheb_set_fused_blocking(int on);
 int cheb_get_fused_blocking(void);
