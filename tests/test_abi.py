@@ -309,3 +309,42 @@ def test_monomial_to_chebyshev_rejects_bad_input():
     assert L.cheb_monomial_to_chebyshev(1, None, dp(out)) == 1
     buf[1] = np.nan
     assert L.cheb_monomial_to_chebyshev(1, dp(buf), dp(out)) == 1
+
+
+def test_graph_and_checkpoint_entry_points_reject_bad_arguments():
+    """The graph capture and checkpointed forward check their arguments on the host
+    before any device work; the graph workspace grows with the segment count."""
+    L = _lib.lib()
+    n, S = 4, 3
+    h = np.zeros(n)
+    J = np.zeros((n, n))
+    g = np.full(S, 0.5)
+    t = np.full(S, 0.3)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: the checks come first
+    gw = L.cheb_anneal_graph_workspace_bytes(n, 0, S)
+    assert gw > L.cheb_workspace_bytes(n, 0)
+    assert L.cheb_anneal_graph_workspace_bytes(n, 0, 2 * S) > gw
+    assert L.cheb_anneal_graph_workspace_bytes(n, 0, 0) == 0
+    assert L.cheb_anneal_graph_workspace_bytes(0, 0, S) == 0
+    handle = ctypes.c_void_p()
+    # no output handle; null schedule; a workspace one byte short; bad method
+    assert L.cheb_anneal_graph_create(n, dp(h), dp(J), S, dp(g), None, dp(t), fake, 0, 1e-6, 0, None, fake, gw,
+                                      None, None) == 1
+    assert L.cheb_anneal_graph_create(n, dp(h), dp(J), S, None, None, dp(t), fake, 0, 1e-6, 0, None, fake, gw,
+                                      None, ctypes.byref(handle)) == 1
+    assert L.cheb_anneal_graph_create(n, dp(h), dp(J), S, dp(g), None, dp(t), fake, 0, 1e-6, 0, None, fake,
+                                      gw - 1, None, ctypes.byref(handle)) == 2
+    assert L.cheb_anneal_graph_create(n, dp(h), dp(J), S, dp(g), None, dp(t), fake, 0, 1e-6, 9, None, fake, gw,
+                                      None, ctypes.byref(handle)) == 1
+    assert not handle.value
+    assert L.cheb_anneal_graph_launch(None, None) == 1
+    L.cheb_anneal_graph_destroy(None)
+    # the checkpointed forward needs the boundaries buffer and an adjoint workspace
+    aw = L.cheb_adjoint_workspace_bytes(n, 0, 8)
+    assert L.cheb_anneal_checkpointed(n, dp(h), dp(J), S, dp(g), dp(t), fake, 0, 1e-6, 0, None, fake, aw,
+                                      None) == 1
+    assert L.cheb_anneal_checkpointed(n, dp(h), dp(J), S, dp(g), dp(t), fake, 0, 1e-6, 0, fake, fake, 16,
+                                      None) == 2
+    assert L.cheb_anneal_general_checkpointed(n, dp(h), dp(J), S, dp(g), None, dp(t), fake, 0, 1e-6, 0, fake,
+                                              fake, aw, None) == 1
