@@ -246,18 +246,24 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def fused_source_hash():
+    """sha256[:16] of the FP32 step kernels' sources (fused.cu, then pair.cuh)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("fused.cu", "pair.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2608_12058_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profile():
     """DRAM bytes per amplitude per launch of each fused kernel, from the committed
     ncu summary, if it was taken on the kernel source that is built now; else None."""
-    import hashlib
-
     path = os.path.join(ROOT, "profiles", "fused_dram_traffic.json")
-    src = os.path.join(ROOT, "paper_2608_12058_b300", "csrc", "fused.cu")
     try:
         with open(path) as f:
             d = json.load(f)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if d.get("fused_cu_sha256_16") != h:
+        if d.get("fused_source_sha256_16") != fused_source_hash():
             return None
         return {k: float(v) for k, v in d["dram_bytes_per_amplitude"].items()}
     except Exception:

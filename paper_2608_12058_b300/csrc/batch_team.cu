@@ -90,6 +90,64 @@ __device__ __forceinline__ float2 combine1(float dh, float dl, float2 v, float2 
     return __ffma2_rn(ci_s, make_float2(p.y, p.x), o);  // ci_s = (-ci, ci)
 }
 
+// Strided pass of a team over bits [11, 11 + H), H = 6..9: 128 tiles of 2^H rows x 8 float4
+// (rows 1024 float4 apart); this CTA takes tiles r, r + T, ... Thread t owns float4
+// t & 7 of the 2^(H-6) rows whose bits 0..5 are t >> 3: it loads them (and their slot
+// b_{k+2}, in two halves) in batches of L2-only loads, keeps them in registers for the
+// flips of row bits 6..H-1 and reads only the flips of bits 0..5 from shared memory.
+// Writes q = scale g S + sgn b_{k+2} over b_{k+2}.
+template <int H>
+__device__ __noinline__ void team_strided(const float4* b1, float4* b2, float4* st, int r, int T, float2 g2h,
+                                             float2 g2l, float sgn) {
+    constexpr int P = 1 << (H - 6);
+    const int t = threadIdx.x;
+    const int u = t & 7, rq = t >> 3;
+    const bool need = sgn != 0.f;
+    const float2 sg = dupf(sgn);
+    constexpr int PH = P > 1 ? P / 2 : 1;  // slot values loaded in two halves (registers)
+    for (int tile = r; tile < 128; tile += T) {
+        float4 v[P], w[PH];
+#pragma unroll
+        for (int i = 0; i < P; ++i) v[i] = ldcg4(b1 + tile * 8 + (int64_t)(rq + 64 * i) * kTileF4 + u);
+        if (need) {
+#pragma unroll
+            for (int i = 0; i < PH; ++i) w[i] = ldcg4(b2 + tile * 8 + (int64_t)(rq + 64 * i) * kTileF4 + u);
+        }
+#pragma unroll
+        for (int i = 0; i < P; ++i) st[((rq + 64 * i) << 3) + u] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            if (need && i == PH) {
+#pragma unroll
+                for (int m = 0; m < PH; ++m)
+                    w[m] = ldcg4(b2 + tile * 8 + (int64_t)(rq + 64 * (PH + m)) * kTileF4 + u);
+            }
+            float2 Sa = make_float2(0.f, 0.f), Sb = Sa;
+#pragma unroll
+            for (int b = P >> 1; b >= 1; b >>= 1) {  // row bits H-1 .. 6 from registers
+                Sa = add2(Sa, lo2(v[i ^ b]));
+                Sb = add2(Sb, hi2(v[i ^ b]));
+            }
+#pragma unroll
+            for (int j = 5; j >= 0; --j) {  // row bits 5 .. 0 from shared memory
+                const float4 pv = st[(((rq ^ (1 << j)) + 64 * i) << 3) + u];
+                Sa = add2(Sa, lo2(pv));
+                Sb = add2(Sb, hi2(pv));
+            }
+            float2 qa = __ffma2_rn(g2h, Sa, __fmul2_rn(g2l, Sa));
+            float2 qb = __ffma2_rn(g2h, Sb, __fmul2_rn(g2l, Sb));
+            if (need) {
+                const float4 wi = w[i % PH];
+                qa = __ffma2_rn(sg, lo2(wi), qa);
+                qb = __ffma2_rn(sg, hi2(wi), qb);
+            }
+            b2[tile * 8 + (int64_t)(rq + 64 * i) * kTileF4 + u] = make_float4(qa.x, qa.y, qb.x, qb.y);
+        }
+        __syncthreads();
+    }
+}
+
 // One instance on a team of CTAs (rank r of T). Returns false after a timeout.
 // Low pass layout (as the fused low pass): thread t holds float4 t and t + 512 of a
 // tile, i.e. amplitudes 2t + 1024 p + w: bit 0 = w, bits 1..9 = t, bit 10 = p.
@@ -131,7 +189,19 @@ __device__ bool team_run(const TeamInst& I, int r, unsigned char* smem, int* fla
         float4* out = (k == 0) ? psi : b2;
         const float sc = (k == 0) ? 1.f : 2.f;
         float sgn = (k == I.K - 1) ? 0.f : -1.f;
-        if (H > 0) {
+        if (H >= 6) {
+            // strided pass over bits [11, n) with rows held in registers (team_strided)
+            const float2 g2h = dupf(sc * ghi), g2l = dupf(sc * glo);
+            switch (H) {
+                case 6: team_strided<6>(b1, b2, st, r, T, g2h, g2l, sgn); break;
+                case 7: team_strided<7>(b1, b2, st, r, T, g2h, g2l, sgn); break;
+                case 8: team_strided<8>(b1, b2, st, r, T, g2h, g2l, sgn); break;
+                default: team_strided<9>(b1, b2, st, r, T, g2h, g2l, sgn); break;
+            }
+            target += T;
+            if (!team_barrier(I.bar, target, flags, &s_ok)) return false;
+            sgn = 1.f;  // b_{k+2} now holds q
+        } else if (H > 0) {
             // strided pass over bits [11, n): 128 tiles of 2^H rows x 8 float4, rows 1024
             // float4 apart; q = scale g S + sgn b_{k+2} written over b_{k+2}
             const int elems = 8 << H;
