@@ -507,9 +507,10 @@ cheb_status_t cheb_get_fused_split_fp64(int n, int* l, int* h);
  * order, as in the separate launches, so results are identical. The lag between a
  * group's A and B tiles keeps about 48 MB of the two vectors live in L2 (one group of
  * 32 MB, two of 16 MB); the environment variable CHEB_PAIR_LAG (1..16) overrides it.
- * on: 0 off, 1 the blocked tail (FP32 only), 2 the blocked strided pair (process-wide;
- * the autotuner's per-(precision, n) choice takes precedence). cheb_get_fused_blocking
- * returns it.
+ * on: 0 off, 1 the blocked tail (FP32 only), 2 the blocked strided pair, -1 automatic
+ * (the default: the blocked strided pair from n = 28 on, separate launches below).
+ * Process-wide; the autotuner's per-(precision, n) choice takes precedence.
+ * cheb_get_fused_blocking returns the setting.
  */
 cheb_status_t cheb_set_fused_blocking(int on);
 int cheb_get_fused_blocking(void);

@@ -510,7 +510,7 @@ cheb_status_t cheb_get_fused_split_fp64(int n, int* l, int* h) {
 }
 
 cheb_status_t cheb_set_fused_blocking(int on) {
-    if (on < 0 || on > 2) return CHEB_ERR_INVALID_ARG;
+    if (on < -1 || on > 2) return CHEB_ERR_INVALID_ARG;
     fused_set_blocking(on);
     return CHEB_OK;
 }

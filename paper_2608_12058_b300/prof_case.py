@@ -128,7 +128,7 @@ def compare(n, steps, split=None):
                 print(f"  blocking {mode}: {ms / steps:.3f} ms/step, "
                       f"{(1 << n) * steps / ms * 1e3:.3e} amplitude-updates/s; profiled: " + ", ".join(parts))
     finally:
-        api.set_fused_blocking(0)
+        api.set_fused_blocking(None)
         if split is not None:
             api.set_fused_split(n, -1)
 
@@ -165,7 +165,7 @@ def ff_compare(n, steps, split=None):
                 print(f"  blocking {mode}: {ms / steps:.3f} ms/step, {(1 << n) * steps / ms * 1e3:.3e} "
                       "amplitude-updates/s")
     finally:
-        api.set_fused_blocking(0)
+        api.set_fused_blocking(None)
         if split is not None:
             api.set_fused_split_fp64(n, -1)
 

@@ -202,19 +202,21 @@ def test_default_split_gives_the_top_range_wide_rows():
 
 
 def test_fused_blocking_switch():
-    """The L2-blocked launches are off by default, take 0 (off), 1 (step tail) or 2
-    (strided pair), and report the setting."""
-    assert api.get_fused_blocking() == 0
+    """The L2-blocked launches are automatic by default (-1), take 0 (off), 1 (step tail)
+    or 2 (strided pair), and report the setting."""
+    assert api.get_fused_blocking() == -1
     assert _lib.lib().cheb_set_fused_blocking(3) == 1  # CHEB_ERR_INVALID_ARG
-    assert _lib.lib().cheb_set_fused_blocking(-1) == 1
+    assert _lib.lib().cheb_set_fused_blocking(-2) == 1
     try:
         api.set_fused_blocking(True)
         assert api.get_fused_blocking() == 1
         api.set_fused_blocking(2)
         assert api.get_fused_blocking() == 2
-    finally:
         api.set_fused_blocking(False)
-    assert api.get_fused_blocking() == 0
+        assert api.get_fused_blocking() == 0
+    finally:
+        api.set_fused_blocking(None)
+    assert api.get_fused_blocking() == -1
 
 
 def test_fused_compensated_switch():

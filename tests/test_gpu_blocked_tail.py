@@ -35,7 +35,7 @@ def split():
     yield set_
     for n in used:
         api.set_fused_split(n, -1)
-    _blocking(False)
+    _blocking(None)  # back to the automatic choice
 
 
 def _expmv(h, J, gamma, t, psi_np, blocking):

@@ -150,7 +150,7 @@ def test_ff_blocked_pair_matches_oracle_and_separate(cuda_lib, oracle, n, split)
         y_sep, _ = _run(h, J, 0.9, 0.3, psi)
         separate = api.launch_count() - c1
     finally:
-        api.set_fused_blocking(0)
+        api.set_fused_blocking(None)
         api.set_fused_split_fp64(n, -1)
     assert info["K"] == oinfo["K"] and info["K"] >= 10
     assert separate - paired == info["K"]
@@ -194,5 +194,5 @@ def test_ff_blocked_pair_bit_identical(cuda_lib, n, split):
         b = _ff_poly(n, one, 0)
         assert bool((a == b).all())
     finally:
-        api.set_fused_blocking(0)
+        api.set_fused_blocking(None)
         api.set_fused_split_fp64(n, -1)
