@@ -1170,13 +1170,6 @@ cheb_status_t checkpointed_impl(int n, const double* h, const double* J, int S, 
     Checkpoint key;
     key.ws = workspace;
     checkpoint_take(key);
-    cheb_status_t st = CHEB_OK;
-    if (S > 1) {
-        // the adjoint workspace starts with a forward workspace
-        st = anneal_run(n, h, J, S, b_s, gamma_s, t_s, psi, precision, tol, method, boundaries, workspace, ws_bytes,
-                        stream, nullptr, S - 1);
-        if (st != CHEB_OK) return st;
-    }
     unsigned char* ws = (unsigned char*)workspace;
     cudaStream_t s0 = (cudaStream_t)stream;
     Ctx C{n, precision, A.fwd, ws, s0};
@@ -1184,8 +1177,22 @@ cheb_status_t checkpointed_impl(int n, const double* h, const double* J, int S, 
     const size_t vb = (size_t)N * A.fwd.cbytes;
     CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), s0));
     double emin = 0, emax = 0;
-    st = bounds_impl(C, h, J, &emin, &emax);
+    cheb_status_t st = bounds_impl(C, h, J, &emin, &emax);
     if (st != CHEB_OK) return st;
+    // the last segment's degree and time slicing, checked before psi changes
+    {
+        Segment G0;
+        st = segment_setup(C, n, h, J, b_s, gamma_s, t_s, S - 1, emin, emax, tol / S, method, G0);
+        if (st != CHEB_OK) return st;
+        if (G0.K > 0 && !SegPool::fits(G0.K, nvec)) return CHEB_ERR_WORKSPACE;
+    }
+    if (S > 1) {
+        // the adjoint workspace starts with a forward workspace
+        st = anneal_run(n, h, J, S, b_s, gamma_s, t_s, psi, precision, tol, method, boundaries, workspace, ws_bytes,
+                        stream, nullptr, S - 1);
+        if (st != CHEB_OK) return st;
+        CUDA_TRY(cudaMemsetAsync(C.flags(), 0, sizeof(int), s0));
+    }
     Segment G;
     st = segment_setup(C, n, h, J, b_s, gamma_s, t_s, S - 1, emin, emax, tol / S, method, G);
     if (st != CHEB_OK) return st;
@@ -1195,7 +1202,6 @@ cheb_status_t checkpointed_impl(int n, const double* h, const double* J, int S, 
     if (K == 0) {
         launch_scale(precision, N, psi_s, psi, G.coef[0].real(), G.coef[0].imag(), s0);
     } else {
-        if (!SegPool::fits(K, nvec)) return CHEB_ERR_WORKSPACE;
         const SegPool P(ws + A.pool, A.vstride, K, nvec);
         const StepRunner runner = make_runner(C, A, n, precision);
         const StepArgs base = segment_base(C, A, G);
