@@ -256,16 +256,25 @@ def fused_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile():
-    """DRAM bytes per amplitude per launch of each fused kernel, from the committed
-    ncu summary, if it was taken on the kernel source that is built now; else None."""
+def traffic_from_profile(l, h):
+    """DRAM bytes per amplitude per launch of each fused kernel for the split (l, h), from
+    the committed ncu summary (k_low by its number l of L2 partner bits, k_pair by its
+    range sizes), if it was taken on the kernel source that is built now; else None."""
     path = os.path.join(ROOT, "profiles", "fused_dram_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         if d.get("fused_source_sha256_16") != fused_source_hash():
             return None
-        return {k: float(v) for k, v in d["dram_bytes_per_amplitude"].items()}
+        per = d["dram_bytes_per_amplitude"]
+        out = {}
+        if str(l) in per["k_low"]:
+            out["k_low"] = float(per["k_low"][str(l)])
+        shape = f"{(h + 1) // 2}+{h // 2}"  # two strided ranges, the first one takes the extra bit
+        if shape in per["k_pair"]:
+            out["k_pair"] = float(per["k_pair"][shape])
+        out["k_strided"] = float(per["k_strided"])
+        return out
     except Exception:
         return None
 
@@ -591,7 +600,7 @@ def run_ours(args, world, rank, local):
         return
 
     peak, peak_kind = _peaks()
-    traffic = traffic_from_profile()
+    traffic = traffic_from_profile(*api.get_fused_split(n))
 
     def kernel_roof(name, count, total_ms, bytes_per_amp):
         if not count:

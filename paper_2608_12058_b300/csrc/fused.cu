@@ -56,6 +56,7 @@ constexpr size_t kWOff = kRingOff + (size_t)kNP * kTB;
 constexpr size_t kBarOff = kWOff + (size_t)kNS * kW * sizeof(int64_t);
 constexpr size_t kAbortOff = kBarOff + (size_t)(2 * kNS + 2 * kNP) * sizeof(uint64_t);
 constexpr size_t kLowSmem = kAbortOff + 16;
+static_assert(kLowSmem <= 227 * 1024, "k_low shared memory");
 
 __device__ __forceinline__ int64_t sel(uint32_t bit, int64_t v) { return bit ? -v : v; }
 
@@ -1082,6 +1083,13 @@ struct ArithF32 {
             q1 = __ffma2_rn(sg, hi2(w), q1);
         }
         return make_float4(q0.x, q0.y, q1.x, q1.y);
+    }
+    // the pair's one-float-per-lane tiles: S and w hold the same float of two rows
+    static constexpr bool kLanes = true;
+    __device__ static float2 finish2(float2 S, float2 w, bool need, float sgn, const Scale& c) {
+        float2 q = __ffma2_rn(c.ghi, S, __fmul2_rn(c.glo, S));
+        if (need) q = __ffma2_rn(dup(sgn), w, q);
+        return q;
     }
 };
 

@@ -596,6 +596,7 @@ struct ArithFF {
     static constexpr int kAmpShift = 0;  // one amplitude per float4
     static constexpr int kRowBits = 3;   // 8 amplitudes per 128-byte row
     using Acc = FFAcc;
+    static constexpr bool kLanes = false;  // float-float sums need whole amplitudes
     struct Scale {
         float g2, g1, g0;
     };

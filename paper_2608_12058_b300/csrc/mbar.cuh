@@ -151,6 +151,10 @@ __device__ __forceinline__ void st_hint(float4* p, float4 v, uint64_t pol) {
                  : "memory");
 }
 
+__device__ __forceinline__ void st_hint1(float* p, float v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+
 // Load that bypasses L1 (data written by other SMs in the same launch).
 __device__ __forceinline__ float4 ld_cg4(const float4* p) {
     float4 v;

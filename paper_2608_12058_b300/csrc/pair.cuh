@@ -26,8 +26,10 @@
 // reads per float4 (the TMA fill, the own value, six partners) against 10 in the
 // one-pass kernels. An A-tile's slot is read with L2-only loads, or by TMA with the tile
 // when tiles have at most 8 bits (a stage then holds both); so is a B-tile's q, which
-// other SMs wrote in this launch. The flip sum runs in descending bit order, as in the
-// one-pass kernels, so the pair and two separate passes agree bit for bit.
+// other SMs wrote in this launch. FP32 tiles whose slot is staged take a layout with
+// one float per lane (tile_lanes), which reads four flips from shared memory instead of
+// six. The flip sum runs in descending bit order, as in the one-pass kernels, so the
+// pair and two separate passes agree bit for bit.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -88,9 +90,11 @@ struct Cfg {
     static constexpr uint32_t kBytesA = (uint32_t)128 << HA;
     static constexpr uint32_t kBytesB = (uint32_t)128 << HB;
     // Tiles of up to 8 bits: a stage holds a tile and its slot rows (three stages of
-    // 64 KB), so the consumers read nothing from global memory. With 9-bit tiles a stage
-    // holds the tile alone and both slots come by L2-only loads (staging a narrower
-    // B-tile's q in the free half of its stage measured 2% slower at n=30, FP32).
+    // 64 KB), so the consumers read nothing from global memory and FP32 tiles take the
+    // one-float-per-lane layout. With 9-bit tiles a stage holds the tile alone and both
+    // slots come by L2-only loads (staging a narrower B-tile's q in the free half of its
+    // stage, and ordering the narrower range first so that its b_{k+2} can be staged,
+    // both measured slower at n=30, FP32).
     static constexpr bool kFull = kHMax <= 8;
     static constexpr uint32_t kStage = kFull ? 2 * kTileMax : kTileMax;
     static constexpr uint32_t kSlotOff = kTileMax;
@@ -146,6 +150,53 @@ __device__ __forceinline__ void tile(const float4* __restrict__ t4, const float4
     for (int i = 0; i < P; ++i)
         st_hint(slot + base + (int64_t)(rq | (i << 6)) * row_stride_f4 + u,
                 Arith::finish(S[i], w[i], need_slot, sgn, sc), pol_store);
+}
+
+// The same tile with one float per lane, for FP32 vectors (whose flip sums and final
+// q = s g S + sgn slot act on each float alone) with the slot rows staged in shared
+// memory (qf, same layout as the tile): warp w holds row bits 0..3, the lane the float
+// within the row and the register index row bits 4..H-1, 2^(H-4) rows kept as float2
+// pairs of rows m and m + 2^(H-5). The flips of bits H-1..4 come from registers and those
+// of bits 3..0 from shared memory: per 128-byte row 6 shared-memory wavefronts for the
+// tile (TMA fill, own values, four partners) against 8 for the float4 layout. The flip
+// sum runs in the same descending bit order, so both layouts give the same bits.
+// Pointers and offsets are in floats.
+template <int H, class Arith>
+__device__ __forceinline__ void tile_lanes(const float* __restrict__ tf, const float* __restrict__ qf, float* slot,
+                                           int64_t base, int64_t row_stride, const typename Arith::Scale& sc,
+                                           float sgn, bool need_slot, uint64_t pol_store) {
+    constexpr int P2 = 1 << (H - 5);  // row pairs per thread
+    const int t = threadIdx.x;
+    const int lane = t & 31, w = t >> 5;
+    auto lo_row = [&](int m) { return w | (m << 4); };
+    auto hi_row = [&](int m) { return w | ((m + P2) << 4); };
+    float2 v[P2];
+#pragma unroll
+    for (int m = 0; m < P2; ++m) v[m] = make_float2(tf[lo_row(m) * 32 + lane], tf[hi_row(m) * 32 + lane]);
+    float2 S[P2];
+    // register bits H-1 .. 4 first (descending); the top one swaps the rows of a pair
+#pragma unroll
+    for (int m = 0; m < P2; ++m) {
+        S[m] = __fadd2_rn(make_float2(0.f, 0.f), make_float2(v[m].y, v[m].x));
+#pragma unroll
+        for (int b = P2 >> 1; b >= 1; b >>= 1) S[m] = __fadd2_rn(S[m], v[m ^ b]);
+    }
+    // then row bits 3 .. 0 from shared memory
+#pragma unroll
+    for (int m = 0; m < P2; ++m) {
+#pragma unroll
+        for (int j = 3; j >= 0; --j)
+            S[m] = __fadd2_rn(S[m], make_float2(tf[(lo_row(m) ^ (1 << j)) * 32 + lane],
+                                                tf[(hi_row(m) ^ (1 << j)) * 32 + lane]));
+    }
+#pragma unroll
+    for (int m = 0; m < P2; ++m) {
+        const float2 q = need_slot ? make_float2(qf[lo_row(m) * 32 + lane], qf[hi_row(m) * 32 + lane])
+                                   : make_float2(0.f, 0.f);
+        const float2 o = Arith::finish2(S[m], q, need_slot, sgn, sc);
+        st_hint1(slot + base + (int64_t)lo_row(m) * row_stride + lane, o.x, pol_store);
+        st_hint1(slot + base + (int64_t)hi_row(m) * row_stride + lane, o.y, pol_store);
+    }
 }
 
 template <int HA, int HB, class Arith>
@@ -297,13 +348,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (ci.kind == kItemA) {
             // first row of the tile: bits [kRowBits, loA) = g, bits of B = idx
             const int64_t base = ci.g * 8 + (ci.idx << (a.loB - kAmpShift));
-            tile<HA, Arith>(t4, qt, a.slot_in, a.slot, base, rsA, sc, a.sgn, need_a, pol_last);
+            if constexpr (Arith::kLanes && C::kFull)
+                tile_lanes<HA, Arith>((const float*)t4, (const float*)qt, (float*)a.slot, base * 4, rsA * 4, sc, a.sgn,
+                                      need_a, pol_last);
+            else
+                tile<HA, Arith>(t4, qt, a.slot_in, a.slot, base, rsA, sc, a.sgn, need_a, pol_last);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
             if (!record(ci.g)) break;
         } else {
             const int64_t base = (ci.g | (ci.idx << sha)) * 8;
-            tile<HB, Arith>(t4, qt, a.slot, a.slot, base, rsB, sc, 1.f, true, pol_first);
+            if constexpr (Arith::kLanes && C::kFull)
+                tile_lanes<HB, Arith>((const float*)t4, (const float*)qt, (float*)a.slot, base * 4, rsB * 4, sc, 1.f, true,
+                                      pol_first);
+            else
+                tile<HB, Arith>(t4, qt, a.slot, a.slot, base, rsB, sc, 1.f, true, pol_first);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
         }
