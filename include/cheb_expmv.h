@@ -508,7 +508,8 @@ cheb_status_t cheb_get_fused_split_fp64(int n, int* l, int* h);
  * group's A and B tiles keeps about 48 MB of the two vectors live in L2 (one group of
  * 32 MB, two of 16 MB); the environment variable CHEB_PAIR_LAG (1..16) overrides it.
  * on: 0 off, 1 the blocked tail (FP32 only), 2 the blocked strided pair, -1 automatic
- * (the default: the blocked strided pair from n = 28 on, separate launches below).
+ * (the default: the blocked strided pair from n = 26 on for FP32 and from n = 28 on for
+ * FP64, separate launches below).
  * Process-wide; the autotuner's per-(precision, n) choice takes precedence.
  * cheb_get_fused_blocking returns the setting.
  */

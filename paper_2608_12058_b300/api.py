@@ -722,7 +722,7 @@ def set_fused_blocking(mode):
     """L2-blocked launches of the fused step (cheb_set_fused_blocking): 0 / False
     separate launches, 1 / True the last strided pass and the low pass as one launch,
     2 the two strided passes as one launch, -1 / None automatic (the default: 2 from
-    n = 28 on); results are identical."""
+    n = 26 on in FP32, from n = 28 on in FP64); results are identical."""
     _lib.check(_lib.lib().cheb_set_fused_blocking(-1 if mode is None else int(mode)), "cheb_set_fused_blocking")
 
 

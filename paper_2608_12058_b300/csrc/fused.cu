@@ -1311,13 +1311,14 @@ int pair_lag(size_t group_bytes) {
     return std::min(std::max(d, 1), 8);
 }
 
-// 0: separate launches, 1: L2-blocked tail, 2: L2-blocked strided pair, -1: automatic
-// (the strided pair from n = 28 on, where it measured 13-15% faster per step; separate
-// launches below, where the vectors partly stay in L2 anyway).
+// 0: separate launches, 1: L2-blocked tail, 2: L2-blocked strided pair, -1: automatic:
+// the strided pair from n = 26 on for FP32 (12-18% faster per step at n = 26..30) and
+// from n = 28 on for the float-float path; separate launches below, where the vectors
+// partly stay in L2 anyway.
 static int g_blocking = -1;
 void fused_set_blocking(int mode) { g_blocking = (mode >= -1 && mode <= 2) ? mode : -1; }
 int fused_get_blocking() { return g_blocking; }
-constexpr int kPairAutoMinN = 28;
+constexpr int kPairAutoMinN[2] = {26, 28};  // FP32, float-float
 
 // Per-n choices of the autotuner (-1: not tuned): the blocked tail, and the AUTO path.
 static int g_block_n[2][kMaxQubits + 1];
@@ -1352,7 +1353,7 @@ int fused_blocking_for(int prec, int n) {
     tuned_init();
     if (prec < 0 || prec > 1) return 0;
     int m = (n >= 0 && n <= kMaxQubits && g_block_n[prec][n] >= 0) ? g_block_n[prec][n] : g_blocking;
-    if (m < 0) m = n >= kPairAutoMinN ? 2 : 0;
+    if (m < 0) m = n >= kPairAutoMinN[prec] ? 2 : 0;
     return (prec == 1 && m == 1) ? 0 : m;  // the blocked tail is FP32 only
 }
 static int blocking_for(int n) { return fused_blocking_for(0, n); }

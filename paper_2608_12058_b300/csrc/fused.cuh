@@ -31,7 +31,7 @@ size_t fused_scratch_bytes(int n, int prec);
 int num_sms();
 // L2-blocked launches: 0 off, 1 the step tail (the last strided pass and the low pass in
 // one launch), 2 the strided pair (both strided passes of a two-pass plan in one launch),
-// -1 automatic (the pair from n = 28 on).
+// -1 automatic (the pair from n = 26 on for FP32, from n = 28 on for the float-float path).
 void fused_set_blocking(int mode);
 int fused_get_blocking();
 // Choices of the autotuner: per (prec, n) the AUTO path (-1 = built-in rule) and, for
