@@ -204,7 +204,12 @@ def cluster(n, count):
     ts = np.full(count, 10.0)
     offs, total = api.batch_offsets(ns)
     x = torch.full((total,), 2 ** (-n / 2), dtype=torch.complex64, device="cuda")
-    infos = api.expmv_batched(ns, hs, Js, gam, ts, x, tol=1e-6)
+    mode = api.get_batch_persistent()
+    api.set_batch_persistent(0)  # per-size launches: n = 14..17 on thread-block clusters
+    try:
+        infos = api.expmv_batched(ns, hs, Js, gam, ts, x, tol=1e-6)
+    finally:
+        api.set_batch_persistent(mode)
     torch.cuda.synchronize()
     assert all(abs(i["norm"] - 1.0) < 1e-4 for i in infos)
     print("ok", sum(i["K"] for i in infos))
