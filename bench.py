@@ -227,14 +227,16 @@ def cpu_baseline_dict(value, dt, info, single=None):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    v, dt, info = cpu_sample_run()
+    for _ in range(max(0, args.warmup)):  # untimed warm-up samples
+        cpu_sample_run()
     steps = max(1, args.steps)
-    vals = [v]
-    for _ in range(steps - 1):
-        vals.append(cpu_sample_run()[0])
-    value = statistics.median(vals)
+    runs = [cpu_sample_run() for _ in range(steps)]
+    value = statistics.median(r[0] for r in runs)
+    dt = statistics.median(r[1] for r in runs)
+    info = runs[0][2]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": steps, "warmup": 0, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "steps": steps, "warmup": max(0, args.warmup), "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "sk_n30_g1.0_t20", "n": 30, "gamma": 1.0, "t": 20.0, "tol": TOL32,
                        "method": "chebyshev", "parallelism": "single",
