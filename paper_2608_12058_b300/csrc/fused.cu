@@ -1439,6 +1439,14 @@ FusedPlan fused_plan(int n, int prec) {
             ++l;
             --h;
         }
+        // 9 + 8 strided ranges over a low pass without L2 partner bits (n = 28): one bit
+        // moves to the low pass, which costs it nothing there (1.29 ms either way), and
+        // the blocked pair runs two 8-bit ranges on one-float tiles (2.85 against 2.93 ms
+        // per step)
+        if (l == 0 && h == 2 * 8 + 1 && fused_split_valid(n, 1, h - 1)) {
+            l = 1;
+            --h;
+        }
     }
     p.l = l;
     p.h = h;

@@ -163,7 +163,7 @@ def test_autotune_cache_file(tmp_path):
         assert api.autotune_load(str(f), "TestDev") == 3
         assert api.get_fused_split(26) == (1, 14)
         assert api.get_fused_split(27) == (0, 16)
-        assert api.get_fused_split(28) == (0, 17)
+        assert api.get_fused_split(28) == (1, 16)
         assert api.get_fused_split_fp64(24) == (5, 9)
     finally:
         api.autotune_reset()
@@ -189,9 +189,10 @@ def _passes(lo, h):
 def test_default_split_gives_the_top_range_wide_rows():
     """Past n = 28 the default split moves one bit to the L2 partner tiles when the top
     strided pass would otherwise be 9 bits at bit 18 or above. An 8-bit top pass there
-    runs on 256-byte rows (n = 30: 9 + 8 bits, the benchmarked split)."""
+    runs on 256-byte rows (n = 30: 9 + 8 bits, the benchmarked split). At n = 28 the
+    9 + 8 ranges over a low pass without partner bits become 8 + 8 with one partner bit."""
     assert api.get_fused_split(30) == (2, 17)
-    expect = {25: (0, 14), 26: (0, 15), 27: (0, 16), 28: (0, 17), 29: (1, 17), 30: (2, 17),
+    expect = {25: (0, 14), 26: (0, 15), 27: (0, 16), 28: (1, 16), 29: (1, 17), 30: (2, 17),
               31: (3, 17), 32: (4, 17), 33: (4, 18)}
     for n, lh in expect.items():
         assert api.get_fused_split(n) == lh, n
