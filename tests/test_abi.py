@@ -351,3 +351,22 @@ def test_graph_and_checkpoint_entry_points_reject_bad_arguments():
                                       None) == 2
     assert L.cheb_anneal_general_checkpointed(n, dp(h), dp(J), S, dp(g), None, dp(t), fake, 0, 1e-6, 0, fake,
                                               fake, aw, None) == 1
+
+
+def test_traffic_profile_covers_the_default_splits():
+    """The committed per-launch DRAM bytes (profiles/fused_dram_traffic.json, which
+    bench.py scales to the n=30 run) hold the low pass for every number of partner bits
+    and the pair for every range shape that the default FP32 splits use at n = 26..30."""
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "profiles",
+                        "fused_dram_traffic.json")
+    with open(path) as f:
+        per = json.load(f)["dram_bytes_per_amplitude"]
+    for n in range(26, 31):
+        l, h = api.get_fused_split(n)
+        shape = f"{(h + 1) // 2}+{h // 2}"  # two strided ranges, the first takes the extra bit
+        assert str(l) in per["k_low"], (n, l)
+        assert shape in per["k_pair"], (n, shape)
+        assert 24.0 <= per["k_pair"][shape] <= 48.0 and 32.0 * 0.99 <= per["k_low"][str(l)] <= 40.0
