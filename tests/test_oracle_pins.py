@@ -152,6 +152,19 @@ def test_term_count_growth(oracle):
         prev = excess
 
 
+def test_term_count_excess_scales_as_cube_root(oracle):
+    """The o(r) of Sec. II.B.2 at large radii: J_m(a) leaves its oscillating range through a
+    transition layer around m = a whose width grows as a^(1/3) (the Airy scaling of Bessel
+    functions of large order, J_{a + tau a^(1/3)}(a) ~ (2/a)^(1/3) Ai(2^(1/3) tau)), so at a
+    fixed tolerance K - a is proportional to a^(1/3): the same constant at a = 1e3 .. 3e4."""
+    ratios = []
+    for a in [1000.0, 10000.0, 30000.0]:
+        _, K, _ = oracle.cheb_coeffs(a, 2.0 ** -23)
+        ratios.append((K - a) / a ** (1 / 3))
+    assert max(ratios) <= 1.1 * min(ratios), ratios
+    assert 3.0 < min(ratios) and max(ratios) < 10.0, ratios
+
+
 # --------------------------------------------------------------------------
 # Matrix-free operator (Sec. II.D) and Clenshaw (Algorithm 2)
 
