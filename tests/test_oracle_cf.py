@@ -53,6 +53,10 @@ def test_cf_equioscillates(oracle, a, K, part):
     # better than the Chebyshev truncation of the same degree
     cheb_err = np.max(np.abs(f(x) - np.polynomial.chebyshev.chebval(x, coef[: K + 1])))
     assert emax < cheb_err
+    # and the truncation is near-best (Sec. II.C: Chebyshev approximations lose at most a
+    # logarithmic Lebesgue factor against the minimax polynomial; for a truncated series
+    # ||f - S_K f|| <= (4 + 4 ln(K) / pi^2) E_K(f), and E_K(f) <= the CF error)
+    assert cheb_err <= (4.0 + 4.0 * np.log(K) / np.pi ** 2) * emax
 
 
 @pytest.mark.parametrize("a,tol", [(10.0, 1e-8), (30.0, 2.0 ** -23), (100.0, 1e-12), (430.0, 2.0 ** -23)])
