@@ -633,6 +633,22 @@ typedef enum {
 cheb_status_t cheb_wait_selftest(void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Host check of the blocked strided pair's work order (no counterpart in the paper; the
+ * pair is this library's L2 blocking of the strided passes of the Clenshaw step,
+ * Sec. II.D). For 2^gbits groups, ranges of HA and HB bits (1..9) and a lag of
+ * 1..2^gbits groups, the item indices handed out by the pair's global counter must
+ * name every A-tile (2^HB per group) and every B-tile (2^HA per group) exactly once,
+ * followed by the end marker, with every B-tile of a group after all of that group's
+ * A-tiles: a B-tile's wait for its group then only depends on items taken before it.
+ * Returns 0 when all of this holds (min_gap, if not NULL, receives the smallest index
+ * distance between a group's last A-tile and its first B-tile), 1 for an item out of
+ * range, 2 for an item handed out twice, 3 for a missing one, 4 for a B-tile before its
+ * group's last A-tile, 5 for a misplaced end marker, -1 for invalid arguments
+ * (gbits 0..16). Host only; no device or stream is used.
+ */
+int cheb_pair_schedule_check(int gbits, int HA, int HB, int lag, long long* min_gap);
+
+/*
  * Device-side status of a workspace (no counterpart in the paper). A call made
  * without an info struct does not synchronise, so a bounded wait that ran out during
  * it is not in its return value; the condition stays recorded in the workspace's

@@ -113,6 +113,7 @@ SIGNATURES = {
     "cheb_energy_grad": (c_int, [c_int, _dp, _dp, c_void_p, c_void_p, c_int, _dp, _dp, _dp, c_void_p, c_size_t,
                                  c_void_p]),
     "cheb_wait_selftest": (c_int, [c_void_p, c_size_t, c_void_p]),
+    "cheb_pair_schedule_check": (c_int, [c_int, c_int, c_int, c_int, ctypes.POINTER(ctypes.c_longlong)]),
     "cheb_workspace_status": (c_int, [c_void_p, c_size_t, c_void_p]),
     "cheb_autotune_workspace_bytes": (c_size_t, [c_int, c_int]),
     "cheb_autotune": (c_int, [c_int, c_int, c_int, c_void_p, c_size_t, c_void_p, ctypes.POINTER(TuneResult)]),

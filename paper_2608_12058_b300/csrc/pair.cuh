@@ -69,7 +69,7 @@ struct Args {
     int* flags;
 };
 
-__device__ __forceinline__ Item decode(unsigned long long i, int gbits, int HA, int HB, int lag) {
+__host__ __device__ __forceinline__ Item decode(unsigned long long i, int gbits, int HA, int HB, int lag) {
     const unsigned long long G = 1ull << gbits, D = (unsigned long long)lag, NA = 1ull << HB, NB = 1ull << HA;
     const unsigned long long seg = NA + NB, head = D * NA;
     if (i < head) return {kItemA, (int64_t)(i / NA), (int64_t)(i % NA)};

@@ -370,3 +370,35 @@ def test_traffic_profile_covers_the_default_splits():
         assert str(l) in per["k_low"], (n, l)
         assert shape in per["k_pair"], (n, shape)
         assert 24.0 <= per["k_pair"][shape] <= 48.0 and 32.0 * 0.99 <= per["k_low"][str(l)] <= 40.0
+
+
+@pytest.mark.parametrize("HA,HB", [(6, 6), (7, 6), (7, 7), (8, 7), (8, 8), (9, 8), (9, 9)])
+@pytest.mark.parametrize("gbits", [0, 1, 3, 6])
+def test_pair_schedule_is_a_complete_ordered_work_list(HA, HB, gbits):
+    """The blocked pair's item order (cheb_pair_schedule_check, the device decode run on
+    the host): every A- and B-tile once, then the end marker, and every B-tile of a group
+    after all of its A-tiles, for lags from one group to all of them."""
+    import ctypes
+
+    lib = _lib.lib()
+    for lag in sorted({1, 2, 3, 1 << gbits}):
+        if lag > (1 << gbits):
+            continue
+        gap = ctypes.c_longlong(0)
+        assert lib.cheb_pair_schedule_check(gbits, HA, HB, lag, ctypes.byref(gap)) == 0, (gbits, lag)
+        assert gap.value >= 1
+
+
+def test_pair_schedule_at_the_benchmarked_sizes():
+    """The work lists of the n=30 split (2, 17) (512 groups, ranges 9 + 8, lag 1) and the
+    n=28 split (1, 16) (256 groups, 8 + 8, lag 2): complete and ordered, with at least
+    one group's A-tiles between a group's last A-tile and its first B-tile."""
+    import ctypes
+
+    lib = _lib.lib()
+    for gbits, HA, HB, lag in [(9, 9, 8, 1), (8, 8, 8, 2)]:
+        gap = ctypes.c_longlong(0)
+        assert lib.cheb_pair_schedule_check(gbits, HA, HB, lag, ctypes.byref(gap)) == 0
+        assert gap.value > (1 << HB) * lag - 1, (gbits, gap.value)
+    assert lib.cheb_pair_schedule_check(3, 9, 8, 9, None) == -1  # lag above the group count
+    assert lib.cheb_pair_schedule_check(3, 10, 8, 1, None) == -1
