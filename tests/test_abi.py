@@ -52,6 +52,12 @@ def test_workspace_bytes():
     # two Clenshaw vectors plus small tables: the state is the caller's (Sec. II.D's
     # in-place b2 += H b1 leaves psi, b1, b2 as the only vectors)
     assert w24 < 2 * (1 << 24) * 8 * 1.05
+    # the largest accepted sizes (n = 31..33, beyond 2^32 bytes per vector) keep the same
+    # layout, without overflow in the size arithmetic
+    for n in (31, 32, 33):
+        for prec, amp in ((0, 8), (1, 16)):
+            w = L.cheb_workspace_bytes(n, prec)
+            assert 2 * (1 << n) * amp <= w < 2 * (1 << n) * amp * 1.05, (n, prec, w)
 
 
 def test_adjoint_workspace_bytes():
